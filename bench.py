@@ -1,0 +1,352 @@
+"""Benchmark of the matrix-free prism-gravity operator on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload paper_210x210x75] [--precision mixed|fp64]
+
+One step = one forward product d = G m plus one adjoint product G^T r (the
+two operator applications of every CG iteration, Section 2.2) on the
+paper-scale synthetic workload (210 x 210 x 75 mesh of 100 m cubes = 3,307,500
+prisms, 178,797 stations).  The metric is prism-station pairs per second:
+2 * N * M pairs per step.  Inputs stay resident; L2 is flushed between timed
+steps (a 256 MB write outside the timed events).
+
+Printed as one JSON line (rank 0).  Extra keys: roofline of the dominant
+kernel (MUFU-bound, "alu"), e2e (same metric through host buffers), the
+oracle timed on the host cores (cpu_baseline), the mixed-vs-FP64-oracle error
+on the oracle's sample stations, FP64-mode throughput on the 80 x 80 x 40
+workload, and the inversion time to relative residual 1e-6 (mixed and FP64).
+Under torchrun (N > 1) every rank runs an independent replica (the operator
+is single-GPU; replicas only) and `value` is the total over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+MUFU_PER_CLK_SM = 16          # reciprocal square roots per clock per SM (MUFU unit count)
+SM_MAX_MHZ = 2032.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="paper_210x210x75")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--near-cells", type=float, default=8.0)
+    ap.add_argument("--no-extras", action="store_true", help="skip fp64/inversion/cpu extras")
+    ap.add_argument("--cpu-stations", type=int, default=16)
+    ap.add_argument("--cpu-cells", type=int, default=48)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples),
+                "power_w_max": max(float(s[3]) for s in self.samples if s[3].replace(".", "").isdigit())
+                if any(s[3].replace(".", "").isdigit() for s in self.samples) else None}
+
+
+def oracle_sample(wl, n_st, n_cells, seed=0):
+    """Times the CPU oracle on a bounded sample of the workload: the forward
+    for n_st stations over the full mesh, the adjoint for n_cells cells over
+    all stations.  Returns (pairs_per_s, seconds, threads, station idx, d_ref)."""
+    import oracle
+    rng = np.random.Generator(np.random.PCG64(100 + seed))
+    idx = np.sort(rng.choice(wl.survey.n, n_st, replace=False))
+    cells = np.sort(rng.choice(wl.mesh.ncells, n_cells, replace=False))
+    r = synth.random_vector(wl.survey.n, 77)
+    sub = wl.survey.subset(idx)
+    t0 = time.perf_counter()
+    d_ref = oracle.forward(wl.mesh, sub, wl.m)
+    t1 = time.perf_counter()
+    nx, ny = wl.mesh.nx, wl.mesh.ny
+    for k in cells:
+        i, j, l = k % nx, (k // nx) % ny, k // (nx * ny)
+        one = synth.Mesh(wl.mesh.xe[i:i + 2].copy(), wl.mesh.ye[j:j + 2].copy(), wl.mesh.ze[l:l + 2].copy())
+        oracle.adjoint(one, wl.survey, r)
+    t2 = time.perf_counter()
+    pairs = n_st * wl.mesh.ncells + n_cells * wl.survey.n
+    return pairs / (t2 - t0), t2 - t0, oracle.get_threads(), idx, d_ref, (t1 - t0, t2 - t1)
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    wl = synth.make_workload(args.workload)
+    pairs_step = 2 * wl.survey.n * wl.mesh.ncells
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(wl, 2, 4)
+    for s in range(args.steps):
+        pps, sec, th, _, _, _ = oracle_sample(wl, args.cpu_stations, args.cpu_cells, seed=s)
+        vals.append(pps)
+    v = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": "prism-station pairs/s for G.m and G^T r", "value": v, "unit": "pairs/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": pairs_step / v * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "cells": wl.mesh.ncells, "stations": wl.survey.n},
+        "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": th, "kind": "oracle",
+                         "sample": f"forward of {args.cpu_stations} seeded stations over all {wl.mesh.ncells} "
+                                   f"cells + adjoint of {args.cpu_cells} seeded cells over all {wl.survey.n} "
+                                   f"stations, per step"},
+        "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def run_ours(args):
+    import torch
+    import paper_2602_03857_b300 as g
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = synth.make_workload(args.workload)
+    N, M = wl.survey.n, wl.mesh.ncells
+    S = g.Survey(wl.survey.x, wl.survey.y, wl.survey.z)
+    opts = {"precision": args.precision, "near_cells": args.near_cells}
+    t0 = time.perf_counter()
+    plan = g.Plan(wl.mesh, S, **opts)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    m = torch.tensor(wl.m, dtype=torch.float64, device=dev)
+    r = torch.tensor(synth.random_vector(N, 77), dtype=torch.float64, device=dev)
+    d = torch.empty(N, dtype=torch.float64, device=dev)
+    gt = torch.empty(M, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 126 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.forward(m, out=d)
+        plan.adjoint(r, out=gt)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    plan.timing(True, read=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = g.launch_count()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush_l2(flush)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    launches = g.launch_count() - launches0
+    stages = plan.timing(False, read=True)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(ms)
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt)
+    pairs_step = 2.0 * N * M
+    value = ws * pairs_step * args.steps / (t_total * 1e-3)
+
+    # e2e: same metric through the public API with pinned host buffers
+    hm = torch.tensor(wl.m, dtype=torch.float64).pin_memory()
+    hr = torch.tensor(synth.random_vector(N, 77), dtype=torch.float64).pin_memory()
+    hd = torch.empty(N, dtype=torch.float64).pin_memory()
+    hg = torch.empty(M, dtype=torch.float64).pin_memory()
+    md = torch.empty_like(m)
+    rd = torch.empty_like(r)
+
+    def e2e_step():
+        md.copy_(hm, non_blocking=True)
+        plan.forward(md, out=d)
+        hd.copy_(d, non_blocking=True)
+        rd.copy_(hr, non_blocking=True)
+        plan.adjoint(rd, out=gt)
+        hg.copy_(gt, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e_ms = []
+    for k in range(args.steps):
+        flush_l2(flush)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e_ms.append(a.elapsed_time(b))
+    e2e_value = ws * pairs_step * args.steps / (sum(e_ms) * 1e-3)
+
+    # roofline of the dominant kernel (MUFU reciprocal square root per pair)
+    fwd_ms, fwd_n = stages["fwd_main"]
+    adj_ms, adj_n = stages["adj_main"]
+    dom = "fwd_main" if fwd_ms >= adj_ms else "adj_main"
+    dms, dn = stages[dom]
+    pairs_launch = float(N) * M
+    achieved = pairs_launch / (dms / max(dn, 1) * 1e-3) / 1e9
+    peak = 148 * MUFU_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e9
+    kernel_name = {"mixed": {"fwd_main": "k_mfwd", "adj_main": "k_madj"},
+                   "fp64": {"fwd_main": "k_fwd64", "adj_main": "k_adj64"}}[args.precision][dom]
+    roof = {"bound": "alu", "kernel": kernel_name, "achieved": achieved, "peak": peak,
+            "unit": "G rsqrt/s (MUFU, 1 per pair)" if args.precision == "mixed" else "G node-evals/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_basis": f"148 SMs x {MUFU_PER_CLK_SM} MUFU/clk x {SM_MAX_MHZ:.0f} MHz",
+            "stage_ms_per_launch": {k: (v[0] / max(v[1], 1)) for k, v in stages.items()}}
+
+    line = {
+        "metric": "prism-station pairs/s for G.m and G^T r", "value": value, "unit": "pairs/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "cells": M, "stations": N, "precision": args.precision,
+                   "near_cells": args.near_cells, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if ws > 1 else "single-gpu"},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": 8 * (M + N),
+                "d2h_bytes_per_step": 8 * (N + M)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "plan_setup_s": setup_s, "plan_bytes": plan.nbytes,
+    }
+    if rank == 0 and not args.no_extras:
+        extras(args, g, torch, wl, plan, d, line)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def extras(args, g, torch, wl, plan, d, line):
+    # CPU oracle on a bounded sample; its forward sample also measures the
+    # error of this run's result against the FP64 oracle
+    pps, sec, th, idx, d_ref, (tf, ta) = oracle_sample(wl, args.cpu_stations, args.cpu_cells)
+    line["cpu_baseline"] = {"value": pps, "unit": "pairs/s", "cores": th, "kind": "oracle",
+                            "sample": f"forward of {args.cpu_stations} seeded stations over all {wl.mesh.ncells} "
+                                      f"cells + adjoint of {args.cpu_cells} seeded cells over all {wl.survey.n} "
+                                      f"stations ({sec:.1f} s)"}
+    dg = d.cpu().numpy()[idx]
+    line["error_vs_fp64_oracle"] = {
+        "max_abs_mgal": float(np.abs(dg - d_ref).max()),
+        "rel_to_max_abs": float(np.abs(dg - d_ref).max() / np.abs(d_ref).max()),
+        "stations_checked": int(len(idx))}
+    # FP64 mode throughput and mixed/FP64 ratio on the 80x80x40 workload
+    wl2 = synth.make_workload("vslab_80x80x40")
+    S2 = g.Survey(wl2.survey.x, wl2.survey.y, wl2.survey.z)
+    res = {}
+    for prec in ("fp64", "mixed"):
+        p2 = g.Plan(wl2.mesh, S2, precision=prec)
+        m2 = torch.tensor(synth.random_vector(wl2.mesh.ncells, 3, 100.0), device="cuda")
+        r2 = torch.tensor(synth.random_vector(wl2.survey.n, 4), device="cuda")
+        p2.forward(m2); p2.adjoint(r2)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        p2.forward(m2); p2.adjoint(r2)
+        b.record(); b.synchronize()
+        res[prec] = 2.0 * wl2.survey.n * wl2.mesh.ncells / (a.elapsed_time(b) * 1e-3)
+        p2.close()
+    line["fp64_vs_mixed"] = {"workload": "vslab_80x80x40", "fp64_pairs_per_s": res["fp64"],
+                             "mixed_pairs_per_s": res["mixed"], "mixed_over_fp64": res["mixed"] / res["fp64"]}
+    # inversion time to relative residual 1e-6, mixed and FP64
+    import oracle
+    wl1 = synth.make_workload("block_20x20x10")
+    d1 = oracle.forward(wl1.mesh, wl1.survey, wl1.m)
+    d1 = synth.add_noise(d1, wl1.noise_abs, wl1.noise_rel, 0)
+    S1 = g.Survey(wl1.survey.x, wl1.survey.y, wl1.survey.z)
+    inv = {}
+    for prec in ("fp64", "mixed"):
+        g.datainv(torch.tensor(d1, device="cuda"), wl1.mesh, S1, precision=prec, tol=1e-6)
+        mm, info = g.datainv(torch.tensor(d1, device="cuda"), wl1.mesh, S1, precision=prec, tol=1e-6)
+        inv[prec] = {"seconds": info["seconds"], "iters": info["iters"], "true_rel_res": info["true_rel_res"]}
+    line["inversion_to_1e-6"] = {"workload": "block_20x20x10", **inv}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

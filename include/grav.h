@@ -1,0 +1,211 @@
+/*
+ * grav.h — C ABI of libgrav.so: a matrix-free rectangular-prism gravity
+ * operator and its depth-weighted data-space inversion on one NVIDIA B300
+ * (sm_103a).
+ *
+ * The operator (the paper's Section 2.1, Eq. 1-6):
+ *     d_i = sum_k G_ik m_k,   G_ik = gamma * sum_{p,q,r in {1,2}} (-1)^(p+q+r) Psi(x_p, y_q, z_r)
+ *     Psi(x,y,z) = z atan(x y / (z R)) - x ln(R + y) - y ln(R + x),  R = |(x,y,z)|     (Eq. 2-3)
+ * with (x_p, y_q, z_r) the prism vertices relative to station i.  G is never
+ * stored: every product recomputes it.
+ *
+ * The inversion (Section 2.2, Eq. 7-11, with W_d = lambda I and
+ * W_m = W^-2 = diag((zc_k + z0)^2)):
+ *     m = m_ref + W^-2 G^T (G W^-2 G^T + lambda I)^-1 (d - G m_ref),
+ *     lambda = lambda_scale * trace(G W^-2 G^T) / N,
+ * solved by conjugate gradients on the N x N system (Section 3.1: the
+ * inversion is iterative CG with no factorisation).
+ *
+ * Conventions
+ *   - Units: metres, kg/m^3, data in mGal (1 mGal = 1e-5 m/s^2);
+ *     gamma = 6.67430e-11 m^3 kg^-1 s^-2.
+ *   - z is DEPTH, positive down.  The mesh top is ze[0].  Every station must
+ *     lie strictly above the mesh top (station z < ze[0]); the result for a
+ *     station at or below the top is unspecified (finite or NaN values, never
+ *     a memory fault).
+ *   - Cell k = (i, j, l) has linear index k = i + nx*(j + ny*l).
+ *   - g_z is reported positive down: a positive contrast below a station
+ *     gives a positive anomaly.
+ *   - Ownership: the caller owns every input and output buffer.  The library
+ *     owns only its scratch, which lives inside a grav_ctx or a grav_plan.
+ *   - Streams: every call enqueues its work on the given stream and returns
+ *     without waiting for it, unless stated otherwise.  Calls sharing one
+ *     grav_ctx or one grav_plan must be ordered (same stream, or explicitly
+ *     synchronised): their scratch is shared.
+ *   - Errors: every function returns GRAV_OK (0) or a negative GRAV_E* code
+ *     and leaves a message for grav_last_error().  Invalid arguments are
+ *     rejected before anything is enqueued.  Kernels never trap; a bounded
+ *     device-side wait that gives up sets a device status word that the next
+ *     synchronising call reports as GRAV_EDEVICE.
+ */
+#ifndef GRAV_H_
+#define GRAV_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (cudaStream_t), passed through opaquely; NULL = legacy default stream. */
+typedef struct CUstream_st *grav_stream_t;
+
+/* ---- status codes --------------------------------------------------------- */
+#define GRAV_OK              0
+#define GRAV_EINVAL         -1   /* bad argument, descriptor or size */
+#define GRAV_ENOMEM         -2   /* device allocation failed / over the HBM budget */
+#define GRAV_ENOTCONVERGED  -3   /* CG hit max_iter; the last iterate is still written */
+#define GRAV_ETIMEDOUT      -4   /* a bounded host wait expired */
+#define GRAV_EDEVICE        -5   /* CUDA error or device status word set */
+#define GRAV_ECANCELED      -6   /* job cancelled */
+#define GRAV_ENOTFOUND      -7   /* unknown job id */
+#define GRAV_EBUSY          -8   /* the serving queue is full */
+
+/* ---- precision modes ------------------------------------------------------ */
+/* GRAV_FP64: Eq. 1-3 evaluated in FP64 once per (station, mesh node) and
+ *   differenced across shared nodes (summation by parts of Eq. 1 + Eq. 5).
+ * GRAV_MIXED: every cell contributes through an FP32 point-mass far-field term
+ *   gamma rho V dz / R^3 with compensated (two-sum) accumulation; cells whose
+ *   centre lies within near_cells cell widths of a station are corrected to
+ *   the exact FP64 prism value (Eq. 1) for that station.  CG dots and step
+ *   lengths stay in FP64.  Requires cubic cells (dx = dy = dz per cell).
+ */
+#define GRAV_FP64    0
+#define GRAV_MIXED   1
+
+/* ---- descriptors ---------------------------------------------------------- */
+typedef struct {
+    int nx, ny, nz;            /* cells per axis, each >= 1 */
+    const double *xe;          /* HOST array, nx+1 strictly increasing x edges (m) */
+    const double *ye;          /* HOST array, ny+1 strictly increasing y edges (m) */
+    const double *ze;          /* HOST array, nz+1 strictly increasing depths (m); ze[0] = mesh top */
+} grav_mesh;
+
+typedef struct {
+    int64_t n;                 /* number of stations, >= 1 */
+    const double *x, *y, *z;   /* DEVICE arrays of n doubles; z = -(height above z = 0) */
+} grav_survey;
+
+typedef struct {
+    int precision;             /* GRAV_FP64 or GRAV_MIXED */
+    double z0;                 /* depth-weight offset (m): W^-2 = (zc + z0)^2, zc = cell-centre depth below ze[0] */
+    double lambda_scale;       /* lambda = lambda_scale * trace(G W^-2 G^T) / N  (default 1e-2) */
+    double lambda;             /* > 0: use this lambda instead of the trace rule */
+    double tol;                /* CG stops when ||dd - A y|| <= tol ||dd|| (recurrence residual) */
+    int max_iter;              /* CG iteration cap */
+    int check_every;           /* host convergence check period in iterations (0 = automatic) */
+    double near_cells;         /* GRAV_MIXED near-field radius in cell widths (default 8) */
+    double timeout_s;          /* bound on every host wait of a call (default 3600 s) */
+} grav_options;
+
+typedef struct {
+    int iters;                 /* CG iterations performed */
+    int converged;             /* 1 if the recurrence residual reached tol */
+    double rel_res;            /* recurrence ||r|| / ||dd|| at exit */
+    double true_rel_res;       /* ||dd - (G W^-2 G^T + lambda I) y|| / ||dd||, recomputed with the same operator */
+    double lambda;             /* lambda used */
+    double trace;              /* trace(G W^-2 G^T) (0 if lambda was given) */
+    double seconds;            /* wall time of the solve */
+} grav_solve_info;
+
+typedef struct grav_ctx grav_ctx;
+typedef struct grav_plan grav_plan;
+
+/* Fills *opt with the defaults: GRAV_FP64, z0 = 50, lambda_scale = 1e-2,
+ * lambda = 0, tol = 1e-6, max_iter = 1000, check_every = 0,
+ * near_cells = 8, timeout_s = 3600. */
+void grav_options_default(grav_options *opt);
+
+/* Library version string (static storage). */
+const char *grav_version(void);
+
+/* ---- context -------------------------------------------------------------- */
+/* Creates a context on CUDA device `device`.  hbm_budget (bytes) caps the
+ * device memory the context's plans and serving jobs may hold (0 = 90 % of
+ * the device's free memory at creation).  Returns GRAV_EINVAL for a bad
+ * device, GRAV_EDEVICE if the device cannot be initialised. */
+int grav_ctx_create(grav_ctx **out, int device, size_t hbm_budget);
+
+/* Destroys the context: waits (bounded by 60 s) for its serving jobs to stop,
+ * frees its scratch.  Plans created from it must be destroyed first. */
+int grav_ctx_destroy(grav_ctx *ctx);
+
+/* Message of the last error on this context (thread-local per context; never NULL). */
+const char *grav_last_error(grav_ctx *ctx);
+
+/* Blocks (bounded by timeout_s) until `stream` is idle and reports any
+ * device status word set by this context's kernels (GRAV_EDEVICE). */
+int grav_ctx_sync(grav_ctx *ctx, grav_stream_t stream, double timeout_s);
+
+/* ---- one-shot operator calls (Section 2.1, Eq. 5-6) ----------------------- */
+/* d[i] = sum_k G_ik m[k] (mGal).  m: DEVICE, nx*ny*nz doubles (kg/m^3).
+ * d: DEVICE, survey->n doubles.  opt may be NULL (defaults).  Builds a
+ * transient plan (GRAV_MIXED: includes the FP64 near-field set-up), enqueues
+ * the product and releases the plan in stream order. */
+int grav_forward(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey,
+                 const double *m, double *d, const grav_options *opt, grav_stream_t stream);
+
+/* gtr[k] = sum_i G_ik r[i], times (zc_k + z0)^2 when depth_weighted != 0.
+ * r: DEVICE, survey->n doubles; gtr: DEVICE, nx*ny*nz doubles. */
+int grav_adjoint(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey,
+                 const double *r, double *gtr, int depth_weighted,
+                 const grav_options *opt, grav_stream_t stream);
+
+/* diag[i] = sum_k G_ik^2 (zc_k + z0)^2, the diagonal of G W^-2 G^T, and
+ * (when trace != NULL, HOST) its sum.  diag: DEVICE, survey->n doubles.
+ * Synchronises the stream when trace != NULL. */
+int grav_diag(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey,
+              double *diag, double *trace, const grav_options *opt, grav_stream_t stream);
+
+/* ---- data-space inversion (Section 2.2, Eq. 10-11) ------------------------ */
+/* m_out = m_ref + W^-2 G^T y with (G W^-2 G^T + lambda I) y = d - G m_ref,
+ * y by CG from y = 0.  d: DEVICE, n doubles (mGal).  m_ref: DEVICE, M
+ * doubles or NULL (zero).  m_out: DEVICE, M doubles.  y_out: DEVICE, n
+ * doubles, or NULL.  info: HOST, may be NULL.  Synchronises `stream`
+ * (bounded host waits).  Returns GRAV_ENOTCONVERGED, with m_out written from
+ * the last iterate, when max_iter is reached. */
+int grav_datainv_solve(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey,
+                       const double *d, const double *m_ref, double *m_out, double *y_out,
+                       grav_solve_info *info, const grav_options *opt, grav_stream_t stream);
+
+/* ---- reusable plans ------------------------------------------------------- */
+/* A plan holds one (mesh, survey, options) problem resident on the device:
+ * the mesh edges, the station arrays' derived forms, the operator scratch and,
+ * for GRAV_MIXED, the FP64 near-field correction of every station.  The
+ * survey arrays are read when the plan is created and must not change while
+ * the plan is used.  Creation enqueues set-up work on `stream`. */
+int grav_plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey,
+                     const grav_options *opt, grav_plan **out, grav_stream_t stream);
+int grav_plan_forward(grav_plan *plan, const double *m, double *d, grav_stream_t stream);
+int grav_plan_adjoint(grav_plan *plan, const double *r, double *gtr, int depth_weighted,
+                      grav_stream_t stream);
+/* Device bytes the plan holds. */
+size_t grav_plan_bytes(const grav_plan *plan);
+/* Releases the plan's memory in stream order after the work already
+ * enqueued on `stream`. */
+int grav_plan_destroy(grav_plan *plan, grav_stream_t stream);
+
+/* ---- measurement ------------------------------------------------------------ */
+/* Total number of CUDA kernels this library has launched in the process
+ * (all contexts).  Used to attribute device work to libgrav in benchmarks. */
+uint64_t grav_launch_count(void);
+
+/* Stage timing of one plan with CUDA events on the launching stream.
+ * enable != 0 starts recording the device time of the plan's main kernels
+ * (0 forward main kernel, 1 adjoint main kernel, 2 forward near-field apply,
+ * 3 adjoint near-field apply); ms/counts (HOST, 4 entries each, may be NULL)
+ * receive the summed milliseconds and launch counts recorded since the last
+ * read (this waits for the recorded events) and reset them. */
+int grav_plan_timing(grav_plan *plan, int enable, double *ms, int64_t *counts);
+
+/* Pipe-rate microbenchmark on `device` (synchronous, ~0.1 s).  out (HOST, 9
+ * doubles): [0] MUFU rsqrt/s, [1] SM MHz seen, [2] MUFU lg2/s, [3] MHz,
+ * [4] FP32 FMA/s, [5] MHz, [6] FP64 FMA/s, [7] MHz, [8] SM count.  The per-clock
+ * rates per SM are out[2k] / (out[2k+1]*1e6 * out[8]). */
+int grav_bench_pipes(int device, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRAV_H_ */

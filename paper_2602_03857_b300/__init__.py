@@ -1,0 +1,394 @@
+"""Python binding of libgrav (argument marshalling only).
+
+Every operator step runs in the CUDA kernels of ``libgrav.so`` (built
+in-tree by ``paper_2602_03857_b300.build``); this module only converts torch
+tensors and numpy arrays into the pointers and sizes of the C ABI declared
+in ``include/grav.h`` and raises on error codes.  There is no CPU fallback:
+if the shared library is missing, importing this package fails.
+
+Notation follows the paper: d = G m (Section 2.1, Eq. 5-6), G^T r, and the
+data-space inversion m = m_ref + W^-2 G^T (G W^-2 G^T + lambda I)^-1 (d - G m_ref)
+(Section 2.2, Eq. 10-11).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgrav.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"libgrav.so not found at {LIB_PATH}: build it with `python paper_2602_03857_b300/build.py` "
+        "(the CUDA library is required; there is no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+GRAV_OK = 0
+GRAV_EINVAL = -1
+GRAV_ENOMEM = -2
+GRAV_ENOTCONVERGED = -3
+GRAV_ETIMEDOUT = -4
+GRAV_EDEVICE = -5
+GRAV_ECANCELED = -6
+GRAV_ENOTFOUND = -7
+GRAV_EBUSY = -8
+GRAV_FP64 = 0
+GRAV_MIXED = 1
+PRECISIONS = {"fp64": GRAV_FP64, "mixed": GRAV_MIXED}
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+class grav_mesh(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("xe", _D), ("ye", _D), ("ze", _D)]
+
+
+class grav_survey(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("x", _P), ("y", _P), ("z", _P)]
+
+
+class grav_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("z0", ctypes.c_double), ("lambda_scale", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("near_cells", ctypes.c_double), ("timeout_s", ctypes.c_double)]
+
+
+class grav_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("true_rel_res", ctypes.c_double), ("lambda_", ctypes.c_double), ("trace", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_i, _vp = ctypes.c_int, ctypes.c_void_p
+_sig("grav_options_default", None, [ctypes.POINTER(grav_options)])
+_sig("grav_version", ctypes.c_char_p, [])
+_sig("grav_ctx_create", _i, [ctypes.POINTER(_vp), _i, ctypes.c_size_t])
+_sig("grav_ctx_destroy", _i, [_vp])
+_sig("grav_last_error", ctypes.c_char_p, [_vp])
+_sig("grav_ctx_sync", _i, [_vp, _vp, ctypes.c_double])
+_sig("grav_forward", _i, [_vp, ctypes.POINTER(grav_mesh), ctypes.POINTER(grav_survey), _vp, _vp,
+                          ctypes.POINTER(grav_options), _vp])
+_sig("grav_adjoint", _i, [_vp, ctypes.POINTER(grav_mesh), ctypes.POINTER(grav_survey), _vp, _vp, _i,
+                          ctypes.POINTER(grav_options), _vp])
+_sig("grav_diag", _i, [_vp, ctypes.POINTER(grav_mesh), ctypes.POINTER(grav_survey), _vp, _D,
+                       ctypes.POINTER(grav_options), _vp])
+_sig("grav_datainv_solve", _i, [_vp, ctypes.POINTER(grav_mesh), ctypes.POINTER(grav_survey), _vp, _vp, _vp,
+                                _vp, ctypes.POINTER(grav_solve_info), ctypes.POINTER(grav_options), _vp])
+_sig("grav_plan_create", _i, [_vp, ctypes.POINTER(grav_mesh), ctypes.POINTER(grav_survey),
+                              ctypes.POINTER(grav_options), ctypes.POINTER(_vp), _vp])
+_sig("grav_plan_forward", _i, [_vp, _vp, _vp, _vp])
+_sig("grav_plan_adjoint", _i, [_vp, _vp, _vp, _i, _vp])
+_sig("grav_plan_bytes", ctypes.c_size_t, [_vp])
+_sig("grav_plan_destroy", _i, [_vp, _vp])
+_sig("grav_launch_count", ctypes.c_uint64, [])
+_sig("grav_plan_timing", _i, [_vp, _i, _D, ctypes.POINTER(ctypes.c_int64)])
+_sig("grav_bench_pipes", _i, [_i, _D])
+
+EXPORTED = [
+    "grav_options_default", "grav_version", "grav_ctx_create", "grav_ctx_destroy", "grav_last_error",
+    "grav_ctx_sync", "grav_forward", "grav_adjoint", "grav_diag", "grav_datainv_solve", "grav_plan_create",
+    "grav_plan_forward", "grav_plan_adjoint", "grav_plan_bytes", "grav_plan_destroy",
+    "grav_launch_count", "grav_plan_timing", "grav_bench_pipes",
+]
+
+STAGES = ("fwd_main", "adj_main", "fwd_near", "adj_near")
+
+
+def launch_count() -> int:
+    """Kernels launched by libgrav so far in this process."""
+    return int(_lib.grav_launch_count())
+
+
+def bench_pipes(device: int = 0) -> dict:
+    """Measured unit throughputs (per second) and SM clocks of the B300 pipes."""
+    out = (ctypes.c_double * 9)()
+    rc = _lib.grav_bench_pipes(int(device), out)
+    if rc != GRAV_OK:
+        raise GravError(rc, _lib.grav_last_error(None).decode())
+    sms = out[8]
+    r = {"sm_count": int(sms)}
+    for k, name in enumerate(("rsqrt", "lg2", "ffma", "dfma")):
+        r[name + "_per_s"] = out[2 * k]
+        r[name + "_mhz"] = out[2 * k + 1]
+        r[name + "_per_clk_sm"] = out[2 * k] / (out[2 * k + 1] * 1e6 * sms) if out[2 * k + 1] > 0 else 0.0
+    return r
+
+
+class GravError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libgrav error {code}: {msg}")
+        self.code = code
+
+
+def version() -> str:
+    return _lib.grav_version().decode()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Context:
+    """A libgrav context on one CUDA device (owns scratch memory pool)."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0):
+        h = _vp()
+        rc = _lib.grav_ctx_create(ctypes.byref(h), int(device), int(hbm_budget))
+        if rc != GRAV_OK:
+            raise GravError(rc, _lib.grav_last_error(None).decode())
+        self.h = h
+        self.device = device
+
+    def check(self, rc: int):
+        if rc != GRAV_OK and rc != GRAV_ENOTCONVERGED:
+            raise GravError(rc, _lib.grav_last_error(self.h).decode())
+        return rc
+
+    def sync(self, stream=None, timeout_s: float = 600.0):
+        self.check(_lib.grav_ctx_sync(self.h, _stream(stream), timeout_s))
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.grav_ctx_destroy(self.h)
+            self.h = None
+
+
+_contexts = {}
+
+
+def context(device: Optional[int] = None) -> Context:
+    torch = _torch()
+    if device is None:
+        device = torch.cuda.current_device()
+    if device not in _contexts:
+        _contexts[device] = Context(device)
+    return _contexts[device]
+
+
+def _stream(stream):
+    if stream is None:
+        return _vp(_torch().cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return _vp(stream)
+    return _vp(stream.cuda_stream)
+
+
+class Mesh:
+    """Rectilinear mesh: host float64 edge arrays (m); ze is depth, positive down."""
+
+    def __init__(self, xe, ye, ze):
+        self.xe = np.ascontiguousarray(xe, dtype=np.float64)
+        self.ye = np.ascontiguousarray(ye, dtype=np.float64)
+        self.ze = np.ascontiguousarray(ze, dtype=np.float64)
+        self.c = grav_mesh(len(self.xe) - 1, len(self.ye) - 1, len(self.ze) - 1,
+                           self.xe.ctypes.data_as(_D), self.ye.ctypes.data_as(_D), self.ze.ctypes.data_as(_D))
+
+    @classmethod
+    def of(cls, m) -> "Mesh":
+        return m if isinstance(m, Mesh) else cls(m.xe, m.ye, m.ze)
+
+    @property
+    def ncells(self) -> int:
+        return self.c.nx * self.c.ny * self.c.nz
+
+
+class Survey:
+    """Stations as device float64 tensors (x, y, z = -height)."""
+
+    def __init__(self, x, y, z, device=None):
+        torch = _torch()
+        dev = torch.device("cuda", device if device is not None else torch.cuda.current_device())
+        self.x = torch.as_tensor(x, dtype=torch.float64, device=dev).contiguous()
+        self.y = torch.as_tensor(y, dtype=torch.float64, device=dev).contiguous()
+        self.z = torch.as_tensor(z, dtype=torch.float64, device=dev).contiguous()
+        self.c = grav_survey(self.x.numel(), self.x.data_ptr(), self.y.data_ptr(), self.z.data_ptr())
+
+    @classmethod
+    def of(cls, s) -> "Survey":
+        return s if isinstance(s, Survey) else cls(s.x, s.y, s.z)
+
+    @property
+    def n(self) -> int:
+        return int(self.c.n)
+
+
+def options(precision="fp64", z0=50.0, lambda_scale=1e-2, lam=0.0, tol=1e-6, max_iter=1000,
+            check_every=0, near_cells=8.0, timeout_s=3600.0) -> grav_options:
+    o = grav_options()
+    _lib.grav_options_default(ctypes.byref(o))
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.z0, o.lambda_scale, o.lambda_ = float(z0), float(lambda_scale), float(lam)
+    o.tol, o.max_iter, o.check_every = float(tol), int(max_iter), int(check_every)
+    o.near_cells, o.timeout_s = float(near_cells), float(timeout_s)
+    return o
+
+
+def _f64(t, n, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.asarray(t), dtype=torch.float64, device="cuda")
+    if t.dtype != torch.float64 or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    t = t.contiguous()
+    if t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} entries, expected {n}")
+    return t
+
+
+def forward(m, mesh, survey, stream=None, ctx: Optional[Context] = None, **opts):
+    """d = G m (mGal) for density contrast m (kg/m^3), k = i + nx*(j + ny*l)."""
+    torch = _torch()
+    ctx = ctx or context()
+    mesh, survey = Mesh.of(mesh), Survey.of(survey)
+    m = _f64(m, mesh.ncells, "m")
+    d = torch.empty(survey.n, dtype=torch.float64, device=m.device)
+    o = options(**opts)
+    ctx.check(_lib.grav_forward(ctx.h, ctypes.byref(mesh.c), ctypes.byref(survey.c), m.data_ptr(), d.data_ptr(),
+                                ctypes.byref(o), _stream(stream)))
+    return d
+
+
+def adjoint(r, mesh, survey, depth_weighted=False, stream=None, ctx: Optional[Context] = None, **opts):
+    """G^T r (times W^-2 = (zc + z0)^2 when depth_weighted)."""
+    torch = _torch()
+    ctx = ctx or context()
+    mesh, survey = Mesh.of(mesh), Survey.of(survey)
+    r = _f64(r, survey.n, "r")
+    out = torch.empty(mesh.ncells, dtype=torch.float64, device=r.device)
+    o = options(**opts)
+    ctx.check(_lib.grav_adjoint(ctx.h, ctypes.byref(mesh.c), ctypes.byref(survey.c), r.data_ptr(), out.data_ptr(),
+                                int(bool(depth_weighted)), ctypes.byref(o), _stream(stream)))
+    return out
+
+
+def diag(mesh, survey, stream=None, ctx: Optional[Context] = None, **opts):
+    """(diag(G W^-2 G^T), trace)."""
+    torch = _torch()
+    ctx = ctx or context()
+    mesh, survey = Mesh.of(mesh), Survey.of(survey)
+    out = torch.empty(survey.n, dtype=torch.float64, device="cuda")
+    tr = ctypes.c_double(0.0)
+    o = options(**opts)
+    ctx.check(_lib.grav_diag(ctx.h, ctypes.byref(mesh.c), ctypes.byref(survey.c), out.data_ptr(), ctypes.byref(tr),
+                             ctypes.byref(o), _stream(stream)))
+    return out, tr.value
+
+
+def datainv(d, mesh, survey, m_ref=None, return_y=False, stream=None, ctx: Optional[Context] = None, **opts):
+    """Data-space inversion (Eq. 10-11) by CG.  Returns (m, info) or (m, y, info)."""
+    torch = _torch()
+    ctx = ctx or context()
+    mesh, survey = Mesh.of(mesh), Survey.of(survey)
+    d = _f64(d, survey.n, "d")
+    mr = _f64(m_ref, mesh.ncells, "m_ref") if m_ref is not None else None
+    m = torch.empty(mesh.ncells, dtype=torch.float64, device=d.device)
+    y = torch.empty(survey.n, dtype=torch.float64, device=d.device) if return_y else None
+    info = grav_solve_info()
+    o = options(**opts)
+    rc = ctx.check(_lib.grav_datainv_solve(ctx.h, ctypes.byref(mesh.c), ctypes.byref(survey.c), d.data_ptr(),
+                                           mr.data_ptr() if mr is not None else None, m.data_ptr(),
+                                           y.data_ptr() if y is not None else None, ctypes.byref(info),
+                                           ctypes.byref(o), _stream(stream)))
+    inf = {"iters": info.iters, "converged": bool(info.converged), "rel_res": info.rel_res,
+           "true_rel_res": info.true_rel_res, "lambda": info.lambda_, "trace": info.trace,
+           "seconds": info.seconds, "status": rc}
+    return (m, y, inf) if return_y else (m, inf)
+
+
+class Plan:
+    """One (mesh, survey, options) problem resident on the device."""
+
+    def __init__(self, mesh, survey, stream=None, ctx: Optional[Context] = None, **opts):
+        self.ctx = ctx or context()
+        self.mesh, self.survey = Mesh.of(mesh), Survey.of(survey)
+        self.opts = opts
+        o = options(**opts)
+        h = _vp()
+        self.ctx.check(_lib.grav_plan_create(self.ctx.h, ctypes.byref(self.mesh.c), ctypes.byref(self.survey.c),
+                                             ctypes.byref(o), ctypes.byref(h), _stream(stream)))
+        self.h = h
+
+    @property
+    def nbytes(self) -> int:
+        return int(_lib.grav_plan_bytes(self.h))
+
+    def forward(self, m, out=None, stream=None):
+        torch = _torch()
+        m = _f64(m, self.mesh.ncells, "m")
+        d = out if out is not None else torch.empty(self.survey.n, dtype=torch.float64, device=m.device)
+        self.ctx.check(_lib.grav_plan_forward(self.h, m.data_ptr(), d.data_ptr(), _stream(stream)))
+        return d
+
+    def adjoint(self, r, depth_weighted=False, out=None, stream=None):
+        torch = _torch()
+        r = _f64(r, self.survey.n, "r")
+        g = out if out is not None else torch.empty(self.mesh.ncells, dtype=torch.float64, device=r.device)
+        self.ctx.check(_lib.grav_plan_adjoint(self.h, r.data_ptr(), g.data_ptr(), int(bool(depth_weighted)),
+                                              _stream(stream)))
+        return g
+
+    def timing(self, enable: bool = True, read: bool = True):
+        """Start/stop stage timing; returns {stage: (ms, count)} recorded since the last read."""
+        ms = (ctypes.c_double * 4)()
+        cnt = (ctypes.c_int64 * 4)()
+        self.ctx.check(_lib.grav_plan_timing(self.h, int(enable), ms if read else None, cnt if read else None))
+        return {STAGES[k]: (ms[k], int(cnt[k])) for k in range(4)} if read else None
+
+    def close(self, stream=None):
+        if getattr(self, "h", None):
+            _lib.grav_plan_destroy(self.h, _stream(stream))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _make_autograd():
+    torch = _torch()
+
+    class GravForward(torch.autograd.Function):
+        """d = G m with backward grad_m = G^T grad_d (the hand-written adjoint kernel)."""
+
+        @staticmethod
+        def forward(ctx_, m, plan: Plan):
+            ctx_.plan = plan
+            return plan.forward(m.detach())
+
+        @staticmethod
+        def backward(ctx_, grad_d):
+            return ctx_.plan.adjoint(grad_d.contiguous()), None
+
+    return GravForward
+
+
+_GravForward = None
+
+
+def GravForwardFn():
+    global _GravForward
+    if _GravForward is None:
+        _GravForward = _make_autograd()
+    return _GravForward
+
+
+def gravity(m, plan: Plan):
+    """Differentiable d = G m through ``plan`` (torch.autograd)."""
+    return GravForwardFn().apply(m, plan)

@@ -1,0 +1,734 @@
+// C ABI of libgrav: context, argument validation, plans, one-shot operator
+// calls and the data-space CG solve (Section 2.2, Eq. 10-11).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <thread>
+
+#include "cg.h"
+#include "device_common.cuh"
+#include "internal.h"
+
+using grav::kSCount;
+
+namespace grav {
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+std::mutex g_err_mu;
+std::string g_last_error = "";
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Polls `ev` until it completes or timeout_s elapses.
+int wait_event(grav_ctx *ctx, cudaEvent_t ev, double timeout_s, const char *what) {
+    const double t0 = now_s();
+    int sleep_us = 20;
+    while (true) {
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return GRAV_OK;
+        if (e != cudaErrorNotReady) return cuda_error(ctx, e, what);
+        if (now_s() - t0 > timeout_s) return set_error(ctx, GRAV_ETIMEDOUT, "%s: timed out after %.1f s", what, timeout_s);
+        std::this_thread::sleep_for(std::chrono::microseconds(sleep_us));
+        sleep_us = std::min(sleep_us * 2, 2000);
+    }
+}
+
+bool is_device_ptr(const void *p, int device) {
+    if (!p) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == device;
+}
+
+bool finite_increasing(const double *e, int n) {
+    for (int i = 0; i <= n; ++i)
+        if (!std::isfinite(e[i])) return false;
+    for (int i = 0; i < n; ++i)
+        if (!(e[i + 1] > e[i])) return false;
+    return true;
+}
+
+int check_options(grav_ctx *ctx, const grav_options &o) {
+    if (o.precision != GRAV_FP64 && o.precision != GRAV_MIXED)
+        return set_error(ctx, GRAV_EINVAL, "precision must be GRAV_FP64 or GRAV_MIXED (got %d)", o.precision);
+    if (!std::isfinite(o.z0) || o.z0 < 0) return set_error(ctx, GRAV_EINVAL, "z0 must be finite and >= 0");
+    if (!(o.lambda_scale > 0) || !std::isfinite(o.lambda_scale))
+        return set_error(ctx, GRAV_EINVAL, "lambda_scale must be > 0");
+    if (!std::isfinite(o.lambda) || o.lambda < 0) return set_error(ctx, GRAV_EINVAL, "lambda must be >= 0");
+    if (!(o.tol > 0) || !(o.tol < 1)) return set_error(ctx, GRAV_EINVAL, "tol must lie in (0, 1)");
+    if (o.max_iter < 1) return set_error(ctx, GRAV_EINVAL, "max_iter must be >= 1");
+    if (o.check_every < 0) return set_error(ctx, GRAV_EINVAL, "check_every must be >= 0");
+    if (!(o.near_cells >= 1.0 && o.near_cells <= 16.0))
+        return set_error(ctx, GRAV_EINVAL, "near_cells must lie in [1, 16]");
+    if (!(o.timeout_s > 0)) return set_error(ctx, GRAV_EINVAL, "timeout_s must be > 0");
+    return GRAV_OK;
+}
+
+grav_options resolve(const grav_options *opt) {
+    grav_options o;
+    grav_options_default(&o);
+    if (opt) o = *opt;
+    return o;
+}
+
+}  // namespace
+
+void note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+void stage_begin(const grav_plan *p, int stage, cudaStream_t s) {
+    StageTimer &t = p->timer;
+    if (!t.enabled) return;
+    if (2 * (t.used + 1) > (int)t.pool.size()) {
+        for (int k = 0; k < 64; ++k) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            t.pool.push_back(e);
+        }
+    }
+    t.stage_of.resize(t.used + 1);
+    t.stage_of[t.used] = stage;
+    cudaEventRecord(t.pool[2 * t.used], s);
+}
+
+void stage_end(const grav_plan *p, int stage, cudaStream_t s) {
+    StageTimer &t = p->timer;
+    if (!t.enabled) return;
+    (void)stage;
+    cudaEventRecord(t.pool[2 * t.used + 1], s);
+    ++t.used;
+}
+
+int set_error(grav_ctx *ctx, int code, const char *fmt, ...) {
+    char buf[768];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx) {
+        std::lock_guard<std::mutex> lk(ctx->err_mu);
+        ctx->last_error = buf;
+    } else {
+        std::lock_guard<std::mutex> lk(g_err_mu);
+        g_last_error = buf;
+    }
+    return code;
+}
+
+int cuda_error(grav_ctx *ctx, cudaError_t e, const char *what) {
+    return set_error(ctx, e == cudaErrorMemoryAllocation ? GRAV_ENOMEM : GRAV_EDEVICE, "%s: %s (%s)", what,
+                     cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+// ---------------------------------------------------------------------------
+// plan internals shared with the solver and the serving scheduler
+// ---------------------------------------------------------------------------
+namespace {
+
+void fp64_sizes(grav_plan *p, int sm) {
+    const int64_t target = (int64_t)sm * 5 * 8;
+    p->ldw = (p->nx + 1 + 1) / 2 * 2;
+    const int nrows = (p->ny + 1) * (p->nz + 1);
+    const int64_t tiles = (p->N + 255) / 256;
+    int nch = (int)std::min<int64_t>(std::max<int64_t>(1, (target + tiles - 1) / tiles), nrows);
+    p->f64_rows_per_chunk = (nrows + nch - 1) / nch;
+    p->f64_nchunk = (nrows + p->f64_rows_per_chunk - 1) / p->f64_rows_per_chunk;
+    const int ngz = (p->nz + 1 + 7) / 8;
+    p->a64_groups = (int)((int64_t)(p->nx + 1) * (p->ny + 1) * ngz);
+    const int64_t ctas = (p->a64_groups + 7) / 8;
+    int64_t nsch = std::max<int64_t>(1, (target + ctas - 1) / ctas);
+    nsch = std::min<int64_t>(nsch, (p->N + 255) / 256);
+    int64_t len = (p->N + nsch - 1) / nsch;
+    len = (len + 255) / 256 * 256;
+    p->a64_schunk_len = (int)len;
+    p->a64_nschunk = (int)((p->N + len - 1) / len);
+    const int64_t dt = (p->N + 127) / 128;
+    int dch = (int)std::min<int64_t>(std::max<int64_t>(1, (target + dt - 1) / dt), p->ny);
+    p->f64_diag_jrows = (p->ny + dch - 1) / dch;
+    p->f64_diag_nchunk = (p->ny + p->f64_diag_jrows - 1) / p->f64_diag_jrows;
+}
+
+size_t fp64_bytes(const grav_plan *p) {
+    const size_t nrows = (size_t)(p->ny + 1) * (p->nz + 1);
+    size_t b = 0;
+    auto add = [&](size_t v) { b += (v + 255) / 256 * 256 + 256; };
+    add(nrows * p->ldw * 8);                                                   // w
+    add((size_t)std::max(p->f64_nchunk, p->f64_diag_nchunk) * p->N * 8);       // part
+    add((size_t)p->N * 32);                                                    // st4
+    add((size_t)p->a64_nschunk * p->Nn * 8);                                   // upart
+    add((size_t)p->Nn * 8);                                                    // u
+    return b;
+}
+
+}  // namespace
+
+int plan_forward_ex(grav_plan *p, const double *m, double *d, const double *add, double add_scale,
+                    cudaStream_t s) {
+    if (p->opt.precision == GRAV_FP64) {
+        launch_node_weights(p, m, s);
+        launch_fwd64(p, s);
+        launch_reduce_rows(p->part, p->f64_nchunk, p->N, kGammaMgal, add, add_scale, nullptr, d, s);
+    } else {
+        launch_mixed_prep_q(p, m, s);
+        launch_mixed_fwd(p, s);
+        launch_mixed_near_fwd(p, m, s);
+        launch_reduce_rows(p->m_part, p->m_fwd_nchunk, p->N, 1.0, add, add_scale, p->near_corr, d, s);
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GRAV_OK : cuda_error(p->ctx, e, "forward launch");
+}
+
+int plan_adjoint_ex(grav_plan *p, const double *r, double *out, int depth_weighted, const double *add,
+                    cudaStream_t s) {
+    if (p->opt.precision == GRAV_FP64) {
+        launch_adj64(p, r, s);
+        launch_adj_finish(p, p->u, kGammaMgal, depth_weighted, add, out, s);
+    } else {
+        launch_mixed_adj(p, r, s);
+        launch_mixed_adj_finish(p, r, depth_weighted, add, out, s);
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GRAV_OK : cuda_error(p->ctx, e, "adjoint launch");
+}
+
+int plan_diag(grav_plan *p, double *diag, cudaStream_t s) {
+    if (p->opt.precision == GRAV_FP64) launch_diag64(p, diag, s);
+    else launch_mixed_diag(p, diag, s);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GRAV_OK : cuda_error(p->ctx, e, "diag launch");
+}
+
+int plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const grav_options &o,
+                grav_plan **out, cudaStream_t s) {
+    if (!out) return set_error(ctx, GRAV_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!mesh || !survey) return set_error(ctx, GRAV_EINVAL, "mesh or survey is NULL");
+    int rc = check_options(ctx, o);
+    if (rc) return rc;
+    if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1)
+        return set_error(ctx, GRAV_EINVAL, "mesh sizes must be >= 1 (got %d x %d x %d)", mesh->nx, mesh->ny, mesh->nz);
+    if ((int64_t)mesh->nx * mesh->ny * mesh->nz > (int64_t)1 << 30 ||
+        (int64_t)(mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1) > (int64_t)1 << 30 || mesh->nx > 1 << 20 ||
+        mesh->ny > 1 << 20 || mesh->nz > 1 << 16)
+        return set_error(ctx, GRAV_EINVAL, "mesh too large");
+    if (!mesh->xe || !mesh->ye || !mesh->ze) return set_error(ctx, GRAV_EINVAL, "mesh edge array is NULL");
+    if (!finite_increasing(mesh->xe, mesh->nx) || !finite_increasing(mesh->ye, mesh->ny) ||
+        !finite_increasing(mesh->ze, mesh->nz))
+        return set_error(ctx, GRAV_EINVAL, "mesh edges must be finite and strictly increasing");
+    if (survey->n < 1 || survey->n > ((int64_t)1 << 30))
+        return set_error(ctx, GRAV_EINVAL, "survey size must lie in [1, 2^30] (got %lld)", (long long)survey->n);
+    if (!is_device_ptr(survey->x, ctx->device) || !is_device_ptr(survey->y, ctx->device) ||
+        !is_device_ptr(survey->z, ctx->device))
+        return set_error(ctx, GRAV_EINVAL, "survey x/y/z must be device pointers on device %d", ctx->device);
+
+    grav_plan *p = new grav_plan();
+    p->ctx = ctx;
+    p->opt = o;
+    p->nx = mesh->nx; p->ny = mesh->ny; p->nz = mesh->nz;
+    p->N = survey->n;
+    p->M = (int64_t)p->nx * p->ny * p->nz;
+    p->Nn = (int64_t)(p->nx + 1) * (p->ny + 1) * (p->nz + 1);
+    p->xe.assign(mesh->xe, mesh->xe + p->nx + 1);
+    p->ye.assign(mesh->ye, mesh->ye + p->ny + 1);
+    p->ze.assign(mesh->ze, mesh->ze + p->nz + 1);
+    p->sx = survey->x; p->sy = survey->y; p->sz = survey->z;
+    {
+        const double a = p->xe[1] - p->xe[0];
+        bool cubic = true;
+        auto uni = [&](const std::vector<double> &e) {
+            for (size_t i = 0; i + 1 < e.size(); ++i)
+                if (std::fabs((e[i + 1] - e[i]) - a) > 1e-9 * a) return false;
+            return true;
+        };
+        cubic = uni(p->xe) && uni(p->ye) && uni(p->ze);
+        p->cubic = cubic;
+    }
+    if (o.precision == GRAV_MIXED && !p->cubic) {
+        delete p;
+        return set_error(ctx, GRAV_EINVAL, "GRAV_MIXED needs a uniform mesh of cubic cells (dx = dy = dz everywhere)");
+    }
+    size_t bytes = 0;
+    auto add = [&](size_t v) { bytes += (v + 255) / 256 * 256 + 256; };
+    add(8ull * (p->nx + 1)); add(8ull * (p->ny + 1)); add(8ull * (p->nz + 1)); add(8ull * p->nz);
+    if (o.precision == GRAV_FP64) {
+        fp64_sizes(p, ctx->sm_count);
+        bytes += fp64_bytes(p);
+    } else {
+        const double a = p->xe[1] - p->xe[0];
+        const double k = o.near_cells;
+        p->ng.radius_cells = k;
+        p->ng.bx = (int)std::ceil(2.0 * k) + 1;
+        p->ng.by = p->ng.bx;
+        int bz = 0;
+        for (int l = 0; l < p->nz; ++l)
+            if (0.5 * (p->ze[l] + p->ze[l + 1]) - p->ze[0] < k * a) bz = l + 1;
+        p->ng.bz = std::max(1, bz);
+        p->ng.slots = p->ng.bx * p->ng.by * p->ng.bz;
+        p->ng.nbx = p->nx + p->ng.bx - 1;
+        p->ng.nby = p->ny + p->ng.by - 1;
+        bytes += mixed_scratch_bytes(p);
+    }
+    if (ctx->hbm_used.load() + bytes > ctx->hbm_budget) {
+        delete p;
+        return set_error(ctx, GRAV_ENOMEM, "plan needs %.3f GB; context budget %.3f GB, %.3f GB in use", bytes / 1e9,
+                         ctx->hbm_budget / 1e9, ctx->hbm_used.load() / 1e9);
+    }
+    void *base = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&base, bytes, ctx->pool, s);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_error(ctx, e, "plan allocation");
+    }
+    ctx->hbm_used += bytes;
+    p->bytes = bytes;
+    p->arena.base = (char *)base;
+    p->arena.size = bytes;
+    p->d_xe = (double *)p->arena.take(8ull * (p->nx + 1));
+    p->d_ye = (double *)p->arena.take(8ull * (p->ny + 1));
+    p->d_ze = (double *)p->arena.take(8ull * (p->nz + 1));
+    p->d_w2 = (double *)p->arena.take(8ull * p->nz);
+    std::vector<double> w2(p->nz);
+    for (int l = 0; l < p->nz; ++l) {
+        const double zc = 0.5 * (p->ze[l] + p->ze[l + 1]) - p->ze[0];
+        w2[l] = (zc + o.z0) * (zc + o.z0);
+    }
+    cudaMemcpyAsync(p->d_xe, p->xe.data(), 8ull * (p->nx + 1), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(p->d_ye, p->ye.data(), 8ull * (p->ny + 1), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(p->d_ze, p->ze.data(), 8ull * (p->nz + 1), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(p->d_w2, w2.data(), 8ull * p->nz, cudaMemcpyHostToDevice, s);
+    if (o.precision == GRAV_FP64) {
+        const size_t nrows = (size_t)(p->ny + 1) * (p->nz + 1);
+        p->w = (double *)p->arena.take(nrows * p->ldw * 8);
+        p->part = (double *)p->arena.take((size_t)std::max(p->f64_nchunk, p->f64_diag_nchunk) * p->N * 8);
+        p->st4 = (double4 *)p->arena.take((size_t)p->N * 32);
+        p->upart = (double *)p->arena.take((size_t)p->a64_nschunk * p->Nn * 8);
+        p->u = (double *)p->arena.take((size_t)p->Nn * 8);
+        if (!p->arena.overflow) fp64_setup(p, s);
+    } else {
+        rc = near_setup_warps(p) < 1 ? GRAV_EINVAL : mixed_setup(p, s);
+    }
+    if (rc || p->arena.overflow) {
+        cudaFreeAsync(base, s);
+        ctx->hbm_used -= bytes;
+        delete p;
+        if (rc == GRAV_EINVAL)
+            return set_error(ctx, GRAV_EINVAL, "near_cells window too large for this mesh (shared-memory limit)");
+        return set_error(ctx, GRAV_EDEVICE, "internal: plan arena overflow");
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaFreeAsync(base, s);
+        ctx->hbm_used -= bytes;
+        delete p;
+        return cuda_error(ctx, e, "plan set-up");
+    }
+    *out = p;
+    return GRAV_OK;
+}
+
+void plan_destroy(grav_plan *p, cudaStream_t s) {
+    if (!p) return;
+    for (cudaEvent_t e : p->timer.pool) cudaEventDestroy(e);
+    if (p->arena.base) cudaFreeAsync(p->arena.base, s);
+    p->ctx->hbm_used -= p->bytes;
+    delete p;
+}
+
+int read_status(grav_ctx *ctx, cudaStream_t s, double timeout_s) {
+    cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaEvent_t ev;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    cudaEventRecord(ev, s);
+    int rc = wait_event(ctx, ev, timeout_s, "stream synchronisation");
+    cudaEventDestroy(ev);
+    if (rc) return rc;
+    if (*ctx->h_status != 0) {
+        const int st = *ctx->h_status;
+        cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
+        return set_error(ctx, GRAV_EDEVICE, "device status word 0x%x (bounded device wait expired)", st);
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GRAV_OK : cuda_error(ctx, e, "device");
+}
+
+// ---------------------------------------------------------------------------
+// Data-space CG: A = G W^-2 G^T + lambda I, y0 = 0, r0 = dd.
+// ---------------------------------------------------------------------------
+int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_out, double *y_out,
+                  grav_solve_info *info, cudaStream_t s, const std::atomic<int> *cancel) {
+    grav_ctx *ctx = p->ctx;
+    const grav_options &o = p->opt;
+    const double t0 = now_s();
+    const int64_t N = p->N, M = p->M;
+    const size_t bytes = 8ull * (5 * N + M + kDotBlocks + kSCount) + 8 * 256;
+    if (ctx->hbm_used.load() + bytes > ctx->hbm_budget) return set_error(ctx, GRAV_ENOMEM, "solve vectors exceed budget");
+    char *base = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync((void **)&base, bytes, ctx->pool, s);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "solve allocation");
+    ctx->hbm_used += bytes;
+    Arena ar;
+    ar.base = base; ar.size = bytes;
+    double *dd = (double *)ar.take(8ull * N);
+    double *r = (double *)ar.take(8ull * N);
+    double *y = (double *)ar.take(8ull * N);
+    double *pv = (double *)ar.take(8ull * N);
+    double *Ap = (double *)ar.take(8ull * N);
+    double *q = (double *)ar.take(8ull * M);
+    double *dp = (double *)ar.take(8ull * kDotBlocks);
+    double *sc = (double *)ar.take(8ull * kSCount);
+    double *hsc = nullptr;
+    cudaMallocHost((void **)&hsc, 8 * kSCount);
+    cudaEvent_t ev;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    int rc = GRAV_OK;
+    double lam = o.lambda, trace = 0.0;
+    int iters = 0;
+    bool converged = false;
+    auto sync_scalars = [&](const char *what) -> int {
+        cudaMemcpyAsync(hsc, sc, 8 * kSCount, cudaMemcpyDeviceToHost, s);
+        cudaEventRecord(ev, s);
+        return wait_event(ctx, ev, o.timeout_s, what);
+    };
+    do {
+        cudaMemsetAsync(sc, 0, 8 * kSCount, s);
+        // dd = d - G m_ref
+        if (m_ref) {
+            if ((rc = plan_forward_ex(p, m_ref, Ap, nullptr, 0.0, s))) break;
+            vec_axpby(1.0, d, -1.0, Ap, N, dd, s);
+        } else {
+            cudaMemcpyAsync(dd, d, 8ull * N, cudaMemcpyDeviceToDevice, s);
+        }
+        // lambda = lambda_scale * trace(G W^-2 G^T) / N
+        if (!(lam > 0)) {
+            if ((rc = plan_diag(p, Ap, s))) break;
+            launch_dot(Ap, nullptr, N, dp, sc + kSTrace, s);
+            if ((rc = sync_scalars("trace"))) break;
+            trace = hsc[kSTrace];
+            lam = o.lambda_scale * trace / (double)N;
+            if (!(lam > 0) || !std::isfinite(lam)) {
+                rc = set_error(ctx, GRAV_EDEVICE, "lambda from the trace is not positive (trace %g)", trace);
+                break;
+            }
+        }
+        cudaMemcpyAsync(r, dd, 8ull * N, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(pv, dd, 8ull * N, cudaMemcpyDeviceToDevice, s);
+        vec_fill(y, N, 0.0, s);
+        launch_dot(r, r, N, dp, sc + kSRR, s);
+        cg_set_scalars(sc, o.tol * o.tol, s);
+        if ((rc = sync_scalars("cg start"))) break;
+        if (hsc[kSFrozen] != 0.0) {
+            converged = true;
+        }
+        const double work = (double)N * (double)M;
+        const int every = o.check_every > 0 ? o.check_every : (work > 2e8 ? 1 : 8);
+        int it = 0;
+        while (!converged && it < o.max_iter) {
+            const int n_it = std::min(every, o.max_iter - it);
+            for (int k = 0; k < n_it; ++k, ++it) {
+                if ((rc = plan_adjoint_ex(p, pv, q, 1, nullptr, s))) break;
+                if ((rc = plan_forward_ex(p, q, Ap, pv, lam, s))) break;
+                launch_dot(pv, Ap, N, dp, sc + kSPAp, s);
+                cg_alpha(sc, s);
+                cg_update_yr(y, r, pv, Ap, N, sc, s);
+                launch_dot(r, r, N, dp, sc + kSRRNew, s);
+                cg_beta(sc, it, s);
+                cg_update_p(pv, r, N, sc, s);
+            }
+            if (rc) break;
+            if ((rc = sync_scalars("cg iteration"))) break;
+            if (hsc[kSFrozen] == 2.0) {
+                rc = set_error(ctx, GRAV_EDEVICE, "CG breakdown: p.Ap <= 0 (operator not SPD in this precision)");
+                break;
+            }
+            if (hsc[kSFrozen] != 0.0) converged = true;
+            if (cancel && cancel->load()) {
+                rc = set_error(ctx, GRAV_ECANCELED, "solve cancelled");
+                break;
+            }
+        }
+        if (rc) break;
+        iters = (int)hsc[kSIters];
+        // m = m_ref + W^-2 G^T y
+        if ((rc = plan_adjoint_ex(p, y, m_out, 1, m_ref, s))) break;
+        // true residual with the same operator: dd - (G W^-2 G^T y + lambda y)
+        if ((rc = plan_adjoint_ex(p, y, q, 1, nullptr, s))) break;
+        if ((rc = plan_forward_ex(p, q, Ap, y, lam, s))) break;
+        vec_axpby(1.0, dd, -1.0, Ap, N, Ap, s);
+        launch_dot(Ap, Ap, N, dp, sc + kSTmp, s);
+        if (y_out) cudaMemcpyAsync(y_out, y, 8ull * N, cudaMemcpyDeviceToDevice, s);
+        if ((rc = sync_scalars("cg finish"))) break;
+        if (info) {
+            info->iters = iters;
+            info->converged = converged ? 1 : 0;
+            info->rel_res = hsc[kSBB] > 0 ? std::sqrt(hsc[kSRR] / hsc[kSBB]) : 0.0;
+            info->true_rel_res = hsc[kSBB] > 0 ? std::sqrt(hsc[kSTmp] / hsc[kSBB]) : 0.0;
+            info->lambda = lam;
+            info->trace = trace;
+        }
+        rc = read_status(ctx, s, o.timeout_s);
+    } while (false);
+    cudaFreeAsync(base, s);
+    ctx->hbm_used -= bytes;
+    cudaEventDestroy(ev);
+    if (rc != GRAV_ETIMEDOUT) cudaStreamSynchronize(s);
+    cudaFreeHost(hsc);
+    if (info) info->seconds = now_s() - t0;
+    if (rc) return rc;
+    if (!converged)
+        return set_error(ctx, GRAV_ENOTCONVERGED, "CG reached max_iter=%d without reaching tol=%g", o.max_iter, o.tol);
+    return GRAV_OK;
+}
+
+}  // namespace grav
+
+using namespace grav;
+
+// ---------------------------------------------------------------------------
+// exported C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void grav_options_default(grav_options *o) {
+    if (!o) return;
+    o->precision = GRAV_FP64;
+    o->z0 = 50.0;
+    o->lambda_scale = 1e-2;
+    o->lambda = 0.0;
+    o->tol = 1e-6;
+    o->max_iter = 1000;
+    o->check_every = 0;
+    o->near_cells = 8.0;
+    o->timeout_s = 3600.0;
+}
+
+const char *grav_version(void) { return "libgrav 0.1.0 (sm_103a)"; }
+
+int grav_ctx_create(grav_ctx **out, int device, size_t hbm_budget) {
+    if (!out) return set_error(nullptr, GRAV_EINVAL, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_error(nullptr, e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return set_error(nullptr, GRAV_EINVAL, "device %d out of range [0, %d)", device, n);
+    DeviceGuard g(device);
+    grav_ctx *ctx = new grav_ctx();
+    ctx->device = device;
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    size_t fr = 0, tot = 0;
+    e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return cuda_error(nullptr, e, "cudaMemGetInfo");
+    }
+    ctx->hbm_budget = hbm_budget ? hbm_budget : (size_t)(0.9 * (double)fr);
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    e = cudaMemPoolCreate(&ctx->pool, &props);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return cuda_error(nullptr, e, "cudaMemPoolCreate");
+    }
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    if ((e = cudaMalloc((void **)&ctx->d_status, 256)) != cudaSuccess ||
+        (e = cudaMemset(ctx->d_status, 0, 256)) != cudaSuccess ||
+        (e = cudaMallocHost((void **)&ctx->h_status, 256)) != cudaSuccess) {
+        cudaMemPoolDestroy(ctx->pool);
+        delete ctx;
+        return cuda_error(nullptr, e, "context allocation");
+    }
+    *out = ctx;
+    return GRAV_OK;
+}
+
+int grav_ctx_destroy(grav_ctx *ctx) {
+    if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    serve_shutdown(ctx);
+    cudaDeviceSynchronize();
+    cudaFree(ctx->d_status);
+    cudaFreeHost(ctx->h_status);
+    cudaMemPoolDestroy(ctx->pool);
+    delete ctx;
+    return GRAV_OK;
+}
+
+const char *grav_last_error(grav_ctx *ctx) {
+    if (ctx) {
+        std::lock_guard<std::mutex> lk(ctx->err_mu);
+        thread_local std::string copy;
+        copy = ctx->last_error;
+        return copy.c_str();
+    }
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    thread_local std::string copy2;
+    copy2 = g_last_error;
+    return copy2.c_str();
+}
+
+int grav_ctx_sync(grav_ctx *ctx, grav_stream_t stream, double timeout_s) {
+    if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
+    if (!(timeout_s > 0)) return set_error(ctx, GRAV_EINVAL, "timeout_s must be > 0");
+    DeviceGuard g(ctx->device);
+    return read_status(ctx, (cudaStream_t)stream, timeout_s);
+}
+
+int grav_plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const grav_options *opt,
+                     grav_plan **out, grav_stream_t stream) {
+    if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    return plan_create(ctx, mesh, survey, resolve(opt), out, (cudaStream_t)stream);
+}
+
+int grav_plan_forward(grav_plan *p, const double *m, double *d, grav_stream_t stream) {
+    if (!p) return set_error(nullptr, GRAV_EINVAL, "plan is NULL");
+    DeviceGuard g(p->ctx->device);
+    if (!is_device_ptr(m, p->ctx->device) || !is_device_ptr(d, p->ctx->device))
+        return set_error(p->ctx, GRAV_EINVAL, "m and d must be device pointers");
+    return plan_forward_ex(p, m, d, nullptr, 0.0, (cudaStream_t)stream);
+}
+
+int grav_plan_adjoint(grav_plan *p, const double *r, double *gtr, int depth_weighted, grav_stream_t stream) {
+    if (!p) return set_error(nullptr, GRAV_EINVAL, "plan is NULL");
+    DeviceGuard g(p->ctx->device);
+    if (!is_device_ptr(r, p->ctx->device) || !is_device_ptr(gtr, p->ctx->device))
+        return set_error(p->ctx, GRAV_EINVAL, "r and gtr must be device pointers");
+    return plan_adjoint_ex(p, r, gtr, depth_weighted, nullptr, (cudaStream_t)stream);
+}
+
+size_t grav_plan_bytes(const grav_plan *p) { return p ? p->bytes : 0; }
+
+uint64_t grav_launch_count(void) { return g_launches.load(); }
+
+int grav_plan_timing(grav_plan *p, int enable, double *ms, int64_t *counts) {
+    if (!p) return set_error(nullptr, GRAV_EINVAL, "plan is NULL");
+    DeviceGuard g(p->ctx->device);
+    StageTimer &t = p->timer;
+    if (ms || counts) {
+        for (int k = 0; k < t.used; ++k) {
+            cudaEventSynchronize(t.pool[2 * k + 1]);
+            float e = 0.f;
+            cudaEventElapsedTime(&e, t.pool[2 * k], t.pool[2 * k + 1]);
+            t.ms[t.stage_of[k]] += e;
+            t.count[t.stage_of[k]] += 1;
+        }
+        t.used = 0;
+        for (int k = 0; k < kStageCount; ++k) {
+            if (ms) ms[k] = t.ms[k];
+            if (counts) counts[k] = t.count[k];
+            t.ms[k] = 0.0;
+            t.count[k] = 0;
+        }
+    }
+    t.enabled = enable != 0;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GRAV_OK : cuda_error(p->ctx, e, "stage timing");
+}
+
+int grav_plan_destroy(grav_plan *p, grav_stream_t stream) {
+    if (!p) return set_error(nullptr, GRAV_EINVAL, "plan is NULL");
+    DeviceGuard g(p->ctx->device);
+    plan_destroy(p, (cudaStream_t)stream);
+    return GRAV_OK;
+}
+
+int grav_forward(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const double *m, double *d,
+                 const grav_options *opt, grav_stream_t stream) {
+    if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    if (!is_device_ptr(m, ctx->device) || !is_device_ptr(d, ctx->device))
+        return set_error(ctx, GRAV_EINVAL, "m and d must be device pointers on device %d", ctx->device);
+    grav_plan *p = nullptr;
+    int rc = plan_create(ctx, mesh, survey, resolve(opt), &p, (cudaStream_t)stream);
+    if (rc) return rc;
+    rc = plan_forward_ex(p, m, d, nullptr, 0.0, (cudaStream_t)stream);
+    plan_destroy(p, (cudaStream_t)stream);
+    return rc;
+}
+
+int grav_adjoint(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const double *r, double *gtr,
+                 int depth_weighted, const grav_options *opt, grav_stream_t stream) {
+    if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    if (!is_device_ptr(r, ctx->device) || !is_device_ptr(gtr, ctx->device))
+        return set_error(ctx, GRAV_EINVAL, "r and gtr must be device pointers on device %d", ctx->device);
+    grav_plan *p = nullptr;
+    int rc = plan_create(ctx, mesh, survey, resolve(opt), &p, (cudaStream_t)stream);
+    if (rc) return rc;
+    rc = plan_adjoint_ex(p, r, gtr, depth_weighted, nullptr, (cudaStream_t)stream);
+    plan_destroy(p, (cudaStream_t)stream);
+    return rc;
+}
+
+int grav_diag(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, double *diag, double *trace,
+              const grav_options *opt, grav_stream_t stream) {
+    if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    if (!is_device_ptr(diag, ctx->device)) return set_error(ctx, GRAV_EINVAL, "diag must be a device pointer");
+    const grav_options o = resolve(opt);
+    grav_plan *p = nullptr;
+    const cudaStream_t s = (cudaStream_t)stream;
+    int rc = plan_create(ctx, mesh, survey, o, &p, s);
+    if (rc) return rc;
+    rc = plan_diag(p, diag, s);
+    if (!rc && trace) {
+        double *buf = nullptr;
+        cudaError_t e = cudaMallocFromPoolAsync((void **)&buf, 8ull * (kDotBlocks + 1), ctx->pool, s);
+        if (e != cudaSuccess) {
+            rc = cuda_error(ctx, e, "trace scratch");
+        } else {
+            launch_dot(diag, nullptr, p->N, buf, buf + kDotBlocks, s);
+            double *h = nullptr;
+            cudaMallocHost((void **)&h, 8);
+            cudaMemcpyAsync(h, buf + kDotBlocks, 8, cudaMemcpyDeviceToHost, s);
+            cudaFreeAsync(buf, s);
+            rc = read_status(ctx, s, o.timeout_s);
+            if (!rc) *trace = *h;
+            cudaFreeHost(h);
+        }
+    }
+    plan_destroy(p, s);
+    return rc;
+}
+
+int grav_datainv_solve(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const double *d,
+                       const double *m_ref, double *m_out, double *y_out, grav_solve_info *info,
+                       const grav_options *opt, grav_stream_t stream) {
+    if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    if (!is_device_ptr(d, ctx->device) || !is_device_ptr(m_out, ctx->device) ||
+        (m_ref && !is_device_ptr(m_ref, ctx->device)) || (y_out && !is_device_ptr(y_out, ctx->device)))
+        return set_error(ctx, GRAV_EINVAL, "d, m_out (and m_ref, y_out when given) must be device pointers");
+    if (info) std::memset(info, 0, sizeof(*info));
+    const cudaStream_t s = (cudaStream_t)stream;
+    grav_plan *p = nullptr;
+    int rc = plan_create(ctx, mesh, survey, resolve(opt), &p, s);
+    if (rc) return rc;
+    rc = solve_on_plan(p, d, m_ref, m_out, y_out, info, s, nullptr);
+    plan_destroy(p, s);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,33 @@
+// Device-resident CG state: slots of the scalar array and vector launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace grav {
+
+enum CgScalar : int {
+    kSRR = 0,      // r.r of the current iterate
+    kSPAp = 1,     // p.(A p)
+    kSAlpha = 2,
+    kSBeta = 3,
+    kSRRNew = 4,
+    kSBB = 5,      // dd.dd
+    kSTol2 = 6,    // tol^2
+    kSFrozen = 7,  // 0 running, 1 converged, 2 breakdown (p.Ap <= 0)
+    kSIters = 8,   // iterations completed before freezing
+    kSTrace = 9,
+    kSTmp = 10,
+    kSCount = 16
+};
+
+void cg_alpha(double *sc, cudaStream_t s);
+void cg_update_yr(double *y, double *r, const double *p, const double *Ap, int64_t n, const double *sc,
+                  cudaStream_t s);
+void cg_beta(double *sc, int it, cudaStream_t s);
+void cg_update_p(double *p, const double *r, int64_t n, const double *sc, cudaStream_t s);
+void vec_axpby(double a, const double *x, double b, const double *y, int64_t n, double *out, cudaStream_t s);
+void vec_fill(double *x, int64_t n, double v, cudaStream_t s);
+void cg_set_scalars(double *sc, double tol2, cudaStream_t s);
+
+}  // namespace grav

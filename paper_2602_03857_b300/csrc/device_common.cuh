@@ -1,0 +1,140 @@
+// Device helpers shared by the libgrav kernels: physical constants, the
+// FP64 corner function of Eq. 2-3, the FP32 far-field point-mass term,
+// bounded mbarrier waits, 1D TMA bulk copies and the device status word.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace grav {
+
+// gamma (CODATA 2018, m^3 kg^-1 s^-2) times 1e5 (m/s^2 -> mGal).
+constexpr double kGammaMgal = 6.67430e-11 * 1.0e5;
+
+// Device status word bits (OR-ed into ctx->d_status; never a trap).
+constexpr int kStatusMbarTimeout = 1;
+constexpr int kStatusBadLaunch = 2;
+
+// Bound on every device-side wait, in nanoseconds of %globaltimer.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Non-blocking probe of phase completion.
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for `phase` of `bar` for at most kWaitLimitNs; returns false on
+// timeout (the caller records the status and leaves the kernel).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase) {
+    if (mbar_test(bar, phase)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (true) {
+        if (mbar_test(bar, phase)) return true;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+        __nanosleep(64);
+    }
+}
+
+// 1D bulk copy global -> shared, completing on `bar` (TMA, no tensor map).
+// dst and src must be 16-byte aligned and bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void set_status(int *status, int bit) {
+    if (status) atomicOr(status, bit);
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 2-3 in FP64.  Arguments are the vertex coordinates relative to the
+// station (z > 0: the vertex lies below the station) and their squares.
+// ln(R + a) for a < 0 is taken as ln((R^2 - a^2) / (R - a)), an exact
+// identity that avoids the cancellation of R + a (the reading adopted for the
+// paper's unspecified "singularity-robust formulation", Section 2.3).  With
+// z > 0, R > 0 and R^2 - a^2 > 0, so every logarithm argument is positive;
+// at x = 0 (y = 0) the x ln (y ln) term is exactly 0 * finite = 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double psi64(double x, double y, double z, double x2, double y2, double z2) {
+    const double R2 = x2 + y2 + z2;
+    const double R = sqrt(R2);
+    const double t_atan = z * atan((x * y) / (z * R));
+    double ry, rx;
+    if (y >= 0.0) ry = R + y; else ry = (x2 + z2) / (R - y);
+    if (x >= 0.0) rx = R + x; else rx = (y2 + z2) / (R - x);
+    return t_atan - x * log(ry) - y * log(rx);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 far-field term of a cubic prism: dz / R^3 (point mass at the cell
+// centre).  dz, R2 in metres; one MUFU reciprocal square root.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float far_kernel(float dz, float R2) {
+    const float rs = rsqrt_approx(R2);
+    const float rs2 = rs * rs;
+    return (dz * rs) * rs2;
+}
+
+// Knuth two-sum: (s, e) with s = fl(a + b), a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Warp-wide sum with a fixed xor butterfly (deterministic, every lane gets it).
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace grav

@@ -1,0 +1,464 @@
+// FP64 node-shared prism-gravity operator (GRAV_FP64).
+//
+// Summation by parts of Eq. 1 + Eq. 5: the 8-corner parity sum of every cell
+// is regrouped per mesh node, so the corner function Psi (Eq. 2-3) is
+// evaluated ONCE per (station, node) instead of once per (station, cell,
+// corner):
+//     d_i    = gamma * sum_n Psi(n - s_i) w_n,   w_n = sum_{cells k at n} sigma(n,k) m_k
+//     (G^T r)_k = gamma * sum_{n corner of k} sigma(n,k) u_n,   u_n = sum_i Psi(n - s_i) r_i
+// with sigma(n,k) = (-1)^(p+q+r) and p = 1 (2) when n is the lower (upper)
+// x-vertex of cell k (same for q along y, r along z).  w is the mixed third
+// difference of the zero-padded density; D^T is its transpose.
+#include <algorithm>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace grav {
+
+namespace {
+
+constexpr int kFwdThreads = 128;
+constexpr int kFwdT = 2;            // stations per thread
+constexpr int kAdjWarps = 8;        // warps per CTA in the adjoint
+constexpr int kAdjTZ = 8;           // node levels per warp
+constexpr int kAdjStage = 256;      // stations per TMA stage
+constexpr int kDiagZC = 4;          // cell layers per sweep in the diagonal kernel
+
+// ---------------------------------------------------------------------------
+// w = D m, laid out as node rows r = b + (ny+1) c of ldw doubles (x fastest,
+// entries a > nx are zero padding so that every row starts 16-byte aligned).
+// ---------------------------------------------------------------------------
+__global__ void k_node_weights(int nx, int ny, int nz, int ldw, const double *__restrict__ m,
+                               double *__restrict__ w) {
+    const int64_t rows = (int64_t)(ny + 1) * (nz + 1);
+    const int64_t total = rows * ldw;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(t % ldw);
+        const int64_t r = t / ldw;
+        const int b = (int)(r % (ny + 1));
+        const int c = (int)(r / (ny + 1));
+        double acc = 0.0;
+        if (a <= nx) {
+#pragma unroll
+            for (int dc = 0; dc < 2; ++dc) {
+                const int l = c - dc;
+                if (l < 0 || l >= nz) continue;
+#pragma unroll
+                for (int db = 0; db < 2; ++db) {
+                    const int j = b - db;
+                    if (j < 0 || j >= ny) continue;
+#pragma unroll
+                    for (int da = 0; da < 2; ++da) {
+                        const int i = a - da;
+                        if (i < 0 || i >= nx) continue;
+                        // node = cell vertex (i+da, j+db, l+dc): sigma = (-1)^(da+db+dc+3)
+                        const double v = m[i + (int64_t)nx * (j + (int64_t)ny * l)];
+                        acc += ((da + db + dc) & 1) ? v : -v;
+                    }
+                }
+            }
+        }
+        w[t] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward: CTA = (station tile of kFwdThreads*T stations, chunk of node rows).
+// Node-weight rows stream through shared memory by 1D TMA bulk copies
+// (double-buffered, mbarrier-completed); stations stay in registers; every
+// thread reads the same node (shared-memory broadcast).  Zero node weights are
+// skipped (warp-uniform branch: every lane sees the same node).
+// ---------------------------------------------------------------------------
+template <int T>
+__global__ void __launch_bounds__(kFwdThreads) k_fwd64(Geo g, int ldw, const double *__restrict__ w,
+                                                       int rows_per_chunk, int rows_per_stage,
+                                                       const double *__restrict__ sx,
+                                                       const double *__restrict__ sy,
+                                                       const double *__restrict__ sz,
+                                                       double *__restrict__ part, int *status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    int *flag = reinterpret_cast<int *>(smem_raw + 16);
+    double *Xs = reinterpret_cast<double *>(smem_raw + 128);
+    double *wbuf = Xs + ldw;
+
+    const int nrows = (g.ny + 1) * (g.nz + 1);
+    const int r0 = blockIdx.y * rows_per_chunk;
+    const int r1 = min(nrows, r0 + rows_per_chunk);
+    const int nst = (r1 > r0) ? (r1 - r0 + rows_per_stage - 1) / rows_per_stage : 0;
+
+    const int64_t s_base = (int64_t)blockIdx.x * (kFwdThreads * T) + threadIdx.x;
+    double xs[T], ys[T], zs[T], acc[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int64_t s = s_base + (int64_t)t * kFwdThreads;
+        const bool ok = s < g.N;
+        xs[t] = ok ? sx[s] : 0.0;
+        ys[t] = ok ? sy[s] : 0.0;
+        zs[t] = ok ? sz[s] : g.ze[0] - 1.0;
+        acc[t] = 0.0;
+    }
+    for (int a = threadIdx.x; a < ldw; a += kFwdThreads) Xs[a] = (a <= g.nx) ? g.xe[a] : 0.0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int st) {
+        const int buf = st & 1;
+        const int ra = r0 + st * rows_per_stage;
+        const int rb = min(r1, ra + rows_per_stage);
+        const uint32_t bytes = (uint32_t)(rb - ra) * (uint32_t)ldw * 8u;
+        mbar_arrive_expect_tx(&bar[buf], bytes);
+        tma_load_1d(wbuf + (size_t)buf * rows_per_stage * ldw, w + (size_t)ra * ldw, bytes, &bar[buf]);
+    };
+    if (threadIdx.x == 0) {
+        if (nst > 0) issue(0);
+        if (nst > 1) issue(1);
+    }
+
+    for (int st = 0; st < nst; ++st) {
+        const int buf = st & 1;
+        if (threadIdx.x == 0) *flag = mbar_wait_bounded(&bar[buf], (st >> 1) & 1) ? 1 : 0;
+        __syncthreads();
+        if (!*flag) {
+            if (threadIdx.x == 0) {
+                set_status(status, kStatusMbarTimeout);
+                if (st + 1 < nst) (void)mbar_wait_bounded(&bar[buf ^ 1], ((st + 1) >> 1) & 1);
+            }
+            return;
+        }
+        const double *wb = wbuf + (size_t)buf * rows_per_stage * ldw;
+        const int ra = r0 + st * rows_per_stage;
+        const int rb = min(r1, ra + rows_per_stage);
+        for (int r = ra; r < rb; ++r) {
+            const int b = r % (g.ny + 1);
+            const int c = r / (g.ny + 1);
+            const double Yb = g.ye[b], Zc = g.ze[c];
+            double dy[T], dz[T], y2[T], z2[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                dy[t] = Yb - ys[t];
+                dz[t] = Zc - zs[t];
+                y2[t] = dy[t] * dy[t];
+                z2[t] = dz[t] * dz[t];
+            }
+            const double *wr = wb + (size_t)(r - ra) * ldw;
+            for (int a = 0; a <= g.nx; ++a) {
+                const double wv = wr[a];
+                if (wv == 0.0) continue;
+                const double xa = Xs[a];
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const double dx = xa - xs[t];
+                    acc[t] = fma(wv, psi64(dx, dy[t], dz[t], dx * dx, y2[t], z2[t]), acc[t]);
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && st + 2 < nst) {
+            fence_proxy_async_smem();
+            issue(st + 2);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int64_t s = s_base + (int64_t)t * kFwdThreads;
+        if (s < g.N) part[(int64_t)blockIdx.y * g.N + s] = acc[t];
+    }
+}
+
+// out[i] = scale * sum_c part[c][i] + add_scale * add[i] + add2[i]  (fixed order)
+__global__ void k_reduce_rows(const double *__restrict__ part, int nchunk, int64_t n, double scale,
+                              const double *__restrict__ add, double add_scale,
+                              const double *__restrict__ add2, double *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < nchunk; ++c) s += part[(int64_t)c * n + i];
+        s *= scale;
+        if (add) s = fma(add_scale, add[i], s);
+        if (add2) s += add2[i];
+        out[i] = s;
+    }
+}
+
+// st4[s].w = r[s]
+__global__ void k_set_r(double4 *__restrict__ st4, const double *__restrict__ r, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        st4[i].w = r[i];
+}
+
+__global__ void k_init_st4(double4 *__restrict__ st4, const double *__restrict__ x, const double *__restrict__ y,
+                           const double *__restrict__ z, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        st4[i] = make_double4(x[i], y[i], z[i], 0.0);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint: u_n = sum_i Psi(n - s_i) r_i.  A warp owns TZ nodes of one node
+// column (a, b) at levels c0..c0+TZ-1; its 32 lanes split the stations of the
+// CTA's station chunk (staged in shared memory by TMA), each lane accumulates
+// its own stations, and a warp-shuffle butterfly reduces the 32 lane partials
+// per node at the end (fixed order: deterministic).
+// ---------------------------------------------------------------------------
+template <int TZ>
+__global__ void __launch_bounds__(kAdjWarps * 32) k_adj64(Geo g, const double4 *__restrict__ st4,
+                                                          int64_t schunk_len, double *__restrict__ upart,
+                                                          int64_t Nn, int *status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    int *flag = reinterpret_cast<int *>(smem_raw + 16);
+    double4 *sbuf = reinterpret_cast<double4 *>(smem_raw + 128);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ngz = (g.nz + 1 + TZ - 1) / TZ;
+    const int64_t ncolumns = (int64_t)(g.nx + 1) * (g.ny + 1);
+    const int64_t group = (int64_t)blockIdx.x * kAdjWarps + warp;
+    const bool gvalid = group < ncolumns * ngz;
+    const int64_t col = gvalid ? group / ngz : 0;
+    const int c0 = gvalid ? (int)(group % ngz) * TZ : 0;
+    const int a = (int)(col % (g.nx + 1));
+    const int b = (int)(col / (g.nx + 1));
+    const double Xa = g.xe[a], Yb = g.ye[b];
+    double Zt[TZ], acc[TZ];
+#pragma unroll
+    for (int t = 0; t < TZ; ++t) {
+        Zt[t] = g.ze[min(c0 + t, g.nz)];
+        acc[t] = 0.0;
+    }
+
+    const int64_t s0 = (int64_t)blockIdx.y * schunk_len;
+    const int64_t s1 = min(g.N, s0 + schunk_len);
+    const int nst = (s1 > s0) ? (int)((s1 - s0 + kAdjStage - 1) / kAdjStage) : 0;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int st) {
+        const int buf = st & 1;
+        const int64_t sa = s0 + (int64_t)st * kAdjStage;
+        const int cnt = (int)min((int64_t)kAdjStage, s1 - sa);
+        const uint32_t bytes = (uint32_t)cnt * 32u;
+        mbar_arrive_expect_tx(&bar[buf], bytes);
+        tma_load_1d(sbuf + buf * kAdjStage, st4 + sa, bytes, &bar[buf]);
+    };
+    if (threadIdx.x == 0) {
+        if (nst > 0) issue(0);
+        if (nst > 1) issue(1);
+    }
+    for (int st = 0; st < nst; ++st) {
+        const int buf = st & 1;
+        if (threadIdx.x == 0) *flag = mbar_wait_bounded(&bar[buf], (st >> 1) & 1) ? 1 : 0;
+        __syncthreads();
+        if (!*flag) {
+            if (threadIdx.x == 0) {
+                set_status(status, kStatusMbarTimeout);
+                if (st + 1 < nst) (void)mbar_wait_bounded(&bar[buf ^ 1], ((st + 1) >> 1) & 1);
+            }
+            return;
+        }
+        const int64_t sa = s0 + (int64_t)st * kAdjStage;
+        const int cnt = (int)min((int64_t)kAdjStage, s1 - sa);
+        const double4 *sb = sbuf + buf * kAdjStage;
+        if (gvalid) {
+            for (int k = lane; k < cnt; k += 32) {
+                const double4 S = sb[k];
+                if (S.w == 0.0) continue;
+                const double dx = Xa - S.x, dy = Yb - S.y;
+                const double x2 = dx * dx, y2 = dy * dy;
+#pragma unroll
+                for (int t = 0; t < TZ; ++t) {
+                    const double dz = Zt[t] - S.z;
+                    acc[t] = fma(S.w, psi64(dx, dy, dz, x2, y2, dz * dz), acc[t]);
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && st + 2 < nst) {
+            fence_proxy_async_smem();
+            issue(st + 2);
+        }
+    }
+    if (!gvalid) return;
+#pragma unroll
+    for (int t = 0; t < TZ; ++t) {
+        const double v = warp_sum(acc[t]);
+        if (lane == t % 32 && c0 + t <= g.nz)
+            upart[(int64_t)blockIdx.y * Nn + a + (int64_t)(g.nx + 1) * (b + (int64_t)(g.ny + 1) * (c0 + t))] = v;
+    }
+}
+
+// out[k] = scale * sum_{8 corners n of k} sigma(n,k) u_n  [* (zc_l + z0)^2]  [+ add[k]]
+__global__ void k_adj_finish(int nx, int ny, int nz, const double *__restrict__ u, double scale,
+                             const double *__restrict__ w2, const double *__restrict__ add,
+                             double *__restrict__ out) {
+    const int64_t M = (int64_t)nx * ny * nz;
+    const int64_t sx = 1, sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M; k += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k % nx);
+        const int j = (int)((k / nx) % ny);
+        const int l = (int)(k / ((int64_t)nx * ny));
+        const int64_t n0 = i + sy * j + sz * l;
+        // sigma = -(-1)^(da+db+dc)
+        const double v = -u[n0] + u[n0 + sx] + u[n0 + sy] - u[n0 + sx + sy] + u[n0 + sz] - u[n0 + sx + sz] -
+                         u[n0 + sy + sz] + u[n0 + sx + sy + sz];
+        double o = scale * v;
+        if (w2) o *= w2[l];
+        if (add) o += add[k];
+        out[k] = o;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// diag_i = sum_k G_ik^2 (zc_k + z0)^2 in FP64.  Thread = station; grid.y =
+// ranges of y-rows of cells.  Along x the right node column of one cell is the
+// left node column of the next, so each step evaluates Psi on 2 new node
+// columns (levels l0..l0+ZC) for ZC cells: 2(ZC+1)/ZC evaluations per cell.
+// ---------------------------------------------------------------------------
+template <int ZC>
+__global__ void __launch_bounds__(128) k_diag64(Geo g, const double *__restrict__ w2, int jrows,
+                                                const double *__restrict__ sx, const double *__restrict__ sy,
+                                                const double *__restrict__ sz, double *__restrict__ part) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.N) return;
+    const double xs = sx[s], ys = sy[s], zs = sz[s];
+    const int j0 = blockIdx.y * jrows;
+    const int j1 = min(g.ny, j0 + jrows);
+    double acc = 0.0;
+    for (int j = j0; j < j1; ++j) {
+        const double dy0 = g.ye[j] - ys, dy1 = g.ye[j + 1] - ys;
+        const double y20 = dy0 * dy0, y21 = dy1 * dy1;
+        for (int l0 = 0; l0 < g.nz; l0 += ZC) {
+            const int nl = min(ZC, g.nz - l0);
+            double dz[ZC + 1], z2[ZC + 1], w2l[ZC];
+#pragma unroll
+            for (int c = 0; c <= ZC; ++c) {
+                dz[c] = g.ze[l0 + min(c, nl)] - zs;
+                z2[c] = dz[c] * dz[c];
+            }
+#pragma unroll
+            for (int c = 0; c < ZC; ++c) w2l[c] = w2[l0 + min(c, nl - 1)];
+            double P0[ZC + 1], P1[ZC + 1];
+            {
+                const double dx = g.xe[0] - xs, x2 = dx * dx;
+#pragma unroll
+                for (int c = 0; c <= ZC; ++c) {
+                    P0[c] = (c <= nl) ? psi64(dx, dy0, dz[c], x2, y20, z2[c]) : 0.0;
+                    P1[c] = (c <= nl) ? psi64(dx, dy1, dz[c], x2, y21, z2[c]) : 0.0;
+                }
+            }
+            for (int i = 0; i < g.nx; ++i) {
+                const double dx = g.xe[i + 1] - xs, x2 = dx * dx;
+                double E[ZC + 1];
+#pragma unroll
+                for (int c = 0; c <= ZC; ++c) {
+                    double q0 = 0.0, q1 = 0.0;
+                    if (c <= nl) {
+                        q0 = psi64(dx, dy0, dz[c], x2, y20, z2[c]);
+                        q1 = psi64(dx, dy1, dz[c], x2, y21, z2[c]);
+                    }
+                    E[c] = P0[c] - q0 - P1[c] + q1;
+                    P0[c] = q0;
+                    P1[c] = q1;
+                }
+#pragma unroll
+                for (int c = 0; c < ZC; ++c) {
+                    if (c < nl) {
+                        const double G = kGammaMgal * (E[c + 1] - E[c]);
+                        acc = fma(G * G, w2l[c], acc);
+                    }
+                }
+            }
+        }
+    }
+    part[(int64_t)blockIdx.y * g.N + s] = acc;
+}
+
+inline int grid_for(int64_t n, int threads, int cap = 148 * 32) {
+    int64_t b = (n + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
+}
+
+Geo make_geo(const grav_plan *p) {
+    Geo g;
+    g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
+    g.xe = p->d_xe; g.ye = p->d_ye; g.ze = p->d_ze;
+    g.N = p->N;
+    return g;
+}
+
+int fwd_rows_per_stage(const grav_plan *p) {
+    // ~16 KB of node weights per stage
+    return std::max(1, std::min(p->f64_rows_per_chunk, (16384 / 8) / p->ldw));
+}
+
+}  // namespace
+
+size_t fwd64_smem_bytes(const grav_plan *p) {
+    return 128 + (size_t)p->ldw * 8 + 2ull * fwd_rows_per_stage(p) * p->ldw * 8;
+}
+
+void launch_node_weights(const grav_plan *p, const double *m, cudaStream_t s) {
+    const int64_t total = (int64_t)(p->ny + 1) * (p->nz + 1) * p->ldw;
+    k_node_weights<<<grid_for(total, 256), 256, 0, s>>>(p->nx, p->ny, p->nz, p->ldw, m, p->w);
+    note_launches(1);
+}
+
+void fp64_setup(grav_plan *p, cudaStream_t s) {
+    k_init_st4<<<grid_for(p->N, 256), 256, 0, s>>>(p->st4, p->sx, p->sy, p->sz, p->N);
+    cudaFuncSetAttribute(k_fwd64<kFwdT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+void launch_fwd64(const grav_plan *p, cudaStream_t s) {
+    const int tiles = (int)((p->N + kFwdThreads * kFwdT - 1) / (kFwdThreads * kFwdT));
+    dim3 grid(tiles, p->f64_nchunk);
+    const size_t smem = fwd64_smem_bytes(p);
+    stage_begin(p, kStageFwdMain, s);
+    k_fwd64<kFwdT><<<grid, kFwdThreads, smem, s>>>(make_geo(p), p->ldw, p->w, p->f64_rows_per_chunk,
+                                                   fwd_rows_per_stage(p), p->sx, p->sy, p->sz, p->part,
+                                                   p->ctx->d_status);
+    stage_end(p, kStageFwdMain, s);
+    note_launches(1);
+}
+
+void launch_reduce_rows(const double *part, int nchunk, int64_t n, double scale, const double *add,
+                        double add_scale, const double *add2, double *out, cudaStream_t s) {
+    k_reduce_rows<<<grid_for(n, 256), 256, 0, s>>>(part, nchunk, n, scale, add, add_scale, add2, out);
+    note_launches(1);
+}
+
+void launch_adj64(const grav_plan *p, const double *r, cudaStream_t s) {
+    k_set_r<<<grid_for(p->N, 256), 256, 0, s>>>(p->st4, r, p->N);
+    dim3 grid((p->a64_groups + kAdjWarps - 1) / kAdjWarps, p->a64_nschunk);
+    const size_t smem = 128 + 2ull * kAdjStage * sizeof(double4);
+    stage_begin(p, kStageAdjMain, s);
+    k_adj64<kAdjTZ><<<grid, kAdjWarps * 32, smem, s>>>(make_geo(p), p->st4, p->a64_schunk_len, p->upart,
+                                                       p->Nn, p->ctx->d_status);
+    stage_end(p, kStageAdjMain, s);
+    note_launches(2);
+    launch_reduce_rows(p->upart, p->a64_nschunk, p->Nn, 1.0, nullptr, 0.0, nullptr, p->u, s);
+}
+
+void launch_adj_finish(const grav_plan *p, const double *u, double scale, int depth_weighted,
+                       const double *add, double *out, cudaStream_t s) {
+    k_adj_finish<<<grid_for(p->M, 256), 256, 0, s>>>(p->nx, p->ny, p->nz, u, scale,
+                                                     depth_weighted ? p->d_w2 : nullptr, add, out);
+    note_launches(1);
+}
+
+void launch_diag64(const grav_plan *p, double *diag, cudaStream_t s) {
+    const int tiles = (int)((p->N + 127) / 128);
+    dim3 grid(tiles, p->f64_diag_nchunk);
+    k_diag64<kDiagZC><<<grid, 128, 0, s>>>(make_geo(p), p->d_w2, p->f64_diag_jrows, p->sx, p->sy, p->sz, p->part);
+    note_launches(1);
+    launch_reduce_rows(p->part, p->f64_diag_nchunk, p->N, 1.0, nullptr, 0.0, nullptr, diag, s);
+}
+
+}  // namespace grav

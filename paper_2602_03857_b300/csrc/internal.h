@@ -1,0 +1,191 @@
+// Internal host-side declarations of libgrav: context, plan, launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "grav.h"
+
+namespace grav {
+
+// Mesh-node lattice geometry handed to the FP64 kernels by value.
+struct Geo {
+    int nx, ny, nz;
+    const double *xe, *ye, *ze;   // device edges
+    int64_t N;                    // stations
+};
+
+// Layout of the FP32 far-field operator (GRAV_MIXED).
+struct MixedGeo {
+    int nx, ny, nz, nzp;          // nzp: nz rounded up to a multiple of 4
+    int ncol;                     // nx * ny
+    const float *cx;              // [nx][2] cell-centre x as (hi, lo) relative to x_ref
+    const float *cy;              // [ny][2]
+    const float *czc;             // [nzp] cell-centre depth (FP32), padded
+    int64_t N;
+};
+
+// Near-field box of GRAV_MIXED: per station, a bx x by x bz block of cells
+// starting at column (i0, j0) (depth layers 0..bz-1).
+struct NearGeo {
+    int bx, by, bz;
+    int slots;                    // bx * by * bz
+    double radius_cells;          // near_cells
+    int nbx, nby;                 // bin grid: i0 + (bx-1) in [0, nbx)
+};
+
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0, used = 0;
+    bool overflow = false;
+    void *take(size_t bytes) {
+        size_t off = (used + 255) & ~size_t(255);
+        if (!base || off + bytes > size) {
+            overflow = true;
+            return nullptr;
+        }
+        used = off + bytes;
+        return base + off;
+    }
+};
+
+}  // namespace grav
+
+struct grav_ctx {
+    int device = 0;
+    size_t hbm_budget = 0;
+    std::atomic<size_t> hbm_used{0};
+    cudaMemPool_t pool = nullptr;
+    int *d_status = nullptr;       // device status word
+    int *h_status = nullptr;       // pinned mirror
+    std::mutex err_mu;
+    std::string last_error;
+    int sm_count = 148;
+    void *serve = nullptr;         // serving scheduler (serve.cpp)
+};
+
+namespace grav {
+// Stages whose device time a plan can record with CUDA events.
+enum Stage : int { kStageFwdMain = 0, kStageAdjMain = 1, kStageFwdNear = 2, kStageAdjNear = 3, kStageCount = 4 };
+struct StageTimer {
+    bool enabled = false;
+    std::vector<cudaEvent_t> pool;         // pairs (start, stop)
+    std::vector<int> stage_of;             // per used pair
+    int used = 0;
+    double ms[kStageCount] = {0, 0, 0, 0};
+    int64_t count[kStageCount] = {0, 0, 0, 0};
+};
+}  // namespace grav
+
+struct grav_plan {
+    grav_ctx *ctx = nullptr;
+    mutable grav::StageTimer timer;
+    grav_options opt{};
+    int nx = 0, ny = 0, nz = 0;
+    int64_t N = 0, M = 0, Nn = 0;
+    std::vector<double> xe, ye, ze;       // host copies
+    bool cubic = false;
+    grav::Arena arena;
+    size_t bytes = 0;
+
+    // common device data
+    double *d_xe = nullptr, *d_ye = nullptr, *d_ze = nullptr;
+    double *d_w2 = nullptr;               // [nz] (zc + z0)^2
+    const double *sx = nullptr, *sy = nullptr, *sz = nullptr;   // caller's survey arrays
+
+    // FP64 path
+    int ldw = 0;                          // padded node-row length (nx+1 rounded to even)
+    int f64_rows_per_chunk = 0, f64_nchunk = 0;
+    int a64_groups = 0, a64_nschunk = 0, a64_schunk_len = 0;
+    int f64_diag_jrows = 0, f64_diag_nchunk = 0;
+    double *w = nullptr;                  // node weights [(ny+1)(nz+1)][ldw]
+    double *part = nullptr;               // forward partials [nchunk][N]
+    double4 *st4 = nullptr;               // stations (x, y, z, r)
+    double *upart = nullptr;              // adjoint partials [nschunk][Nn]
+    double *u = nullptr;                  // [Nn]
+
+    // mixed path
+    grav::MixedGeo mg{};
+    grav::NearGeo ng{};
+    float *m_cx = nullptr, *m_cy = nullptr, *m_czc = nullptr;
+    float *qT = nullptr;                  // [ncol][nzp] gamma*1e5*V*rho (FP32)
+    float *m_w2f = nullptr;               // [nzp] (zc + z0)^2 in FP32
+    float4 *st32 = nullptr;               // stations (xh, xl, yh, yl)
+    float2 *stz = nullptr;                // stations (z, r)
+    int m_fwd_cols_per_chunk = 0, m_fwd_nchunk = 0;
+    int m_adj_tz = 0, m_adj_ngz = 0, m_adj_nschunk = 0, m_adj_schunk_len = 0;
+    double *m_part = nullptr;             // [nchunk][N] forward partials (hi+lo in FP64)
+    double *m_apart = nullptr;            // [nschunk][M] adjoint partials
+    double *dG = nullptr;                 // [N][slots] near-field correction (mGal per kg/m^3)
+    int *st_i0 = nullptr, *st_j0 = nullptr;   // box origin per station
+    double *diag_corr = nullptr;          // [N] near-field correction of diag(G W^-2 G^T)
+    int *bin_start = nullptr;             // [nbins+1]
+    int *bin_st = nullptr;                // [N] station indices sorted by bin
+    double *near_corr = nullptr;          // [N] forward near-field correction scratch
+    double *m_cellacc = nullptr;          // [M] adjoint scratch
+
+    // CG / diag scratch
+    double *diag = nullptr;               // [N]
+    double *vec = nullptr;                // CG vectors
+    double *scal = nullptr;               // device scalars
+};
+
+namespace grav {
+
+// error helpers (api.cu)
+int set_error(grav_ctx *ctx, int code, const char *fmt, ...);
+int cuda_error(grav_ctx *ctx, cudaError_t e, const char *what);
+
+// plan internals (api.cu), used by the solver and the serving scheduler
+int plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const grav_options &o,
+                grav_plan **out, cudaStream_t s);
+void plan_destroy(grav_plan *p, cudaStream_t s);
+int plan_forward_ex(grav_plan *p, const double *m, double *d, const double *add, double add_scale, cudaStream_t s);
+int plan_adjoint_ex(grav_plan *p, const double *r, double *out, int depth_weighted, const double *add,
+                    cudaStream_t s);
+int plan_diag(grav_plan *p, double *diag, cudaStream_t s);
+int read_status(grav_ctx *ctx, cudaStream_t s, double timeout_s);
+int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_out, double *y_out,
+                  grav_solve_info *info, cudaStream_t s, const std::atomic<int> *cancel);
+
+// serving scheduler (serve.cpp)
+void serve_shutdown(grav_ctx *ctx);
+
+// kernel-launch accounting and stage timing (api.cu)
+void note_launches(int n);
+void stage_begin(const grav_plan *p, int stage, cudaStream_t s);
+void stage_end(const grav_plan *p, int stage, cudaStream_t s);
+
+// FP64 launchers (fp64_kernels.cu)
+void fp64_setup(grav_plan *p, cudaStream_t s);
+void launch_node_weights(const grav_plan *p, const double *m, cudaStream_t s);
+void launch_fwd64(const grav_plan *p, cudaStream_t s);
+void launch_reduce_rows(const double *part, int nchunk, int64_t n, double scale, const double *add,
+                        double add_scale, const double *add2, double *out, cudaStream_t s);
+void launch_adj64(const grav_plan *p, const double *r, cudaStream_t s);
+void launch_adj_finish(const grav_plan *p, const double *u, double scale, int depth_weighted,
+                       const double *add, double *out, cudaStream_t s);
+void launch_diag64(const grav_plan *p, double *diag, cudaStream_t s);
+size_t fwd64_smem_bytes(const grav_plan *p);
+
+// mixed launchers (mixed_kernels.cu)
+int mixed_setup(grav_plan *p, cudaStream_t s);   // 0 or a GRAV_E* code
+int near_setup_warps(const grav_plan *p);         // 0: window too large for shared memory
+void launch_mixed_prep_q(const grav_plan *p, const double *m, cudaStream_t s);
+void launch_mixed_fwd(const grav_plan *p, cudaStream_t s);
+void launch_mixed_near_fwd(const grav_plan *p, const double *m, cudaStream_t s);
+void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s);
+void launch_mixed_adj_finish(const grav_plan *p, const double *r, int depth_weighted, const double *add,
+                             double *out, cudaStream_t s);
+void launch_mixed_diag(const grav_plan *p, double *diag, cudaStream_t s);
+size_t mixed_scratch_bytes(const grav_plan *p);
+
+// vector kernels (cg_kernels.cu)
+void launch_dot(const double *a, const double *b, int64_t n, double *partials, double *out, cudaStream_t s);
+constexpr int kDotBlocks = 296;
+
+}  // namespace grav

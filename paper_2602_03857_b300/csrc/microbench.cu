@@ -1,0 +1,123 @@
+// Pipe-rate microbenchmarks: throughput of the MUFU reciprocal square root
+// and base-2 logarithm, FP32 FMA and FP64 FMA on this device, plus the SM
+// clock seen while they run.  They give the per-clock unit rates behind the
+// ALU rooflines of the operator kernels.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace grav {
+namespace {
+
+constexpr int kChains = 8;
+
+__device__ __forceinline__ float lg2_approx(float x) {
+    float r;
+    asm volatile("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float rsqrt_v(float x) {
+    float r;
+    asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// op: 0 rsqrt, 1 lg2, 2 ffma, 3 dfma
+template <int OP>
+__global__ void k_pipe(int iters, float seed, float *out, unsigned long long *clk) {
+    const uint64_t t0 = globaltimer_ns();
+    const long long c0 = clock64();
+    if (OP == 3) {
+        double a[kChains];
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) a[k] = seed + 0.001 * (threadIdx.x + k);
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int k = 0; k < kChains; ++k) a[k] = fma(a[k], 0.999999, 1e-7);
+        }
+        double s = 0;
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) s += a[k];
+        if (s == 12345.678) out[0] = (float)s;
+    } else {
+        float a[kChains];
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) a[k] = seed + 0.001f * (threadIdx.x + k);
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int k = 0; k < kChains; ++k) {
+                if (OP == 0) a[k] = rsqrt_v(a[k]);
+                else if (OP == 1) a[k] = lg2_approx(a[k] + 2.0f);
+                else a[k] = fmaf(a[k], 0.999999f, 1e-7f);
+            }
+        }
+        float s = 0;
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) s += a[k];
+        if (s == 12345.678f) out[0] = s;
+    }
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const long long c1 = clock64();
+        const uint64_t t1 = globaltimer_ns();
+        clk[0] = (unsigned long long)(c1 - c0);
+        clk[1] = (unsigned long long)(t1 - t0);
+    }
+}
+
+template <int OP>
+int run_one(int sms, double *ops_per_s, double *clk_mhz) {
+    float *out = nullptr;
+    unsigned long long *clk = nullptr;
+    if (cudaMalloc(&out, 16) != cudaSuccess) return -1;
+    if (cudaMalloc(&clk, 16) != cudaSuccess) return -1;
+    const int blocks = sms * 8, threads = 256;
+    const int iters = (OP == 3) ? 256 : 4096;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_pipe<OP><<<blocks, threads>>>(iters / 16, 1.5f, out, clk);   // warm-up
+    cudaEventRecord(e0);
+    k_pipe<OP><<<blocks, threads>>>(iters, 1.5f, out, clk);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    unsigned long long h[2] = {0, 0};
+    cudaMemcpy(h, clk, 16, cudaMemcpyDeviceToHost);
+    *ops_per_s = (double)blocks * threads * iters * kChains / (ms * 1e-3);
+    *clk_mhz = h[1] ? (double)h[0] / (double)h[1] * 1e3 : 0.0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    cudaFree(clk);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+}  // namespace grav
+
+extern "C" int grav_bench_pipes(int device, double *out) {
+    using namespace grav;
+    if (!out) return set_error(nullptr, GRAV_EINVAL, "out is NULL");
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n)
+        return set_error(nullptr, GRAV_EINVAL, "bad device");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    int rc = 0;
+    rc |= run_one<0>(sms, &out[0], &out[1]);
+    rc |= run_one<1>(sms, &out[2], &out[3]);
+    rc |= run_one<2>(sms, &out[4], &out[5]);
+    rc |= run_one<3>(sms, &out[6], &out[7]);
+    out[8] = sms;
+    cudaSetDevice(prev);
+    return rc ? set_error(nullptr, GRAV_EDEVICE, "pipe microbenchmark failed") : GRAV_OK;
+}

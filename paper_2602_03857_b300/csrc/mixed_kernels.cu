@@ -1,0 +1,783 @@
+// Mixed-precision prism-gravity operator (GRAV_MIXED), cubic cells.
+//
+// Far field (every cell, FP32): a uniform cube attracts like a point mass
+// at its centre up to a relative error O((a/R)^4) (its quadrupole moment
+// vanishes), so G_ik ~ gamma V dz / R^3.  One MUFU reciprocal square root
+// per (station, cell) pair; per-column FP32 sums are folded into a (hi, lo)
+// pair by Knuth's two-sum (compensated accumulation), partials are combined
+// in FP64 in a fixed order.
+//
+// Near field (FP64): for every station, the cells whose centre lies within
+// near_cells cell widths get the correction dG = G_exact - G_far, where
+// G_exact is Eq. 1 evaluated in FP64 with the corner function shared across
+// the nodes of the station's window box.  dG is built once per plan and
+// applied on every product (forward: per-station row sums; adjoint: a
+// deterministic per-cell gather over stations binned by box origin).
+#include <algorithm>
+#include <cmath>
+#include <cub/device/device_radix_sort.cuh>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace grav {
+
+namespace {
+
+constexpr int kMfThreads = 128;
+constexpr int kMfT = 8;              // stations per thread (far forward)
+constexpr int kMaWarps = 8;          // warps per CTA (far adjoint)
+constexpr int kMaStage = 512;        // stations per TMA stage (far adjoint)
+constexpr int kNsWarps = 8;          // warps per CTA (near set-up)
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct MfwdSmem {
+    size_t cx, cy, cz, q, total;
+};
+__host__ __device__ MfwdSmem mfwd_layout(const MixedGeo &g, int cols_per_stage) {
+    MfwdSmem L;
+    L.cx = 128;
+    L.cy = L.cx + 8ull * g.nx;
+    L.cz = align_up(L.cy + 8ull * g.ny, 16);
+    L.q = align_up(L.cz + 4ull * g.nzp, 128);
+    L.total = L.q + 2ull * cols_per_stage * g.nzp * 4;
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// qT[col][l] = gamma*1e5*V * m[i + nx*(j + ny*l)], col = i + nx*j; l >= nz: 0.
+// ---------------------------------------------------------------------------
+__global__ void k_prep_q(MixedGeo g, const double *__restrict__ m, float scale, float *__restrict__ qT) {
+    const int64_t total = (int64_t)g.ncol * g.nzp;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(t % g.nzp);
+        const int64_t col = t / g.nzp;
+        qT[t] = (l < g.nz) ? (float)(scale * m[col + (int64_t)g.ncol * l]) : 0.0f;
+    }
+}
+
+// stations: st32 = (xh, xl, yh, yl) of (x - xref, y - yref); stz = (z, r)
+__global__ void k_prep_stations(const double *__restrict__ x, const double *__restrict__ y,
+                                const double *__restrict__ z, int64_t n, double xref, double yref,
+                                float4 *__restrict__ st32, float2 *__restrict__ stz) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double xr = x[i] - xref, yr = y[i] - yref;
+        const float xh = (float)xr, yh = (float)yr;
+        st32[i] = make_float4(xh, (float)(xr - (double)xh), yh, (float)(yr - (double)yh));
+        stz[i] = make_float2((float)z[i], 0.0f);
+    }
+}
+
+__global__ void k_set_rz(float2 *__restrict__ stz, const double *__restrict__ r, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        stz[i].y = (float)r[i];
+}
+
+// The far-field geometry of one (station, cell) pair exactly as every mixed
+// kernel computes it (same FP32 operations in the same order).
+__device__ __forceinline__ float far_h2(float2 X, float2 Y, float xh, float xl, float yh, float yl) {
+    const float dx = (X.x - xh) + (X.y - xl);
+    const float dy = (Y.x - yh) + (Y.y - yl);
+    return fmaf(dx, dx, dy * dy);
+}
+
+// ---------------------------------------------------------------------------
+// Far-field forward.  CTA = (station tile of kMfThreads*T stations, chunk of
+// columns).  Column densities qT stream through shared memory by TMA bulk
+// copies (double-buffered); stations (hi/lo coordinates, accumulators) stay
+// in registers; the inner loop reads 4 layers of q and depth per LDS.128
+// (broadcast) and issues per pair: FADD, FFMA, MUFU.RSQ, 3 FMUL, FFMA.
+// ---------------------------------------------------------------------------
+template <int T>
+__global__ void __launch_bounds__(kMfThreads) k_mfwd(MixedGeo g, const float *__restrict__ qT,
+                                                     const float4 *__restrict__ st32,
+                                                     const float2 *__restrict__ stz, int cols_per_chunk,
+                                                     int cols_per_stage, double *__restrict__ part,
+                                                     int *status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const MfwdSmem L = mfwd_layout(g, cols_per_stage);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    int *flag = reinterpret_cast<int *>(smem_raw + 16);
+    float2 *cxs = reinterpret_cast<float2 *>(smem_raw + L.cx);
+    float2 *cys = reinterpret_cast<float2 *>(smem_raw + L.cy);
+    float *czs = reinterpret_cast<float *>(smem_raw + L.cz);
+    float *qbuf = reinterpret_cast<float *>(smem_raw + L.q);
+
+    const int c0 = blockIdx.y * cols_per_chunk;
+    const int c1 = min(g.ncol, c0 + cols_per_chunk);
+    const int nst = (c1 > c0) ? (c1 - c0 + cols_per_stage - 1) / cols_per_stage : 0;
+
+    const int64_t s_base = (int64_t)blockIdx.x * (kMfThreads * T) + threadIdx.x;
+    float xh[T], xl[T], yh[T], yl[T], zs[T], hi[T], lo[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int64_t s = s_base + (int64_t)t * kMfThreads;
+        const bool ok = s < g.N;
+        const float4 P = ok ? st32[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+        xh[t] = P.x; xl[t] = P.y; yh[t] = P.z; yl[t] = P.w;
+        zs[t] = ok ? stz[s].x : -1.0f;
+        hi[t] = 0.f; lo[t] = 0.f;
+    }
+    for (int i = threadIdx.x; i < g.nx; i += kMfThreads) cxs[i] = make_float2(g.cx[2 * i], g.cx[2 * i + 1]);
+    for (int j = threadIdx.x; j < g.ny; j += kMfThreads) cys[j] = make_float2(g.cy[2 * j], g.cy[2 * j + 1]);
+    for (int l = threadIdx.x; l < g.nzp; l += kMfThreads) czs[l] = g.czc[l];
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int st) {
+        const int buf = st & 1;
+        const int ca = c0 + st * cols_per_stage;
+        const int cb = min(c1, ca + cols_per_stage);
+        const uint32_t bytes = (uint32_t)(cb - ca) * (uint32_t)g.nzp * 4u;
+        mbar_arrive_expect_tx(&bar[buf], bytes);
+        tma_load_1d(qbuf + (size_t)buf * cols_per_stage * g.nzp, qT + (size_t)ca * g.nzp, bytes, &bar[buf]);
+    };
+    if (threadIdx.x == 0) {
+        if (nst > 0) issue(0);
+        if (nst > 1) issue(1);
+    }
+    const int nl4 = g.nzp >> 2;
+    for (int st = 0; st < nst; ++st) {
+        const int buf = st & 1;
+        if (threadIdx.x == 0) *flag = mbar_wait_bounded(&bar[buf], (st >> 1) & 1) ? 1 : 0;
+        __syncthreads();
+        if (!*flag) {
+            if (threadIdx.x == 0) {
+                set_status(status, kStatusMbarTimeout);
+                if (st + 1 < nst) (void)mbar_wait_bounded(&bar[buf ^ 1], ((st + 1) >> 1) & 1);
+            }
+            return;
+        }
+        const int ca = c0 + st * cols_per_stage;
+        const int cb = min(c1, ca + cols_per_stage);
+        const float *qb = qbuf + (size_t)buf * cols_per_stage * g.nzp;
+        for (int col = ca; col < cb; ++col) {
+            const int i = col % g.nx, j = col / g.nx;
+            const float2 X = cxs[i], Y = cys[j];
+            float h2[T], cs[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                h2[t] = far_h2(X, Y, xh[t], xl[t], yh[t], yl[t]);
+                cs[t] = 0.f;
+            }
+            const float4 *q4 = reinterpret_cast<const float4 *>(qb + (size_t)(col - ca) * g.nzp);
+            const float4 *z4 = reinterpret_cast<const float4 *>(czs);
+            for (int l4 = 0; l4 < nl4; ++l4) {
+                const float4 q = q4[l4], z = z4[l4];
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    float dz, R2;
+                    dz = z.x - zs[t]; R2 = fmaf(dz, dz, h2[t]); cs[t] = fmaf(q.x, far_kernel(dz, R2), cs[t]);
+                    dz = z.y - zs[t]; R2 = fmaf(dz, dz, h2[t]); cs[t] = fmaf(q.y, far_kernel(dz, R2), cs[t]);
+                    dz = z.z - zs[t]; R2 = fmaf(dz, dz, h2[t]); cs[t] = fmaf(q.z, far_kernel(dz, R2), cs[t]);
+                    dz = z.w - zs[t]; R2 = fmaf(dz, dz, h2[t]); cs[t] = fmaf(q.w, far_kernel(dz, R2), cs[t]);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                float s, e;
+                two_sum(hi[t], cs[t], s, e);
+                hi[t] = s;
+                lo[t] += e;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && st + 2 < nst) {
+            fence_proxy_async_smem();
+            issue(st + 2);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int64_t s = s_base + (int64_t)t * kMfThreads;
+        if (s < g.N) part[(int64_t)blockIdx.y * g.N + s] = (double)hi[t] + (double)lo[t];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Far-field adjoint: acc_k = sum_i r_i dz/R^3.  A warp owns TZ cells of one
+// column (layers lg*TZ ...); its lanes split the stations of the CTA's chunk
+// (x/y hi-lo and (z, r) staged in shared memory by two TMA bulk copies per
+// stage).  Each lane sums its stations of one stage in FP32, folds that stage
+// sum into (hi, lo) by two-sum, and at the end the 32 lane values are reduced
+// by a warp-shuffle butterfly in FP64 (fixed order: deterministic).
+// ---------------------------------------------------------------------------
+template <int TZ>
+__global__ void __launch_bounds__(kMaWarps * 32) k_madj(MixedGeo g, const float4 *__restrict__ st32,
+                                                        const float2 *__restrict__ stz, int ngz,
+                                                        int64_t schunk_len, double *__restrict__ apart,
+                                                        int *status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    int *flag = reinterpret_cast<int *>(smem_raw + 16);
+    float4 *sxy = reinterpret_cast<float4 *>(smem_raw + 128);
+    float2 *szr = reinterpret_cast<float2 *>(smem_raw + 128 + 2 * kMaStage * sizeof(float4));
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t group = (int64_t)blockIdx.x * kMaWarps + warp;
+    const bool gvalid = group < (int64_t)g.ncol * ngz;
+    const int col = gvalid ? (int)(group / ngz) : 0;
+    const int l0 = gvalid ? (int)(group % ngz) * TZ : 0;
+    const int i = col % g.nx, j = col / g.nx;
+    const float2 X = make_float2(g.cx[2 * i], g.cx[2 * i + 1]);
+    const float2 Y = make_float2(g.cy[2 * j], g.cy[2 * j + 1]);
+    float zc[TZ], hi[TZ], lo[TZ];
+#pragma unroll
+    for (int t = 0; t < TZ; ++t) {
+        zc[t] = g.czc[min(l0 + t, g.nzp - 1)];
+        hi[t] = 0.f; lo[t] = 0.f;
+    }
+    const int64_t s0 = (int64_t)blockIdx.y * schunk_len;
+    const int64_t s1 = min(g.N, s0 + schunk_len);
+    const int nst = (s1 > s0) ? (int)((s1 - s0 + kMaStage - 1) / kMaStage) : 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int st) {
+        const int buf = st & 1;
+        const int64_t sa = s0 + (int64_t)st * kMaStage;
+        const int cnt = (int)min((int64_t)kMaStage, s1 - sa);
+        const uint32_t b1 = (uint32_t)cnt * 16u;
+        const uint32_t b2 = (uint32_t)((cnt * 8 + 15) / 16 * 16);
+        mbar_arrive_expect_tx(&bar[buf], b1 + b2);
+        tma_load_1d(sxy + buf * kMaStage, st32 + sa, b1, &bar[buf]);
+        tma_load_1d(szr + buf * kMaStage, stz + sa, b2, &bar[buf]);
+    };
+    if (threadIdx.x == 0) {
+        if (nst > 0) issue(0);
+        if (nst > 1) issue(1);
+    }
+    for (int st = 0; st < nst; ++st) {
+        const int buf = st & 1;
+        if (threadIdx.x == 0) *flag = mbar_wait_bounded(&bar[buf], (st >> 1) & 1) ? 1 : 0;
+        __syncthreads();
+        if (!*flag) {
+            if (threadIdx.x == 0) {
+                set_status(status, kStatusMbarTimeout);
+                if (st + 1 < nst) (void)mbar_wait_bounded(&bar[buf ^ 1], ((st + 1) >> 1) & 1);
+            }
+            return;
+        }
+        const int64_t sa = s0 + (int64_t)st * kMaStage;
+        const int cnt = (int)min((int64_t)kMaStage, s1 - sa);
+        const float4 *pb = sxy + buf * kMaStage;
+        const float2 *zb = szr + buf * kMaStage;
+        if (gvalid) {
+            float cs[TZ];
+#pragma unroll
+            for (int t = 0; t < TZ; ++t) cs[t] = 0.f;
+            for (int k = lane; k < cnt; k += 32) {
+                const float4 P = pb[k];
+                const float2 Z = zb[k];
+                const float h2 = far_h2(X, Y, P.x, P.y, P.z, P.w);
+#pragma unroll
+                for (int t = 0; t < TZ; ++t) {
+                    const float dz = zc[t] - Z.x;
+                    const float R2 = fmaf(dz, dz, h2);
+                    cs[t] = fmaf(Z.y, far_kernel(dz, R2), cs[t]);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < TZ; ++t) {
+                float s, e;
+                two_sum(hi[t], cs[t], s, e);
+                hi[t] = s;
+                lo[t] += e;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && st + 2 < nst) {
+            fence_proxy_async_smem();
+            issue(st + 2);
+        }
+    }
+    if (!gvalid) return;
+#pragma unroll
+    for (int t = 0; t < TZ; ++t) {
+        const double v = warp_sum((double)hi[t] + (double)lo[t]);
+        if (lane == t % 32 && l0 + t < g.nz)
+            apart[(int64_t)blockIdx.y * g.ncol * (int64_t)g.nz + col + (int64_t)g.ncol * (l0 + t)] = v;
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Near-field set-up: warp per station.  Psi on the (bx+1)(by+1)(bz+1) nodes
+// of the station's window box (FP64, each node evaluated once), then per box
+// cell: dG = G_exact - G_far when the cell centre lies within the window
+// radius, else 0.  Also returns the near-field part of diag(G W^-2 G^T),
+// sum w2 (G_exact^2 - G_far^2), the box origin and the station's bin key.
+// The mesh is uniform cubic: x edges x0 + i a, y edges y0 + j a.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
+    Geo g, MixedGeo mg, NearGeo ng, double x0, double y0, double a, double vol_mgal,
+    const double *__restrict__ sx, const double *__restrict__ sy, const double *__restrict__ sz,
+    const double *__restrict__ w2, const float4 *__restrict__ st32, const float2 *__restrict__ stz,
+    double *__restrict__ dG, int *__restrict__ st_i0, int *__restrict__ st_j0, double *__restrict__ diag_corr,
+    unsigned *__restrict__ keys, int *__restrict__ vals, unsigned key_sentinel) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nbx1 = ng.bx + 1, nby1 = ng.by + 1;
+    const int nnode = nbx1 * nby1 * (ng.bz + 1);
+    double *P = reinterpret_cast<double *>(smem_raw) + (size_t)warp * nnode;
+    const int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (s >= g.N) return;   // warp-uniform
+    const double xs = sx[s], ys = sy[s], zs = sz[s];
+    const double lim = 1.0e9;
+    const double fx = fmin(fmax((xs - x0) / a - 0.5 - ng.radius_cells, -lim), lim);
+    const double fy = fmin(fmax((ys - y0) / a - 0.5 - ng.radius_cells, -lim), lim);
+    const int i0 = (int)floor(fx) + 1;
+    const int j0 = (int)floor(fy) + 1;
+    for (int t = lane; t < nnode; t += 32) {
+        const int ia = i0 + t % nbx1;
+        const int jb = j0 + (t / nbx1) % nby1;
+        const int c = t / (nbx1 * nby1);
+        double v = 0.0;
+        if (ia >= 0 && ia <= g.nx && jb >= 0 && jb <= g.ny && c <= g.nz) {
+            const double x = g.xe[ia] - xs, y = g.ye[jb] - ys, z = g.ze[c] - zs;
+            v = psi64(x, y, z, x * x, y * y, z * z);
+        }
+        P[t] = v;
+    }
+    __syncwarp();
+    const float4 S = st32[s];
+    const float zf = stz[s].x;
+    const double r2max = (ng.radius_cells * a) * (ng.radius_cells * a);
+    const int sxs = 1, sys = nbx1, szs = nbx1 * nby1;
+    double dcorr = 0.0;
+    for (int t = lane; t < ng.slots; t += 32) {
+        const int ai = t % ng.bx;
+        const int bj = (t / ng.bx) % ng.by;
+        const int l = t / (ng.bx * ng.by);
+        const int i = i0 + ai, j = j0 + bj;
+        double val = 0.0;
+        if (i >= 0 && i < g.nx && j >= 0 && j < g.ny && l < g.nz) {
+            const double xc = 0.5 * (g.xe[i] + g.xe[i + 1]) - xs;
+            const double yc = 0.5 * (g.ye[j] + g.ye[j + 1]) - ys;
+            const double zc = 0.5 * (g.ze[l] + g.ze[l + 1]) - zs;
+            if (xc * xc + yc * yc + zc * zc < r2max) {
+                const int n0 = ai + sys * bj + szs * l;
+                // sigma(n, k) = -(-1)^(da+db+dc) for the vertex (i+da, j+db, l+dc)
+                const double E = -P[n0] + P[n0 + sxs] + P[n0 + sys] - P[n0 + sxs + sys] + P[n0 + szs] -
+                                 P[n0 + sxs + szs] - P[n0 + sys + szs] + P[n0 + sxs + sys + szs];
+                const double gex = kGammaMgal * E;
+                const float2 X = make_float2(mg.cx[2 * i], mg.cx[2 * i + 1]);
+                const float2 Y = make_float2(mg.cy[2 * j], mg.cy[2 * j + 1]);
+                const float h2 = far_h2(X, Y, S.x, S.y, S.z, S.w);
+                const float dz = mg.czc[l] - zf;
+                const float R2 = fmaf(dz, dz, h2);
+                const double gfar = vol_mgal * (double)far_kernel(dz, R2);
+                val = gex - gfar;
+                dcorr += w2[l] * (gex * gex - gfar * gfar);
+            }
+        }
+        dG[s * ng.slots + t] = val;
+    }
+    dcorr = warp_sum(dcorr);
+    if (lane == 0) {
+        diag_corr[s] = dcorr;
+        st_i0[s] = i0;
+        st_j0[s] = j0;
+        const bool hit = (i0 <= g.nx - 1) && (i0 + ng.bx - 1 >= 0) && (j0 <= g.ny - 1) && (j0 + ng.by - 1 >= 0);
+        keys[s] = hit ? (unsigned)((i0 + ng.bx - 1) + ng.nbx * (j0 + ng.by - 1)) : key_sentinel;
+        vals[s] = (int)s;
+    }
+}
+
+// bin_start[b] = first position p with key_sorted[p] >= b, b in [0, nbins]
+__global__ void k_bin_bounds(const unsigned *__restrict__ ks, int64_t n, int nbins, int *__restrict__ bin_start) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= nbins; b += gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (ks[mid] < (unsigned)b) lo = mid + 1; else hi = mid;
+        }
+        bin_start[b] = (int)lo;
+    }
+}
+
+// corr[s] = sum_slots dG[s][slot] * m[cell(s, slot)]   (warp per station)
+__global__ void k_near_fwd(int nx, int ny, int nz, NearGeo ng, int64_t N, const double *__restrict__ dG,
+                           const int *__restrict__ st_i0, const int *__restrict__ st_j0,
+                           const double *__restrict__ m, double *__restrict__ corr) {
+    const int lane = threadIdx.x & 31;
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= N) return;
+    const int i0 = st_i0[s], j0 = st_j0[s];
+    double acc = 0.0;
+    for (int t = lane; t < ng.slots; t += 32) {
+        const int i = i0 + t % ng.bx;
+        const int j = j0 + (t / ng.bx) % ng.by;
+        const int l = t / (ng.bx * ng.by);
+        if (i >= 0 && i < nx && j >= 0 && j < ny && l < nz)
+            acc = fma(dG[s * ng.slots + t], m[i + (int64_t)nx * (j + (int64_t)ny * l)], acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) corr[s] = acc;
+}
+
+// out[k] = sum over stations whose window box holds cell k of dG * r, for the
+// top bz layers; bins visited in fixed order, stations sorted within a bin.
+__global__ void k_near_adj(int nx, int ny, int nz, NearGeo ng, const double *__restrict__ dG,
+                           const int *__restrict__ bin_start, const int *__restrict__ bin_st,
+                           const double *__restrict__ r, double *__restrict__ out) {
+    const int lz = min(ng.bz, nz);
+    const int64_t total = (int64_t)nx * ny * lz;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k % nx);
+        const int j = (int)((k / nx) % ny);
+        const int l = (int)(k / ((int64_t)nx * ny));
+        double acc = 0.0;
+        for (int bj = j - ng.by + 1; bj <= j; ++bj) {
+            for (int bi = i - ng.bx + 1; bi <= i; ++bi) {
+                const int key = (bi + ng.bx - 1) + ng.nbx * (bj + ng.by - 1);
+                const int p1 = bin_start[key + 1];
+                const int slot = (i - bi) + ng.bx * ((j - bj) + ng.by * l);
+                for (int p = bin_start[key]; p < p1; ++p) {
+                    const int s = bin_st[p];
+                    acc = fma(dG[(int64_t)s * ng.slots + slot], r[s], acc);
+                }
+            }
+        }
+        out[k] = acc;
+    }
+}
+
+// out[k] = (vol * sum_c apart[c][k] + near[k] (top bz layers)) [* w2_l] [+ add[k]]
+__global__ void k_madj_finish(int nx, int ny, int nz, int bz, const double *__restrict__ apart, int nschunk,
+                              double vol, const double *__restrict__ near, const double *__restrict__ w2,
+                              const double *__restrict__ add, double *__restrict__ out) {
+    const int64_t M = (int64_t)nx * ny * nz;
+    const int64_t plane = (int64_t)nx * ny;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M; k += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(k / plane);
+        double s = 0.0;
+        for (int c = 0; c < nschunk; ++c) s += apart[(int64_t)c * M + k];
+        s *= vol;
+        if (l < bz) s += near[k];
+        if (w2) s *= w2[l];
+        if (add) s += add[k];
+        out[k] = s;
+    }
+}
+
+// Far-field part of diag(G W^-2 G^T): sum_k w2_l (dz/R^3)^2 per station
+// (times vol^2 later); thread = T stations, grid.y = column chunks.
+template <int T>
+__global__ void __launch_bounds__(kMfThreads) k_mdiag(MixedGeo g, const float *__restrict__ w2f,
+                                                      const float4 *__restrict__ st32,
+                                                      const float2 *__restrict__ stz, int cols_per_chunk,
+                                                      double *__restrict__ part) {
+    const int64_t s_base = (int64_t)blockIdx.x * (kMfThreads * T) + threadIdx.x;
+    float xh[T], xl[T], yh[T], yl[T], zs[T], hi[T], lo[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int64_t s = s_base + (int64_t)t * kMfThreads;
+        const bool ok = s < g.N;
+        const float4 P = ok ? st32[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+        xh[t] = P.x; xl[t] = P.y; yh[t] = P.z; yl[t] = P.w;
+        zs[t] = ok ? stz[s].x : -1.0f;
+        hi[t] = 0.f; lo[t] = 0.f;
+    }
+    const int c0 = blockIdx.y * cols_per_chunk;
+    const int c1 = min(g.ncol, c0 + cols_per_chunk);
+    for (int col = c0; col < c1; ++col) {
+        const int i = col % g.nx, j = col / g.nx;
+        const float2 X = make_float2(g.cx[2 * i], g.cx[2 * i + 1]);
+        const float2 Y = make_float2(g.cy[2 * j], g.cy[2 * j + 1]);
+        float h2[T], cs[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            h2[t] = far_h2(X, Y, xh[t], xl[t], yh[t], yl[t]);
+            cs[t] = 0.f;
+        }
+        for (int l = 0; l < g.nz; ++l) {
+            const float zc = g.czc[l], wl = w2f[l];
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const float dz = zc - zs[t];
+                const float k = far_kernel(dz, fmaf(dz, dz, h2[t]));
+                cs[t] = fmaf(wl, k * k, cs[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            float s, e;
+            two_sum(hi[t], cs[t], s, e);
+            hi[t] = s;
+            lo[t] += e;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int64_t s = s_base + (int64_t)t * kMfThreads;
+        if (s < g.N) part[(int64_t)blockIdx.y * g.N + s] = (double)hi[t] + (double)lo[t];
+    }
+}
+
+inline int grid_for(int64_t n, int threads, int cap = 148 * 32) {
+    int64_t b = (n + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
+}
+
+Geo make_geo(const grav_plan *p) {
+    Geo g;
+    g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
+    g.xe = p->d_xe; g.ye = p->d_ye; g.ze = p->d_ze;
+    g.N = p->N;
+    return g;
+}
+
+constexpr int kMfColsPerStage = 32;
+
+int adj_tz(int nz) {
+    // pick TZ in {8, 16} minimising padded layers x (per-pair cost + per-station overhead / TZ)
+    const double c8 = std::ceil(nz / 8.0) * 8 * (7.0 + 10.0 / 8);
+    const double c16 = std::ceil(nz / 16.0) * 16 * (7.0 + 10.0 / 16);
+    return (c16 <= c8) ? 16 : 8;
+}
+
+}  // namespace
+
+// Plan-time sizing and device set-up of the mixed path.  Allocations come from
+// the plan's arena (see api.cu, which calls mixed_scratch_bytes first).
+struct MixedSizes {
+    int cols_per_chunk, nchunk, tz, ngz, nschunk;
+    int64_t schunk_len;
+    size_t cub_temp;
+    int nbins;
+    int key_bits;
+};
+
+static MixedSizes mixed_sizes(const grav_plan *p) {
+    MixedSizes z{};
+    const int ncol = p->nx * p->ny;
+    const int tiles = (int)((p->N + kMfThreads * kMfT - 1) / (kMfThreads * kMfT));
+    // aim at >= 16 waves of ~6 resident CTAs per SM, each CTA >= 16 columns
+    const int64_t target = 148LL * 6 * 16;
+    int nchunk = (int)std::min<int64_t>(std::max<int64_t>(1, (target + tiles - 1) / tiles), std::max(1, ncol / 16));
+    z.cols_per_chunk = (ncol + nchunk - 1) / nchunk;
+    z.nchunk = (ncol + z.cols_per_chunk - 1) / z.cols_per_chunk;
+    z.tz = adj_tz(p->nz);
+    z.ngz = (p->nz + z.tz - 1) / z.tz;
+    const int64_t groups_ctas = ((int64_t)ncol * z.ngz + kMaWarps - 1) / kMaWarps;
+    int64_t nsch = std::max<int64_t>(1, (148LL * 8 + groups_ctas - 1) / groups_ctas);
+    nsch = std::min<int64_t>(nsch, (p->N + kMaStage - 1) / kMaStage);
+    int64_t len = (p->N + nsch - 1) / nsch;
+    len = (len + kMaStage - 1) / kMaStage * kMaStage;   // keeps every chunk start 16-byte aligned
+    z.schunk_len = len;
+    z.nschunk = (int)((p->N + len - 1) / len);
+    z.nbins = p->ng.nbx * p->ng.nby;
+    int bits = 1;
+    while ((1LL << bits) <= (int64_t)z.nbins) ++bits;
+    z.key_bits = bits;
+    size_t tmp = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, tmp, (unsigned *)nullptr, (unsigned *)nullptr, (int *)nullptr,
+                                    (int *)nullptr, (int)p->N, 0, bits);
+    z.cub_temp = tmp;
+    return z;
+}
+
+size_t mixed_scratch_bytes(const grav_plan *p) {
+    const MixedSizes z = mixed_sizes(p);
+    const int64_t N = p->N, M = p->M;
+    const int nzp = (p->nz + 3) / 4 * 4;
+    const int64_t lz = std::min(p->ng.bz, p->nz);
+    size_t b = 0;
+    auto add = [&](size_t v) { b += (v + 255) / 256 * 256 + 256; };
+    add(8ull * p->nx); add(8ull * p->ny); add(4ull * nzp); add(4ull * nzp);   // cx, cy, czc, w2f
+    add(4ull * p->nx * p->ny * nzp);                                       // qT
+    add(16ull * (N + 2)); add(8ull * (N + 4));                             // st32, stz (padded)
+    add(8ull * z.nchunk * N);                                               // m_part
+    add(8ull * z.nschunk * M);                                              // m_apart
+    add(8ull * N * p->ng.slots);                                            // dG
+    add(4ull * N); add(4ull * N);                                           // i0, j0
+    add(8ull * N); add(8ull * N);                                           // diag_corr, near_corr
+    add(8ull * p->nx * p->ny * lz);                                         // near adjoint
+    add(4ull * N); add(4ull * N); add(4ull * N); add(4ull * N);             // keys, keys_sorted, vals, bin_st
+    add(4ull * (z.nbins + 2));                                              // bin_start
+    add(z.cub_temp);
+    add(8ull * std::max<int64_t>(N, 1) * std::max(z.nchunk, 1));            // diag partials
+    return b;
+}
+
+static void *take(grav_plan *p, size_t bytes) {
+    void *q = p->arena.take(bytes);
+    return q;
+}
+
+int near_setup_warps(const grav_plan *p) {
+    const size_t per_warp = (size_t)(p->ng.bx + 1) * (p->ng.by + 1) * (p->ng.bz + 1) * 8;
+    const size_t cap = 200 * 1024;
+    return (int)std::min<size_t>(kNsWarps, cap / per_warp);
+}
+
+int mixed_setup(grav_plan *p, cudaStream_t s) {
+    const MixedSizes z = mixed_sizes(p);
+    const int ns_warps = near_setup_warps(p);
+    if (ns_warps < 1) return GRAV_EINVAL;
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const int nzp = (nz + 3) / 4 * 4;
+    const double a = p->xe[1] - p->xe[0];
+    const double xref = 0.5 * (p->xe.front() + p->xe.back());
+    const double yref = 0.5 * (p->ye.front() + p->ye.back());
+    std::vector<float> hcx(2 * nx), hcy(2 * ny), hcz(nzp), hw2(nzp, 0.0f);
+    for (int i = 0; i < nx; ++i) {
+        const double v = 0.5 * (p->xe[i] + p->xe[i + 1]) - xref;
+        hcx[2 * i] = (float)v;
+        hcx[2 * i + 1] = (float)(v - (double)(float)v);
+    }
+    for (int j = 0; j < ny; ++j) {
+        const double v = 0.5 * (p->ye[j] + p->ye[j + 1]) - yref;
+        hcy[2 * j] = (float)v;
+        hcy[2 * j + 1] = (float)(v - (double)(float)v);
+    }
+    for (int l = 0; l < nzp; ++l) {
+        const int ll = std::min(l, nz - 1);
+        hcz[l] = (float)(0.5 * (p->ze[ll] + p->ze[ll + 1]));
+        if (l < nz) {
+            const double zc = 0.5 * (p->ze[l] + p->ze[l + 1]) - p->ze[0];
+            hw2[l] = (float)((zc + p->opt.z0) * (zc + p->opt.z0));
+        }
+    }
+    p->m_cx = (float *)take(p, 8ull * nx);
+    p->m_cy = (float *)take(p, 8ull * ny);
+    p->m_czc = (float *)take(p, 4ull * nzp);
+    float *w2f = (float *)take(p, 4ull * nzp);
+    p->qT = (float *)take(p, 4ull * nx * ny * nzp);
+    p->st32 = (float4 *)take(p, 16ull * (p->N + 2));
+    p->stz = (float2 *)take(p, 8ull * (p->N + 4));
+    p->m_fwd_cols_per_chunk = z.cols_per_chunk;
+    p->m_fwd_nchunk = z.nchunk;
+    p->m_adj_tz = z.tz;
+    p->m_adj_ngz = z.ngz;
+    p->m_adj_nschunk = z.nschunk;
+    p->m_adj_schunk_len = (int)z.schunk_len;
+    p->m_part = (double *)take(p, 8ull * z.nchunk * p->N);
+    p->m_apart = (double *)take(p, 8ull * z.nschunk * p->M);
+    p->dG = (double *)take(p, 8ull * p->N * p->ng.slots);
+    p->st_i0 = (int *)take(p, 4ull * p->N);
+    p->st_j0 = (int *)take(p, 4ull * p->N);
+    p->diag_corr = (double *)take(p, 8ull * p->N);
+    p->near_corr = (double *)take(p, 8ull * p->N);
+    const int64_t lz = std::min(p->ng.bz, nz);
+    p->m_cellacc = (double *)take(p, 8ull * nx * ny * lz);
+    unsigned *keys = (unsigned *)take(p, 4ull * p->N);
+    unsigned *keys_sorted = (unsigned *)take(p, 4ull * p->N);
+    int *vals = (int *)take(p, 4ull * p->N);
+    p->bin_st = (int *)take(p, 4ull * p->N);
+    p->bin_start = (int *)take(p, 4ull * (z.nbins + 2));
+    void *cub_tmp = take(p, std::max<size_t>(z.cub_temp, 16));
+    p->m_w2f = w2f;
+    if (p->arena.overflow) return GRAV_EDEVICE;
+
+    p->mg.nx = nx; p->mg.ny = ny; p->mg.nz = nz; p->mg.nzp = nzp; p->mg.ncol = nx * ny;
+    p->mg.cx = p->m_cx; p->mg.cy = p->m_cy; p->mg.czc = p->m_czc; p->mg.N = p->N;
+
+    cudaMemcpyAsync(p->m_cx, hcx.data(), 8ull * nx, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(p->m_cy, hcy.data(), 8ull * ny, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(p->m_czc, hcz.data(), 4ull * nzp, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(w2f, hw2.data(), 4ull * nzp, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(p->stz, 0, 8ull * (p->N + 4), s);
+    k_prep_stations<<<grid_for(p->N, 256), 256, 0, s>>>(p->sx, p->sy, p->sz, p->N, xref, yref, p->st32, p->stz);
+
+    const int nnode = (p->ng.bx + 1) * (p->ng.by + 1) * (p->ng.bz + 1);
+    const size_t smem = (size_t)ns_warps * nnode * 8;
+    cudaFuncSetAttribute(k_near_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    const double vol_mgal = kGammaMgal * a * a * a;
+    k_near_setup<<<(unsigned)((p->N + ns_warps - 1) / ns_warps), ns_warps * 32, smem, s>>>(
+        make_geo(p), p->mg, p->ng, p->xe[0], p->ye[0], a, vol_mgal, p->sx, p->sy, p->sz, p->d_w2, p->st32,
+        p->stz, p->dG, p->st_i0, p->st_j0, p->diag_corr, keys, vals, (unsigned)z.nbins);
+    size_t tmp = z.cub_temp;
+    cub::DeviceRadixSort::SortPairs(cub_tmp, tmp, keys, keys_sorted, vals, p->bin_st, (int)p->N, 0, z.key_bits, s);
+    k_bin_bounds<<<grid_for(z.nbins + 1, 256), 256, 0, s>>>(keys_sorted, p->N, z.nbins, p->bin_start);
+    note_launches(4);
+    // the diagonal's far-field partials reuse m_part (same chunking as the forward)
+    return GRAV_OK;
+}
+
+size_t mfwd_smem(const grav_plan *p) { return mfwd_layout(p->mg, kMfColsPerStage).total; }
+
+void launch_mixed_prep_q(const grav_plan *p, const double *m, cudaStream_t s) {
+    const double a = p->xe[1] - p->xe[0];
+    const float scale = (float)(kGammaMgal * a * a * a);
+    const int64_t total = (int64_t)p->mg.ncol * p->mg.nzp;
+    k_prep_q<<<grid_for(total, 256), 256, 0, s>>>(p->mg, m, scale, p->qT);
+    note_launches(1);
+}
+
+void launch_mixed_fwd(const grav_plan *p, cudaStream_t s) {
+    const int tiles = (int)((p->N + kMfThreads * kMfT - 1) / (kMfThreads * kMfT));
+    dim3 grid(tiles, p->m_fwd_nchunk);
+    const size_t smem = mfwd_smem(p);
+    cudaFuncSetAttribute(k_mfwd<kMfT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    stage_begin(p, kStageFwdMain, s);
+    k_mfwd<kMfT><<<grid, kMfThreads, smem, s>>>(p->mg, p->qT, p->st32, p->stz, p->m_fwd_cols_per_chunk,
+                                               kMfColsPerStage, p->m_part, p->ctx->d_status);
+    stage_end(p, kStageFwdMain, s);
+    note_launches(1);
+}
+
+void launch_mixed_near_fwd(const grav_plan *p, const double *m, cudaStream_t s) {
+    const int64_t threads = p->N * 32;
+    stage_begin(p, kStageFwdNear, s);
+    k_near_fwd<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(p->nx, p->ny, p->nz, p->ng, p->N, p->dG, p->st_i0,
+                                                                p->st_j0, m, p->near_corr);
+    stage_end(p, kStageFwdNear, s);
+    note_launches(1);
+}
+
+void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
+    k_set_rz<<<grid_for(p->N, 256), 256, 0, s>>>(p->stz, r, p->N);
+    const int64_t groups = (int64_t)p->mg.ncol * p->m_adj_ngz;
+    dim3 grid((unsigned)((groups + kMaWarps - 1) / kMaWarps), p->m_adj_nschunk);
+    const size_t smem = 128 + 2ull * kMaStage * (sizeof(float4) + sizeof(float2));
+    note_launches(1);
+    stage_begin(p, kStageAdjMain, s);
+    if (p->m_adj_tz == 16) {
+        cudaFuncSetAttribute(k_madj<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        k_madj<16><<<grid, kMaWarps * 32, smem, s>>>(p->mg, p->st32, p->stz, p->m_adj_ngz, p->m_adj_schunk_len,
+                                                     p->m_apart, p->ctx->d_status);
+    } else {
+        cudaFuncSetAttribute(k_madj<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        k_madj<8><<<grid, kMaWarps * 32, smem, s>>>(p->mg, p->st32, p->stz, p->m_adj_ngz, p->m_adj_schunk_len,
+                                                    p->m_apart, p->ctx->d_status);
+    }
+    stage_end(p, kStageAdjMain, s);
+    const int64_t lz = std::min(p->ng.bz, p->nz);
+    stage_begin(p, kStageAdjNear, s);
+    k_near_adj<<<grid_for((int64_t)p->nx * p->ny * lz, 128), 128, 0, s>>>(p->nx, p->ny, p->nz, p->ng, p->dG,
+                                                                         p->bin_start, p->bin_st, r, p->m_cellacc);
+    stage_end(p, kStageAdjNear, s);
+    note_launches(2);
+}
+
+void launch_mixed_adj_finish(const grav_plan *p, const double *r, int depth_weighted, const double *add,
+                             double *out, cudaStream_t s) {
+    (void)r;
+    const double a = p->xe[1] - p->xe[0];
+    k_madj_finish<<<grid_for(p->M, 256), 256, 0, s>>>(p->nx, p->ny, p->nz, std::min(p->ng.bz, p->nz), p->m_apart,
+                                                      p->m_adj_nschunk, kGammaMgal * a * a * a, p->m_cellacc,
+                                                      depth_weighted ? p->d_w2 : nullptr, add, out);
+    note_launches(1);
+}
+
+void launch_mixed_diag(const grav_plan *p, double *diag, cudaStream_t s) {
+    const int tiles = (int)((p->N + kMfThreads * kMfT - 1) / (kMfThreads * kMfT));
+    dim3 grid(tiles, p->m_fwd_nchunk);
+    k_mdiag<kMfT><<<grid, kMfThreads, 0, s>>>(p->mg, p->m_w2f, p->st32, p->stz, p->m_fwd_cols_per_chunk,
+                                             p->m_part);
+    note_launches(1);
+    const double a = p->xe[1] - p->xe[0];
+    const double v = kGammaMgal * a * a * a;
+    launch_reduce_rows(p->m_part, p->m_fwd_nchunk, p->N, v * v, nullptr, 0.0, p->diag_corr, diag, s);
+}
+
+}  // namespace grav
