@@ -186,6 +186,33 @@ size_t grav_plan_bytes(const grav_plan *plan);
  * enqueued on `stream`. */
 int grav_plan_destroy(grav_plan *plan, grav_stream_t stream);
 
+/* ---- forward product without device allocation --------------------------- */
+/* The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory while they run (a framework whose allocator
+ * owns all device memory, a fixed pre-reserved memory budget, or code that
+ * cannot afford the device synchronisation an allocation may imply): it needs
+ * no grav_ctx and calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Computes the same d = G m as grav_forward with GRAV_FP64, on the CURRENT
+ * CUDA device and on `stream`.  mesh: HOST edge arrays as for every other
+ * call.  survey arrays, m (nx*ny*nz doubles) and d (n doubles): DEVICE
+ * pointers on the current device, owned by the caller.
+ *
+ * Scratch: one 64 MiB static device array inside libgrav (mesh edges, node
+ * weights, per-chunk partial sums, a status word), held by every GPU that
+ * loads the library until the process exits.  Problems whose node weights
+ * ((ny+1)(nz+1)(nx+1 rounded up to even) doubles) plus one partial per
+ * station do not fit are rejected with GRAV_EINVAL and a message naming the
+ * sizes.  Every call shares that array and keeps the previous call's
+ * contents, so calls that overlap on the GPU (different streams, threads or
+ * processes' contexts on the same device without ordering) race and give
+ * wrong results: order them on one stream.  The first call on each device
+ * looks the array's device address up (cudaGetSymbolAddress) and caches it;
+ * make that first call before any stream capture.  Returns without waiting
+ * for the GPU. */
+int grav_forward_fp64_noalloc(const grav_mesh *mesh, const grav_survey *survey, const double *m, double *d,
+                              grav_stream_t stream);
+
 /* ---- measurement ------------------------------------------------------------ */
 /* Total number of CUDA kernels this library has launched in the process
  * (all contexts).  Used to attribute device work to libgrav in benchmarks. */

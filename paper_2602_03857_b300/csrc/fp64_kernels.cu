@@ -462,3 +462,27 @@ void launch_diag64(const grav_plan *p, double *diag, cudaStream_t s) {
 }
 
 }  // namespace grav
+
+namespace grav {
+
+// Raw-pointer launchers of the FP64 forward kernels for callers that manage
+// their own scratch (no plan): node weights into w, per-chunk partials into
+// part.  Returns the number of kernels launched.
+int launch_fwd64_raw(Geo g, int ldw, const double *m, double *w, int rows_per_chunk, int nchunk,
+                     const double *sx, const double *sy, const double *sz, double *part, int *status,
+                     cudaStream_t s) {
+    const int64_t total = (int64_t)(g.ny + 1) * (g.nz + 1) * ldw;
+    k_node_weights<<<grid_for(total, 256), 256, 0, s>>>(g.nx, g.ny, g.nz, ldw, m, w);
+    const int rps = std::max(1, std::min(rows_per_chunk, (16384 / 8) / ldw));
+    const size_t smem = 128 + (size_t)ldw * 8 + 2ull * rps * ldw * 8;
+    cudaFuncSetAttribute(k_fwd64<kFwdT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    const int tiles = (int)((g.N + kFwdThreads * kFwdT - 1) / (kFwdThreads * kFwdT));
+    dim3 grid(tiles, nchunk);
+    k_fwd64<kFwdT><<<grid, kFwdThreads, smem, s>>>(g, ldw, w, rows_per_chunk, rps, sx, sy, sz, part, status);
+    note_launches(2);
+    return 2;
+}
+
+int fwd64_stations_per_cta() { return kFwdThreads * kFwdT; }
+
+}  // namespace grav

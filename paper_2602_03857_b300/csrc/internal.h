@@ -171,6 +171,10 @@ void launch_adj_finish(const grav_plan *p, const double *u, double scale, int de
                        const double *add, double *out, cudaStream_t s);
 void launch_diag64(const grav_plan *p, double *diag, cudaStream_t s);
 size_t fwd64_smem_bytes(const grav_plan *p);
+int launch_fwd64_raw(Geo g, int ldw, const double *m, double *w, int rows_per_chunk, int nchunk,
+                     const double *sx, const double *sy, const double *sz, double *part, int *status,
+                     cudaStream_t s);
+int fwd64_stations_per_cta();
 
 // mixed launchers (mixed_kernels.cu)
 int mixed_setup(grav_plan *p, cudaStream_t s);   // 0 or a GRAV_E* code
