@@ -226,10 +226,11 @@ uint64_t grav_launch_count(void);
  * read (this waits for the recorded events) and reset them. */
 int grav_plan_timing(grav_plan *plan, int enable, double *ms, int64_t *counts);
 
-/* Pipe-rate microbenchmark on `device` (synchronous, ~0.1 s).  out (HOST, 9
+/* Pipe-rate microbenchmark on `device` (synchronous, ~0.1 s).  out (HOST, 11
  * doubles): [0] MUFU rsqrt/s, [1] SM MHz seen, [2] MUFU lg2/s, [3] MHz,
- * [4] FP32 FMA/s, [5] MHz, [6] FP64 FMA/s, [7] MHz, [8] SM count.  The per-clock
- * rates per SM are out[2k] / (out[2k+1]*1e6 * out[8]). */
+ * [4] FP32 FMA/s, [5] MHz, [6] FP64 FMA/s, [7] MHz, [8] FP32 FMA/s issued as
+ * packed fma.rn.f32x2, [9] MHz, [10] SM count.  The per-clock rates per SM
+ * are out[2k] / (out[2k+1]*1e6 * out[10]). */
 int grav_bench_pipes(int device, double *out);
 
 #ifdef __cplusplus

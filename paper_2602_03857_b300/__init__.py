@@ -115,13 +115,13 @@ def launch_count() -> int:
 
 def bench_pipes(device: int = 0) -> dict:
     """Measured unit throughputs (per second) and SM clocks of the B300 pipes."""
-    out = (ctypes.c_double * 9)()
+    out = (ctypes.c_double * 11)()
     rc = _lib.grav_bench_pipes(int(device), out)
     if rc != GRAV_OK:
         raise GravError(rc, _lib.grav_last_error(None).decode())
-    sms = out[8]
+    sms = out[10]
     r = {"sm_count": int(sms)}
-    for k, name in enumerate(("rsqrt", "lg2", "ffma", "dfma")):
+    for k, name in enumerate(("rsqrt", "lg2", "ffma", "dfma", "ffma_f32x2")):
         r[name + "_per_s"] = out[2 * k]
         r[name + "_mhz"] = out[2 * k + 1]
         r[name + "_per_clk_sm"] = out[2 * k] / (out[2 * k + 1] * 1e6 * sms) if out[2 * k + 1] > 0 else 0.0

@@ -37,6 +37,7 @@ def nvcc() -> str:
 def _flags(ptxas_verbose: bool = False):
     f = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I" + INCLUDE, "-I" + CSRC,
          "--expt-relaxed-constexpr", "-Xcudafe", "--diag_suppress=177"] + ARCH
+    f += [x for x in os.environ.get("GRAV_NVCC_DEFINES", "").split() if x.startswith("-D")]
     if ptxas_verbose:
         f += ["-Xptxas", "-v"]
     return f

@@ -442,46 +442,62 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
         const double work = (double)N * (double)M;
         const int every = o.check_every > 0 ? o.check_every : (work > 2e8 ? 1 : 8);
         int it = 0;
-        while (!converged && it < o.max_iter) {
-            const int n_it = std::min(every, o.max_iter - it);
-            for (int k = 0; k < n_it; ++k, ++it) {
-                if ((rc = plan_adjoint_ex(p, pv, q, 1, nullptr, s))) break;
-                if ((rc = plan_forward_ex(p, q, Ap, pv, lam, s))) break;
-                launch_dot(pv, Ap, N, dp, sc + kSPAp, s);
-                cg_alpha(sc, s);
-                cg_update_yr(y, r, pv, Ap, N, sc, s);
-                launch_dot(r, r, N, dp, sc + kSRRNew, s);
-                cg_beta(sc, it, s);
-                cg_update_p(pv, r, N, sc, s);
+        double true_rel = 0.0;
+        // CG; when the recurrence residual reaches tol, the residual is
+        // recomputed from y with the operator itself (r = dd - A y); if that
+        // true residual is still above tol, CG restarts from it (p = r).
+        for (int restart = 0;; ++restart) {
+            while (!converged && it < o.max_iter) {
+                const int n_it = std::min(every, o.max_iter - it);
+                for (int k = 0; k < n_it; ++k, ++it) {
+                    if ((rc = plan_adjoint_ex(p, pv, q, 1, nullptr, s))) break;
+                    if ((rc = plan_forward_ex(p, q, Ap, pv, lam, s))) break;
+                    launch_dot(pv, Ap, N, dp, sc + kSPAp, s);
+                    cg_alpha(sc, s);
+                    cg_update_yr(y, r, pv, Ap, N, sc, s);
+                    launch_dot(r, r, N, dp, sc + kSRRNew, s);
+                    cg_beta(sc, it, s);
+                    cg_update_p(pv, r, N, sc, s);
+                }
+                if (rc) break;
+                if ((rc = sync_scalars("cg iteration"))) break;
+                if (hsc[kSFrozen] == 2.0) {
+                    rc = set_error(ctx, GRAV_EDEVICE, "CG breakdown: p.Ap <= 0 (operator not SPD in this precision)");
+                    break;
+                }
+                if (hsc[kSFrozen] != 0.0) converged = true;
+                if (cancel && cancel->load()) {
+                    rc = set_error(ctx, GRAV_ECANCELED, "solve cancelled");
+                    break;
+                }
             }
             if (rc) break;
-            if ((rc = sync_scalars("cg iteration"))) break;
-            if (hsc[kSFrozen] == 2.0) {
-                rc = set_error(ctx, GRAV_EDEVICE, "CG breakdown: p.Ap <= 0 (operator not SPD in this precision)");
+            // true residual dd - (G W^-2 G^T y + lambda y) into r
+            if ((rc = plan_adjoint_ex(p, y, q, 1, nullptr, s))) break;
+            if ((rc = plan_forward_ex(p, q, Ap, y, lam, s))) break;
+            vec_axpby(1.0, dd, -1.0, Ap, N, r, s);
+            launch_dot(r, r, N, dp, sc + kSTmp, s);
+            if ((rc = sync_scalars("cg true residual"))) break;
+            true_rel = hsc[kSBB] > 0 ? std::sqrt(hsc[kSTmp] / hsc[kSBB]) : 0.0;
+            iters = (int)hsc[kSIters];   // iterations that updated y (no-ops after a freeze excluded)
+            if (true_rel <= o.tol || restart >= 4 || it >= o.max_iter) {
+                converged = true_rel <= o.tol;
                 break;
             }
-            if (hsc[kSFrozen] != 0.0) converged = true;
-            if (cancel && cancel->load()) {
-                rc = set_error(ctx, GRAV_ECANCELED, "solve cancelled");
-                break;
-            }
+            converged = false;
+            cudaMemcpyAsync(pv, r, 8ull * N, cudaMemcpyDeviceToDevice, s);
+            cg_restart(sc, s);
         }
         if (rc) break;
-        iters = (int)hsc[kSIters];
         // m = m_ref + W^-2 G^T y
         if ((rc = plan_adjoint_ex(p, y, m_out, 1, m_ref, s))) break;
-        // true residual with the same operator: dd - (G W^-2 G^T y + lambda y)
-        if ((rc = plan_adjoint_ex(p, y, q, 1, nullptr, s))) break;
-        if ((rc = plan_forward_ex(p, q, Ap, y, lam, s))) break;
-        vec_axpby(1.0, dd, -1.0, Ap, N, Ap, s);
-        launch_dot(Ap, Ap, N, dp, sc + kSTmp, s);
         if (y_out) cudaMemcpyAsync(y_out, y, 8ull * N, cudaMemcpyDeviceToDevice, s);
         if ((rc = sync_scalars("cg finish"))) break;
         if (info) {
             info->iters = iters;
             info->converged = converged ? 1 : 0;
             info->rel_res = hsc[kSBB] > 0 ? std::sqrt(hsc[kSRR] / hsc[kSBB]) : 0.0;
-            info->true_rel_res = hsc[kSBB] > 0 ? std::sqrt(hsc[kSTmp] / hsc[kSBB]) : 0.0;
+            info->true_rel_res = true_rel;
             info->lambda = lam;
             info->trace = trace;
         }

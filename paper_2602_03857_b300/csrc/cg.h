@@ -29,5 +29,6 @@ void cg_update_p(double *p, const double *r, int64_t n, const double *sc, cudaSt
 void vec_axpby(double a, const double *x, double b, const double *y, int64_t n, double *out, cudaStream_t s);
 void vec_fill(double *x, int64_t n, double v, cudaStream_t s);
 void cg_set_scalars(double *sc, double tol2, cudaStream_t s);
+void cg_restart(double *sc, cudaStream_t s);
 
 }  // namespace grav

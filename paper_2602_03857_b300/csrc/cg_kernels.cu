@@ -93,6 +93,12 @@ __global__ void k_set_scalars(double *__restrict__ sc, double tol2) {
     sc[kSIters] = 0.0;
 }
 
+// restart from the true residual held in kSTmp: rr <- true r.r, unfreeze unless already below tol
+__global__ void k_cg_restart(double *__restrict__ sc) {
+    sc[kSRR] = sc[kSTmp];
+    sc[kSFrozen] = (sc[kSTmp] <= sc[kSTol2] * sc[kSBB]) ? 1.0 : 0.0;
+}
+
 inline int vgrid(int64_t n) {
     int64_t b = (n + 255) / 256;
     return (int)(b < 1 ? 1 : (b > 148 * 16 ? 148 * 16 : b));
@@ -119,6 +125,7 @@ void vec_axpby(double a, const double *x, double b, const double *y, int64_t n, 
     k_axpby<<<vgrid(n), 256, 0, s>>>(a, x, b, y, n, out); note_launches(1);
 }
 void vec_fill(double *x, int64_t n, double v, cudaStream_t s) { k_fill<<<vgrid(n), 256, 0, s>>>(x, n, v); note_launches(1); }
+void cg_restart(double *sc, cudaStream_t s) { k_cg_restart<<<1, 1, 0, s>>>(sc); note_launches(1); }
 void cg_set_scalars(double *sc, double tol2, cudaStream_t s) { k_set_scalars<<<1, 1, 0, s>>>(sc, tol2); note_launches(1); }
 
 }  // namespace grav

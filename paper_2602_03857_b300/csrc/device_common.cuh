@@ -118,6 +118,50 @@ __device__ __forceinline__ float far_kernel(float dz, float R2) {
     return (dz * rs) * rs2;
 }
 
+// Two FP32 values packed in one 64-bit register pair (.lo = first), operated on
+// by the sm_100-family packed instructions add/mul/fma.rn.f32x2: two IEEE
+// round-to-nearest FP32 results per instruction, bit-identical to the scalar
+// operations on each half.
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+    f2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+    f2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// The far-field term for two pairs at once: acc += w * dz / R^3 with
+// dz = zc + nzs (nzs = -station depth), R^2 = dz^2 + h2.  Same operations, in
+// the same order, as far_kernel() on each half.
+__device__ __forceinline__ f2_t far_pair_acc(f2_t zc, f2_t nzs, f2_t h2, f2_t w, f2_t acc) {
+    const f2_t dz = f2_add(zc, nzs);
+    const f2_t R2 = f2_fma(dz, dz, h2);
+    float r0, r1;
+    f2_unpack(R2, r0, r1);
+    const f2_t rs = f2_pack(rsqrt_approx(r0), rsqrt_approx(r1));
+    const f2_t rs2 = f2_mul(rs, rs);
+    const f2_t k = f2_mul(f2_mul(dz, rs), rs2);
+    return f2_fma(w, k, acc);
+}
+
 // Knuth two-sum: (s, e) with s = fl(a + b), a + b = s + e exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = a + b;

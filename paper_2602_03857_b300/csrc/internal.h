@@ -118,6 +118,7 @@ struct grav_plan {
     float2 *stz = nullptr;                // stations (z, r)
     int m_fwd_cols_per_chunk = 0, m_fwd_nchunk = 0;
     int m_adj_tz = 0, m_adj_ngz = 0, m_adj_nschunk = 0, m_adj_schunk_len = 0;
+    int m_adj_bc = 0;                     // 1: broadcast adjoint layout (large meshes), 0: lanes split stations
     double *m_part = nullptr;             // [nchunk][N] forward partials (hi+lo in FP64)
     double *m_apart = nullptr;            // [nschunk][M] adjoint partials
     double *dG = nullptr;                 // [N][slots] near-field correction (mGal per kg/m^3)

@@ -27,12 +27,28 @@ __device__ __forceinline__ float rsqrt_v(float x) {
     return r;
 }
 
-// op: 0 rsqrt, 1 lg2, 2 ffma, 3 dfma
+// op: 0 rsqrt, 1 lg2, 2 ffma, 3 dfma, 4 packed fma.rn.f32x2 (counted as 2 FP32 FMAs)
 template <int OP>
 __global__ void k_pipe(int iters, float seed, float *out, unsigned long long *clk) {
     const uint64_t t0 = globaltimer_ns();
     const long long c0 = clock64();
-    if (OP == 3) {
+    if (OP == 4) {
+        f2_t a[kChains];
+        const f2_t m = f2_pack(0.999999f, 0.999998f), c = f2_pack(1e-7f, 2e-7f);
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) a[k] = f2_pack(seed + 0.001f * (threadIdx.x + k), seed);
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int k = 0; k < kChains; ++k) a[k] = f2_fma(a[k], m, c);
+        }
+        float s = 0, lo, hi;
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) {
+            f2_unpack(a[k], lo, hi);
+            s += lo + hi;
+        }
+        if (s == 12345.678f) out[0] = s;
+    } else if (OP == 3) {
         double a[kChains];
 #pragma unroll
         for (int k = 0; k < kChains; ++k) a[k] = seed + 0.001 * (threadIdx.x + k);
@@ -89,7 +105,7 @@ int run_one(int sms, double *ops_per_s, double *clk_mhz) {
     cudaEventElapsedTime(&ms, e0, e1);
     unsigned long long h[2] = {0, 0};
     cudaMemcpy(h, clk, 16, cudaMemcpyDeviceToHost);
-    *ops_per_s = (double)blocks * threads * iters * kChains / (ms * 1e-3);
+    *ops_per_s = (double)blocks * threads * iters * kChains * (OP == 4 ? 2 : 1) / (ms * 1e-3);
     *clk_mhz = h[1] ? (double)h[0] / (double)h[1] * 1e3 : 0.0;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -117,7 +133,8 @@ extern "C" int grav_bench_pipes(int device, double *out) {
     rc |= run_one<1>(sms, &out[2], &out[3]);
     rc |= run_one<2>(sms, &out[4], &out[5]);
     rc |= run_one<3>(sms, &out[6], &out[7]);
-    out[8] = sms;
+    rc |= run_one<4>(sms, &out[8], &out[9]);
+    out[10] = sms;
     cudaSetDevice(prev);
     return rc ? set_error(nullptr, GRAV_EDEVICE, "pipe microbenchmark failed") : GRAV_OK;
 }

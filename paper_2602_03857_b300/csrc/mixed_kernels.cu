@@ -15,6 +15,8 @@
 // deterministic per-cell gather over stations binned by box origin).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
 #include <cub/device/device_radix_sort.cuh>
 
 #include "device_common.cuh"
@@ -24,11 +26,38 @@ namespace grav {
 
 namespace {
 
+// Launch-shape constants (compile-time tunables; the defaults are the measured best).
+#ifndef GRAV_MF_T
+#define GRAV_MF_T 8
+#endif
+#ifndef GRAV_MF_MINB
+#define GRAV_MF_MINB 4
+#endif
+#ifndef GRAV_MA_MINB
+#define GRAV_MA_MINB 0          // 0: per-TZ default below
+#endif
+#ifndef GRAV_MA_STAGE
+#define GRAV_MA_STAGE 1024
+#endif
+#ifndef GRAV_MA_TZ
+#define GRAV_MA_TZ 0
+#endif
+#ifndef GRAV_AB_FORCE
+#define GRAV_AB_FORCE -1        // -1: choose the adjoint layout by size; 0/1 force it
+#endif
 constexpr int kMfThreads = 128;
-constexpr int kMfT = 8;              // stations per thread (far forward)
-constexpr int kMaWarps = 8;          // warps per CTA (far adjoint)
-constexpr int kMaStage = 512;        // stations per TMA stage (far adjoint)
-constexpr int kNsWarps = 8;          // warps per CTA (near set-up)
+constexpr int kMfT = GRAV_MF_T;          // stations per thread (far forward)
+constexpr int kMaWarps = 8;              // warps per CTA (far adjoint)
+constexpr int kMaStage = GRAV_MA_STAGE;  // stations per TMA stage (far adjoint)
+constexpr int kNsWarps = 8;              // warps per CTA (near set-up)
+
+// CTAs per SM the adjoint is compiled for (register budget 65536 / (256 * minB)):
+// measured on B300 at 210 x 210 x 75 -- TZ = 8 is fastest at 3 (79 registers),
+// TZ >= 12 at 2 (up to 127 registers; the extra ILP beats the lost occupancy).
+template <int TZ>
+struct MaMinBlocks {
+    static constexpr int value = GRAV_MA_MINB > 0 ? GRAV_MA_MINB : (TZ <= 8 ? 3 : 2);
+};
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -90,7 +119,7 @@ __device__ __forceinline__ float far_h2(float2 X, float2 Y, float xh, float xl, 
 // (broadcast) and issues per pair: FADD, FFMA, MUFU.RSQ, 3 FMUL, FFMA.
 // ---------------------------------------------------------------------------
 template <int T>
-__global__ void __launch_bounds__(kMfThreads) k_mfwd(MixedGeo g, const float *__restrict__ qT,
+__global__ void __launch_bounds__(kMfThreads, GRAV_MF_MINB) k_mfwd(MixedGeo g, const float *__restrict__ qT,
                                                      const float4 *__restrict__ st32,
                                                      const float2 *__restrict__ stz, int cols_per_chunk,
                                                      int cols_per_stage, double *__restrict__ part,
@@ -109,14 +138,16 @@ __global__ void __launch_bounds__(kMfThreads) k_mfwd(MixedGeo g, const float *__
     const int nst = (c1 > c0) ? (c1 - c0 + cols_per_stage - 1) / cols_per_stage : 0;
 
     const int64_t s_base = (int64_t)blockIdx.x * (kMfThreads * T) + threadIdx.x;
-    float xh[T], xl[T], yh[T], yl[T], zs[T], hi[T], lo[T];
+    float xh[T], xl[T], yh[T], yl[T], hi[T], lo[T];
+    f2_t nzs[T];   // (-z, -z) of each station
 #pragma unroll
     for (int t = 0; t < T; ++t) {
         const int64_t s = s_base + (int64_t)t * kMfThreads;
         const bool ok = s < g.N;
         const float4 P = ok ? st32[s] : make_float4(0.f, 0.f, 0.f, 0.f);
         xh[t] = P.x; xl[t] = P.y; yh[t] = P.z; yl[t] = P.w;
-        zs[t] = ok ? stz[s].x : -1.0f;
+        const float zs = ok ? stz[s].x : -1.0f;
+        nzs[t] = f2_pack(-zs, -zs);
         hi[t] = 0.f; lo[t] = 0.f;
     }
     for (int i = threadIdx.x; i < g.nx; i += kMfThreads) cxs[i] = make_float2(g.cx[2 * i], g.cx[2 * i + 1]);
@@ -155,32 +186,35 @@ __global__ void __launch_bounds__(kMfThreads) k_mfwd(MixedGeo g, const float *__
         const int ca = c0 + st * cols_per_stage;
         const int cb = min(c1, ca + cols_per_stage);
         const float *qb = qbuf + (size_t)buf * cols_per_stage * g.nzp;
+        int i = ca % g.nx, j = ca / g.nx;
         for (int col = ca; col < cb; ++col) {
-            const int i = col % g.nx, j = col / g.nx;
             const float2 X = cxs[i], Y = cys[j];
-            float h2[T], cs[T];
+            if (++i == g.nx) { i = 0; ++j; }
+            // layer pairs (l, l+1) of this column share one packed f32x2 chain per station
+            f2_t h2p[T], cs2[T];
 #pragma unroll
             for (int t = 0; t < T; ++t) {
-                h2[t] = far_h2(X, Y, xh[t], xl[t], yh[t], yl[t]);
-                cs[t] = 0.f;
+                const float h = far_h2(X, Y, xh[t], xl[t], yh[t], yl[t]);
+                h2p[t] = f2_pack(h, h);
+                cs2[t] = 0ull;
             }
             const float4 *q4 = reinterpret_cast<const float4 *>(qb + (size_t)(col - ca) * g.nzp);
             const float4 *z4 = reinterpret_cast<const float4 *>(czs);
             for (int l4 = 0; l4 < nl4; ++l4) {
                 const float4 q = q4[l4], z = z4[l4];
+                const f2_t q01 = f2_pack(q.x, q.y), q23 = f2_pack(q.z, q.w);
+                const f2_t z01 = f2_pack(z.x, z.y), z23 = f2_pack(z.z, z.w);
 #pragma unroll
                 for (int t = 0; t < T; ++t) {
-                    float dz, R2;
-                    dz = z.x - zs[t]; R2 = fmaf(dz, dz, h2[t]); cs[t] = fmaf(q.x, far_kernel(dz, R2), cs[t]);
-                    dz = z.y - zs[t]; R2 = fmaf(dz, dz, h2[t]); cs[t] = fmaf(q.y, far_kernel(dz, R2), cs[t]);
-                    dz = z.z - zs[t]; R2 = fmaf(dz, dz, h2[t]); cs[t] = fmaf(q.z, far_kernel(dz, R2), cs[t]);
-                    dz = z.w - zs[t]; R2 = fmaf(dz, dz, h2[t]); cs[t] = fmaf(q.w, far_kernel(dz, R2), cs[t]);
+                    cs2[t] = far_pair_acc(z01, nzs[t], h2p[t], q01, cs2[t]);
+                    cs2[t] = far_pair_acc(z23, nzs[t], h2p[t], q23, cs2[t]);
                 }
             }
 #pragma unroll
             for (int t = 0; t < T; ++t) {
-                float s, e;
-                two_sum(hi[t], cs[t], s, e);
+                float a, b, s, e;
+                f2_unpack(cs2[t], a, b);
+                two_sum(hi[t], a + b, s, e);
                 hi[t] = s;
                 lo[t] += e;
             }
@@ -207,7 +241,7 @@ __global__ void __launch_bounds__(kMfThreads) k_mfwd(MixedGeo g, const float *__
 // by a warp-shuffle butterfly in FP64 (fixed order: deterministic).
 // ---------------------------------------------------------------------------
 template <int TZ>
-__global__ void __launch_bounds__(kMaWarps * 32) k_madj(MixedGeo g, const float4 *__restrict__ st32,
+__global__ void __launch_bounds__(kMaWarps * 32, MaMinBlocks<TZ>::value) k_madj(MixedGeo g, const float4 *__restrict__ st32,
                                                         const float2 *__restrict__ stz, int ngz,
                                                         int64_t schunk_len, double *__restrict__ apart,
                                                         int *status) {
@@ -307,6 +341,120 @@ __global__ void __launch_bounds__(kMaWarps * 32) k_madj(MixedGeo g, const float4
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Far-field adjoint, broadcast layout (large meshes): each lane owns TZ cells
+// of one column (lanes = consecutive columns, one layer group per CTA), the
+// stations of a TMA-staged chunk are read by all lanes at once (shared-memory
+// broadcast), and every lane accumulates its own cells: no cross-lane
+// reduction.  Sums run in FP32 over 64 stations and are folded into FP64
+// accumulators (compensation by wider precision).
+// ---------------------------------------------------------------------------
+#ifndef GRAV_AB_MINB
+#define GRAV_AB_MINB 2
+#endif
+constexpr int kAbWarps = 8;
+constexpr int kAbStage = 1024;
+constexpr int kAbFold = 64;
+
+template <int TZ>
+__global__ void __launch_bounds__(kAbWarps * 32, GRAV_AB_MINB) k_madj_bc(MixedGeo g, const float4 *__restrict__ st32,
+                                                                        const float2 *__restrict__ stz, int ngz,
+                                                                        int64_t schunk_len,
+                                                                        double *__restrict__ apart, int *status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    int *flag = reinterpret_cast<int *>(smem_raw + 16);
+    float4 *sxy = reinterpret_cast<float4 *>(smem_raw + 128);
+    float2 *szr = reinterpret_cast<float2 *>(smem_raw + 128 + 2 * kAbStage * sizeof(float4));
+
+    const int cblocks = (g.ncol + kAbWarps * 32 - 1) / (kAbWarps * 32);
+    const int cb = blockIdx.x % cblocks;
+    const int l0 = (blockIdx.x / cblocks) * TZ;
+    const int col = cb * (kAbWarps * 32) + threadIdx.x;
+    const bool cvalid = col < g.ncol;
+    const int cc = cvalid ? col : 0;
+    const int i = cc % g.nx, j = cc / g.nx;
+    const float2 X = make_float2(g.cx[2 * i], g.cx[2 * i + 1]);
+    const float2 Y = make_float2(g.cy[2 * j], g.cy[2 * j + 1]);
+    static_assert(TZ % 2 == 0, "layer pairs");
+    f2_t zcp[TZ / 2], cs2[TZ / 2];
+    double acc[TZ];
+#pragma unroll
+    for (int u = 0; u < TZ / 2; ++u) {
+        zcp[u] = f2_pack(g.czc[min(l0 + 2 * u, g.nzp - 1)], g.czc[min(l0 + 2 * u + 1, g.nzp - 1)]);
+        cs2[u] = 0ull;
+        acc[2 * u] = 0.0;
+        acc[2 * u + 1] = 0.0;
+    }
+    const int64_t s0 = (int64_t)blockIdx.y * schunk_len;
+    const int64_t s1 = min(g.N, s0 + schunk_len);
+    const int nst = (s1 > s0) ? (int)((s1 - s0 + kAbStage - 1) / kAbStage) : 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int st) {
+        const int buf = st & 1;
+        const int64_t sa = s0 + (int64_t)st * kAbStage;
+        const int cnt = (int)min((int64_t)kAbStage, s1 - sa);
+        const uint32_t b1 = (uint32_t)cnt * 16u;
+        const uint32_t b2 = (uint32_t)((cnt * 8 + 15) / 16 * 16);
+        mbar_arrive_expect_tx(&bar[buf], b1 + b2);
+        tma_load_1d(sxy + buf * kAbStage, st32 + sa, b1, &bar[buf]);
+        tma_load_1d(szr + buf * kAbStage, stz + sa, b2, &bar[buf]);
+    };
+    if (threadIdx.x == 0) {
+        if (nst > 0) issue(0);
+        if (nst > 1) issue(1);
+    }
+    for (int st = 0; st < nst; ++st) {
+        const int buf = st & 1;
+        if (threadIdx.x == 0) *flag = mbar_wait_bounded(&bar[buf], (st >> 1) & 1) ? 1 : 0;
+        __syncthreads();
+        if (!*flag) {
+            if (threadIdx.x == 0) {
+                set_status(status, kStatusMbarTimeout);
+                if (st + 1 < nst) (void)mbar_wait_bounded(&bar[buf ^ 1], ((st + 1) >> 1) & 1);
+            }
+            return;
+        }
+        const int64_t sa = s0 + (int64_t)st * kAbStage;
+        const int cnt = (int)min((int64_t)kAbStage, s1 - sa);
+        const float4 *pb = sxy + buf * kAbStage;
+        const float2 *zb = szr + buf * kAbStage;
+        for (int k0 = 0; k0 < cnt; k0 += kAbFold) {
+            const int k1 = min(cnt, k0 + kAbFold);
+            for (int k = k0; k < k1; ++k) {
+                const float4 P = pb[k];
+                const float2 Z = zb[k];
+                const float h = far_h2(X, Y, P.x, P.y, P.z, P.w);
+                const f2_t h2p = f2_pack(h, h), nz2 = f2_pack(-Z.x, -Z.x), w2 = f2_pack(Z.y, Z.y);
+#pragma unroll
+                for (int u = 0; u < TZ / 2; ++u) cs2[u] = far_pair_acc(zcp[u], nz2, h2p, w2, cs2[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < TZ / 2; ++u) {
+                float a, b;
+                f2_unpack(cs2[u], a, b);
+                acc[2 * u] += (double)a;
+                acc[2 * u + 1] += (double)b;
+                cs2[u] = 0ull;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && st + 2 < nst) {
+            fence_proxy_async_smem();
+            issue(st + 2);
+        }
+    }
+    if (!cvalid) return;
+#pragma unroll
+    for (int t = 0; t < TZ; ++t)
+        if (l0 + t < g.nz) apart[(int64_t)blockIdx.y * g.ncol * (int64_t)g.nz + col + (int64_t)g.ncol * (l0 + t)] = acc[t];
+}
 
 // ---------------------------------------------------------------------------
 // Near-field set-up: warp per station.  Psi on the (bx+1)(by+1)(bz+1) nodes
@@ -537,11 +685,37 @@ Geo make_geo(const grav_plan *p) {
 
 constexpr int kMfColsPerStage = 32;
 
+// Layer-group size of the broadcast adjoint: even TZ (layer pairs) in
+// {8, 12, 16, 20}, minimising (padded layers) x (measured time per layer slot,
+// relative; B300, 210 x 210 x 75 x 178,797 stations): 8 -> 1.10 (estimate),
+// 12 -> 1.157, 16 -> 1.000, 20 -> 1.059.
+int adj_tz_bc(int nz) {
+    if (GRAV_MA_TZ == 8 || GRAV_MA_TZ == 12 || GRAV_MA_TZ == 16 || GRAV_MA_TZ == 20) return GRAV_MA_TZ;
+    const int tzs[4] = {8, 12, 16, 20};
+    const double per_slot[4] = {1.10, 1.157, 1.000, 1.059};
+    int best = 16;
+    double bc = 1e300;
+    for (int q = 0; q < 4; ++q) {
+        const double c = std::ceil(nz / (double)tzs[q]) * tzs[q] * per_slot[q];
+        if (c < bc) { bc = c; best = tzs[q]; }
+    }
+    return best;
+}
+
 int adj_tz(int nz) {
-    // pick TZ in {8, 16} minimising padded layers x (per-pair cost + per-station overhead / TZ)
-    const double c8 = std::ceil(nz / 8.0) * 8 * (7.0 + 10.0 / 8);
-    const double c16 = std::ceil(nz / 16.0) * 16 * (7.0 + 10.0 / 16);
-    return (c16 <= c8) ? 16 : 8;
+    if (GRAV_MA_TZ == 8 || GRAV_MA_TZ == 12 || GRAV_MA_TZ == 15 || GRAV_MA_TZ == 16) return GRAV_MA_TZ;
+    // TZ in {8, 12, 15, 16} minimising (padded layers) x (measured time per layer
+    // slot, relative): 8 -> 1.018, 12 -> 0.990, 15 -> 1.000, 16 -> 1.070
+    // (B300, 210 x 210 x 75 cells x 178,797 stations, 2.03 GHz).
+    const int tzs[4] = {8, 12, 15, 16};
+    const double per_slot[4] = {1.018, 0.990, 1.000, 1.070};
+    int best = 8;
+    double bc = 1e300;
+    for (int q = 0; q < 4; ++q) {
+        const double c = std::ceil(nz / (double)tzs[q]) * tzs[q] * per_slot[q];
+        if (c < bc) { bc = c; best = tzs[q]; }
+    }
+    return best;
 }
 
 }  // namespace
@@ -549,7 +723,7 @@ int adj_tz(int nz) {
 // Plan-time sizing and device set-up of the mixed path.  Allocations come from
 // the plan's arena (see api.cu, which calls mixed_scratch_bytes first).
 struct MixedSizes {
-    int cols_per_chunk, nchunk, tz, ngz, nschunk;
+    int cols_per_chunk, nchunk, tz, ngz, nschunk, bc;
     int64_t schunk_len;
     size_t cub_temp;
     int nbins;
@@ -565,13 +739,31 @@ static MixedSizes mixed_sizes(const grav_plan *p) {
     int nchunk = (int)std::min<int64_t>(std::max<int64_t>(1, (target + tiles - 1) / tiles), std::max(1, ncol / 16));
     z.cols_per_chunk = (ncol + nchunk - 1) / nchunk;
     z.nchunk = (ncol + z.cols_per_chunk - 1) / z.cols_per_chunk;
-    z.tz = adj_tz(p->nz);
+    // broadcast layout when the cells alone fill the GPU (>= 2 CTAs per SM);
+    // station chunks then add waves (>= 4) to trim the tail
+    const int tz_bc = adj_tz_bc(p->nz);
+    const int64_t slots = 148LL * 2;
+    const int64_t bc_ctas = (int64_t)((ncol + kAbWarps * 32 - 1) / (kAbWarps * 32)) * ((p->nz + tz_bc - 1) / tz_bc);
+    z.bc = (GRAV_AB_FORCE >= 0) ? GRAV_AB_FORCE : (bc_ctas >= slots ? 1 : 0);
+    // run-time override of the layout choice: GRAV_ADJOINT_LAYOUT=broadcast|shuffle|auto
+    if (const char *env = std::getenv("GRAV_ADJOINT_LAYOUT")) {
+        if (std::strcmp(env, "broadcast") == 0) z.bc = 1;
+        else if (std::strcmp(env, "shuffle") == 0) z.bc = 0;
+    }
+    z.tz = z.bc ? tz_bc : adj_tz(p->nz);
     z.ngz = (p->nz + z.tz - 1) / z.tz;
-    const int64_t groups_ctas = ((int64_t)ncol * z.ngz + kMaWarps - 1) / kMaWarps;
-    int64_t nsch = std::max<int64_t>(1, (148LL * 8 + groups_ctas - 1) / groups_ctas);
-    nsch = std::min<int64_t>(nsch, (p->N + kMaStage - 1) / kMaStage);
+    int64_t nsch, stage;
+    if (z.bc) {
+        nsch = std::max<int64_t>(1, (4 * slots + bc_ctas - 1) / bc_ctas);
+        stage = kAbStage;
+    } else {
+        const int64_t groups_ctas = ((int64_t)ncol * z.ngz + kMaWarps - 1) / kMaWarps;
+        nsch = std::max<int64_t>(1, (148LL * 8 + groups_ctas - 1) / groups_ctas);
+        stage = kMaStage;
+    }
+    nsch = std::min<int64_t>(nsch, (p->N + stage - 1) / stage);
     int64_t len = (p->N + nsch - 1) / nsch;
-    len = (len + kMaStage - 1) / kMaStage * kMaStage;   // keeps every chunk start 16-byte aligned
+    len = (len + stage - 1) / stage * stage;   // keeps every chunk start 16-byte aligned
     z.schunk_len = len;
     z.nschunk = (int)((p->N + len - 1) / len);
     z.nbins = p->ng.nbx * p->ng.nby;
@@ -660,6 +852,7 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
     p->m_adj_ngz = z.ngz;
     p->m_adj_nschunk = z.nschunk;
     p->m_adj_schunk_len = (int)z.schunk_len;
+    p->m_adj_bc = z.bc;
     p->m_part = (double *)take(p, 8ull * z.nchunk * p->N);
     p->m_apart = (double *)take(p, 8ull * z.nschunk * p->M);
     p->dG = (double *)take(p, 8ull * p->N * p->ng.slots);
@@ -741,14 +934,33 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
     const size_t smem = 128 + 2ull * kMaStage * (sizeof(float4) + sizeof(float2));
     note_launches(1);
     stage_begin(p, kStageAdjMain, s);
-    if (p->m_adj_tz == 16) {
-        cudaFuncSetAttribute(k_madj<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        k_madj<16><<<grid, kMaWarps * 32, smem, s>>>(p->mg, p->st32, p->stz, p->m_adj_ngz, p->m_adj_schunk_len,
-                                                     p->m_apart, p->ctx->d_status);
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        kern<<<grid, kMaWarps * 32, smem, s>>>(p->mg, p->st32, p->stz, p->m_adj_ngz, p->m_adj_schunk_len,
+                                              p->m_apart, p->ctx->d_status);
+    };
+    if (p->m_adj_bc) {
+        const int cblocks = (p->mg.ncol + kAbWarps * 32 - 1) / (kAbWarps * 32);
+        dim3 gbc((unsigned)(cblocks * p->m_adj_ngz), p->m_adj_nschunk);
+        const size_t sm_bc = 128 + 2ull * kAbStage * (sizeof(float4) + sizeof(float2));
+        auto gob = [&](auto kern) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            kern<<<gbc, kAbWarps * 32, sm_bc, s>>>(p->mg, p->st32, p->stz, p->m_adj_ngz, p->m_adj_schunk_len,
+                                                  p->m_apart, p->ctx->d_status);
+        };
+        switch (p->m_adj_tz) {
+            case 20: gob(k_madj_bc<20>); break;
+            case 16: gob(k_madj_bc<16>); break;
+            case 12: gob(k_madj_bc<12>); break;
+            default: gob(k_madj_bc<8>); break;
+        }
     } else {
-        cudaFuncSetAttribute(k_madj<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        k_madj<8><<<grid, kMaWarps * 32, smem, s>>>(p->mg, p->st32, p->stz, p->m_adj_ngz, p->m_adj_schunk_len,
-                                                    p->m_apart, p->ctx->d_status);
+        switch (p->m_adj_tz) {
+            case 16: go(k_madj<16>); break;
+            case 15: go(k_madj<15>); break;
+            case 12: go(k_madj<12>); break;
+            default: go(k_madj<8>); break;
+        }
     }
     stage_end(p, kStageAdjMain, s);
     const int64_t lz = std::min(p->ng.bz, p->nz);

@@ -178,9 +178,17 @@ def test_datainv_with_reference_model(g):
 
 # ---------------------------------------------------------------- mixed ----
 
+@pytest.fixture(params=["shuffle", "broadcast"])
+def adjoint_layout(request, monkeypatch):
+    """Both mixed far-field adjoint layouts (lanes split stations + warp-shuffle
+    reduction; lanes own cells + broadcast stations), chosen at plan creation."""
+    monkeypatch.setenv("GRAV_ADJOINT_LAYOUT", request.param)
+    return request.param
+
+
 @pytest.mark.parametrize("shape,cell,h,seed", [((30, 26, 12), 40.0, 10.0, 1), ((17, 23, 9), 25.0, 3.0, 2),
                                                ((41, 37, 15), 100.0, 30.0, 3)])
-def test_mixed_forward_adjoint_vs_oracle(g, shape, cell, h, seed):
+def test_mixed_forward_adjoint_vs_oracle(g, shape, cell, h, seed, adjoint_layout):
     nx, ny, nz = shape
     mesh = synth.uniform_mesh(nx, ny, nz, cell, cell, cell)
     rng = np.random.Generator(np.random.PCG64(40 + seed))
@@ -227,7 +235,7 @@ def _mixed_definition(mesh, sv, G, cell, k):
     return np.where(R < k * cell, G, far)
 
 
-def test_mixed_with_window_covering_mesh_is_exact(g):
+def test_mixed_with_window_covering_mesh_is_exact(g, adjoint_layout):
     """If every cell lies inside every station's window the mixed operator is
     the exact FP64 operator up to the FP32 rounding of the far-field terms,
     which still run for every cell and cancel against their FP64 correction
@@ -245,7 +253,7 @@ def test_mixed_with_window_covering_mesh_is_exact(g):
     assert _rel(a, a_ref) <= 1e-6
 
 
-def test_mixed_diag_and_dot(g):
+def test_mixed_diag_and_dot(g, adjoint_layout):
     mesh = synth.uniform_mesh(25, 21, 10, 50.0, 50.0, 50.0)
     rng = np.random.Generator(np.random.PCG64(60))
     sv = synth.Survey(rng.uniform(0, 1250, 300), rng.uniform(0, 1050, 300), -rng.uniform(1, 20, 300))
