@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip fp64/inversion/cpu extras")
     ap.add_argument("--cpu-stations", type=int, default=16)
     ap.add_argument("--cpu-cells", type=int, default=48)
+    ap.add_argument("--serve", action="store_true",
+                    help="replay the seeded 256-job Poisson request stream through the serving scheduler")
+    ap.add_argument("--serve-jobs", type=int, default=256)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-slots", type=int, default=4)
     return ap.parse_args()
 
 
@@ -161,6 +166,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def measured_traffic(kernel_name, args):
+    """DRAM bytes per launch of `kernel_name` from the committed full-size ncu
+    capture, if it was taken on this workload and the kernel sources are
+    unchanged since (sha256 recorded with the capture)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic_paper_210x210x75_mixed.json")
+    if args.workload != "paper_210x210x75" or args.precision != "mixed" or not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    if rec.get("near_cells") != args.near_cells:
+        return None
+    src = b"".join(open(os.path.join(ROOT, f), "rb").read() for f in rec["source_files"])
+    if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+        return None
+    k = rec["kernels"].get(kernel_name.replace(" ", ""))
+    return None if k is None else k["dram_read_bytes"] + k["dram_write_bytes"]
+
+
 def flush_l2(buf):
     buf.add_(1.0)
 
@@ -261,12 +284,15 @@ def run_ours(args):
     pairs_launch = float(N) * M
     achieved = pairs_launch / (dms / max(dn, 1) * 1e-3) / 1e9
     peak = 148 * MUFU_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e9
-    kernel_name = {"mixed": {"fwd_main": "k_mfwd", "adj_main": "k_madj"},
-                   "fp64": {"fwd_main": "k_fwd64", "adj_main": "k_adj64"}}[args.precision][dom]
+    desc = plan.describe()
+    kernel_name = desc["fwd_kernel"] if dom == "fwd_main" else desc["adj_kernel"]
+    traffic = measured_traffic(kernel_name, args)
     roof = {"bound": "alu", "kernel": kernel_name, "achieved": achieved, "peak": peak,
             "unit": "G rsqrt/s (MUFU, 1 per pair)" if args.precision == "mixed" else "G node-evals/s",
-            "frac": achieved / peak, "traffic": None,
-            "peak_basis": f"148 SMs x {MUFU_PER_CLK_SM} MUFU/clk x {SM_MAX_MHZ:.0f} MHz",
+            "frac": achieved / peak, "traffic": traffic,
+            "traffic_note": "ncu dram__bytes_read+write per launch at full size (profiles/), null if the "
+                            "kernel sources changed since the capture",
+            "peak_basis": f"148 SMs x {MUFU_PER_CLK_SM} MUFU/clk x {SM_MAX_MHZ:.0f} MHz (MUFU unit count x max SM clock)",
             "stage_ms_per_launch": {k: (v[0] / max(v[1], 1)) for k, v in stages.items()}}
 
     line = {
@@ -340,10 +366,68 @@ def extras(args, g, torch, wl, plan, d, line):
     line["inversion_to_1e-6"] = {"workload": "block_20x20x10", **inv}
 
 
+def run_serve(args):
+    """Request-loop benchmark: jobs arrive at their seeded Poisson times (rate
+    args.serve_rate), each a forward or an inversion (mixed precision, CG
+    tolerance 1e-4 as in the paper's inner CG) on its own mesh and survey;
+    latency = completion - submission (steady clock inside libgrav)."""
+    import torch
+    import paper_2602_03857_b300 as g
+    torch.cuda.set_device(0)
+    jobs = synth.serving_jobs(args.serve_jobs, args.serve_rate, seed=0)
+    prepared = []
+    for j in jobs:
+        S = g.Survey(j.survey.x, j.survey.y, j.survey.z)
+        m = torch.tensor(j.m, dtype=torch.float64, device="cuda")
+        if j.kind == "forward":
+            inp, out = m, torch.empty(j.survey.n, dtype=torch.float64, device="cuda")
+        else:
+            inp = g.forward(m, j.mesh, S, precision="mixed")
+            out = torch.empty(j.mesh.ncells, dtype=torch.float64, device="cuda")
+        prepared.append((j, S, inp, out))
+    torch.cuda.synchronize()
+    ctx = g.Context(0)
+    ctx.serve_config(args.serve_slots)
+    opts = dict(precision="mixed", tol=1e-4, max_iter=500)
+    t0 = time.perf_counter()
+    ids = []
+    for j, S, inp, out in prepared:
+        delay = j.arrival_s - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(ctx.submit(j.kind, j.mesh, S, inp, out, **opts))
+    results = [ctx.wait(i, 3600.0) for i in ids]
+    wall = time.perf_counter() - t0
+    lat, lat_f, lat_i, busy = [], [], [], []
+    pairs = 0.0
+    for (j, S, inp, out), i in zip(prepared, ids):
+        ts, tb, te = ctx.job_times(i)
+        lat.append(te - ts)
+        (lat_f if j.kind == "forward" else lat_i).append(te - ts)
+        busy.append((tb, te))
+        pairs += float(j.survey.n) * j.mesh.ncells
+    ctx.close()
+    pct = lambda v, q: float(np.percentile(np.array(v), q)) if v else None
+    line = {"metric": "serving latency and throughput (mixed precision)", "jobs": len(jobs),
+            "arrival_rate_hz": args.serve_rate, "slots": args.serve_slots, "wall_s": wall,
+            "throughput_jobs_per_s": len(jobs) / wall,
+            "offered_load_jobs_per_s": len(jobs) / max(j.arrival_s for j in jobs),
+            "p50_latency_s": pct(lat, 50), "p99_latency_s": pct(lat, 99),
+            "forward": {"n": len(lat_f), "p50_s": pct(lat_f, 50), "p99_s": pct(lat_f, 99)},
+            "invert": {"n": len(lat_i), "p50_s": pct(lat_i, 50), "p99_s": pct(lat_i, 99)},
+            "results": {str(k): results.count(k) for k in sorted(set(results))},
+            "pairs_per_forward_pass_total": pairs, "data": "synthetic",
+            "config": {"workload": "serving mix: 50k-500k cubic prisms (25-100 m), 1k-20k stations, "
+                                   "block/dyke models, forward or inversion 50/50", "tol": 1e-4}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -186,6 +186,57 @@ size_t grav_plan_bytes(const grav_plan *plan);
  * enqueued on `stream`. */
 int grav_plan_destroy(grav_plan *plan, grav_stream_t stream);
 
+/* ---- serving: continuous admission of jobs ------------------------------- */
+/* A context runs a scheduler with K slots (default 4, or GRAV_SERVE_SLOTS in
+ * the environment, or grav_serve_config before the first submit).  Each slot
+ * is a host worker thread with its own non-blocking CUDA stream.  Submitted
+ * jobs wait in a FIFO queue; a free slot takes the head job as soon as the
+ * job's device footprint (its plan, plus the CG vectors for an inversion)
+ * fits in the context's HBM budget next to the jobs already running.  Jobs
+ * therefore start while others are still on the GPU and their kernels
+ * overlap on the device.  Each job builds its own plan, and every kernel is
+ * deterministic, so a job's result is bitwise the same alone and in a mix.
+ * The serving entry points are the request-loop counterpart of the paper's
+ * single inversion run (Section 3.1); the paper has no serving layer. */
+#define GRAV_JOB_FORWARD   0   /* output d = G input */
+#define GRAV_JOB_INVERT    1   /* output m from data `input`, as grav_datainv_solve */
+
+#define GRAV_JOB_QUEUED    0
+#define GRAV_JOB_RUNNING   1
+#define GRAV_JOB_DONE      2   /* finished; grav_wait returns GRAV_OK or GRAV_ENOTCONVERGED */
+#define GRAV_JOB_FAILED    3
+#define GRAV_JOB_CANCELED  4
+
+typedef struct {
+    int kind;                  /* GRAV_JOB_FORWARD or GRAV_JOB_INVERT */
+    grav_mesh mesh;            /* HOST edges, copied at submit */
+    grav_survey survey;        /* DEVICE arrays: must stay valid and unchanged until the job finishes */
+    const double *input;       /* DEVICE: m (FORWARD, M doubles) or d (INVERT, n doubles) */
+    const double *m_ref;       /* DEVICE, M doubles, or NULL (INVERT only) */
+    double *output;            /* DEVICE: d (FORWARD, n doubles) or m (INVERT, M doubles) */
+    grav_options opt;          /* copied at submit */
+} grav_job;
+
+/* Sets the number of slots (1..64); GRAV_EBUSY once the scheduler has started. */
+int grav_serve_config(grav_ctx *ctx, int slots);
+/* Validates and queues a job (never waits for the GPU).  GRAV_EINVAL for a bad
+ * descriptor, GRAV_ENOMEM if the job alone exceeds the context budget,
+ * GRAV_EBUSY if the queue is full.  *job_id receives the job's id. */
+int grav_submit(grav_ctx *ctx, const grav_job *job, uint64_t *job_id);
+/* Non-blocking: *state (GRAV_JOB_*) and, for inversions, the solve info so far. */
+int grav_poll(grav_ctx *ctx, uint64_t job_id, int *state, grav_solve_info *info);
+/* Waits at most timeout_s for the job to finish; returns the job's result
+ * (GRAV_OK, GRAV_ENOTCONVERGED, GRAV_ECANCELED or the error that failed it),
+ * or GRAV_ETIMEDOUT. */
+int grav_wait(grav_ctx *ctx, uint64_t job_id, double timeout_s);
+/* Cancels a queued job at once, or asks a running inversion to stop at its
+ * next CG check (a running forward job completes). */
+int grav_cancel(grav_ctx *ctx, uint64_t job_id);
+/* Steady-clock times (seconds) of submission, start and end of a job (0 if not yet). */
+int grav_job_times(grav_ctx *ctx, uint64_t job_id, double *t_submit, double *t_start, double *t_end);
+/* Forgets a finished job's record (GRAV_EBUSY while queued or running). */
+int grav_job_release(grav_ctx *ctx, uint64_t job_id);
+
 /* ---- forward product without device allocation --------------------------- */
 /* The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory while they run (a framework whose allocator
@@ -217,6 +268,12 @@ int grav_forward_fp64_noalloc(const grav_mesh *mesh, const grav_survey *survey, 
 /* Total number of CUDA kernels this library has launched in the process
  * (all contexts).  Used to attribute device work to libgrav in benchmarks. */
 uint64_t grav_launch_count(void);
+
+/* Writes a one-line JSON description of the plan's launch configuration
+ * (kernels chosen, chunking, near-field box, device bytes) into buf (HOST,
+ * len bytes, NUL-terminated, truncated if short).  Returns the length needed
+ * including the NUL, or a negative GRAV_E* code. */
+int grav_plan_describe(const grav_plan *plan, char *buf, size_t len);
 
 /* Stage timing of one plan with CUDA events on the launching stream.
  * enable != 0 starts recording the device time of the plan's main kernels

@@ -39,6 +39,8 @@ GRAV_ENOTFOUND = -7
 GRAV_EBUSY = -8
 GRAV_FP64 = 0
 GRAV_MIXED = 1
+GRAV_JOB_FORWARD, GRAV_JOB_INVERT = 0, 1
+JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "canceled"}
 PRECISIONS = {"fp64": GRAV_FP64, "mixed": GRAV_MIXED}
 
 _P = ctypes.c_void_p
@@ -58,6 +60,11 @@ class grav_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("z0", ctypes.c_double), ("lambda_scale", ctypes.c_double),
                 ("lambda_", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("near_cells", ctypes.c_double), ("timeout_s", ctypes.c_double)]
+
+
+class grav_job(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("mesh", grav_mesh), ("survey", grav_survey), ("input", _P),
+                ("m_ref", _P), ("output", _P), ("opt", grav_options)]
 
 
 class grav_solve_info(ctypes.Structure):
@@ -97,12 +104,22 @@ _sig("grav_plan_destroy", _i, [_vp, _vp])
 _sig("grav_launch_count", ctypes.c_uint64, [])
 _sig("grav_plan_timing", _i, [_vp, _i, _D, ctypes.POINTER(ctypes.c_int64)])
 _sig("grav_bench_pipes", _i, [_i, _D])
+_sig("grav_plan_describe", _i, [_vp, ctypes.c_char_p, ctypes.c_size_t])
+_sig("grav_serve_config", _i, [_vp, _i])
+_sig("grav_submit", _i, [_vp, ctypes.POINTER(grav_job), ctypes.POINTER(ctypes.c_uint64)])
+_sig("grav_poll", _i, [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(grav_solve_info)])
+_sig("grav_wait", _i, [_vp, ctypes.c_uint64, ctypes.c_double])
+_sig("grav_cancel", _i, [_vp, ctypes.c_uint64])
+_sig("grav_job_times", _i, [_vp, ctypes.c_uint64, _D, _D, _D])
+_sig("grav_job_release", _i, [_vp, ctypes.c_uint64])
 
 EXPORTED = [
     "grav_options_default", "grav_version", "grav_ctx_create", "grav_ctx_destroy", "grav_last_error",
     "grav_ctx_sync", "grav_forward", "grav_adjoint", "grav_diag", "grav_datainv_solve", "grav_plan_create",
     "grav_plan_forward", "grav_plan_adjoint", "grav_plan_bytes", "grav_plan_destroy",
-    "grav_launch_count", "grav_plan_timing", "grav_bench_pipes",
+    "grav_launch_count", "grav_plan_timing", "grav_bench_pipes", "grav_plan_describe",
+    "grav_serve_config", "grav_submit", "grav_poll", "grav_wait", "grav_cancel", "grav_job_times",
+    "grav_job_release",
 ]
 
 STAGES = ("fwd_main", "adj_main", "fwd_near", "adj_near")
@@ -166,6 +183,52 @@ class Context:
         if getattr(self, "h", None):
             _lib.grav_ctx_destroy(self.h)
             self.h = None
+            self._jobs = {}
+
+    # ---- serving -----------------------------------------------------------
+    def serve_config(self, slots: int):
+        self.check(_lib.grav_serve_config(self.h, int(slots)))
+
+    def submit(self, kind: str, mesh, survey, inp, out, m_ref=None, **opts) -> int:
+        """Queue a job ("forward": out = G inp; "invert": out = m from data inp).
+        The tensors are kept alive by the context until the job is released."""
+        mesh, survey = Mesh.of(mesh), Survey.of(survey)
+        j = grav_job()
+        j.kind = GRAV_JOB_FORWARD if kind == "forward" else GRAV_JOB_INVERT
+        j.mesh, j.survey = mesh.c, survey.c
+        j.input, j.output = inp.data_ptr(), out.data_ptr()
+        j.m_ref = m_ref.data_ptr() if m_ref is not None else None
+        j.opt = options(**opts)
+        jid = ctypes.c_uint64(0)
+        self.check(_lib.grav_submit(self.h, ctypes.byref(j), ctypes.byref(jid)))
+        if not hasattr(self, "_jobs"):
+            self._jobs = {}
+        self._jobs[jid.value] = (mesh, survey, inp, out, m_ref)
+        return jid.value
+
+    def poll(self, job_id: int):
+        st = ctypes.c_int(0)
+        info = grav_solve_info()
+        self.check(_lib.grav_poll(self.h, ctypes.c_uint64(job_id), ctypes.byref(st), ctypes.byref(info)))
+        return JOB_STATES[st.value], {"iters": info.iters, "converged": bool(info.converged),
+                                       "true_rel_res": info.true_rel_res, "lambda": info.lambda_}
+
+    def wait(self, job_id: int, timeout_s: float = 600.0) -> int:
+        """Job result code (GRAV_OK, GRAV_ENOTCONVERGED, GRAV_ECANCELED, ...) or GRAV_ETIMEDOUT."""
+        return int(_lib.grav_wait(self.h, ctypes.c_uint64(job_id), float(timeout_s)))
+
+    def cancel(self, job_id: int):
+        self.check(_lib.grav_cancel(self.h, ctypes.c_uint64(job_id)))
+
+    def job_times(self, job_id: int):
+        a, b, c = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+        self.check(_lib.grav_job_times(self.h, ctypes.c_uint64(job_id), ctypes.byref(a), ctypes.byref(b),
+                                       ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def release(self, job_id: int):
+        self.check(_lib.grav_job_release(self.h, ctypes.c_uint64(job_id)))
+        getattr(self, "_jobs", {}).pop(job_id, None)
 
 
 _contexts = {}
@@ -341,6 +404,15 @@ class Plan:
         self.ctx.check(_lib.grav_plan_adjoint(self.h, r.data_ptr(), g.data_ptr(), int(bool(depth_weighted)),
                                               _stream(stream)))
         return g
+
+    def describe(self) -> dict:
+        """Launch configuration chosen for this plan (kernels, chunking, bytes)."""
+        import json
+        buf = ctypes.create_string_buffer(1024)
+        rc = _lib.grav_plan_describe(self.h, buf, 1024)
+        if rc < 0:
+            raise GravError(rc, _lib.grav_last_error(None).decode())
+        return json.loads(buf.value.decode())
 
     def timing(self, enable: bool = True, read: bool = True):
         """Start/stop stage timing; returns {stage: (ms, count)} recorded since the last read."""

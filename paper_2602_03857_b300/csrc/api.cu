@@ -218,8 +218,8 @@ int plan_diag(grav_plan *p, double *diag, cudaStream_t s) {
     return e == cudaSuccess ? GRAV_OK : cuda_error(p->ctx, e, "diag launch");
 }
 
-int plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const grav_options &o,
-                grav_plan **out, cudaStream_t s) {
+int plan_prepare(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const grav_options &o,
+                 grav_plan **out) {
     if (!out) return set_error(ctx, GRAV_EINVAL, "out is NULL");
     *out = nullptr;
     if (!mesh || !survey) return set_error(ctx, GRAV_EINVAL, "mesh or survey is NULL");
@@ -287,7 +287,23 @@ int plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey,
         p->ng.nbx = p->nx + p->ng.bx - 1;
         p->ng.nby = p->ny + p->ng.by - 1;
         bytes += mixed_scratch_bytes(p);
+        if (near_setup_warps(p) < 1) {
+            delete p;
+            return set_error(ctx, GRAV_EINVAL, "near_cells window too large for this mesh (shared-memory limit)");
+        }
     }
+    p->bytes = bytes;
+    *out = p;
+    return GRAV_OK;
+}
+
+// Allocates the prepared plan's arena from the context pool (stream-ordered)
+// and enqueues its set-up.  On failure the plan is deleted.
+int plan_allocate(grav_plan *p, cudaStream_t s) {
+    grav_ctx *ctx = p->ctx;
+    const grav_options &o = p->opt;
+    const size_t bytes = p->bytes;
+    int rc = GRAV_OK;
     if (ctx->hbm_used.load() + bytes > ctx->hbm_budget) {
         delete p;
         return set_error(ctx, GRAV_ENOMEM, "plan needs %.3f GB; context budget %.3f GB, %.3f GB in use", bytes / 1e9,
@@ -300,7 +316,6 @@ int plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey,
         return cuda_error(ctx, e, "plan allocation");
     }
     ctx->hbm_used += bytes;
-    p->bytes = bytes;
     p->arena.base = (char *)base;
     p->arena.size = bytes;
     p->d_xe = (double *)p->arena.take(8ull * (p->nx + 1));
@@ -325,15 +340,13 @@ int plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey,
         p->u = (double *)p->arena.take((size_t)p->Nn * 8);
         if (!p->arena.overflow) fp64_setup(p, s);
     } else {
-        rc = near_setup_warps(p) < 1 ? GRAV_EINVAL : mixed_setup(p, s);
+        rc = mixed_setup(p, s);
     }
     if (rc || p->arena.overflow) {
         cudaFreeAsync(base, s);
         ctx->hbm_used -= bytes;
         delete p;
-        if (rc == GRAV_EINVAL)
-            return set_error(ctx, GRAV_EINVAL, "near_cells window too large for this mesh (shared-memory limit)");
-        return set_error(ctx, GRAV_EDEVICE, "internal: plan arena overflow");
+        return set_error(ctx, GRAV_EDEVICE, "internal: plan set-up failed (arena overflow or bad window)");
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -342,9 +355,21 @@ int plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey,
         delete p;
         return cuda_error(ctx, e, "plan set-up");
     }
+    return GRAV_OK;
+}
+
+int plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const grav_options &o,
+                grav_plan **out, cudaStream_t s) {
+    grav_plan *p = nullptr;
+    int rc = plan_prepare(ctx, mesh, survey, o, &p);
+    if (rc) return rc;
+    rc = plan_allocate(p, s);
+    if (rc) return rc;
     *out = p;
     return GRAV_OK;
 }
+
+size_t solve_bytes(const grav_plan *p) { return 8ull * (5 * p->N + p->M + kDotBlocks + kSCount) + 8 * 256; }
 
 void plan_destroy(grav_plan *p, cudaStream_t s) {
     if (!p) return;
@@ -355,15 +380,19 @@ void plan_destroy(grav_plan *p, cudaStream_t s) {
 }
 
 int read_status(grav_ctx *ctx, cudaStream_t s, double timeout_s) {
-    cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    // one pinned host mirror per host thread (serving slots read concurrently)
+    thread_local int *h_status = nullptr;
+    if (!h_status && cudaMallocHost((void **)&h_status, 64) != cudaSuccess) return cuda_error(ctx, cudaGetLastError(), "pinned status");
+    *h_status = 0;
+    cudaMemcpyAsync(h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaEvent_t ev;
     cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     cudaEventRecord(ev, s);
     int rc = wait_event(ctx, ev, timeout_s, "stream synchronisation");
     cudaEventDestroy(ev);
     if (rc) return rc;
-    if (*ctx->h_status != 0) {
-        const int st = *ctx->h_status;
+    if (*h_status != 0) {
+        const int st = *h_status;
         cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
         return set_error(ctx, GRAV_EDEVICE, "device status word 0x%x (bounded device wait expired)", st);
     }
@@ -380,7 +409,7 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
     const grav_options &o = p->opt;
     const double t0 = now_s();
     const int64_t N = p->N, M = p->M;
-    const size_t bytes = 8ull * (5 * N + M + kDotBlocks + kSCount) + 8 * 256;
+    const size_t bytes = solve_bytes(p);
     if (ctx->hbm_used.load() + bytes > ctx->hbm_budget) return set_error(ctx, GRAV_ENOMEM, "solve vectors exceed budget");
     char *base = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync((void **)&base, bytes, ctx->pool, s);
@@ -637,6 +666,36 @@ int grav_plan_adjoint(grav_plan *p, const double *r, double *gtr, int depth_weig
 size_t grav_plan_bytes(const grav_plan *p) { return p ? p->bytes : 0; }
 
 uint64_t grav_launch_count(void) { return g_launches.load(); }
+
+int grav_plan_describe(const grav_plan *p, char *buf, size_t len) {
+    if (!p) return set_error(nullptr, GRAV_EINVAL, "plan is NULL");
+    char tmp[1024];
+    int n;
+    if (p->opt.precision == GRAV_FP64) {
+        n = snprintf(tmp, sizeof(tmp),
+                     "{\"precision\": \"fp64\", \"fwd_kernel\": \"k_fwd64<2>\", \"adj_kernel\": \"k_adj64<8>\", "
+                     "\"fwd_row_chunks\": %d, \"adj_station_chunks\": %d, \"bytes\": %zu}",
+                     p->f64_nchunk, p->a64_nschunk, p->bytes);
+    } else {
+        char adj[64];
+        if (p->m_adj_bc)
+            snprintf(adj, sizeof(adj), "k_madj_bc<%d, %d>", p->m_adj_tz, mixed_adj_last_group(p));
+        else
+            snprintf(adj, sizeof(adj), "k_madj<%d>", p->m_adj_tz);
+        n = snprintf(tmp, sizeof(tmp),
+                     "{\"precision\": \"mixed\", \"fwd_kernel\": \"k_mfwd<8>\", \"adj_kernel\": \"%s\", "
+                     "\"adj_layout\": \"%s\", \"fwd_column_chunks\": %d, \"adj_station_chunks\": %d, "
+                     "\"near_cells\": %g, \"near_box\": [%d, %d, %d], \"bytes\": %zu}",
+                     adj, p->m_adj_bc ? "broadcast" : "shuffle", p->m_fwd_nchunk, p->m_adj_nschunk,
+                     p->opt.near_cells, p->ng.bx, p->ng.by, p->ng.bz, p->bytes);
+    }
+    if (n < 0) return set_error(p->ctx, GRAV_EDEVICE, "describe failed");
+    if (buf && len > 0) {
+        std::strncpy(buf, tmp, len - 1);
+        buf[len - 1] = 0;
+    }
+    return n + 1;
+}
 
 int grav_plan_timing(grav_plan *p, int enable, double *ms, int64_t *counts) {
     if (!p) return set_error(nullptr, GRAV_EINVAL, "plan is NULL");

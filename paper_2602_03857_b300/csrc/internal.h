@@ -144,6 +144,10 @@ int cuda_error(grav_ctx *ctx, cudaError_t e, const char *what);
 // plan internals (api.cu), used by the solver and the serving scheduler
 int plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const grav_options &o,
                 grav_plan **out, cudaStream_t s);
+int plan_prepare(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const grav_options &o,
+                 grav_plan **out);                      // validation + sizing, no device work
+int plan_allocate(grav_plan *p, cudaStream_t s);        // deletes p on failure
+size_t solve_bytes(const grav_plan *p);
 void plan_destroy(grav_plan *p, cudaStream_t s);
 int plan_forward_ex(grav_plan *p, const double *m, double *d, const double *add, double add_scale, cudaStream_t s);
 int plan_adjoint_ex(grav_plan *p, const double *r, double *out, int depth_weighted, const double *add,
@@ -188,6 +192,7 @@ void launch_mixed_adj_finish(const grav_plan *p, const double *r, int depth_weig
                              double *out, cudaStream_t s);
 void launch_mixed_diag(const grav_plan *p, double *diag, cudaStream_t s);
 size_t mixed_scratch_bytes(const grav_plan *p);
+int mixed_adj_last_group(const grav_plan *p);
 
 // vector kernels (cg_kernels.cu)
 void launch_dot(const double *a, const double *b, int64_t n, double *partials, double *out, cudaStream_t s);

@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(kMaWarps * 32, MaMinBlocks<TZ>::value) k_madj(
 // of one column (lanes = consecutive columns, one layer group per CTA), the
 // stations of a TMA-staged chunk are read by all lanes at once (shared-memory
 // broadcast), and every lane accumulates its own cells: no cross-lane
-// reduction.  Sums run in FP32 over 64 stations and are folded into FP64
+// reduction.  Sums run in FP32 over 128 stations and are folded into FP64
 // accumulators (compensation by wider precision).
 // ---------------------------------------------------------------------------
 #ifndef GRAV_AB_MINB
@@ -355,22 +355,17 @@ __global__ void __launch_bounds__(kMaWarps * 32, MaMinBlocks<TZ>::value) k_madj(
 #endif
 constexpr int kAbWarps = 8;
 constexpr int kAbStage = 1024;
-constexpr int kAbFold = 64;
+constexpr int kAbFold = 128;
 
 template <int TZ>
-__global__ void __launch_bounds__(kAbWarps * 32, GRAV_AB_MINB) k_madj_bc(MixedGeo g, const float4 *__restrict__ st32,
-                                                                        const float2 *__restrict__ stz, int ngz,
-                                                                        int64_t schunk_len,
-                                                                        double *__restrict__ apart, int *status) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+__device__ __forceinline__ void madj_bc_body(const MixedGeo &g, const float4 *__restrict__ st32,
+                                             const float2 *__restrict__ stz, int l0, int cb, int64_t schunk_len,
+                                             double *__restrict__ apart, int *status, unsigned char *smem_raw) {
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
     int *flag = reinterpret_cast<int *>(smem_raw + 16);
     float4 *sxy = reinterpret_cast<float4 *>(smem_raw + 128);
     float2 *szr = reinterpret_cast<float2 *>(smem_raw + 128 + 2 * kAbStage * sizeof(float4));
 
-    const int cblocks = (g.ncol + kAbWarps * 32 - 1) / (kAbWarps * 32);
-    const int cb = blockIdx.x % cblocks;
-    const int l0 = (blockIdx.x / cblocks) * TZ;
     const int col = cb * (kAbWarps * 32) + threadIdx.x;
     const bool cvalid = col < g.ncol;
     const int cc = cvalid ? col : 0;
@@ -454,6 +449,23 @@ __global__ void __launch_bounds__(kAbWarps * 32, GRAV_AB_MINB) k_madj_bc(MixedGe
 #pragma unroll
     for (int t = 0; t < TZ; ++t)
         if (l0 + t < g.nz) apart[(int64_t)blockIdx.y * g.ncol * (int64_t)g.nz + col + (int64_t)g.ncol * (l0 + t)] = acc[t];
+}
+
+// Layer groups 0 .. ngz-2 hold TZ layers, the last group TZL (TZL <= TZ, a
+// multiple of 4 covering the remaining layers), so at most 3 padded layers.
+template <int TZ, int TZL>
+__global__ void __launch_bounds__(kAbWarps * 32, GRAV_AB_MINB) k_madj_bc(MixedGeo g, const float4 *__restrict__ st32,
+                                                                        const float2 *__restrict__ stz, int ngz,
+                                                                        int64_t schunk_len,
+                                                                        double *__restrict__ apart, int *status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int cblocks = (g.ncol + kAbWarps * 32 - 1) / (kAbWarps * 32);
+    const int cb = blockIdx.x % cblocks;
+    const int grp = blockIdx.x / cblocks;
+    if (TZL == TZ || grp < ngz - 1)
+        madj_bc_body<TZ>(g, st32, stz, grp * TZ, cb, schunk_len, apart, status, smem_raw);
+    else
+        madj_bc_body<TZL>(g, st32, stz, grp * TZ, cb, schunk_len, apart, status, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -572,30 +584,39 @@ __global__ void k_near_fwd(int nx, int ny, int nz, NearGeo ng, int64_t N, const 
 }
 
 // out[k] = sum over stations whose window box holds cell k of dG * r, for the
-// top bz layers; bins visited in fixed order, stations sorted within a bin.
-__global__ void k_near_adj(int nx, int ny, int nz, NearGeo ng, const double *__restrict__ dG,
-                           const int *__restrict__ bin_start, const int *__restrict__ bin_st,
-                           const double *__restrict__ r, double *__restrict__ out) {
-    const int lz = min(ng.bz, nz);
-    const int64_t total = (int64_t)nx * ny * lz;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(k % nx);
-        const int j = (int)((k / nx) % ny);
-        const int l = (int)(k / ((int64_t)nx * ny));
-        double acc = 0.0;
-        for (int bj = j - ng.by + 1; bj <= j; ++bj) {
-            for (int bi = i - ng.bx + 1; bi <= i; ++bi) {
-                const int key = (bi + ng.bx - 1) + ng.nbx * (bj + ng.by - 1);
-                const int p1 = bin_start[key + 1];
-                const int slot = (i - bi) + ng.bx * ((j - bj) + ng.by * l);
-                for (int p = bin_start[key]; p < p1; ++p) {
-                    const int s = bin_st[p];
-                    acc = fma(dG[(int64_t)s * ng.slots + slot], r[s], acc);
-                }
-            }
+// top bz layers.  A warp owns 32 consecutive cells of one row (y) and layer;
+// the stations whose box covers row y have box-origin bins in bin rows
+// y-by+1 .. y, and within one bin row the bins of the 32 columns are
+// consecutive keys, i.e. one contiguous range of the sorted station list.  For
+// each such station the lanes read one box row of dG (consecutive slots:
+// coalesced).  Per cell the stations are visited in (bin row, bin, station)
+// order: deterministic.
+__global__ void __launch_bounds__(256) k_near_adj(int nx, int ny, NearGeo ng, const double *__restrict__ dG,
+                                                  const int *__restrict__ bin_start, const int *__restrict__ bin_st,
+                                                  const int *__restrict__ st_i0, const double *__restrict__ r,
+                                                  double *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    const int l = blockIdx.z;
+    if (y >= ny) return;   // warp-uniform
+    const int tx0 = blockIdx.x * 32;
+    const int x = tx0 + lane;
+    // shifted bin coordinates: sbi = i0 + bx - 1, sbj = j0 + by - 1
+    const int sbi_lo = tx0;
+    const int sbi_hi = min(ng.nbx - 1, tx0 + 31 + ng.bx - 1);
+    double acc = 0.0;
+    for (int sbj = y; sbj <= y + ng.by - 1; ++sbj) {
+        const int b = y - (sbj - (ng.by - 1));   // row of the cell inside the station's box
+        const int p0 = bin_start[sbi_lo + ng.nbx * sbj];
+        const int p1 = bin_start[sbi_hi + ng.nbx * sbj + 1];
+        const int64_t row = (int64_t)ng.bx * (b + (int64_t)ng.by * l);
+        for (int p = p0; p < p1; ++p) {
+            const int s = bin_st[p];
+            const int a = x - st_i0[s];
+            if (a >= 0 && a < ng.bx && x < nx) acc = fma(dG[(int64_t)s * ng.slots + row + a], r[s], acc);
         }
-        out[k] = acc;
     }
+    if (x < nx) out[x + (int64_t)nx * (y + (int64_t)ny * l)] = acc;
 }
 
 // out[k] = (vol * sum_c apart[c][k] + near[k] (top bz layers)) [* w2_l] [+ add[k]]
@@ -685,21 +706,15 @@ Geo make_geo(const grav_plan *p) {
 
 constexpr int kMfColsPerStage = 32;
 
-// Layer-group size of the broadcast adjoint: even TZ (layer pairs) in
-// {8, 12, 16, 20}, minimising (padded layers) x (measured time per layer slot,
-// relative; B300, 210 x 210 x 75 x 178,797 stations): 8 -> 1.10 (estimate),
-// 12 -> 1.157, 16 -> 1.000, 20 -> 1.059.
-int adj_tz_bc(int nz) {
-    if (GRAV_MA_TZ == 8 || GRAV_MA_TZ == 12 || GRAV_MA_TZ == 16 || GRAV_MA_TZ == 20) return GRAV_MA_TZ;
-    const int tzs[4] = {8, 12, 16, 20};
-    const double per_slot[4] = {1.10, 1.157, 1.000, 1.059};
-    int best = 16;
-    double bc = 1e300;
-    for (int q = 0; q < 4; ++q) {
-        const double c = std::ceil(nz / (double)tzs[q]) * tzs[q] * per_slot[q];
-        if (c < bc) { bc = c; best = tzs[q]; }
-    }
-    return best;
+// Layer groups of the broadcast adjoint: 16 layers (8 packed pairs; measured
+// fastest per layer among 8/12/16/20 at 2 CTAs per SM), the last group
+// rounded up to a multiple of 4.  Meshes with fewer than 16 layers use one
+// group of ceil4(nz).
+int adj_tz_bc(int nz) { return nz >= 16 ? 16 : (nz + 3) / 4 * 4; }
+int adj_tzl_bc(int nz) {
+    if (nz < 16) return (nz + 3) / 4 * 4;
+    const int rem = nz - 16 * ((nz + 15) / 16 - 1);
+    return (rem + 3) / 4 * 4;
 }
 
 int adj_tz(int nz) {
@@ -896,6 +911,8 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
     return GRAV_OK;
 }
 
+int mixed_adj_last_group(const grav_plan *p) { return p->m_adj_bc ? adj_tzl_bc(p->nz) : p->m_adj_tz; }
+
 size_t mfwd_smem(const grav_plan *p) { return mfwd_layout(p->mg, kMfColsPerStage).total; }
 
 void launch_mixed_prep_q(const grav_plan *p, const double *m, cudaStream_t s) {
@@ -948,11 +965,20 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
             kern<<<gbc, kAbWarps * 32, sm_bc, s>>>(p->mg, p->st32, p->stz, p->m_adj_ngz, p->m_adj_schunk_len,
                                                   p->m_apart, p->ctx->d_status);
         };
-        switch (p->m_adj_tz) {
-            case 20: gob(k_madj_bc<20>); break;
-            case 16: gob(k_madj_bc<16>); break;
-            case 12: gob(k_madj_bc<12>); break;
-            default: gob(k_madj_bc<8>); break;
+        const int tzl = adj_tzl_bc(p->nz);
+        if (p->m_adj_tz == 16) {
+            switch (tzl) {
+                case 4: gob(k_madj_bc<16, 4>); break;
+                case 8: gob(k_madj_bc<16, 8>); break;
+                case 12: gob(k_madj_bc<16, 12>); break;
+                default: gob(k_madj_bc<16, 16>); break;
+            }
+        } else {
+            switch (p->m_adj_tz) {
+                case 4: gob(k_madj_bc<4, 4>); break;
+                case 8: gob(k_madj_bc<8, 8>); break;
+                default: gob(k_madj_bc<12, 12>); break;
+            }
         }
     } else {
         switch (p->m_adj_tz) {
@@ -963,10 +989,11 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
         }
     }
     stage_end(p, kStageAdjMain, s);
-    const int64_t lz = std::min(p->ng.bz, p->nz);
+    const int lz = std::min(p->ng.bz, p->nz);
     stage_begin(p, kStageAdjNear, s);
-    k_near_adj<<<grid_for((int64_t)p->nx * p->ny * lz, 128), 128, 0, s>>>(p->nx, p->ny, p->nz, p->ng, p->dG,
-                                                                         p->bin_start, p->bin_st, r, p->m_cellacc);
+    dim3 gna((unsigned)((p->nx + 31) / 32), (unsigned)((p->ny + 7) / 8), (unsigned)lz);
+    k_near_adj<<<gna, 256, 0, s>>>(p->nx, p->ny, p->ng, p->dG, p->bin_start, p->bin_st, p->st_i0, r,
+                                   p->m_cellacc);
     stage_end(p, kStageAdjNear, s);
     note_launches(2);
 }
