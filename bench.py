@@ -14,7 +14,9 @@ Printed as one JSON line (rank 0).  Extra keys: roofline of the dominant
 kernel (MUFU-bound, "alu"), e2e (same metric through host buffers), the
 oracle timed on the host cores (cpu_baseline), the mixed-vs-FP64-oracle error
 on the oracle's sample stations, FP64-mode throughput on the 80 x 80 x 40
-workload, and the inversion time to relative residual 1e-6 (mixed and FP64).
+workload, the error of the literal FP32 corner-term scheme there (against the
+FP64 mode, beside the mixed scheme's), and the inversion time to relative
+residual 1e-6 (mixed and FP64).
 Under torchrun (N > 1) every rank runs an independent replica (the operator
 is single-GPU; replicas only) and `value` is the total over ranks.
 """
@@ -57,6 +59,10 @@ def parse():
     ap.add_argument("--serve-jobs", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--invert", action="store_true", help="time one data-space inversion on --workload")
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--max-iter", type=int, default=5000)
+    ap.add_argument("--precond", default="none", choices=["none", "jacobi"])
     return ap.parse_args()
 
 
@@ -166,6 +172,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def aggregate(t_local_ms, ws, pairs_step, steps, device):
+    """Whole-job throughput of `ws` replicas: the timed region is the MAX over
+    ranks of each rank's device time (all-reduce when ws > 1), and every rank
+    processed `steps` steps of `pairs_step` pairs.  Returns (t_ms, pairs/s)."""
+    t = float(t_local_ms)
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return t, ws * pairs_step * steps / (t * 1e-3)
+
+
 def measured_traffic(kernel_name, args):
     """DRAM bytes per launch of `kernel_name` from the committed full-size ncu
     capture, if it was taken on this workload and the kernel sources are
@@ -238,14 +258,8 @@ def run_ours(args):
     launches = g.launch_count() - launches0
     stages = plan.timing(False, read=True)
     ms = [a.elapsed_time(b) for a, b in ev]
-    t_total = sum(ms)
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt)
     pairs_step = 2.0 * N * M
-    value = ws * pairs_step * args.steps / (t_total * 1e-3)
+    t_total, value = aggregate(sum(ms), ws, pairs_step, args.steps, dev)
 
     # e2e: same metric through the public API with pinned host buffers
     hm = torch.tensor(wl.m, dtype=torch.float64).pin_memory()
@@ -352,12 +366,29 @@ def extras(args, g, torch, wl, plan, d, line):
         p2.close()
     line["fp64_vs_mixed"] = {"workload": "vslab_80x80x40", "fp64_pairs_per_s": res["fp64"],
                              "mixed_pairs_per_s": res["mixed"], "mixed_over_fp64": res["mixed"] / res["fp64"]}
-    # inversion time to relative residual 1e-6, mixed and FP64
-    import oracle
+    # the literal FP32 corner-term scheme (forward only) against the FP64 mode
+    # on every station of the 80x80x40 workload, next to the mixed scheme
+    mv = torch.tensor(wl2.m, device="cuda")
+    ref = g.forward(mv, wl2.mesh, S2, precision="fp64")
+    corner = {}
+    for prec in ("mixed_corner", "mixed"):
+        p2 = g.Plan(wl2.mesh, S2, precision=prec)
+        p2.forward(mv)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        dv = p2.forward(mv)
+        b.record(); b.synchronize()
+        corner[prec] = {"rel_err_to_max": float((dv - ref).abs().max() / ref.abs().max()),
+                        "forward_ms": a.elapsed_time(b)}
+        p2.close()
+    line["fp32_corner_vs_mixed"] = {"workload": "vslab_80x80x40", "stations_checked": wl2.survey.n,
+                                    "reference": "FP64 mode", **corner}
+    # inversion time to relative residual 1e-6, mixed and FP64 (data from the FP64 forward)
     wl1 = synth.make_workload("block_20x20x10")
-    d1 = oracle.forward(wl1.mesh, wl1.survey, wl1.m)
-    d1 = synth.add_noise(d1, wl1.noise_abs, wl1.noise_rel, 0)
     S1 = g.Survey(wl1.survey.x, wl1.survey.y, wl1.survey.z)
+    d1 = g.forward(torch.tensor(wl1.m, device="cuda"), wl1.mesh, S1, precision="fp64").cpu().numpy()
+    d1 = synth.add_noise(d1, wl1.noise_abs, wl1.noise_rel, 0)
     inv = {}
     for prec in ("fp64", "mixed"):
         g.datainv(torch.tensor(d1, device="cuda"), wl1.mesh, S1, precision=prec, tol=1e-6)
@@ -422,12 +453,46 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_invert(args):
+    """Time to relative residual args.tol for the data-space inversion of
+    Eq. 10-11 on args.workload: data d = G m_true from the FP64 operator when
+    it is affordable (else the mixed one), then m = W^-2 G^T y by CG with the
+    operator of args.precision; the clock covers plan set-up, diag/trace, CG
+    and the final recovery (one call of grav_datainv_solve)."""
+    import torch
+    import paper_2602_03857_b300 as g
+    torch.cuda.set_device(0)
+    wl = synth.make_workload(args.workload)
+    S = g.Survey(wl.survey.x, wl.survey.y, wl.survey.z)
+    m = torch.tensor(wl.m, dtype=torch.float64, device="cuda")
+    data_prec = "fp64" if wl.survey.n * wl.mesh.ncells <= 2e9 else "mixed"
+    d = g.forward(m, wl.mesh, S, precision=data_prec, near_cells=args.near_cells)
+    torch.cuda.synchronize()
+    opts = dict(precision=args.precision, near_cells=args.near_cells, tol=args.tol, max_iter=args.max_iter,
+                precond=args.precond)
+    t0 = time.perf_counter()
+    m_out, info = g.datainv(d, wl.mesh, S, **opts)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    misfit = g.forward(m_out, wl.mesh, S, precision=data_prec, near_cells=args.near_cells) - d
+    line = {"metric": "inversion time to relative residual", "workload": args.workload,
+            "precision": args.precision, "precond": args.precond, "tol": args.tol, "seconds": wall,
+            "iters": info["iters"],
+            "converged": info["converged"], "true_rel_res": info["true_rel_res"], "lambda": info["lambda"],
+            "cells": wl.mesh.ncells, "stations": wl.survey.n, "data_operator": data_prec,
+            "rms_misfit_mgal": float(torch.sqrt(torch.mean(misfit * misfit))),
+            "rms_data_mgal": float(torch.sqrt(torch.mean(d * d))), "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.serve:
         run_serve(args)
+    elif args.invert:
+        run_invert(args)
     else:
         run_ours(args)
 

@@ -73,6 +73,13 @@ typedef struct CUstream_st *grav_stream_t;
  */
 #define GRAV_FP64    0
 #define GRAV_MIXED   1
+/* GRAV_MIXED_CORNER: the literal reading "FP32 corner terms with compensated
+ *   summation, FP64 only for near-field prisms": Eq. 2-3 in FP32 at every mesh
+ *   node (node-shared) plus the same FP64 near-window correction as
+ *   GRAV_MIXED.  Forward product only (grav_forward / grav_plan_forward); it
+ *   exists to measure that scheme's error, which FP32 cancellation of the
+ *   corner differences makes far larger than GRAV_MIXED's (see DESIGN). */
+#define GRAV_MIXED_CORNER 2
 
 /* ---- descriptors ---------------------------------------------------------- */
 typedef struct {
@@ -97,6 +104,13 @@ typedef struct {
     int check_every;           /* host convergence check period in iterations (0 = automatic) */
     double near_cells;         /* GRAV_MIXED near-field radius in cell widths (default 8) */
     double timeout_s;          /* bound on every host wait of a call (default 3600 s) */
+    int precond;               /* CG preconditioner: 0 none, 1 Jacobi, diag(G W^-2 G^T + lambda I)^-1 (default 0) */
+    int cache_g;               /* GRAV_FP64 only: 1 = build G explicitly once (FP64, N*M*8 bytes) when it fits the
+                                  context budget and stream it for every product; 0 = always recompute (default 0) */
+    int outer_max;             /* > 0: the paper's outer model-update loop (Section 2.2): at most outer_max
+                                  updates y += alpha dy, dy from <= inner_max CG iterations on A dy = dd - A y,
+                                  alpha by backtracking on the objective of Eq. 7; 0 = one CG solve (default) */
+    int inner_max;             /* CG iterations per outer update (default 20) */
 } grav_options;
 
 typedef struct {
@@ -107,6 +121,8 @@ typedef struct {
     double lambda;             /* lambda used */
     double trace;              /* trace(G W^-2 G^T) (0 if lambda was given) */
     double seconds;            /* wall time of the solve */
+    int outer;                 /* outer updates performed (outer_max > 0) */
+    double alpha_min;          /* smallest accepted step length of the outer loop (1 if never backtracked) */
 } grav_solve_info;
 
 typedef struct grav_ctx grav_ctx;
@@ -114,7 +130,8 @@ typedef struct grav_plan grav_plan;
 
 /* Fills *opt with the defaults: GRAV_FP64, z0 = 50, lambda_scale = 1e-2,
  * lambda = 0, tol = 1e-6, max_iter = 1000, check_every = 0,
- * near_cells = 8, timeout_s = 3600. */
+ * near_cells = 8, timeout_s = 3600, precond = 0, cache_g = 0, outer_max = 0,
+ * inner_max = 20. */
 void grav_options_default(grav_options *opt);
 
 /* Library version string (static storage). */
@@ -283,11 +300,12 @@ int grav_plan_describe(const grav_plan *plan, char *buf, size_t len);
  * read (this waits for the recorded events) and reset them. */
 int grav_plan_timing(grav_plan *plan, int enable, double *ms, int64_t *counts);
 
-/* Pipe-rate microbenchmark on `device` (synchronous, ~0.1 s).  out (HOST, 11
+/* Pipe-rate microbenchmark on `device` (synchronous, ~0.2 s).  out (HOST, 19
  * doubles): [0] MUFU rsqrt/s, [1] SM MHz seen, [2] MUFU lg2/s, [3] MHz,
  * [4] FP32 FMA/s, [5] MHz, [6] FP64 FMA/s, [7] MHz, [8] FP32 FMA/s issued as
- * packed fma.rn.f32x2, [9] MHz, [10] SM count.  The per-clock rates per SM
- * are out[2k] / (out[2k+1]*1e6 * out[10]). */
+ * packed fma.rn.f32x2, [9] MHz, [10] SM count, then CUDA's FP64 functions:
+ * [11] log/s, [12] MHz, [13] atan/s, [14] MHz, [15] sqrt/s, [16] MHz,
+ * [17] divisions/s, [18] MHz.  Per-clock rates per SM: rate / (MHz*1e6 * out[10]). */
 int grav_bench_pipes(int device, double *out);
 
 #ifdef __cplusplus

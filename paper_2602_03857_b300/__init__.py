@@ -39,9 +39,10 @@ GRAV_ENOTFOUND = -7
 GRAV_EBUSY = -8
 GRAV_FP64 = 0
 GRAV_MIXED = 1
+GRAV_MIXED_CORNER = 2
 GRAV_JOB_FORWARD, GRAV_JOB_INVERT = 0, 1
 JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "canceled"}
-PRECISIONS = {"fp64": GRAV_FP64, "mixed": GRAV_MIXED}
+PRECISIONS = {"fp64": GRAV_FP64, "mixed": GRAV_MIXED, "mixed_corner": GRAV_MIXED_CORNER}
 
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -59,7 +60,9 @@ class grav_survey(ctypes.Structure):
 class grav_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("z0", ctypes.c_double), ("lambda_scale", ctypes.c_double),
                 ("lambda_", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("check_every", ctypes.c_int), ("near_cells", ctypes.c_double), ("timeout_s", ctypes.c_double)]
+                ("check_every", ctypes.c_int), ("near_cells", ctypes.c_double), ("timeout_s", ctypes.c_double),
+                ("precond", ctypes.c_int), ("cache_g", ctypes.c_int), ("outer_max", ctypes.c_int),
+                ("inner_max", ctypes.c_int)]
 
 
 class grav_job(ctypes.Structure):
@@ -70,7 +73,7 @@ class grav_job(ctypes.Structure):
 class grav_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("rel_res", ctypes.c_double),
                 ("true_rel_res", ctypes.c_double), ("lambda_", ctypes.c_double), ("trace", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("outer", ctypes.c_int), ("alpha_min", ctypes.c_double)]
 
 
 def _sig(name, res, args):
@@ -132,16 +135,18 @@ def launch_count() -> int:
 
 def bench_pipes(device: int = 0) -> dict:
     """Measured unit throughputs (per second) and SM clocks of the B300 pipes."""
-    out = (ctypes.c_double * 11)()
+    out = (ctypes.c_double * 19)()
     rc = _lib.grav_bench_pipes(int(device), out)
     if rc != GRAV_OK:
         raise GravError(rc, _lib.grav_last_error(None).decode())
     sms = out[10]
     r = {"sm_count": int(sms)}
-    for k, name in enumerate(("rsqrt", "lg2", "ffma", "dfma", "ffma_f32x2")):
-        r[name + "_per_s"] = out[2 * k]
-        r[name + "_mhz"] = out[2 * k + 1]
-        r[name + "_per_clk_sm"] = out[2 * k] / (out[2 * k + 1] * 1e6 * sms) if out[2 * k + 1] > 0 else 0.0
+    slots = [(name, 2 * k) for k, name in enumerate(("rsqrt", "lg2", "ffma", "dfma", "ffma_f32x2"))]
+    slots += [(name, 11 + 2 * k) for k, name in enumerate(("log_f64", "atan_f64", "sqrt_f64", "div_f64"))]
+    for name, i in slots:
+        r[name + "_per_s"] = out[i]
+        r[name + "_mhz"] = out[i + 1]
+        r[name + "_per_clk_sm"] = out[i] / (out[i + 1] * 1e6 * sms) if out[i + 1] > 0 else 0.0
     return r
 
 
@@ -291,13 +296,17 @@ class Survey:
 
 
 def options(precision="fp64", z0=50.0, lambda_scale=1e-2, lam=0.0, tol=1e-6, max_iter=1000,
-            check_every=0, near_cells=8.0, timeout_s=3600.0) -> grav_options:
+            check_every=0, near_cells=8.0, timeout_s=3600.0, precond="none", cache_g=False, outer_max=0,
+            inner_max=20) -> grav_options:
     o = grav_options()
     _lib.grav_options_default(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.z0, o.lambda_scale, o.lambda_ = float(z0), float(lambda_scale), float(lam)
     o.tol, o.max_iter, o.check_every = float(tol), int(max_iter), int(check_every)
     o.near_cells, o.timeout_s = float(near_cells), float(timeout_s)
+    o.precond = {"none": 0, "jacobi": 1}[precond] if isinstance(precond, str) else int(precond)
+    o.cache_g = int(bool(cache_g))
+    o.outer_max, o.inner_max = int(outer_max), int(inner_max)
     return o
 
 
@@ -369,7 +378,7 @@ def datainv(d, mesh, survey, m_ref=None, return_y=False, stream=None, ctx: Optio
                                            ctypes.byref(o), _stream(stream)))
     inf = {"iters": info.iters, "converged": bool(info.converged), "rel_res": info.rel_res,
            "true_rel_res": info.true_rel_res, "lambda": info.lambda_, "trace": info.trace,
-           "seconds": info.seconds, "status": rc}
+           "seconds": info.seconds, "status": rc, "outer": info.outer, "alpha_min": info.alpha_min}
     return (m, y, inf) if return_y else (m, inf)
 
 

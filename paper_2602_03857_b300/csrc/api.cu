@@ -70,8 +70,9 @@ bool finite_increasing(const double *e, int n) {
 }
 
 int check_options(grav_ctx *ctx, const grav_options &o) {
-    if (o.precision != GRAV_FP64 && o.precision != GRAV_MIXED)
-        return set_error(ctx, GRAV_EINVAL, "precision must be GRAV_FP64 or GRAV_MIXED (got %d)", o.precision);
+    if (o.precision != GRAV_FP64 && o.precision != GRAV_MIXED && o.precision != GRAV_MIXED_CORNER)
+        return set_error(ctx, GRAV_EINVAL, "precision must be GRAV_FP64, GRAV_MIXED or GRAV_MIXED_CORNER (got %d)",
+                         o.precision);
     if (!std::isfinite(o.z0) || o.z0 < 0) return set_error(ctx, GRAV_EINVAL, "z0 must be finite and >= 0");
     if (!(o.lambda_scale > 0) || !std::isfinite(o.lambda_scale))
         return set_error(ctx, GRAV_EINVAL, "lambda_scale must be > 0");
@@ -82,6 +83,10 @@ int check_options(grav_ctx *ctx, const grav_options &o) {
     if (!(o.near_cells >= 1.0 && o.near_cells <= 16.0))
         return set_error(ctx, GRAV_EINVAL, "near_cells must lie in [1, 16]");
     if (!(o.timeout_s > 0)) return set_error(ctx, GRAV_EINVAL, "timeout_s must be > 0");
+    if (o.precond != 0 && o.precond != 1) return set_error(ctx, GRAV_EINVAL, "precond must be 0 (none) or 1 (Jacobi)");
+    if (o.cache_g != 0 && o.cache_g != 1) return set_error(ctx, GRAV_EINVAL, "cache_g must be 0 or 1");
+    if (o.outer_max < 0 || o.outer_max > 100000) return set_error(ctx, GRAV_EINVAL, "outer_max must lie in [0, 1e5]");
+    if (o.outer_max > 0 && o.inner_max < 1) return set_error(ctx, GRAV_EINVAL, "inner_max must be >= 1");
     return GRAV_OK;
 }
 
@@ -184,10 +189,16 @@ size_t fp64_bytes(const grav_plan *p) {
 
 int plan_forward_ex(grav_plan *p, const double *m, double *d, const double *add, double add_scale,
                     cudaStream_t s) {
-    if (p->opt.precision == GRAV_FP64) {
+    if (p->cached) {
+        launch_cached_fwd(p, m, add, add_scale, d, s);
+    } else if (p->opt.precision == GRAV_FP64) {
         launch_node_weights(p, m, s);
         launch_fwd64(p, s);
         launch_reduce_rows(p->part, p->f64_nchunk, p->N, kGammaMgal, add, add_scale, nullptr, d, s);
+    } else if (p->opt.precision == GRAV_MIXED_CORNER) {
+        launch_corner_fwd(p, m, s);
+        launch_mixed_near_fwd(p, m, s);
+        launch_reduce_rows(p->cr_part, p->cr_nchunk, p->N, kGammaMgal, add, add_scale, p->near_corr, d, s);
     } else {
         launch_mixed_prep_q(p, m, s);
         launch_mixed_fwd(p, s);
@@ -200,7 +211,11 @@ int plan_forward_ex(grav_plan *p, const double *m, double *d, const double *add,
 
 int plan_adjoint_ex(grav_plan *p, const double *r, double *out, int depth_weighted, const double *add,
                     cudaStream_t s) {
-    if (p->opt.precision == GRAV_FP64) {
+    if (p->opt.precision == GRAV_MIXED_CORNER)
+        return set_error(p->ctx, GRAV_EINVAL, "GRAV_MIXED_CORNER provides the forward product only");
+    if (p->cached) {
+        launch_cached_adj(p, r, depth_weighted, add, out, s);
+    } else if (p->opt.precision == GRAV_FP64) {
         launch_adj64(p, r, s);
         launch_adj_finish(p, p->u, kGammaMgal, depth_weighted, add, out, s);
     } else {
@@ -212,7 +227,10 @@ int plan_adjoint_ex(grav_plan *p, const double *r, double *out, int depth_weight
 }
 
 int plan_diag(grav_plan *p, double *diag, cudaStream_t s) {
-    if (p->opt.precision == GRAV_FP64) launch_diag64(p, diag, s);
+    if (p->opt.precision == GRAV_MIXED_CORNER)
+        return set_error(p->ctx, GRAV_EINVAL, "GRAV_MIXED_CORNER provides the forward product only");
+    if (p->cached) launch_cached_diag(p, diag, s);
+    else if (p->opt.precision == GRAV_FP64) launch_diag64(p, diag, s);
     else launch_mixed_diag(p, diag, s);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GRAV_OK : cuda_error(p->ctx, e, "diag launch");
@@ -254,18 +272,21 @@ int plan_prepare(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey
     p->sx = survey->x; p->sy = survey->y; p->sz = survey->z;
     {
         const double a = p->xe[1] - p->xe[0];
-        bool cubic = true;
-        auto uni = [&](const std::vector<double> &e) {
+        const double c = p->ze[1] - p->ze[0];
+        auto uni = [&](const std::vector<double> &e, double h) {
             for (size_t i = 0; i + 1 < e.size(); ++i)
-                if (std::fabs((e[i + 1] - e[i]) - a) > 1e-9 * a) return false;
+                if (std::fabs((e[i + 1] - e[i]) - h) > 1e-9 * h) return false;
             return true;
         };
-        cubic = uni(p->xe) && uni(p->ye) && uni(p->ze);
-        p->cubic = cubic;
+        p->square = uni(p->xe, a) && uni(p->ye, a) && uni(p->ze, c);
+        p->cubic = p->square && std::fabs(a - c) <= 1e-9 * a;
+        p->cell_a = a;
+        p->cell_c = c;
     }
-    if (o.precision == GRAV_MIXED && !p->cubic) {
+    if (o.precision != GRAV_FP64 && !p->square) {
         delete p;
-        return set_error(ctx, GRAV_EINVAL, "GRAV_MIXED needs a uniform mesh of cubic cells (dx = dy = dz everywhere)");
+        return set_error(ctx, GRAV_EINVAL,
+                         "GRAV_MIXED needs a uniform mesh of square-based prisms (dx = dy everywhere, dz uniform)");
     }
     size_t bytes = 0;
     auto add = [&](size_t v) { bytes += (v + 255) / 256 * 256 + 256; };
@@ -273,15 +294,29 @@ int plan_prepare(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey
     if (o.precision == GRAV_FP64) {
         fp64_sizes(p, ctx->sm_count);
         bytes += fp64_bytes(p);
+        // stored G when asked for and it fits next to what is already in use
+        const double gbytes = 8.0 * (double)p->N * (double)p->M;
+        if (o.cache_g && (double)ctx->hbm_used.load() + (double)bytes + gbytes + 8.0 * p->N * 64 <= (double)ctx->hbm_budget) {
+            p->cached = 1;
+            const int64_t tiles = (p->N + 127) / 128;
+            p->c_nchunk = (int)std::min<int64_t>(std::max<int64_t>(1, (int64_t)ctx->sm_count * 16 / tiles), 64);
+            p->c_nchunk = (int)std::min<int64_t>(p->c_nchunk, p->M);
+            bytes += (size_t)gbytes + 256;
+            // the forward partials reuse `part`; make sure it has c_nchunk rows
+            const int rows = std::max(p->f64_nchunk, p->f64_diag_nchunk);
+            if (p->c_nchunk > rows) bytes += (size_t)(p->c_nchunk - rows) * p->N * 8 + 256;
+        }
     } else {
-        const double a = p->xe[1] - p->xe[0];
+        const double a = p->cell_a;
+        const double L = std::max(p->cell_a, p->cell_c);   // the window radius is k cell widths, width = largest edge
         const double k = o.near_cells;
         p->ng.radius_cells = k;
-        p->ng.bx = (int)std::ceil(2.0 * k) + 1;
+        p->ng.width = L;
+        p->ng.bx = (int)std::ceil(2.0 * k * L / a) + 1;
         p->ng.by = p->ng.bx;
         int bz = 0;
         for (int l = 0; l < p->nz; ++l)
-            if (0.5 * (p->ze[l] + p->ze[l + 1]) - p->ze[0] < k * a) bz = l + 1;
+            if (0.5 * (p->ze[l] + p->ze[l + 1]) - p->ze[0] < k * L) bz = l + 1;
         p->ng.bz = std::max(1, bz);
         p->ng.slots = p->ng.bx * p->ng.by * p->ng.bz;
         p->ng.nbx = p->nx + p->ng.bx - 1;
@@ -334,11 +369,16 @@ int plan_allocate(grav_plan *p, cudaStream_t s) {
     if (o.precision == GRAV_FP64) {
         const size_t nrows = (size_t)(p->ny + 1) * (p->nz + 1);
         p->w = (double *)p->arena.take(nrows * p->ldw * 8);
-        p->part = (double *)p->arena.take((size_t)std::max(p->f64_nchunk, p->f64_diag_nchunk) * p->N * 8);
+        p->part = (double *)p->arena.take((size_t)std::max(std::max(p->f64_nchunk, p->f64_diag_nchunk), p->c_nchunk) *
+                                          p->N * 8);
         p->st4 = (double4 *)p->arena.take((size_t)p->N * 32);
         p->upart = (double *)p->arena.take((size_t)p->a64_nschunk * p->Nn * 8);
         p->u = (double *)p->arena.take((size_t)p->Nn * 8);
-        if (!p->arena.overflow) fp64_setup(p, s);
+        if (p->cached) p->Gc = (double *)p->arena.take((size_t)p->N * p->M * 8);
+        if (!p->arena.overflow) {
+            fp64_setup(p, s);
+            if (p->cached) launch_build_g64(p, p->Gc, nullptr, s);
+        }
     } else {
         rc = mixed_setup(p, s);
     }
@@ -369,7 +409,7 @@ int plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey,
     return GRAV_OK;
 }
 
-size_t solve_bytes(const grav_plan *p) { return 8ull * (5 * p->N + p->M + kDotBlocks + kSCount) + 8 * 256; }
+size_t solve_bytes(const grav_plan *p) { return 8ull * (12 * p->N + p->M + kDotBlocks + kSCount) + 16 * 256; }
 
 void plan_destroy(grav_plan *p, cudaStream_t s) {
     if (!p) return;
@@ -409,6 +449,8 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
     const grav_options &o = p->opt;
     const double t0 = now_s();
     const int64_t N = p->N, M = p->M;
+    if (o.precision == GRAV_MIXED_CORNER)
+        return set_error(ctx, GRAV_EINVAL, "GRAV_MIXED_CORNER provides the forward product only (no inversion)");
     const size_t bytes = solve_bytes(p);
     if (ctx->hbm_used.load() + bytes > ctx->hbm_budget) return set_error(ctx, GRAV_ENOMEM, "solve vectors exceed budget");
     char *base = nullptr;
@@ -423,6 +465,13 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
     double *pv = (double *)ar.take(8ull * N);
     double *Ap = (double *)ar.take(8ull * N);
     double *q = (double *)ar.take(8ull * M);
+    double *zv = (double *)ar.take(8ull * N);     // z = M^-1 r (preconditioned CG)
+    double *dinv = (double *)ar.take(8ull * N);   // diag(A)^-1 (preconditioned CG)
+    double *yo = (double *)ar.take(8ull * N);     // outer loop: accumulated y
+    double *Ay = (double *)ar.take(8ull * N);     // outer loop: A y
+    double *ro = (double *)ar.take(8ull * N);     // outer loop: dd - A y
+    double *wv = (double *)ar.take(8ull * N);     // outer loop: work vectors
+    double *fv = (double *)ar.take(8ull * N);
     double *dp = (double *)ar.take(8ull * kDotBlocks);
     double *sc = (double *)ar.take(8ull * kSCount);
     double *hsc = nullptr;
@@ -447,23 +496,138 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
         } else {
             cudaMemcpyAsync(dd, d, 8ull * N, cudaMemcpyDeviceToDevice, s);
         }
-        // lambda = lambda_scale * trace(G W^-2 G^T) / N
-        if (!(lam > 0)) {
-            if ((rc = plan_diag(p, Ap, s))) break;
-            launch_dot(Ap, nullptr, N, dp, sc + kSTrace, s);
-            if ((rc = sync_scalars("trace"))) break;
-            trace = hsc[kSTrace];
-            lam = o.lambda_scale * trace / (double)N;
-            if (!(lam > 0) || !std::isfinite(lam)) {
-                rc = set_error(ctx, GRAV_EDEVICE, "lambda from the trace is not positive (trace %g)", trace);
-                break;
+        // lambda = lambda_scale * trace(G W^-2 G^T) / N; the diagonal also feeds
+        // the Jacobi preconditioner M = diag(G W^-2 G^T + lambda I)
+        const bool pc = o.precond == 1;
+        if (!(lam > 0) || pc) {
+            if ((rc = plan_diag(p, dinv, s))) break;
+            if (!(lam > 0)) {
+                launch_dot(dinv, nullptr, N, dp, sc + kSTrace, s);
+                if ((rc = sync_scalars("trace"))) break;
+                trace = hsc[kSTrace];
+                lam = o.lambda_scale * trace / (double)N;
+                if (!(lam > 0) || !std::isfinite(lam)) {
+                    rc = set_error(ctx, GRAV_EDEVICE, "lambda from the trace is not positive (trace %g)", trace);
+                    break;
+                }
             }
+            if (pc) vec_jacobi_inv(dinv, lam, N, dinv, s);
         }
+        double true_rel = 0.0;
+        // one CG iteration on A x = b with x in `xv`, residual `rv`, direction pv
+        auto cg_step = [&](double *xv, double *rv, int it_global) -> int {
+            int r2 = plan_adjoint_ex(p, pv, q, 1, nullptr, s);
+            if (!r2) r2 = plan_forward_ex(p, q, Ap, pv, lam, s);
+            if (r2) return r2;
+            launch_dot(pv, Ap, N, dp, sc + kSPAp, s);
+            cg_alpha(sc, s);
+            cg_update_yr(xv, rv, pv, Ap, N, sc, s);
+            if (pc) {
+                vec_mul(dinv, rv, N, zv, s);
+                launch_dot(rv, zv, N, dp, sc + kSRRNew, s);
+                launch_dot(rv, rv, N, dp, sc + kSResNew, s);
+                cg_beta(sc, it_global, kSResNew, s);
+                cg_update_p(pv, zv, N, sc, s);
+            } else {
+                launch_dot(rv, rv, N, dp, sc + kSRRNew, s);
+                cg_beta(sc, it_global, kSRRNew, s);
+                cg_update_p(pv, rv, N, sc, s);
+            }
+            return GRAV_OK;
+        };
+        int outer_done = 0;
+        double alpha_min = 1.0;
+        if (o.outer_max > 0) {
+            // The paper's outer model-update loop in data space (m = m_ref + W^-2 G^T y):
+            // dy from <= inner_max CG iterations on A dy = dd - A y, then y += alpha dy
+            // with alpha halved until the objective of Eq. 7 decreases.  Along the
+            // step phi(alpha) is a quadratic whose coefficients are dot products:
+            //   d - G m = e0 + alpha e1, e0 = r + lam y, e1 = lam dy - A dy
+            //   (m - m_ref)^T W_m^-1 (m - m_ref) = (y + alpha dy)^T (f0 + alpha f1),
+            //   f0 = A y - lam y, f1 = A dy - lam dy.
+            vec_fill(yo, N, 0.0, s);
+            launch_dot(dd, dd, N, dp, sc + kSTmp, s);
+            if ((rc = sync_scalars("outer start"))) break;
+            const double bb0 = hsc[kSTmp];
+            int total_it = 0;
+            for (int k = 0;; ++k) {
+                if ((rc = plan_adjoint_ex(p, yo, q, 1, nullptr, s))) break;
+                if ((rc = plan_forward_ex(p, q, Ay, yo, lam, s))) break;
+                vec_axpby(1.0, dd, -1.0, Ay, N, ro, s);
+                launch_dot(ro, ro, N, dp, sc + kSTmp, s);
+                if ((rc = sync_scalars("outer residual"))) break;
+                true_rel = bb0 > 0 ? std::sqrt(hsc[kSTmp] / bb0) : 0.0;
+                if (true_rel <= o.tol || k >= o.outer_max || total_it >= o.max_iter) break;
+                if (cancel && cancel->load()) {
+                    rc = set_error(ctx, GRAV_ECANCELED, "solve cancelled");
+                    break;
+                }
+                // inner CG from dy = 0 (dy in y, residual in r)
+                cudaMemcpyAsync(r, ro, 8ull * N, cudaMemcpyDeviceToDevice, s);
+                vec_fill(y, N, 0.0, s);
+                if (pc) {
+                    vec_mul(dinv, r, N, zv, s);
+                    cudaMemcpyAsync(pv, zv, 8ull * N, cudaMemcpyDeviceToDevice, s);
+                    launch_dot(r, zv, N, dp, sc + kSRR, s);
+                    launch_dot(r, r, N, dp, sc + kSTmp, s);
+                    cg_set_scalars(sc, o.tol * o.tol, kSTmp, s);
+                } else {
+                    cudaMemcpyAsync(pv, r, 8ull * N, cudaMemcpyDeviceToDevice, s);
+                    launch_dot(r, r, N, dp, sc + kSRR, s);
+                    cg_set_scalars(sc, o.tol * o.tol, kSRR, s);
+                }
+                const int n_in = std::min(o.inner_max, o.max_iter - total_it);
+                for (int it = 0; it < n_in && !rc; ++it) rc = cg_step(y, r, total_it + it);
+                if (rc) break;
+                // A dy and the line-search dot products
+                if ((rc = plan_adjoint_ex(p, y, q, 1, nullptr, s))) break;
+                if ((rc = plan_forward_ex(p, q, Ap, y, lam, s))) break;
+                vec_axpby(1.0, ro, lam, yo, N, wv, s);          // e0
+                vec_axpby(lam, y, -1.0, Ap, N, fv, s);          // e1
+                launch_dot(wv, wv, N, dp, sc + kSPhi + 0, s);
+                launch_dot(wv, fv, N, dp, sc + kSPhi + 1, s);
+                launch_dot(fv, fv, N, dp, sc + kSPhi + 2, s);
+                vec_axpby(1.0, Ay, -lam, yo, N, wv, s);         // f0
+                vec_axpby(1.0, Ap, -lam, y, N, fv, s);          // f1
+                launch_dot(yo, wv, N, dp, sc + kSPhi + 3, s);
+                launch_dot(yo, fv, N, dp, sc + kSPhi + 4, s);
+                launch_dot(y, wv, N, dp, sc + kSPhi + 5, s);
+                launch_dot(y, fv, N, dp, sc + kSPhi + 6, s);
+                if ((rc = sync_scalars("outer line search"))) break;
+                if (hsc[kSFrozen] == 2.0) {
+                    rc = set_error(ctx, GRAV_EDEVICE, "CG breakdown: p.Ap <= 0 (operator not SPD in this precision)");
+                    break;
+                }
+                total_it = (int)hsc[kSIters];
+                const double *c = hsc + kSPhi;
+                auto phi = [&](double a) {
+                    return (c[0] + 2 * a * c[1] + a * a * c[2]) / lam + c[3] + a * (c[4] + c[5]) + a * a * c[6];
+                };
+                const double phi0 = phi(0.0);
+                double alpha = 1.0;
+                while (phi(alpha) >= phi0 && alpha > 1.0 / 1024) alpha *= 0.5;
+                alpha_min = std::min(alpha_min, alpha);
+                vec_axpby(1.0, yo, alpha, y, N, yo, s);
+                outer_done = k + 1;
+            }
+            if (rc) break;
+            cudaMemcpyAsync(y, yo, 8ull * N, cudaMemcpyDeviceToDevice, s);
+            iters = total_it;
+            converged = true_rel <= o.tol;
+        } else {
         cudaMemcpyAsync(r, dd, 8ull * N, cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(pv, dd, 8ull * N, cudaMemcpyDeviceToDevice, s);
         vec_fill(y, N, 0.0, s);
-        launch_dot(r, r, N, dp, sc + kSRR, s);
-        cg_set_scalars(sc, o.tol * o.tol, s);
+        if (pc) {
+            vec_mul(dinv, r, N, zv, s);
+            cudaMemcpyAsync(pv, zv, 8ull * N, cudaMemcpyDeviceToDevice, s);
+            launch_dot(r, zv, N, dp, sc + kSRR, s);
+            launch_dot(r, r, N, dp, sc + kSTmp, s);
+            cg_set_scalars(sc, o.tol * o.tol, kSTmp, s);
+        } else {
+            cudaMemcpyAsync(pv, dd, 8ull * N, cudaMemcpyDeviceToDevice, s);
+            launch_dot(r, r, N, dp, sc + kSRR, s);
+            cg_set_scalars(sc, o.tol * o.tol, kSRR, s);
+        }
         if ((rc = sync_scalars("cg start"))) break;
         if (hsc[kSFrozen] != 0.0) {
             converged = true;
@@ -471,7 +635,6 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
         const double work = (double)N * (double)M;
         const int every = o.check_every > 0 ? o.check_every : (work > 2e8 ? 1 : 8);
         int it = 0;
-        double true_rel = 0.0;
         // CG; when the recurrence residual reaches tol, the residual is
         // recomputed from y with the operator itself (r = dd - A y); if that
         // true residual is still above tol, CG restarts from it (p = r).
@@ -484,9 +647,17 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
                     launch_dot(pv, Ap, N, dp, sc + kSPAp, s);
                     cg_alpha(sc, s);
                     cg_update_yr(y, r, pv, Ap, N, sc, s);
-                    launch_dot(r, r, N, dp, sc + kSRRNew, s);
-                    cg_beta(sc, it, s);
-                    cg_update_p(pv, r, N, sc, s);
+                    if (pc) {
+                        vec_mul(dinv, r, N, zv, s);
+                        launch_dot(r, zv, N, dp, sc + kSRRNew, s);
+                        launch_dot(r, r, N, dp, sc + kSResNew, s);
+                        cg_beta(sc, it, kSResNew, s);
+                        cg_update_p(pv, zv, N, sc, s);
+                    } else {
+                        launch_dot(r, r, N, dp, sc + kSRRNew, s);
+                        cg_beta(sc, it, kSRRNew, s);
+                        cg_update_p(pv, r, N, sc, s);
+                    }
                 }
                 if (rc) break;
                 if ((rc = sync_scalars("cg iteration"))) break;
@@ -514,10 +685,18 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
                 break;
             }
             converged = false;
-            cudaMemcpyAsync(pv, r, 8ull * N, cudaMemcpyDeviceToDevice, s);
-            cg_restart(sc, s);
+            if (pc) {
+                vec_mul(dinv, r, N, zv, s);
+                cudaMemcpyAsync(pv, zv, 8ull * N, cudaMemcpyDeviceToDevice, s);
+                launch_dot(r, zv, N, dp, sc + kSRR, s);
+                cg_restart(sc, 0, s);
+            } else {
+                cudaMemcpyAsync(pv, r, 8ull * N, cudaMemcpyDeviceToDevice, s);
+                cg_restart(sc, 1, s);
+            }
         }
         if (rc) break;
+        }  // single CG solve
         // m = m_ref + W^-2 G^T y
         if ((rc = plan_adjoint_ex(p, y, m_out, 1, m_ref, s))) break;
         if (y_out) cudaMemcpyAsync(y_out, y, 8ull * N, cudaMemcpyDeviceToDevice, s);
@@ -525,7 +704,10 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
         if (info) {
             info->iters = iters;
             info->converged = converged ? 1 : 0;
-            info->rel_res = hsc[kSBB] > 0 ? std::sqrt(hsc[kSRR] / hsc[kSBB]) : 0.0;
+            info->rel_res = o.outer_max > 0 ? true_rel
+                                            : (hsc[kSBB] > 0 ? std::sqrt(hsc[o.precond == 1 ? kSResNew : kSRR] / hsc[kSBB]) : 0.0);
+            info->outer = outer_done;
+            info->alpha_min = alpha_min;
             info->true_rel_res = true_rel;
             info->lambda = lam;
             info->trace = trace;
@@ -564,6 +746,10 @@ void grav_options_default(grav_options *o) {
     o->check_every = 0;
     o->near_cells = 8.0;
     o->timeout_s = 3600.0;
+    o->precond = 0;
+    o->cache_g = 0;
+    o->outer_max = 0;
+    o->inner_max = 20;
 }
 
 const char *grav_version(void) { return "libgrav 0.1.0 (sm_103a)"; }
@@ -673,20 +859,28 @@ int grav_plan_describe(const grav_plan *p, char *buf, size_t len) {
     int n;
     if (p->opt.precision == GRAV_FP64) {
         n = snprintf(tmp, sizeof(tmp),
-                     "{\"precision\": \"fp64\", \"fwd_kernel\": \"k_fwd64<2>\", \"adj_kernel\": \"k_adj64<8>\", "
-                     "\"fwd_row_chunks\": %d, \"adj_station_chunks\": %d, \"bytes\": %zu}",
-                     p->f64_nchunk, p->a64_nschunk, p->bytes);
+                     "{\"precision\": \"fp64\", \"fwd_kernel\": \"%s\", \"adj_kernel\": \"%s\", "
+                     "\"stored_g\": %s, \"fwd_row_chunks\": %d, \"adj_station_chunks\": %d, \"bytes\": %zu}",
+                     p->cached ? "k_gemv_cached" : "k_fwd64<2>", p->cached ? "k_gemvt_cached" : "k_adj64<8>",
+                     p->cached ? "true" : "false", p->f64_nchunk, p->a64_nschunk, p->bytes);
     } else {
         char adj[64];
+        // template arguments as the compiled kernels carry them (the last one:
+        // quadrupole far field for square-based, non-cubic prisms)
+        const int quad = p->cubic ? 0 : 1;
+        char fwd[64];
+        snprintf(fwd, sizeof(fwd), "k_mfwd<8, %d>", quad);
         if (p->m_adj_bc)
-            snprintf(adj, sizeof(adj), "k_madj_bc<%d, %d>", p->m_adj_tz, mixed_adj_last_group(p));
+            snprintf(adj, sizeof(adj), "k_madj_bc<%d, %d, %d>", p->m_adj_tz, mixed_adj_last_group(p), quad);
         else
-            snprintf(adj, sizeof(adj), "k_madj<%d>", p->m_adj_tz);
+            snprintf(adj, sizeof(adj), "k_madj<%d, %d>", p->m_adj_tz, quad);
+        const bool corner = p->opt.precision == GRAV_MIXED_CORNER;
         n = snprintf(tmp, sizeof(tmp),
-                     "{\"precision\": \"mixed\", \"fwd_kernel\": \"k_mfwd<8>\", \"adj_kernel\": \"%s\", "
+                     "{\"precision\": \"%s\", \"fwd_kernel\": \"%s\", \"adj_kernel\": \"%s\", "
                      "\"adj_layout\": \"%s\", \"fwd_column_chunks\": %d, \"adj_station_chunks\": %d, "
                      "\"near_cells\": %g, \"near_box\": [%d, %d, %d], \"bytes\": %zu}",
-                     adj, p->m_adj_bc ? "broadcast" : "shuffle", p->m_fwd_nchunk, p->m_adj_nschunk,
+                     corner ? "mixed_corner" : "mixed", corner ? "k_cfwd32<4>" : fwd, corner ? "none" : adj,
+                     p->m_adj_bc ? "broadcast" : "shuffle", corner ? p->cr_nchunk : p->m_fwd_nchunk, p->m_adj_nschunk,
                      p->opt.near_cells, p->ng.bx, p->ng.by, p->ng.bz, p->bytes);
     }
     if (n < 0) return set_error(p->ctx, GRAV_EDEVICE, "describe failed");

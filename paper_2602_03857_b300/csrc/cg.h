@@ -18,17 +18,21 @@ enum CgScalar : int {
     kSIters = 8,   // iterations completed before freezing
     kSTrace = 9,
     kSTmp = 10,
-    kSCount = 16
+    kSResNew = 11, // r.r after the update (convergence test of the preconditioned CG)
+    kSPhi = 12,    // 7 slots: dot products of the outer loop's line search
+    kSCount = 24
 };
 
 void cg_alpha(double *sc, cudaStream_t s);
 void cg_update_yr(double *y, double *r, const double *p, const double *Ap, int64_t n, const double *sc,
                   cudaStream_t s);
-void cg_beta(double *sc, int it, cudaStream_t s);
+void cg_beta(double *sc, int it, int conv_slot, cudaStream_t s);
 void cg_update_p(double *p, const double *r, int64_t n, const double *sc, cudaStream_t s);
 void vec_axpby(double a, const double *x, double b, const double *y, int64_t n, double *out, cudaStream_t s);
 void vec_fill(double *x, int64_t n, double v, cudaStream_t s);
-void cg_set_scalars(double *sc, double tol2, cudaStream_t s);
-void cg_restart(double *sc, cudaStream_t s);
+void cg_set_scalars(double *sc, double tol2, int bb_slot, cudaStream_t s);
+void cg_restart(double *sc, int copy_rr, cudaStream_t s);
+void vec_mul(const double *a, const double *b, int64_t n, double *out, cudaStream_t s);
+void vec_jacobi_inv(const double *diag, double lam, int64_t n, double *out, cudaStream_t s);
 
 }  // namespace grav

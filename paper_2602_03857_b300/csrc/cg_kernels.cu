@@ -54,16 +54,18 @@ __global__ void k_cg_update_yr(double *__restrict__ y, double *__restrict__ r, c
     }
 }
 
-__global__ void k_cg_beta(double *__restrict__ sc, int it) {
+// beta = rz_new / rz (rz = r.z, z = M^-1 r; z = r without preconditioner);
+// convergence on the residual norm held in conv_slot.
+__global__ void k_cg_beta(double *__restrict__ sc, int it, int conv_slot) {
     if (sc[kSFrozen] != 0.0) {
         sc[kSBeta] = 0.0;
         return;
     }
-    const double rr_new = sc[kSRRNew];
-    sc[kSBeta] = rr_new / sc[kSRR];
-    sc[kSRR] = rr_new;
+    const double rz_new = sc[kSRRNew];
+    sc[kSBeta] = rz_new / sc[kSRR];
+    sc[kSRR] = rz_new;
     sc[kSIters] = (double)(it + 1);
-    if (rr_new <= sc[kSTol2] * sc[kSBB]) sc[kSFrozen] = 1.0;
+    if (sc[conv_slot] <= sc[kSTol2] * sc[kSBB]) sc[kSFrozen] = 1.0;
 }
 
 __global__ void k_cg_update_p(double *__restrict__ p, const double *__restrict__ r, int64_t n,
@@ -86,16 +88,28 @@ __global__ void k_fill(double *__restrict__ x, int64_t n, double v) {
         x[i] = v;
 }
 
-__global__ void k_set_scalars(double *__restrict__ sc, double tol2) {
-    sc[kSBB] = sc[kSRR];
+__global__ void k_set_scalars(double *__restrict__ sc, double tol2, int bb_slot) {
+    sc[kSBB] = sc[bb_slot];
     sc[kSTol2] = tol2;
-    sc[kSFrozen] = (sc[kSRR] <= 0.0) ? 1.0 : 0.0;
+    sc[kSFrozen] = (sc[kSBB] <= 0.0) ? 1.0 : 0.0;
     sc[kSIters] = 0.0;
 }
 
-// restart from the true residual held in kSTmp: rr <- true r.r, unfreeze unless already below tol
-__global__ void k_cg_restart(double *__restrict__ sc) {
-    sc[kSRR] = sc[kSTmp];
+__global__ void k_mul(const double *__restrict__ a, const double *__restrict__ b, int64_t n, double *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i] * b[i];
+}
+
+__global__ void k_jacobi_inv(const double *__restrict__ diag, double lam, int64_t n, double *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = 1.0 / (diag[i] + lam);
+}
+
+// restart from the true residual whose r.r is in kSTmp: unfreeze unless it is
+// already below tol; without preconditioner rz = r.r (copy_rr), with one the
+// caller has put r.z in kSRR.
+__global__ void k_cg_restart(double *__restrict__ sc, int copy_rr) {
+    if (copy_rr) sc[kSRR] = sc[kSTmp];
     sc[kSFrozen] = (sc[kSTmp] <= sc[kSTol2] * sc[kSBB]) ? 1.0 : 0.0;
 }
 
@@ -117,7 +131,9 @@ void cg_update_yr(double *y, double *r, const double *p, const double *Ap, int64
                   cudaStream_t s) {
     k_cg_update_yr<<<vgrid(n), 256, 0, s>>>(y, r, p, Ap, n, sc); note_launches(1);
 }
-void cg_beta(double *sc, int it, cudaStream_t s) { k_cg_beta<<<1, 1, 0, s>>>(sc, it); note_launches(1); }
+void cg_beta(double *sc, int it, int conv_slot, cudaStream_t s) {
+    k_cg_beta<<<1, 1, 0, s>>>(sc, it, conv_slot); note_launches(1);
+}
 void cg_update_p(double *p, const double *r, int64_t n, const double *sc, cudaStream_t s) {
     k_cg_update_p<<<vgrid(n), 256, 0, s>>>(p, r, n, sc); note_launches(1);
 }
@@ -125,7 +141,15 @@ void vec_axpby(double a, const double *x, double b, const double *y, int64_t n, 
     k_axpby<<<vgrid(n), 256, 0, s>>>(a, x, b, y, n, out); note_launches(1);
 }
 void vec_fill(double *x, int64_t n, double v, cudaStream_t s) { k_fill<<<vgrid(n), 256, 0, s>>>(x, n, v); note_launches(1); }
-void cg_restart(double *sc, cudaStream_t s) { k_cg_restart<<<1, 1, 0, s>>>(sc); note_launches(1); }
-void cg_set_scalars(double *sc, double tol2, cudaStream_t s) { k_set_scalars<<<1, 1, 0, s>>>(sc, tol2); note_launches(1); }
+void cg_restart(double *sc, int copy_rr, cudaStream_t s) { k_cg_restart<<<1, 1, 0, s>>>(sc, copy_rr); note_launches(1); }
+void cg_set_scalars(double *sc, double tol2, int bb_slot, cudaStream_t s) {
+    k_set_scalars<<<1, 1, 0, s>>>(sc, tol2, bb_slot); note_launches(1);
+}
+void vec_mul(const double *a, const double *b, int64_t n, double *out, cudaStream_t s) {
+    k_mul<<<vgrid(n), 256, 0, s>>>(a, b, n, out); note_launches(1);
+}
+void vec_jacobi_inv(const double *diag, double lam, int64_t n, double *out, cudaStream_t s) {
+    k_jacobi_inv<<<vgrid(n), 256, 0, s>>>(diag, lam, n, out); note_launches(1);
+}
 
 }  // namespace grav

@@ -102,6 +102,20 @@ __device__ __forceinline__ double psi64(double x, double y, double z, double x2,
     return t_atan - x * log(ry) - y * log(rx);
 }
 
+// Eq. 2-3 evaluated entirely in FP32 (CUDA's IEEE sqrtf/logf/atanf and
+// divisions), with the same cancellation-free logarithm forms as psi64.  Used
+// only by the GRAV_MIXED_CORNER variant, the literal "FP32 corner terms"
+// reading, whose far-field error this library reports.
+__device__ __forceinline__ float psi32(float x, float y, float z) {
+    const float x2 = x * x, y2 = y * y, z2 = z * z;
+    const float R = sqrtf(x2 + y2 + z2);
+    const float t_atan = z * atanf((x * y) / (z * R));
+    float ry, rx;
+    if (y >= 0.0f) ry = R + y; else ry = (x2 + z2) / (R - y);
+    if (x >= 0.0f) rx = R + x; else rx = (y2 + z2) / (R - x);
+    return t_atan - x * logf(ry) - y * logf(rx);
+}
+
 // ---------------------------------------------------------------------------
 // FP32 far-field term of a cubic prism: dz / R^3 (point mass at the cell
 // centre).  dz, R2 in metres; one MUFU reciprocal square root.
@@ -160,6 +174,45 @@ __device__ __forceinline__ f2_t far_pair_acc(f2_t zc, f2_t nzs, f2_t h2, f2_t w,
     const f2_t rs2 = f2_mul(rs, rs);
     const f2_t k = f2_mul(f2_mul(dz, rs), rs2);
     return f2_fma(w, k, acc);
+}
+
+// Far-field term of a square-based prism (dx = dy = a, dz = c) to second
+// order: dz / R^3 * (1 + qc / R^2 * (9 - 15 dz^2 / R^2)) with qc = (a^2 - c^2) / 24
+// (the quadrupole of a uniform box; it vanishes for a cube).  qc = 0 gives
+// exactly far_kernel().
+__device__ __forceinline__ float far_kernel_q(float dz, float R2, float qc) {
+    const float rs = rsqrt_approx(R2);
+    const float rs2 = rs * rs;
+    const float k = (dz * rs) * rs2;
+    const float t = (dz * dz) * rs2;
+    const float u = fmaf(-15.0f, t, 9.0f);
+    const float f = fmaf(qc * rs2, u, 1.0f);
+    return k * f;
+}
+
+// The same for two pairs at once (same operations per half).
+__device__ __forceinline__ f2_t far_pair_acc_q(f2_t zc, f2_t nzs, f2_t h2, f2_t w, f2_t acc, f2_t qc) {
+    const f2_t dz = f2_add(zc, nzs);
+    const f2_t R2 = f2_fma(dz, dz, h2);
+    float r0, r1;
+    f2_unpack(R2, r0, r1);
+    const f2_t rs = f2_pack(rsqrt_approx(r0), rsqrt_approx(r1));
+    const f2_t rs2 = f2_mul(rs, rs);
+    const f2_t k = f2_mul(f2_mul(dz, rs), rs2);
+    const f2_t t = f2_mul(f2_mul(dz, dz), rs2);
+    const f2_t u = f2_fma(f2_pack(-15.0f, -15.0f), t, f2_pack(9.0f, 9.0f));
+    const f2_t f = f2_fma(f2_mul(qc, rs2), u, f2_pack(1.0f, 1.0f));
+    return f2_fma(w, f2_mul(k, f), acc);
+}
+
+template <bool QUAD>
+__device__ __forceinline__ f2_t far_pair(f2_t zc, f2_t nzs, f2_t h2, f2_t w, f2_t acc, f2_t qc) {
+    return QUAD ? far_pair_acc_q(zc, nzs, h2, w, acc, qc) : far_pair_acc(zc, nzs, h2, w, acc);
+}
+
+template <bool QUAD>
+__device__ __forceinline__ float far_k(float dz, float R2, float qc) {
+    return QUAD ? far_kernel_q(dz, R2, qc) : far_kernel(dz, R2);
 }
 
 // Knuth two-sum: (s, e) with s = fl(a + b), a + b = s + e exactly.

@@ -322,10 +322,11 @@ __global__ void k_adj_finish(int nx, int ny, int nz, const double *__restrict__ 
 // left node column of the next, so each step evaluates Psi on 2 new node
 // columns (levels l0..l0+ZC) for ZC cells: 2(ZC+1)/ZC evaluations per cell.
 // ---------------------------------------------------------------------------
-template <int ZC>
+template <int ZC, bool WRITE_G>
 __global__ void __launch_bounds__(128) k_diag64(Geo g, const double *__restrict__ w2, int jrows,
                                                 const double *__restrict__ sx, const double *__restrict__ sy,
-                                                const double *__restrict__ sz, double *__restrict__ part) {
+                                                const double *__restrict__ sz, double *__restrict__ part,
+                                                double *__restrict__ Gout) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.N) return;
     const double xs = sx[s], ys = sy[s], zs = sz[s];
@@ -373,6 +374,7 @@ __global__ void __launch_bounds__(128) k_diag64(Geo g, const double *__restrict_
                     if (c < nl) {
                         const double G = kGammaMgal * (E[c + 1] - E[c]);
                         acc = fma(G * G, w2l[c], acc);
+                        if (WRITE_G) Gout[(i + (int64_t)g.nx * (j + (int64_t)g.ny * (l0 + c))) * g.N + s] = G;
                     }
                 }
             }
@@ -399,7 +401,97 @@ int fwd_rows_per_stage(const grav_plan *p) {
     return std::max(1, std::min(p->f64_rows_per_chunk, (16384 / 8) / p->ldw));
 }
 
+// ---------------------------------------------------------------------------
+// Stored-G products (G built once in FP64, cell-major: Gc[k][i], station i
+// fastest).  Both read the matrix once, coalesced: HBM-bound.
+// d: CTA = (128 stations, chunk of cells) -> partials [chunk][N].
+// G^T r: warp per cell, lanes over stations, shuffle reduction.
+// ---------------------------------------------------------------------------
+// SQUARE: sum_k G_ik^2 w2[layer(k)] (the diagonal of G W^-2 G^T) instead of G m.
+template <bool SQUARE>
+__global__ void __launch_bounds__(128) k_gemv_cached(const double *__restrict__ Gc, int64_t N, int64_t M,
+                                                     int64_t plane, int64_t cells_per_chunk,
+                                                     const double *__restrict__ m, double *__restrict__ part) {
+    const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    const int64_t k0 = (int64_t)blockIdx.y * cells_per_chunk;
+    const int64_t k1 = min(M, k0 + cells_per_chunk);
+    if (i >= N) return;
+    double a0 = 0.0, a1 = 0.0;
+    int64_t k = k0;
+    for (; k + 1 < k1; k += 2) {
+        const double g0 = Gc[k * N + i], g1 = Gc[(k + 1) * N + i];
+        if (SQUARE) {
+            a0 = fma(g0 * g0, m[k / plane], a0);
+            a1 = fma(g1 * g1, m[(k + 1) / plane], a1);
+        } else {
+            a0 = fma(g0, m[k], a0);
+            a1 = fma(g1, m[k + 1], a1);
+        }
+    }
+    if (k < k1) {
+        const double g0 = Gc[k * N + i];
+        a0 = SQUARE ? fma(g0 * g0, m[k / plane], a0) : fma(g0, m[k], a0);
+    }
+    part[(int64_t)blockIdx.y * N + i] = a0 + a1;
+}
+
+__global__ void __launch_bounds__(256) k_gemvt_cached(const double *__restrict__ Gc, int64_t N, int64_t M, int nx,
+                                                      int ny, const double *__restrict__ r,
+                                                      const double *__restrict__ w2, const double *__restrict__ add,
+                                                      double *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= M) return;
+    const double *row = Gc + k * N;
+    double a = 0.0;
+    for (int64_t i = lane; i < N; i += 32) a = fma(row[i], r[i], a);
+    a = warp_sum(a);
+    if (lane == 0) {
+        if (w2) a *= w2[k / ((int64_t)nx * ny)];
+        if (add) a += add[k];
+        out[k] = a;
+    }
+}
+
 }  // namespace
+
+void launch_build_g64(const grav_plan *p, double *Gc, double *diag, cudaStream_t s) {
+    const int tiles = (int)((p->N + 127) / 128);
+    dim3 grid(tiles, p->f64_diag_nchunk);
+    k_diag64<kDiagZC, true><<<grid, 128, 0, s>>>(make_geo(p), p->d_w2, p->f64_diag_jrows, p->sx, p->sy, p->sz,
+                                                 p->part, Gc);
+    note_launches(1);
+    if (diag) launch_reduce_rows(p->part, p->f64_diag_nchunk, p->N, 1.0, nullptr, 0.0, nullptr, diag, s);
+}
+
+void launch_cached_fwd(const grav_plan *p, const double *m, const double *add, double add_scale, double *d,
+                       cudaStream_t s) {
+    const int64_t per = (p->M + p->c_nchunk - 1) / p->c_nchunk;
+    dim3 grid((unsigned)((p->N + 127) / 128), (unsigned)p->c_nchunk);
+    stage_begin(p, kStageFwdMain, s);
+    k_gemv_cached<false><<<grid, 128, 0, s>>>(p->Gc, p->N, p->M, (int64_t)p->nx * p->ny, per, m, p->part);
+    stage_end(p, kStageFwdMain, s);
+    note_launches(1);
+    launch_reduce_rows(p->part, p->c_nchunk, p->N, 1.0, add, add_scale, nullptr, d, s);
+}
+
+void launch_cached_diag(const grav_plan *p, double *diag, cudaStream_t s) {
+    const int64_t per = (p->M + p->c_nchunk - 1) / p->c_nchunk;
+    dim3 grid((unsigned)((p->N + 127) / 128), (unsigned)p->c_nchunk);
+    k_gemv_cached<true><<<grid, 128, 0, s>>>(p->Gc, p->N, p->M, (int64_t)p->nx * p->ny, per, p->d_w2, p->part);
+    note_launches(1);
+    launch_reduce_rows(p->part, p->c_nchunk, p->N, 1.0, nullptr, 0.0, nullptr, diag, s);
+}
+
+void launch_cached_adj(const grav_plan *p, const double *r, int depth_weighted, const double *add, double *out,
+                       cudaStream_t s) {
+    const int64_t threads = p->M * 32;
+    stage_begin(p, kStageAdjMain, s);
+    k_gemvt_cached<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(p->Gc, p->N, p->M, p->nx, p->ny, r,
+                                                                    depth_weighted ? p->d_w2 : nullptr, add, out);
+    stage_end(p, kStageAdjMain, s);
+    note_launches(1);
+}
 
 size_t fwd64_smem_bytes(const grav_plan *p) {
     return 128 + (size_t)p->ldw * 8 + 2ull * fwd_rows_per_stage(p) * p->ldw * 8;
@@ -456,7 +548,8 @@ void launch_adj_finish(const grav_plan *p, const double *u, double scale, int de
 void launch_diag64(const grav_plan *p, double *diag, cudaStream_t s) {
     const int tiles = (int)((p->N + 127) / 128);
     dim3 grid(tiles, p->f64_diag_nchunk);
-    k_diag64<kDiagZC><<<grid, 128, 0, s>>>(make_geo(p), p->d_w2, p->f64_diag_jrows, p->sx, p->sy, p->sz, p->part);
+    k_diag64<kDiagZC, false><<<grid, 128, 0, s>>>(make_geo(p), p->d_w2, p->f64_diag_jrows, p->sx, p->sy, p->sz,
+                                                  p->part, nullptr);
     note_launches(1);
     launch_reduce_rows(p->part, p->f64_diag_nchunk, p->N, 1.0, nullptr, 0.0, nullptr, diag, s);
 }

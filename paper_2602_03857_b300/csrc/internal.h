@@ -27,6 +27,10 @@ struct MixedGeo {
     const float *cy;              // [ny][2]
     const float *czc;             // [nzp] cell-centre depth (FP32), padded
     int64_t N;
+    float qc;                     // (a^2 - c^2) / 24: quadrupole coefficient of the a x a x c cells (0: cubes)
+    const float *ex;              // [nx+1][2] x edges as (hi, lo) relative to x_ref (GRAV_MIXED_CORNER)
+    const float *ey;              // [ny+1][2]
+    const float *ez;              // [nz+1] edge depths (FP32)
 };
 
 // Near-field box of GRAV_MIXED: per station, a bx x by x bz block of cells
@@ -35,6 +39,7 @@ struct NearGeo {
     int bx, by, bz;
     int slots;                    // bx * by * bz
     double radius_cells;          // near_cells
+    double width;                 // cell width the radius is measured in: max(a, c)
     int nbx, nby;                 // bin grid: i0 + (bx-1) in [0, nbx)
 };
 
@@ -89,6 +94,8 @@ struct grav_plan {
     int64_t N = 0, M = 0, Nn = 0;
     std::vector<double> xe, ye, ze;       // host copies
     bool cubic = false;
+    bool square = false;                  // uniform a x a x c cells (GRAV_MIXED)
+    double cell_a = 0, cell_c = 0;
     grav::Arena arena;
     size_t bytes = 0;
 
@@ -107,6 +114,9 @@ struct grav_plan {
     double4 *st4 = nullptr;               // stations (x, y, z, r)
     double *upart = nullptr;              // adjoint partials [nschunk][Nn]
     double *u = nullptr;                  // [Nn]
+    int cached = 0;                       // 1: explicit G stored (FP64, cell-major [M][N])
+    int c_nchunk = 0;                     // cell chunks of the stored-G forward product
+    double *Gc = nullptr;
 
     // mixed path
     grav::MixedGeo mg{};
@@ -128,6 +138,9 @@ struct grav_plan {
     int *bin_st = nullptr;                // [N] station indices sorted by bin
     double *near_corr = nullptr;          // [N] forward near-field correction scratch
     double *m_cellacc = nullptr;          // [M] adjoint scratch
+    float *cr_w32 = nullptr;              // GRAV_MIXED_CORNER: node weights, FP32 rows of cr_ldw
+    double *cr_part = nullptr;            // [cr_nchunk][N] row-chunk partials of the corner forward
+    int cr_ldw = 0, cr_rows_per_chunk = 0, cr_nchunk = 0;
 
     // CG / diag scratch
     double *diag = nullptr;               // [N]
@@ -175,6 +188,12 @@ void launch_adj64(const grav_plan *p, const double *r, cudaStream_t s);
 void launch_adj_finish(const grav_plan *p, const double *u, double scale, int depth_weighted,
                        const double *add, double *out, cudaStream_t s);
 void launch_diag64(const grav_plan *p, double *diag, cudaStream_t s);
+void launch_build_g64(const grav_plan *p, double *Gc, double *diag, cudaStream_t s);
+void launch_cached_fwd(const grav_plan *p, const double *m, const double *add, double add_scale, double *d,
+                       cudaStream_t s);
+void launch_cached_diag(const grav_plan *p, double *diag, cudaStream_t s);
+void launch_cached_adj(const grav_plan *p, const double *r, int depth_weighted, const double *add, double *out,
+                       cudaStream_t s);
 size_t fwd64_smem_bytes(const grav_plan *p);
 int launch_fwd64_raw(Geo g, int ldw, const double *m, double *w, int rows_per_chunk, int nchunk,
                      const double *sx, const double *sy, const double *sz, double *part, int *status,
@@ -193,6 +212,7 @@ void launch_mixed_adj_finish(const grav_plan *p, const double *r, int depth_weig
 void launch_mixed_diag(const grav_plan *p, double *diag, cudaStream_t s);
 size_t mixed_scratch_bytes(const grav_plan *p);
 int mixed_adj_last_group(const grav_plan *p);
+void launch_corner_fwd(const grav_plan *p, const double *m, cudaStream_t s);
 
 // vector kernels (cg_kernels.cu)
 void launch_dot(const double *a, const double *b, int64_t n, double *partials, double *out, cudaStream_t s);

@@ -27,7 +27,8 @@ __device__ __forceinline__ float rsqrt_v(float x) {
     return r;
 }
 
-// op: 0 rsqrt, 1 lg2, 2 ffma, 3 dfma, 4 packed fma.rn.f32x2 (counted as 2 FP32 FMAs)
+// op: 0 rsqrt, 1 lg2, 2 ffma, 3 dfma, 4 packed fma.rn.f32x2 (counted as 2 FP32 FMAs),
+//     5 FP64 log, 6 FP64 atan, 7 FP64 sqrt, 8 FP64 division (CUDA's implementations)
 template <int OP>
 __global__ void k_pipe(int iters, float seed, float *out, unsigned long long *clk) {
     const uint64_t t0 = globaltimer_ns();
@@ -48,6 +49,23 @@ __global__ void k_pipe(int iters, float seed, float *out, unsigned long long *cl
             s += lo + hi;
         }
         if (s == 12345.678f) out[0] = s;
+    } else if (OP >= 5) {
+        double a[kChains];
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) a[k] = 1.5 + seed + 0.001 * (threadIdx.x + k);
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int k = 0; k < kChains; ++k) {
+                if (OP == 5) a[k] = log(a[k]) + 2.5;
+                else if (OP == 6) a[k] = atan(a[k]) + 1.25;
+                else if (OP == 7) a[k] = sqrt(a[k]) + 1.5;
+                else a[k] = 3.0 / a[k] + 1.0;
+            }
+        }
+        double s = 0;
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) s += a[k];
+        if (s == 12345.678) out[0] = (float)s;
     } else if (OP == 3) {
         double a[kChains];
 #pragma unroll
@@ -92,7 +110,7 @@ int run_one(int sms, double *ops_per_s, double *clk_mhz) {
     if (cudaMalloc(&out, 16) != cudaSuccess) return -1;
     if (cudaMalloc(&clk, 16) != cudaSuccess) return -1;
     const int blocks = sms * 8, threads = 256;
-    const int iters = (OP == 3) ? 256 : 4096;
+    const int iters = (OP == 3) ? 256 : (OP >= 5 ? 16 : 4096);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -135,6 +153,10 @@ extern "C" int grav_bench_pipes(int device, double *out) {
     rc |= run_one<3>(sms, &out[6], &out[7]);
     rc |= run_one<4>(sms, &out[8], &out[9]);
     out[10] = sms;
+    rc |= run_one<5>(sms, &out[11], &out[12]);
+    rc |= run_one<6>(sms, &out[13], &out[14]);
+    rc |= run_one<7>(sms, &out[15], &out[16]);
+    rc |= run_one<8>(sms, &out[17], &out[18]);
     cudaSetDevice(prev);
     return rc ? set_error(nullptr, GRAV_EDEVICE, "pipe microbenchmark failed") : GRAV_OK;
 }

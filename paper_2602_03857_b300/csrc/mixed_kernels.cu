@@ -18,6 +18,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <cub/device/device_radix_sort.cuh>
+#include <type_traits>
 
 #include "device_common.cuh"
 #include "internal.h"
@@ -118,7 +119,7 @@ __device__ __forceinline__ float far_h2(float2 X, float2 Y, float xh, float xl, 
 // in registers; the inner loop reads 4 layers of q and depth per LDS.128
 // (broadcast) and issues per pair: FADD, FFMA, MUFU.RSQ, 3 FMUL, FFMA.
 // ---------------------------------------------------------------------------
-template <int T>
+template <int T, bool QUAD>
 __global__ void __launch_bounds__(kMfThreads, GRAV_MF_MINB) k_mfwd(MixedGeo g, const float *__restrict__ qT,
                                                      const float4 *__restrict__ st32,
                                                      const float2 *__restrict__ stz, int cols_per_chunk,
@@ -172,6 +173,7 @@ __global__ void __launch_bounds__(kMfThreads, GRAV_MF_MINB) k_mfwd(MixedGeo g, c
         if (nst > 1) issue(1);
     }
     const int nl4 = g.nzp >> 2;
+    const f2_t qc2 = f2_pack(g.qc, g.qc);
     for (int st = 0; st < nst; ++st) {
         const int buf = st & 1;
         if (threadIdx.x == 0) *flag = mbar_wait_bounded(&bar[buf], (st >> 1) & 1) ? 1 : 0;
@@ -206,8 +208,8 @@ __global__ void __launch_bounds__(kMfThreads, GRAV_MF_MINB) k_mfwd(MixedGeo g, c
                 const f2_t z01 = f2_pack(z.x, z.y), z23 = f2_pack(z.z, z.w);
 #pragma unroll
                 for (int t = 0; t < T; ++t) {
-                    cs2[t] = far_pair_acc(z01, nzs[t], h2p[t], q01, cs2[t]);
-                    cs2[t] = far_pair_acc(z23, nzs[t], h2p[t], q23, cs2[t]);
+                    cs2[t] = far_pair<QUAD>(z01, nzs[t], h2p[t], q01, cs2[t], qc2);
+                    cs2[t] = far_pair<QUAD>(z23, nzs[t], h2p[t], q23, cs2[t], qc2);
                 }
             }
 #pragma unroll
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(kMfThreads, GRAV_MF_MINB) k_mfwd(MixedGeo g, c
 // sum into (hi, lo) by two-sum, and at the end the 32 lane values are reduced
 // by a warp-shuffle butterfly in FP64 (fixed order: deterministic).
 // ---------------------------------------------------------------------------
-template <int TZ>
+template <int TZ, bool QUAD>
 __global__ void __launch_bounds__(kMaWarps * 32, MaMinBlocks<TZ>::value) k_madj(MixedGeo g, const float4 *__restrict__ st32,
                                                         const float2 *__restrict__ stz, int ngz,
                                                         int64_t schunk_len, double *__restrict__ apart,
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(kMaWarps * 32, MaMinBlocks<TZ>::value) k_madj(
                 for (int t = 0; t < TZ; ++t) {
                     const float dz = zc[t] - Z.x;
                     const float R2 = fmaf(dz, dz, h2);
-                    cs[t] = fmaf(Z.y, far_kernel(dz, R2), cs[t]);
+                    cs[t] = fmaf(Z.y, far_k<QUAD>(dz, R2, g.qc), cs[t]);
                 }
             }
 #pragma unroll
@@ -357,7 +359,7 @@ constexpr int kAbWarps = 8;
 constexpr int kAbStage = 1024;
 constexpr int kAbFold = 128;
 
-template <int TZ>
+template <int TZ, bool QUAD>
 __device__ __forceinline__ void madj_bc_body(const MixedGeo &g, const float4 *__restrict__ st32,
                                              const float2 *__restrict__ stz, int l0, int cb, int64_t schunk_len,
                                              double *__restrict__ apart, int *status, unsigned char *smem_raw) {
@@ -373,6 +375,7 @@ __device__ __forceinline__ void madj_bc_body(const MixedGeo &g, const float4 *__
     const float2 X = make_float2(g.cx[2 * i], g.cx[2 * i + 1]);
     const float2 Y = make_float2(g.cy[2 * j], g.cy[2 * j + 1]);
     static_assert(TZ % 2 == 0, "layer pairs");
+    const f2_t qc2 = f2_pack(g.qc, g.qc);
     f2_t zcp[TZ / 2], cs2[TZ / 2];
     double acc[TZ];
 #pragma unroll
@@ -428,7 +431,7 @@ __device__ __forceinline__ void madj_bc_body(const MixedGeo &g, const float4 *__
                 const float h = far_h2(X, Y, P.x, P.y, P.z, P.w);
                 const f2_t h2p = f2_pack(h, h), nz2 = f2_pack(-Z.x, -Z.x), w2 = f2_pack(Z.y, Z.y);
 #pragma unroll
-                for (int u = 0; u < TZ / 2; ++u) cs2[u] = far_pair_acc(zcp[u], nz2, h2p, w2, cs2[u]);
+                for (int u = 0; u < TZ / 2; ++u) cs2[u] = far_pair<QUAD>(zcp[u], nz2, h2p, w2, cs2[u], qc2);
             }
 #pragma unroll
             for (int u = 0; u < TZ / 2; ++u) {
@@ -453,7 +456,7 @@ __device__ __forceinline__ void madj_bc_body(const MixedGeo &g, const float4 *__
 
 // Layer groups 0 .. ngz-2 hold TZ layers, the last group TZL (TZL <= TZ, a
 // multiple of 4 covering the remaining layers), so at most 3 padded layers.
-template <int TZ, int TZL>
+template <int TZ, int TZL, bool QUAD>
 __global__ void __launch_bounds__(kAbWarps * 32, GRAV_AB_MINB) k_madj_bc(MixedGeo g, const float4 *__restrict__ st32,
                                                                         const float2 *__restrict__ stz, int ngz,
                                                                         int64_t schunk_len,
@@ -463,9 +466,147 @@ __global__ void __launch_bounds__(kAbWarps * 32, GRAV_AB_MINB) k_madj_bc(MixedGe
     const int cb = blockIdx.x % cblocks;
     const int grp = blockIdx.x / cblocks;
     if (TZL == TZ || grp < ngz - 1)
-        madj_bc_body<TZ>(g, st32, stz, grp * TZ, cb, schunk_len, apart, status, smem_raw);
+        madj_bc_body<TZ, QUAD>(g, st32, stz, grp * TZ, cb, schunk_len, apart, status, smem_raw);
     else
-        madj_bc_body<TZL>(g, st32, stz, grp * TZ, cb, schunk_len, apart, status, smem_raw);
+        madj_bc_body<TZL, QUAD>(g, st32, stz, grp * TZ, cb, schunk_len, apart, status, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// GRAV_MIXED_CORNER forward (diagnostic of the literal FP32 corner-term
+// scheme): node weights in FP32 rows, Eq. 2-3 in FP32 once per (station,
+// node), FP32 row sums folded by two-sum; structure as the FP64 forward.
+// ---------------------------------------------------------------------------
+__global__ void k_node_weights32(int nx, int ny, int nz, int ldw, const double *__restrict__ m,
+                                 float *__restrict__ w) {
+    const int64_t total = (int64_t)(ny + 1) * (nz + 1) * ldw;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(t % ldw);
+        const int64_t r = t / ldw;
+        const int b = (int)(r % (ny + 1));
+        const int c = (int)(r / (ny + 1));
+        double acc = 0.0;
+        if (a <= nx) {
+            for (int dc = 0; dc < 2; ++dc) {
+                const int l = c - dc;
+                if (l < 0 || l >= nz) continue;
+                for (int db = 0; db < 2; ++db) {
+                    const int j = b - db;
+                    if (j < 0 || j >= ny) continue;
+                    for (int da = 0; da < 2; ++da) {
+                        const int i = a - da;
+                        if (i < 0 || i >= nx) continue;
+                        const double v = m[i + (int64_t)nx * (j + (int64_t)ny * l)];
+                        acc += ((da + db + dc) & 1) ? v : -v;
+                    }
+                }
+            }
+        }
+        w[t] = (float)acc;
+    }
+}
+
+constexpr int kCfThreads = 128;
+constexpr int kCfT = 4;
+
+template <int T>
+__global__ void __launch_bounds__(kCfThreads) k_cfwd32(MixedGeo g, int ldw, const float *__restrict__ w,
+                                                      int rows_per_chunk, int rows_per_stage,
+                                                      const float4 *__restrict__ st32, const float2 *__restrict__ stz,
+                                                      double *__restrict__ part, int *status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    int *flag = reinterpret_cast<int *>(smem_raw + 16);
+    float2 *exs = reinterpret_cast<float2 *>(smem_raw + 128);
+    float *wbuf = reinterpret_cast<float *>(smem_raw + 128 + (size_t)((g.nx + 1 + 1) / 2 * 2) * 8);
+    const int nrows = (g.ny + 1) * (g.nz + 1);
+    const int r0 = blockIdx.y * rows_per_chunk;
+    const int r1 = min(nrows, r0 + rows_per_chunk);
+    const int nst = (r1 > r0) ? (r1 - r0 + rows_per_stage - 1) / rows_per_stage : 0;
+    const int64_t s_base = (int64_t)blockIdx.x * (kCfThreads * T) + threadIdx.x;
+    float xh[T], xl[T], yh[T], yl[T], zs[T], hi[T], lo[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int64_t s = s_base + (int64_t)t * kCfThreads;
+        const bool ok = s < g.N;
+        const float4 P = ok ? st32[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+        xh[t] = P.x; xl[t] = P.y; yh[t] = P.z; yl[t] = P.w;
+        zs[t] = ok ? stz[s].x : -1.0f;
+        hi[t] = 0.f; lo[t] = 0.f;
+    }
+    for (int a = threadIdx.x; a <= g.nx; a += kCfThreads) exs[a] = make_float2(g.ex[2 * a], g.ex[2 * a + 1]);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int st) {
+        const int buf = st & 1;
+        const int ra = r0 + st * rows_per_stage;
+        const int rb = min(r1, ra + rows_per_stage);
+        const uint32_t bytes = (uint32_t)(rb - ra) * (uint32_t)ldw * 4u;
+        mbar_arrive_expect_tx(&bar[buf], bytes);
+        tma_load_1d(wbuf + (size_t)buf * rows_per_stage * ldw, w + (size_t)ra * ldw, bytes, &bar[buf]);
+    };
+    if (threadIdx.x == 0) {
+        if (nst > 0) issue(0);
+        if (nst > 1) issue(1);
+    }
+    for (int st = 0; st < nst; ++st) {
+        const int buf = st & 1;
+        if (threadIdx.x == 0) *flag = mbar_wait_bounded(&bar[buf], (st >> 1) & 1) ? 1 : 0;
+        __syncthreads();
+        if (!*flag) {
+            if (threadIdx.x == 0) {
+                set_status(status, kStatusMbarTimeout);
+                if (st + 1 < nst) (void)mbar_wait_bounded(&bar[buf ^ 1], ((st + 1) >> 1) & 1);
+            }
+            return;
+        }
+        const float *wb = wbuf + (size_t)buf * rows_per_stage * ldw;
+        const int ra = r0 + st * rows_per_stage;
+        const int rb = min(r1, ra + rows_per_stage);
+        for (int r = ra; r < rb; ++r) {
+            const int b = r % (g.ny + 1), c = r / (g.ny + 1);
+            const float2 EY = make_float2(g.ey[2 * b], g.ey[2 * b + 1]);
+            const float Zc = g.ez[c];
+            float dy[T], dz[T], rs[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                dy[t] = (EY.x - yh[t]) + (EY.y - yl[t]);
+                dz[t] = Zc - zs[t];
+                rs[t] = 0.f;
+            }
+            const float *wr = wb + (size_t)(r - ra) * ldw;
+            for (int a = 0; a <= g.nx; ++a) {
+                const float wv = wr[a];
+                if (wv == 0.0f) continue;
+                const float2 EX = exs[a];
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const float dx = (EX.x - xh[t]) + (EX.y - xl[t]);
+                    rs[t] = fmaf(wv, psi32(dx, dy[t], dz[t]), rs[t]);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                float sum, e;
+                two_sum(hi[t], rs[t], sum, e);
+                hi[t] = sum;
+                lo[t] += e;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && st + 2 < nst) {
+            fence_proxy_async_smem();
+            issue(st + 2);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int64_t s = s_base + (int64_t)t * kCfThreads;
+        if (s < g.N) part[(int64_t)blockIdx.y * g.N + s] = (double)hi[t] + (double)lo[t];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -476,6 +617,7 @@ __global__ void __launch_bounds__(kAbWarps * 32, GRAV_AB_MINB) k_madj_bc(MixedGe
 // sum w2 (G_exact^2 - G_far^2), the box origin and the station's bin key.
 // The mesh is uniform cubic: x edges x0 + i a, y edges y0 + j a.
 // ---------------------------------------------------------------------------
+template <bool CORNER>
 __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
     Geo g, MixedGeo mg, NearGeo ng, double x0, double y0, double a, double vol_mgal,
     const double *__restrict__ sx, const double *__restrict__ sy, const double *__restrict__ sz,
@@ -486,13 +628,19 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nbx1 = ng.bx + 1, nby1 = ng.by + 1;
     const int nnode = nbx1 * nby1 * (ng.bz + 1);
+    const int nwarps = blockDim.x >> 5;
     double *P = reinterpret_cast<double *>(smem_raw) + (size_t)warp * nnode;
+    float *P32 = reinterpret_cast<float *>(reinterpret_cast<double *>(smem_raw) + (size_t)nwarps * nnode) +
+                 (size_t)warp * nnode;
     const int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     if (s >= g.N) return;   // warp-uniform
     const double xs = sx[s], ys = sy[s], zs = sz[s];
     const double lim = 1.0e9;
-    const double fx = fmin(fmax((xs - x0) / a - 0.5 - ng.radius_cells, -lim), lim);
-    const double fy = fmin(fmax((ys - y0) / a - 0.5 - ng.radius_cells, -lim), lim);
+    // window radius k * width in units of the horizontal cell size a (width =
+    // max(a, c), so the radius spans k * width / a >= k columns)
+    const double rad = ng.radius_cells * ng.width / a;
+    const double fx = fmin(fmax((xs - x0) / a - 0.5 - rad, -lim), lim);
+    const double fy = fmin(fmax((ys - y0) / a - 0.5 - rad, -lim), lim);
     const int i0 = (int)floor(fx) + 1;
     const int j0 = (int)floor(fy) + 1;
     for (int t = lane; t < nnode; t += 32) {
@@ -506,10 +654,27 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
         }
         P[t] = v;
     }
-    __syncwarp();
     const float4 S = st32[s];
     const float zf = stz[s].x;
-    const double r2max = (ng.radius_cells * a) * (ng.radius_cells * a);
+    if (CORNER) {
+        // the FP32 corner function at the same nodes, from exactly the FP32
+        // coordinates the node-shared FP32 forward uses
+        for (int t = lane; t < nnode; t += 32) {
+            const int ia = i0 + t % nbx1;
+            const int jb = j0 + (t / nbx1) % nby1;
+            const int c = t / (nbx1 * nby1);
+            float v = 0.0f;
+            if (ia >= 0 && ia <= g.nx && jb >= 0 && jb <= g.ny && c <= g.nz) {
+                const float dx = (mg.ex[2 * ia] - S.x) + (mg.ex[2 * ia + 1] - S.y);
+                const float dy = (mg.ey[2 * jb] - S.z) + (mg.ey[2 * jb + 1] - S.w);
+                const float dz = mg.ez[c] - zf;
+                v = psi32(dx, dy, dz);
+            }
+            P32[t] = v;
+        }
+    }
+    __syncwarp();
+    const double r2max = (ng.radius_cells * ng.width) * (ng.radius_cells * ng.width);
     const int sxs = 1, sys = nbx1, szs = nbx1 * nby1;
     double dcorr = 0.0;
     for (int t = lane; t < ng.slots; t += 32) {
@@ -528,12 +693,21 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
                 const double E = -P[n0] + P[n0 + sxs] + P[n0 + sys] - P[n0 + sxs + sys] + P[n0 + szs] -
                                  P[n0 + sxs + szs] - P[n0 + sys + szs] + P[n0 + sxs + sys + szs];
                 const double gex = kGammaMgal * E;
-                const float2 X = make_float2(mg.cx[2 * i], mg.cx[2 * i + 1]);
-                const float2 Y = make_float2(mg.cy[2 * j], mg.cy[2 * j + 1]);
-                const float h2 = far_h2(X, Y, S.x, S.y, S.z, S.w);
-                const float dz = mg.czc[l] - zf;
-                const float R2 = fmaf(dz, dz, h2);
-                const double gfar = vol_mgal * (double)far_kernel(dz, R2);
+                double gfar;
+                if (CORNER) {
+                    const double E32 = -(double)P32[n0] + (double)P32[n0 + sxs] + (double)P32[n0 + sys] -
+                                       (double)P32[n0 + sxs + sys] + (double)P32[n0 + szs] -
+                                       (double)P32[n0 + sxs + szs] - (double)P32[n0 + sys + szs] +
+                                       (double)P32[n0 + sxs + sys + szs];
+                    gfar = kGammaMgal * E32;
+                } else {
+                    const float2 X = make_float2(mg.cx[2 * i], mg.cx[2 * i + 1]);
+                    const float2 Y = make_float2(mg.cy[2 * j], mg.cy[2 * j + 1]);
+                    const float h2 = far_h2(X, Y, S.x, S.y, S.z, S.w);
+                    const float dz = mg.czc[l] - zf;
+                    const float R2 = fmaf(dz, dz, h2);
+                    gfar = vol_mgal * (double)far_kernel_q(dz, R2, mg.qc);
+                }
                 val = gex - gfar;
                 dcorr += w2[l] * (gex * gex - gfar * gfar);
             }
@@ -639,7 +813,7 @@ __global__ void k_madj_finish(int nx, int ny, int nz, int bz, const double *__re
 
 // Far-field part of diag(G W^-2 G^T): sum_k w2_l (dz/R^3)^2 per station
 // (times vol^2 later); thread = T stations, grid.y = column chunks.
-template <int T>
+template <int T, bool QUAD>
 __global__ void __launch_bounds__(kMfThreads) k_mdiag(MixedGeo g, const float *__restrict__ w2f,
                                                       const float4 *__restrict__ st32,
                                                       const float2 *__restrict__ stz, int cols_per_chunk,
@@ -672,7 +846,7 @@ __global__ void __launch_bounds__(kMfThreads) k_mdiag(MixedGeo g, const float *_
 #pragma unroll
             for (int t = 0; t < T; ++t) {
                 const float dz = zc - zs[t];
-                const float k = far_kernel(dz, fmaf(dz, dz, h2[t]));
+                const float k = far_k<QUAD>(dz, fmaf(dz, dz, h2[t]), g.qc);
                 cs[t] = fmaf(wl, k * k, cs[t]);
             }
         }
@@ -792,6 +966,29 @@ static MixedSizes mixed_sizes(const grav_plan *p) {
     return z;
 }
 
+// GRAV_MIXED_CORNER forward sizing: FP32 node-weight rows padded to 16 bytes,
+// row chunks so that the grid holds >= 8 CTAs per SM.
+struct CornerSizes {
+    int ldw, rows_per_chunk, nchunk;
+};
+constexpr int kCfRowsPerStage = 8;
+
+static CornerSizes corner_sizes(const grav_plan *p) {
+    CornerSizes c{};
+    c.ldw = (p->nx + 1 + 3) / 4 * 4;
+    const int nrows = (p->ny + 1) * (p->nz + 1);
+    const int64_t tiles = (p->N + kCfThreads * kCfT - 1) / (kCfThreads * kCfT);
+    const int64_t want = std::max<int64_t>(1, (148LL * 8 + tiles - 1) / tiles);
+    const int nchunk = (int)std::min<int64_t>(want, std::max(1, nrows / kCfRowsPerStage));
+    c.rows_per_chunk = (nrows + nchunk - 1) / nchunk;
+    c.nchunk = (nrows + c.rows_per_chunk - 1) / c.rows_per_chunk;
+    return c;
+}
+
+static size_t cfwd_smem(const grav_plan *p) {
+    return 128 + (size_t)((p->nx + 2) / 2 * 2) * 8 + 2ull * kCfRowsPerStage * corner_sizes(p).ldw * 4;
+}
+
 size_t mixed_scratch_bytes(const grav_plan *p) {
     const MixedSizes z = mixed_sizes(p);
     const int64_t N = p->N, M = p->M;
@@ -812,6 +1009,12 @@ size_t mixed_scratch_bytes(const grav_plan *p) {
     add(4ull * (z.nbins + 2));                                              // bin_start
     add(z.cub_temp);
     add(8ull * std::max<int64_t>(N, 1) * std::max(z.nchunk, 1));            // diag partials
+    if (p->opt.precision == GRAV_MIXED_CORNER) {
+        const CornerSizes c = corner_sizes(p);
+        add(8ull * (p->nx + 1)); add(8ull * (p->ny + 1)); add(4ull * (p->nz + 1));   // ex, ey, ez
+        add(4ull * (p->ny + 1) * (p->nz + 1) * c.ldw);                              // FP32 node weights
+        add(8ull * c.nchunk * N);                                                   // row-chunk partials
+    }
     return b;
 }
 
@@ -821,7 +1024,8 @@ static void *take(grav_plan *p, size_t bytes) {
 }
 
 int near_setup_warps(const grav_plan *p) {
-    const size_t per_warp = (size_t)(p->ng.bx + 1) * (p->ng.by + 1) * (p->ng.bz + 1) * 8;
+    const size_t per_node = p->opt.precision == GRAV_MIXED_CORNER ? 12 : 8;   // FP64 (+ FP32) corner values
+    const size_t per_warp = (size_t)(p->ng.bx + 1) * (p->ng.by + 1) * (p->ng.bz + 1) * per_node;
     const size_t cap = 200 * 1024;
     return (int)std::min<size_t>(kNsWarps, cap / per_warp);
 }
@@ -884,10 +1088,43 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
     p->bin_start = (int *)take(p, 4ull * (z.nbins + 2));
     void *cub_tmp = take(p, std::max<size_t>(z.cub_temp, 16));
     p->m_w2f = w2f;
+    const bool corner = p->opt.precision == GRAV_MIXED_CORNER;
+    std::vector<float> hex, hey, hez;
+    if (corner) {
+        const CornerSizes c = corner_sizes(p);
+        p->cr_ldw = c.ldw;
+        p->cr_rows_per_chunk = c.rows_per_chunk;
+        p->cr_nchunk = c.nchunk;
+        hex.resize(2 * (nx + 1));
+        hey.resize(2 * (ny + 1));
+        hez.resize(nz + 1);
+        for (int i = 0; i <= nx; ++i) {
+            const double v = p->xe[i] - xref;
+            hex[2 * i] = (float)v;
+            hex[2 * i + 1] = (float)(v - (double)(float)v);
+        }
+        for (int j = 0; j <= ny; ++j) {
+            const double v = p->ye[j] - yref;
+            hey[2 * j] = (float)v;
+            hey[2 * j + 1] = (float)(v - (double)(float)v);
+        }
+        for (int l = 0; l <= nz; ++l) hez[l] = (float)p->ze[l];
+        p->mg.ex = (const float *)take(p, 8ull * (nx + 1));
+        p->mg.ey = (const float *)take(p, 8ull * (ny + 1));
+        p->mg.ez = (const float *)take(p, 4ull * (nz + 1));
+        p->cr_w32 = (float *)take(p, 4ull * (ny + 1) * (nz + 1) * c.ldw);
+        p->cr_part = (double *)take(p, 8ull * c.nchunk * p->N);
+    }
     if (p->arena.overflow) return GRAV_EDEVICE;
+    if (corner) {
+        cudaMemcpyAsync((void *)p->mg.ex, hex.data(), 8ull * (nx + 1), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync((void *)p->mg.ey, hey.data(), 8ull * (ny + 1), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync((void *)p->mg.ez, hez.data(), 4ull * (nz + 1), cudaMemcpyHostToDevice, s);
+    }
 
     p->mg.nx = nx; p->mg.ny = ny; p->mg.nz = nz; p->mg.nzp = nzp; p->mg.ncol = nx * ny;
     p->mg.cx = p->m_cx; p->mg.cy = p->m_cy; p->mg.czc = p->m_czc; p->mg.N = p->N;
+    p->mg.qc = p->cubic ? 0.0f : (float)((p->cell_a * p->cell_a - p->cell_c * p->cell_c) / 24.0);
 
     cudaMemcpyAsync(p->m_cx, hcx.data(), 8ull * nx, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(p->m_cy, hcy.data(), 8ull * ny, cudaMemcpyHostToDevice, s);
@@ -897,12 +1134,15 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
     k_prep_stations<<<grid_for(p->N, 256), 256, 0, s>>>(p->sx, p->sy, p->sz, p->N, xref, yref, p->st32, p->stz);
 
     const int nnode = (p->ng.bx + 1) * (p->ng.by + 1) * (p->ng.bz + 1);
-    const size_t smem = (size_t)ns_warps * nnode * 8;
-    cudaFuncSetAttribute(k_near_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    const double vol_mgal = kGammaMgal * a * a * a;
-    k_near_setup<<<(unsigned)((p->N + ns_warps - 1) / ns_warps), ns_warps * 32, smem, s>>>(
-        make_geo(p), p->mg, p->ng, p->xe[0], p->ye[0], a, vol_mgal, p->sx, p->sy, p->sz, p->d_w2, p->st32,
-        p->stz, p->dG, p->st_i0, p->st_j0, p->diag_corr, keys, vals, (unsigned)z.nbins);
+    const size_t smem = (size_t)ns_warps * nnode * (corner ? 12 : 8);
+    const double vol_mgal = kGammaMgal * p->cell_a * p->cell_a * p->cell_c;
+    auto setup = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        kern<<<(unsigned)((p->N + ns_warps - 1) / ns_warps), ns_warps * 32, smem, s>>>(
+            make_geo(p), p->mg, p->ng, p->xe[0], p->ye[0], a, vol_mgal, p->sx, p->sy, p->sz, p->d_w2, p->st32,
+            p->stz, p->dG, p->st_i0, p->st_j0, p->diag_corr, keys, vals, (unsigned)z.nbins);
+    };
+    if (corner) setup(k_near_setup<true>); else setup(k_near_setup<false>);
     size_t tmp = z.cub_temp;
     cub::DeviceRadixSort::SortPairs(cub_tmp, tmp, keys, keys_sorted, vals, p->bin_st, (int)p->N, 0, z.key_bits, s);
     k_bin_bounds<<<grid_for(z.nbins + 1, 256), 256, 0, s>>>(keys_sorted, p->N, z.nbins, p->bin_start);
@@ -916,8 +1156,7 @@ int mixed_adj_last_group(const grav_plan *p) { return p->m_adj_bc ? adj_tzl_bc(p
 size_t mfwd_smem(const grav_plan *p) { return mfwd_layout(p->mg, kMfColsPerStage).total; }
 
 void launch_mixed_prep_q(const grav_plan *p, const double *m, cudaStream_t s) {
-    const double a = p->xe[1] - p->xe[0];
-    const float scale = (float)(kGammaMgal * a * a * a);
+    const float scale = (float)(kGammaMgal * p->cell_a * p->cell_a * p->cell_c);
     const int64_t total = (int64_t)p->mg.ncol * p->mg.nzp;
     k_prep_q<<<grid_for(total, 256), 256, 0, s>>>(p->mg, m, scale, p->qT);
     note_launches(1);
@@ -927,12 +1166,29 @@ void launch_mixed_fwd(const grav_plan *p, cudaStream_t s) {
     const int tiles = (int)((p->N + kMfThreads * kMfT - 1) / (kMfThreads * kMfT));
     dim3 grid(tiles, p->m_fwd_nchunk);
     const size_t smem = mfwd_smem(p);
-    cudaFuncSetAttribute(k_mfwd<kMfT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    stage_begin(p, kStageFwdMain, s);
-    k_mfwd<kMfT><<<grid, kMfThreads, smem, s>>>(p->mg, p->qT, p->st32, p->stz, p->m_fwd_cols_per_chunk,
-                                               kMfColsPerStage, p->m_part, p->ctx->d_status);
-    stage_end(p, kStageFwdMain, s);
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        stage_begin(p, kStageFwdMain, s);
+        kern<<<grid, kMfThreads, smem, s>>>(p->mg, p->qT, p->st32, p->stz, p->m_fwd_cols_per_chunk, kMfColsPerStage,
+                                            p->m_part, p->ctx->d_status);
+        stage_end(p, kStageFwdMain, s);
+    };
+    if (p->cubic) go(k_mfwd<kMfT, false>); else go(k_mfwd<kMfT, true>);
     note_launches(1);
+}
+
+void launch_corner_fwd(const grav_plan *p, const double *m, cudaStream_t s) {
+    const int64_t total = (int64_t)(p->ny + 1) * (p->nz + 1) * p->cr_ldw;
+    k_node_weights32<<<grid_for(total, 256), 256, 0, s>>>(p->nx, p->ny, p->nz, p->cr_ldw, m, p->cr_w32);
+    const int tiles = (int)((p->N + kCfThreads * kCfT - 1) / (kCfThreads * kCfT));
+    dim3 grid(tiles, p->cr_nchunk);
+    cudaFuncSetAttribute(k_cfwd32<kCfT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    stage_begin(p, kStageFwdMain, s);
+    k_cfwd32<kCfT><<<grid, kCfThreads, cfwd_smem(p), s>>>(p->mg, p->cr_ldw, p->cr_w32, p->cr_rows_per_chunk,
+                                                          kCfRowsPerStage, p->st32, p->stz, p->cr_part,
+                                                          p->ctx->d_status);
+    stage_end(p, kStageFwdMain, s);
+    note_launches(2);
 }
 
 void launch_mixed_near_fwd(const grav_plan *p, const double *m, cudaStream_t s) {
@@ -966,27 +1222,35 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
                                                   p->m_apart, p->ctx->d_status);
         };
         const int tzl = adj_tzl_bc(p->nz);
-        if (p->m_adj_tz == 16) {
-            switch (tzl) {
-                case 4: gob(k_madj_bc<16, 4>); break;
-                case 8: gob(k_madj_bc<16, 8>); break;
-                case 12: gob(k_madj_bc<16, 12>); break;
-                default: gob(k_madj_bc<16, 16>); break;
+        auto pick = [&](auto quad) {
+            constexpr bool Q = decltype(quad)::value;
+            if (p->m_adj_tz == 16) {
+                switch (tzl) {
+                    case 4: gob(k_madj_bc<16, 4, Q>); break;
+                    case 8: gob(k_madj_bc<16, 8, Q>); break;
+                    case 12: gob(k_madj_bc<16, 12, Q>); break;
+                    default: gob(k_madj_bc<16, 16, Q>); break;
+                }
+            } else {
+                switch (p->m_adj_tz) {
+                    case 4: gob(k_madj_bc<4, 4, Q>); break;
+                    case 8: gob(k_madj_bc<8, 8, Q>); break;
+                    default: gob(k_madj_bc<12, 12, Q>); break;
+                }
             }
-        } else {
-            switch (p->m_adj_tz) {
-                case 4: gob(k_madj_bc<4, 4>); break;
-                case 8: gob(k_madj_bc<8, 8>); break;
-                default: gob(k_madj_bc<12, 12>); break;
-            }
-        }
+        };
+        if (p->cubic) pick(std::false_type{}); else pick(std::true_type{});
     } else {
-        switch (p->m_adj_tz) {
-            case 16: go(k_madj<16>); break;
-            case 15: go(k_madj<15>); break;
-            case 12: go(k_madj<12>); break;
-            default: go(k_madj<8>); break;
-        }
+        auto pick = [&](auto quad) {
+            constexpr bool Q = decltype(quad)::value;
+            switch (p->m_adj_tz) {
+                case 16: go(k_madj<16, Q>); break;
+                case 15: go(k_madj<15, Q>); break;
+                case 12: go(k_madj<12, Q>); break;
+                default: go(k_madj<8, Q>); break;
+            }
+        };
+        if (p->cubic) pick(std::false_type{}); else pick(std::true_type{});
     }
     stage_end(p, kStageAdjMain, s);
     const int lz = std::min(p->ng.bz, p->nz);
@@ -1001,9 +1265,9 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
 void launch_mixed_adj_finish(const grav_plan *p, const double *r, int depth_weighted, const double *add,
                              double *out, cudaStream_t s) {
     (void)r;
-    const double a = p->xe[1] - p->xe[0];
     k_madj_finish<<<grid_for(p->M, 256), 256, 0, s>>>(p->nx, p->ny, p->nz, std::min(p->ng.bz, p->nz), p->m_apart,
-                                                      p->m_adj_nschunk, kGammaMgal * a * a * a, p->m_cellacc,
+                                                      p->m_adj_nschunk,
+                                                      kGammaMgal * p->cell_a * p->cell_a * p->cell_c, p->m_cellacc,
                                                       depth_weighted ? p->d_w2 : nullptr, add, out);
     note_launches(1);
 }
@@ -1011,11 +1275,14 @@ void launch_mixed_adj_finish(const grav_plan *p, const double *r, int depth_weig
 void launch_mixed_diag(const grav_plan *p, double *diag, cudaStream_t s) {
     const int tiles = (int)((p->N + kMfThreads * kMfT - 1) / (kMfThreads * kMfT));
     dim3 grid(tiles, p->m_fwd_nchunk);
-    k_mdiag<kMfT><<<grid, kMfThreads, 0, s>>>(p->mg, p->m_w2f, p->st32, p->stz, p->m_fwd_cols_per_chunk,
-                                             p->m_part);
+    if (p->cubic)
+        k_mdiag<kMfT, false><<<grid, kMfThreads, 0, s>>>(p->mg, p->m_w2f, p->st32, p->stz, p->m_fwd_cols_per_chunk,
+                                                         p->m_part);
+    else
+        k_mdiag<kMfT, true><<<grid, kMfThreads, 0, s>>>(p->mg, p->m_w2f, p->st32, p->stz, p->m_fwd_cols_per_chunk,
+                                                        p->m_part);
     note_launches(1);
-    const double a = p->xe[1] - p->xe[0];
-    const double v = kGammaMgal * a * a * a;
+    const double v = kGammaMgal * p->cell_a * p->cell_a * p->cell_c;
     launch_reduce_rows(p->m_part, p->m_fwd_nchunk, p->N, v * v, nullptr, 0.0, p->diag_corr, diag, s);
 }
 

@@ -228,11 +228,56 @@ def paper_210x210x75(seed: int = 0, n_stations: int = 178_797) -> Workload:
                     description="210x210x75 mesh of 100 m cubes (3,307,500 cells), 178,797 random stations at 1-50 m, layered + 3 dipping dykes")
 
 
+def two_body_160x160x80(seed: int = 0) -> Workload:
+    """The paper's two-body synthetic (Section 4.1) in shape: 2.05M cubic 125 m
+    cells (20 x 20 x 10 km) under 66 x 66 = 4,356 stations at 10 m height; two
+    prisms at +1000 kg/m^3: 13-17 km laterally and 1.5-3 km deep, 6-10 km
+    laterally and 0.5-3 km deep; 1 % RMS Gaussian noise."""
+    a = 125.0
+    mesh = uniform_mesh(160, 160, 80, a, a, a)
+    survey = grid_survey(0.0, 20000.0, 66, 0.0, 20000.0, 66, 10.0)
+    m = np.zeros((80, 160, 160))
+    idx = lambda v: int(round(v / a))
+    m[idx(1500):idx(3000), idx(13000):idx(17000), idx(13000):idx(17000)] = 1000.0
+    m[idx(500):idx(3000), idx(6000):idx(10000), idx(6000):idx(10000)] = 1000.0
+    return Workload("two_body_160x160x80", mesh, survey, m.ravel(), z0=50.0, tol=1e-6, noise_rel=0.01,
+                    precision="mixed", description="two prisms +1000 kg/m^3, 160x160x80 of 125 m, 66x66 stations")
+
+
+def tube_slab_100x100x50(seed: int = 0) -> Workload:
+    """The paper's curvilinear-tube + dipping-slab synthetic (Section 4.2) in
+    shape: 100 x 100 x 50 prisms of 200 x 200 x 100 m (square-based, not cubic),
+    196 x 196 = 38,416 stations at 10 m height; a sinuous tube of varying width
+    at -1000 kg/m^3 from 1 to 4 km depth and a slab dipping 40 degrees toward
+    +y at +1000 kg/m^3.  The paper describes the bodies only qualitatively; this
+    is one seeded realisation."""
+    rng = np.random.Generator(np.random.PCG64(8000 + seed))
+    mesh = uniform_mesh(100, 100, 50, 200.0, 200.0, 100.0)
+    survey = grid_survey(0.0, 20000.0, 196, 0.0, 20000.0, 196, 10.0)
+    X, Y, Z = _cell_centres(mesh)
+    m = np.zeros(X.shape)
+    # tube: centreline y = 6 km + 1.5 km sin(2 pi x / 8 km + phase) for x in [2, 18] km
+    phase = rng.uniform(0, 2 * math.pi)
+    yc = 6000.0 + 1500.0 * np.sin(2 * math.pi * X / 8000.0 + phase)
+    width = 600.0 + 300.0 * np.sin(2 * math.pi * X / 5000.0)
+    tube = (np.abs(Y - yc) < 0.5 * width) & (X > 2000) & (X < 18000) & (Z > 1000) & (Z < 4000)
+    m[tube] = -1000.0
+    # slab: top trace at y = 12 km, dipping 40 degrees toward +y, 600 m thick, x in [4, 16] km
+    dip = math.radians(40.0)
+    dist = (Y - 12000.0) * math.sin(dip) - Z * math.cos(dip)
+    slab = (np.abs(dist) < 300.0) & (X > 4000) & (X < 16000) & (Y >= 12000.0) & (Z < 4500)
+    m[slab] = 1000.0
+    return Workload("tube_slab_100x100x50", mesh, survey, m.ravel(), z0=50.0, tol=1e-6, precision="mixed",
+                    description="100x100x50 prisms of 200x200x100 m, 196x196 stations, tube -1000 + 40 deg slab +1000")
+
+
 WORKLOADS: Dict[str, Callable[..., Workload]] = {
     "block_20x20x10": block_20x20x10,
     "vslab_80x80x40": vslab_80x80x40,
     "dipdyke_150x150x60": dipdyke_150x150x60,
     "paper_210x210x75": paper_210x210x75,
+    "two_body_160x160x80": two_body_160x160x80,
+    "tube_slab_100x100x50": tube_slab_100x100x50,
 }
 
 

@@ -62,3 +62,12 @@ def test_ctx_create_rejects_bad_device_without_gpu(lib):
     rc = g._lib.grav_ctx_create(ctypes.byref(h), -1, 0)
     assert rc != 0
     assert len(g._lib.grav_last_error(None)) > 0
+
+
+def test_binding_constants_match_header():
+    import paper_2602_03857_b300 as g
+    text = open(HEADER).read()
+    for name, val in re.findall(r"#define\s+(GRAV_[A-Z0-9_]+)\s+(-?\d+)\b", text):
+        if hasattr(g, name):
+            assert getattr(g, name) == int(val), name
+    assert g.PRECISIONS == {"fp64": 0, "mixed": 1, "mixed_corner": 2}
