@@ -338,10 +338,12 @@ def run_ours(args):
 def extras(args, g, torch, wl, plan, d, line):
     # CPU oracle on a bounded sample; its forward sample also measures the
     # error of this run's result against the FP64 oracle
-    pps, sec, th, idx, d_ref, (tf, ta) = oracle_sample(wl, args.cpu_stations, args.cpu_cells)
+    # (4x the stations and 2x the cells of one reference-arm step: ~10-15 s of CPU work)
+    n_st, n_cells = 4 * args.cpu_stations, 2 * args.cpu_cells
+    pps, sec, th, idx, d_ref, (tf, ta) = oracle_sample(wl, n_st, n_cells)
     line["cpu_baseline"] = {"value": pps, "unit": "pairs/s", "cores": th, "kind": "oracle",
-                            "sample": f"forward of {args.cpu_stations} seeded stations over all {wl.mesh.ncells} "
-                                      f"cells + adjoint of {args.cpu_cells} seeded cells over all {wl.survey.n} "
+                            "sample": f"forward of {n_st} seeded stations over all {wl.mesh.ncells} "
+                                      f"cells + adjoint of {n_cells} seeded cells over all {wl.survey.n} "
                                       f"stations ({sec:.1f} s)"}
     dg = d.cpu().numpy()[idx]
     line["error_vs_fp64_oracle"] = {

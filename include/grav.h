@@ -90,7 +90,9 @@ typedef struct {
 } grav_mesh;
 
 typedef struct {
-    int64_t n;                 /* number of stations, >= 1 */
+    int64_t n;                 /* number of stations: >= 1 for plans and jobs; the one-shot calls also take
+                                  n = 0 (x, y, z unused): forward writes nothing, adjoint writes zeros, diag
+                                  writes nothing (trace 0), the inversion writes m_ref (or zeros) */
     const double *x, *y, *z;   /* DEVICE arrays of n doubles; z = -(height above z = 0) */
 } grav_survey;
 
@@ -123,6 +125,7 @@ typedef struct {
     double seconds;            /* wall time of the solve */
     int outer;                 /* outer updates performed (outer_max > 0) */
     double alpha_min;          /* smallest accepted step length of the outer loop (1 if never backtracked) */
+    int restarts;              /* single CG solve: restarts from the recomputed true residual */
 } grav_solve_info;
 
 typedef struct grav_ctx grav_ctx;
@@ -305,8 +308,18 @@ int grav_plan_timing(grav_plan *plan, int enable, double *ms, int64_t *counts);
  * [4] FP32 FMA/s, [5] MHz, [6] FP64 FMA/s, [7] MHz, [8] FP32 FMA/s issued as
  * packed fma.rn.f32x2, [9] MHz, [10] SM count, then CUDA's FP64 functions:
  * [11] log/s, [12] MHz, [13] atan/s, [14] MHz, [15] sqrt/s, [16] MHz,
- * [17] divisions/s, [18] MHz.  Per-clock rates per SM: rate / (MHz*1e6 * out[10]). */
+ * [17] divisions/s, [18] MHz, then this library's table-driven FP64 functions
+ * used inside Eq. 2-3: [19] log/s, [20] MHz, [21] atan(a/b)/s, [22] MHz.
+ * out: HOST, >= 23 doubles.  Per-clock rates per SM: rate / (MHz*1e6 * out[10]). */
 int grav_bench_pipes(int device, double *out);
+
+/* Self-check of the FP64 elementary functions inside Eq. 2-3 (the paper has
+ * no counterpart): out[i] = f(a[i], b[i]) on ctx's device, with fn = 0 this
+ * library's log(a), 1 its atan(a / b) (b > 0), 2 CUDA's log(a), 3 CUDA's
+ * atan(a / b).  a, b (fn 1 and 3 only), out: DEVICE, n doubles.  Enqueued on
+ * `stream`; GRAV_EINVAL for a bad fn, n < 0 or NULL pointers. */
+int grav_eval_fn64(grav_ctx *ctx, int fn, const double *a, const double *b, double *out, int64_t n,
+                   grav_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -73,7 +73,8 @@ class grav_job(ctypes.Structure):
 class grav_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("rel_res", ctypes.c_double),
                 ("true_rel_res", ctypes.c_double), ("lambda_", ctypes.c_double), ("trace", ctypes.c_double),
-                ("seconds", ctypes.c_double), ("outer", ctypes.c_int), ("alpha_min", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("outer", ctypes.c_int), ("alpha_min", ctypes.c_double),
+                ("restarts", ctypes.c_int)]
 
 
 def _sig(name, res, args):
@@ -115,6 +116,7 @@ _sig("grav_wait", _i, [_vp, ctypes.c_uint64, ctypes.c_double])
 _sig("grav_cancel", _i, [_vp, ctypes.c_uint64])
 _sig("grav_job_times", _i, [_vp, ctypes.c_uint64, _D, _D, _D])
 _sig("grav_job_release", _i, [_vp, ctypes.c_uint64])
+_sig("grav_eval_fn64", _i, [_vp, _i, _vp, _vp, _vp, ctypes.c_int64, _vp])
 
 EXPORTED = [
     "grav_options_default", "grav_version", "grav_ctx_create", "grav_ctx_destroy", "grav_last_error",
@@ -122,10 +124,24 @@ EXPORTED = [
     "grav_plan_forward", "grav_plan_adjoint", "grav_plan_bytes", "grav_plan_destroy",
     "grav_launch_count", "grav_plan_timing", "grav_bench_pipes", "grav_plan_describe",
     "grav_serve_config", "grav_submit", "grav_poll", "grav_wait", "grav_cancel", "grav_job_times",
-    "grav_job_release",
+    "grav_job_release", "grav_eval_fn64",
 ]
 
 STAGES = ("fwd_main", "adj_main", "fwd_near", "adj_near")
+
+
+def eval_fn64(fn: str, a, b=None, stream=None, ctx: Optional["Context"] = None):
+    """Self-check hook: the library's FP64 log(a) / atan(a / b) ("log", "atan")
+    or CUDA's ("cuda_log", "cuda_atan") on CUDA float64 tensors."""
+    torch = _torch()
+    ctx = ctx or context()
+    code = {"log": 0, "atan": 1, "cuda_log": 2, "cuda_atan": 3}[fn]
+    a = _f64(a, a.numel(), "a")
+    b = _f64(b, a.numel(), "b") if b is not None else None
+    out = torch.empty_like(a)
+    ctx.check(_lib.grav_eval_fn64(ctx.h, code, a.data_ptr(), b.data_ptr() if b is not None else None,
+                                  out.data_ptr(), a.numel(), _stream(stream)))
+    return out
 
 
 def launch_count() -> int:
@@ -135,14 +151,15 @@ def launch_count() -> int:
 
 def bench_pipes(device: int = 0) -> dict:
     """Measured unit throughputs (per second) and SM clocks of the B300 pipes."""
-    out = (ctypes.c_double * 19)()
+    out = (ctypes.c_double * 23)()
     rc = _lib.grav_bench_pipes(int(device), out)
     if rc != GRAV_OK:
         raise GravError(rc, _lib.grav_last_error(None).decode())
     sms = out[10]
     r = {"sm_count": int(sms)}
     slots = [(name, 2 * k) for k, name in enumerate(("rsqrt", "lg2", "ffma", "dfma", "ffma_f32x2"))]
-    slots += [(name, 11 + 2 * k) for k, name in enumerate(("log_f64", "atan_f64", "sqrt_f64", "div_f64"))]
+    slots += [(name, 11 + 2 * k) for k, name in enumerate(("log_f64", "atan_f64", "sqrt_f64", "div_f64",
+                                                            "log64_table", "atan_ratio64_table"))]
     for name, i in slots:
         r[name + "_per_s"] = out[i]
         r[name + "_mhz"] = out[i + 1]
@@ -378,7 +395,8 @@ def datainv(d, mesh, survey, m_ref=None, return_y=False, stream=None, ctx: Optio
                                            ctypes.byref(o), _stream(stream)))
     inf = {"iters": info.iters, "converged": bool(info.converged), "rel_res": info.rel_res,
            "true_rel_res": info.true_rel_res, "lambda": info.lambda_, "trace": info.trace,
-           "seconds": info.seconds, "status": rc, "outer": info.outer, "alpha_min": info.alpha_min}
+           "seconds": info.seconds, "status": rc, "outer": info.outer, "alpha_min": info.alpha_min,
+           "restarts": info.restarts}
     return (m, y, inf) if return_y else (m, inf)
 
 

@@ -69,6 +69,21 @@ bool finite_increasing(const double *e, int n) {
     return true;
 }
 
+int check_mesh(grav_ctx *ctx, const grav_mesh *mesh) {
+    if (!mesh) return set_error(ctx, GRAV_EINVAL, "mesh is NULL");
+    if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1)
+        return set_error(ctx, GRAV_EINVAL, "mesh sizes must be >= 1 (got %d x %d x %d)", mesh->nx, mesh->ny, mesh->nz);
+    if ((int64_t)mesh->nx * mesh->ny * mesh->nz > (int64_t)1 << 30 ||
+        (int64_t)(mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1) > (int64_t)1 << 30 || mesh->nx > 1 << 20 ||
+        mesh->ny > 1 << 20 || mesh->nz > 1 << 16)
+        return set_error(ctx, GRAV_EINVAL, "mesh too large");
+    if (!mesh->xe || !mesh->ye || !mesh->ze) return set_error(ctx, GRAV_EINVAL, "mesh edge array is NULL");
+    if (!finite_increasing(mesh->xe, mesh->nx) || !finite_increasing(mesh->ye, mesh->ny) ||
+        !finite_increasing(mesh->ze, mesh->nz))
+        return set_error(ctx, GRAV_EINVAL, "mesh edges must be finite and strictly increasing");
+    return GRAV_OK;
+}
+
 int check_options(grav_ctx *ctx, const grav_options &o) {
     if (o.precision != GRAV_FP64 && o.precision != GRAV_MIXED && o.precision != GRAV_MIXED_CORNER)
         return set_error(ctx, GRAV_EINVAL, "precision must be GRAV_FP64, GRAV_MIXED or GRAV_MIXED_CORNER (got %d)",
@@ -95,6 +110,19 @@ grav_options resolve(const grav_options *opt) {
     grav_options_default(&o);
     if (opt) o = *opt;
     return o;
+}
+
+// An empty survey (n == 0) is a valid no-op for the one-shot calls; this
+// validates the rest of the arguments for that case.  Returns 1 when the
+// survey is empty and everything else is valid, 0 when it is not empty, or a
+// negative status.
+int empty_survey(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const grav_options *opt) {
+    if (!survey) return set_error(ctx, GRAV_EINVAL, "survey is NULL");
+    if (survey->n != 0) return 0;
+    int rc = check_options(ctx, resolve(opt));
+    if (rc) return rc;
+    if ((rc = check_mesh(ctx, mesh))) return rc;
+    return 1;
 }
 
 }  // namespace
@@ -243,16 +271,7 @@ int plan_prepare(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey
     if (!mesh || !survey) return set_error(ctx, GRAV_EINVAL, "mesh or survey is NULL");
     int rc = check_options(ctx, o);
     if (rc) return rc;
-    if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1)
-        return set_error(ctx, GRAV_EINVAL, "mesh sizes must be >= 1 (got %d x %d x %d)", mesh->nx, mesh->ny, mesh->nz);
-    if ((int64_t)mesh->nx * mesh->ny * mesh->nz > (int64_t)1 << 30 ||
-        (int64_t)(mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1) > (int64_t)1 << 30 || mesh->nx > 1 << 20 ||
-        mesh->ny > 1 << 20 || mesh->nz > 1 << 16)
-        return set_error(ctx, GRAV_EINVAL, "mesh too large");
-    if (!mesh->xe || !mesh->ye || !mesh->ze) return set_error(ctx, GRAV_EINVAL, "mesh edge array is NULL");
-    if (!finite_increasing(mesh->xe, mesh->nx) || !finite_increasing(mesh->ye, mesh->ny) ||
-        !finite_increasing(mesh->ze, mesh->nz))
-        return set_error(ctx, GRAV_EINVAL, "mesh edges must be finite and strictly increasing");
+    if ((rc = check_mesh(ctx, mesh))) return rc;
     if (survey->n < 1 || survey->n > ((int64_t)1 << 30))
         return set_error(ctx, GRAV_EINVAL, "survey size must lie in [1, 2^30] (got %lld)", (long long)survey->n);
     if (!is_device_ptr(survey->x, ctx->device) || !is_device_ptr(survey->y, ctx->device) ||
@@ -535,7 +554,7 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             }
             return GRAV_OK;
         };
-        int outer_done = 0;
+        int outer_done = 0, restarts = 0;
         double alpha_min = 1.0;
         if (o.outer_max > 0) {
             // The paper's outer model-update loop in data space (m = m_ref + W^-2 G^T y):
@@ -638,7 +657,7 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
         // CG; when the recurrence residual reaches tol, the residual is
         // recomputed from y with the operator itself (r = dd - A y); if that
         // true residual is still above tol, CG restarts from it (p = r).
-        for (int restart = 0;; ++restart) {
+        for (restarts = 0;; ++restarts) {
             while (!converged && it < o.max_iter) {
                 const int n_it = std::min(every, o.max_iter - it);
                 for (int k = 0; k < n_it; ++k, ++it) {
@@ -680,7 +699,7 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             if ((rc = sync_scalars("cg true residual"))) break;
             true_rel = hsc[kSBB] > 0 ? std::sqrt(hsc[kSTmp] / hsc[kSBB]) : 0.0;
             iters = (int)hsc[kSIters];   // iterations that updated y (no-ops after a freeze excluded)
-            if (true_rel <= o.tol || restart >= 4 || it >= o.max_iter) {
+            if (true_rel <= o.tol || restarts >= 4 || it >= o.max_iter) {
                 converged = true_rel <= o.tol;
                 break;
             }
@@ -708,6 +727,7 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
                                             : (hsc[kSBB] > 0 ? std::sqrt(hsc[o.precond == 1 ? kSResNew : kSRR] / hsc[kSBB]) : 0.0);
             info->outer = outer_done;
             info->alpha_min = alpha_min;
+            info->restarts = restarts;
             info->true_rel_res = true_rel;
             info->lambda = lam;
             info->trace = trace;
@@ -783,9 +803,16 @@ int grav_ctx_create(grav_ctx **out, int device, size_t hbm_budget) {
     }
     uint64_t thr = UINT64_MAX;
     cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    std::vector<double> fn(fn_table_size());
+    fill_fn_table(fn.data());
     if ((e = cudaMalloc((void **)&ctx->d_status, 256)) != cudaSuccess ||
         (e = cudaMemset(ctx->d_status, 0, 256)) != cudaSuccess ||
-        (e = cudaMallocHost((void **)&ctx->h_status, 256)) != cudaSuccess) {
+        (e = cudaMallocHost((void **)&ctx->h_status, 256)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&ctx->d_fn, 8 * fn.size())) != cudaSuccess ||
+        (e = cudaMemcpy(ctx->d_fn, fn.data(), 8 * fn.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        if (ctx->d_status) cudaFree(ctx->d_status);
+        if (ctx->h_status) cudaFreeHost(ctx->h_status);
+        if (ctx->d_fn) cudaFree(ctx->d_fn);
         cudaMemPoolDestroy(ctx->pool);
         delete ctx;
         return cuda_error(nullptr, e, "context allocation");
@@ -801,6 +828,7 @@ int grav_ctx_destroy(grav_ctx *ctx) {
     cudaDeviceSynchronize();
     cudaFree(ctx->d_status);
     cudaFreeHost(ctx->h_status);
+    cudaFree(ctx->d_fn);
     cudaMemPoolDestroy(ctx->pool);
     delete ctx;
     return GRAV_OK;
@@ -927,6 +955,9 @@ int grav_forward(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey
                  const grav_options *opt, grav_stream_t stream) {
     if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
     DeviceGuard g(ctx->device);
+    int e0 = empty_survey(ctx, mesh, survey, opt);
+    if (e0 < 0) return e0;
+    if (e0) return GRAV_OK;   // no stations: nothing to write
     if (!is_device_ptr(m, ctx->device) || !is_device_ptr(d, ctx->device))
         return set_error(ctx, GRAV_EINVAL, "m and d must be device pointers on device %d", ctx->device);
     grav_plan *p = nullptr;
@@ -941,6 +972,13 @@ int grav_adjoint(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey
                  int depth_weighted, const grav_options *opt, grav_stream_t stream) {
     if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
     DeviceGuard g(ctx->device);
+    int e0 = empty_survey(ctx, mesh, survey, opt);
+    if (e0 < 0) return e0;
+    if (e0) {   // no stations: G^T r = 0
+        if (!is_device_ptr(gtr, ctx->device)) return set_error(ctx, GRAV_EINVAL, "gtr must be a device pointer");
+        const cudaError_t e = cudaMemsetAsync(gtr, 0, 8ull * mesh->nx * mesh->ny * mesh->nz, (cudaStream_t)stream);
+        return e == cudaSuccess ? GRAV_OK : cuda_error(ctx, e, "adjoint of an empty survey");
+    }
     if (!is_device_ptr(r, ctx->device) || !is_device_ptr(gtr, ctx->device))
         return set_error(ctx, GRAV_EINVAL, "r and gtr must be device pointers on device %d", ctx->device);
     grav_plan *p = nullptr;
@@ -955,6 +993,12 @@ int grav_diag(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, d
               const grav_options *opt, grav_stream_t stream) {
     if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
     DeviceGuard g(ctx->device);
+    int e0 = empty_survey(ctx, mesh, survey, opt);
+    if (e0 < 0) return e0;
+    if (e0) {   // no stations: an empty diagonal, trace 0
+        if (trace) *trace = 0.0;
+        return GRAV_OK;
+    }
     if (!is_device_ptr(diag, ctx->device)) return set_error(ctx, GRAV_EINVAL, "diag must be a device pointer");
     const grav_options o = resolve(opt);
     grav_plan *p = nullptr;
@@ -987,6 +1031,21 @@ int grav_datainv_solve(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *
                        const grav_options *opt, grav_stream_t stream) {
     if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
     DeviceGuard g(ctx->device);
+    int e0 = empty_survey(ctx, mesh, survey, opt);
+    if (e0 < 0) return e0;
+    if (e0) {   // no data: the minimiser of Eq. 7 is m_ref (0 when not given)
+        if (!is_device_ptr(m_out, ctx->device) || (m_ref && !is_device_ptr(m_ref, ctx->device)))
+            return set_error(ctx, GRAV_EINVAL, "m_out (and m_ref when given) must be device pointers");
+        if (info) {
+            std::memset(info, 0, sizeof(*info));
+            info->converged = 1;
+            info->alpha_min = 1.0;
+        }
+        const size_t bytes = 8ull * mesh->nx * mesh->ny * mesh->nz;
+        const cudaError_t e = m_ref ? cudaMemcpyAsync(m_out, m_ref, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream)
+                                    : cudaMemsetAsync(m_out, 0, bytes, (cudaStream_t)stream);
+        return e == cudaSuccess ? GRAV_OK : cuda_error(ctx, e, "inversion of an empty survey");
+    }
     if (!is_device_ptr(d, ctx->device) || !is_device_ptr(m_out, ctx->device) ||
         (m_ref && !is_device_ptr(m_ref, ctx->device)) || (y_out && !is_device_ptr(y_out, ctx->device)))
         return set_error(ctx, GRAV_EINVAL, "d, m_out (and m_ref, y_out when given) must be device pointers");

@@ -84,22 +84,101 @@ __device__ __forceinline__ void set_status(int *status, int bit) {
 }
 
 // ---------------------------------------------------------------------------
-// Eq. 2-3 in FP64.  Arguments are the vertex coordinates relative to the
-// station (z > 0: the vertex lies below the station) and their squares.
-// ln(R + a) for a < 0 is taken as ln((R^2 - a^2) / (R - a)), an exact
-// identity that avoids the cancellation of R + a (the reading adopted for the
-// paper's unspecified "singularity-robust formulation", Section 2.3).  With
-// z > 0, R > 0 and R^2 - a^2 > 0, so every logarithm argument is positive;
-// at x = 0 (y = 0) the x ln (y ln) term is exactly 0 * finite = 0.
+// FP64 elementary functions of Eq. 2-3, table-driven (the tables live in the
+// context, built on the host from long-double logl/atanl; layout below).
+//
+// log64: P. T. P. Tang, "Table-driven implementation of the logarithm
+// function in IEEE floating-point arithmetic", ACM TOMS 16 (1990) 378-400.
+// x = 2^k m, m in [1, 2); F = 1 + j/256 nearest to m; f = m - F (exact);
+// ln x = k ln2 + ln F + ln(1 + u), u = f / F, |u| <= 2^-9, with ln 2 and ln F
+// split into a high part on the 2^-42 grid (so k ln2_hi + lnF_hi is exact)
+// and a low part, and ln(1 + u) - u by its Taylor series to u^6 (truncation
+// below 2^-65).  u is carried as uh + ul (ul from the exact residual
+// f - uh F).  Zero, negative, subnormal, infinite and NaN arguments go to
+// CUDA's log.
+//
+// atan_ratio64(a, b) = atan(a / b) for b > 0: with v = min(|a|, b) /
+// max(|a|, b) in [0, 1] and c = j/64 nearest to v, atan(v) = atan(c) +
+// atan(w), w = (v - c) / (1 + v c) = (p - c q) / (q + c p) for v = p / q —
+// one division for the ratio and the reduction together, |w| <= 2^-7 — and
+// atan(w) by its Taylor series to w^7 (truncation below 2^-65); for |a| > b,
+// atan(a/b) = sign(a) (pi/2 - atan(b/|a|)).  The table holds atan(c) and
+// pi/2 - atan(c) as high + low doubles.  Error: log64 <= 1 ulp; atan_ratio64
+// (the ratio's three roundings included) about 1.1 ulp at worst, below CUDA's
+// atan of a rounded quotient.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double psi64(double x, double y, double z, double x2, double y2, double z2) {
+constexpr int kFnLogJ = 256;                            // log table: F = 1 + j/256, j = 0..256
+constexpr int kFnLog = 0;                               // [3 j + 0..2] = 1/F, ln F hi, ln F lo
+constexpr int kFnLn2 = kFnLog + 3 * (kFnLogJ + 1);      // ln 2 hi, ln 2 lo
+constexpr int kFnAtanJ = 64;                            // atan table: c = j/64, j = 0..64
+constexpr int kFnAtan = kFnLn2 + 2;                     // [4 j + 0..3] = atan c hi, lo, pi/2 - atan c hi, lo
+constexpr int kFnTableSize = kFnAtan + 4 * (kFnAtanJ + 1);
+
+__device__ __forceinline__ double log64(double x, const double *__restrict__ T) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)(b >> 52);
+    if (e <= 0 || e >= 0x7ff) return log(x);
+    const long long mb = b & 0x000fffffffffffffLL;
+    const int j = (int)((mb + (1LL << 43)) >> 44);
+    const double m = __longlong_as_double(mb | 0x3ff0000000000000LL);
+    const double F = fma((double)j, 1.0 / kFnLogJ, 1.0);
+    const double f = m - F;
+    const double inv = __ldg(T + kFnLog + 3 * j);
+    const double uh = f * inv;
+    const double ul = fma(-uh, F, f) * inv;
+    const double u2 = uh * uh;
+    double p = fma(uh, -1.0 / 6.0, 1.0 / 5.0);
+    p = fma(p, uh, -0.25);
+    p = fma(p, uh, 1.0 / 3.0);
+    p = fma(p, uh, -0.5);
+    const double k = (double)(e - 1023);
+    const double hi = fma(k, __ldg(T + kFnLn2), __ldg(T + kFnLog + 3 * j + 1));
+    const double lo = fma(k, __ldg(T + kFnLn2 + 1), __ldg(T + kFnLog + 3 * j + 2));
+    return hi + (uh + fma(u2, p, ul + lo));
+}
+
+__device__ __forceinline__ double atan_ratio64(double a, double b, const double *__restrict__ T) {
+    const double pa = fabs(a);
+    const bool big = pa > b;
+    const double p = big ? b : pa, q = big ? pa : b;   // v = p / q in [0, 1]
+    const float vf = __fdividef((float)p, (float)q);
+    int j = __float2int_rn(vf * (float)kFnAtanJ);
+    j = min(max(j, 0), kFnAtanJ);
+    const double c = (double)j * (1.0 / kFnAtanJ);
+    const double w = fma(-c, q, p) / fma(c, p, q);
+    const double w2 = w * w;
+    double r = fma(w2, -1.0 / 7.0, 1.0 / 5.0);
+    r = fma(r, w2, -1.0 / 3.0);
+    r = fma(w2 * w, r, w);
+    // base + r with base = table high + low; |base_hi| >= |r| for j >= 1 (and
+    // base = 0 for j = 0), so Fast2Sum gives the rounding error of base_hi + r
+    const double *t = T + kFnAtan + 4 * j + (big ? 2 : 0);
+    const double th = __ldg(t), rr = big ? -r : r;
+    const double sh = th + rr;
+    const double er = rr - (sh - th);
+    const double res = sh + (er + __ldg(t + 1));
+    return a < 0.0 ? -res : res;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 2-3 in FP64.  Arguments are the vertex coordinates relative to the
+// station (z > 0: the vertex lies below the station) and their squares; T is
+// the function table above.  ln(R + a) for a < 0 is taken as
+// ln((R^2 - a^2) / (R - a)), an exact identity that avoids the cancellation
+// of R + a (the reading adopted for the paper's unspecified
+// "singularity-robust formulation", Section 2.3).  With z > 0, R > 0 and
+// R^2 - a^2 > 0, so every logarithm argument is positive; at x = 0 (y = 0)
+// the x ln (y ln) term is exactly 0 * finite = 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double psi64(double x, double y, double z, double x2, double y2, double z2,
+                                        const double *__restrict__ T) {
     const double R2 = x2 + y2 + z2;
     const double R = sqrt(R2);
-    const double t_atan = z * atan((x * y) / (z * R));
+    const double t_atan = z * atan_ratio64(x * y, z * R, T);
     double ry, rx;
     if (y >= 0.0) ry = R + y; else ry = (x2 + z2) / (R - y);
     if (x >= 0.0) rx = R + x; else rx = (y2 + z2) / (R - x);
-    return t_atan - x * log(ry) - y * log(rx);
+    return t_atan - x * log64(ry, T) - y * log64(rx, T);
 }
 
 // Eq. 2-3 evaluated entirely in FP32 (CUDA's IEEE sqrtf/logf/atanf and

@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd64(Geo g, int ldw, const dou
 #pragma unroll
                 for (int t = 0; t < T; ++t) {
                     const double dx = xa - xs[t];
-                    acc[t] = fma(wv, psi64(dx, dy[t], dz[t], dx * dx, y2[t], z2[t]), acc[t]);
+                    acc[t] = fma(wv, psi64(dx, dy[t], dz[t], dx * dx, y2[t], z2[t], g.fn), acc[t]);
                 }
             }
         }
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adj64(Geo g, const double4 *
 #pragma unroll
                 for (int t = 0; t < TZ; ++t) {
                     const double dz = Zt[t] - S.z;
-                    acc[t] = fma(S.w, psi64(dx, dy, dz, x2, y2, dz * dz), acc[t]);
+                    acc[t] = fma(S.w, psi64(dx, dy, dz, x2, y2, dz * dz, g.fn), acc[t]);
                 }
             }
         }
@@ -351,8 +351,8 @@ __global__ void __launch_bounds__(128) k_diag64(Geo g, const double *__restrict_
                 const double dx = g.xe[0] - xs, x2 = dx * dx;
 #pragma unroll
                 for (int c = 0; c <= ZC; ++c) {
-                    P0[c] = (c <= nl) ? psi64(dx, dy0, dz[c], x2, y20, z2[c]) : 0.0;
-                    P1[c] = (c <= nl) ? psi64(dx, dy1, dz[c], x2, y21, z2[c]) : 0.0;
+                    P0[c] = (c <= nl) ? psi64(dx, dy0, dz[c], x2, y20, z2[c], g.fn) : 0.0;
+                    P1[c] = (c <= nl) ? psi64(dx, dy1, dz[c], x2, y21, z2[c], g.fn) : 0.0;
                 }
             }
             for (int i = 0; i < g.nx; ++i) {
@@ -362,8 +362,8 @@ __global__ void __launch_bounds__(128) k_diag64(Geo g, const double *__restrict_
                 for (int c = 0; c <= ZC; ++c) {
                     double q0 = 0.0, q1 = 0.0;
                     if (c <= nl) {
-                        q0 = psi64(dx, dy0, dz[c], x2, y20, z2[c]);
-                        q1 = psi64(dx, dy1, dz[c], x2, y21, z2[c]);
+                        q0 = psi64(dx, dy0, dz[c], x2, y20, z2[c], g.fn);
+                        q1 = psi64(dx, dy1, dz[c], x2, y21, z2[c], g.fn);
                     }
                     E[c] = P0[c] - q0 - P1[c] + q1;
                     P0[c] = q0;
@@ -388,13 +388,6 @@ inline int grid_for(int64_t n, int threads, int cap = 148 * 32) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
 }
 
-Geo make_geo(const grav_plan *p) {
-    Geo g;
-    g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
-    g.xe = p->d_xe; g.ye = p->d_ye; g.ze = p->d_ze;
-    g.N = p->N;
-    return g;
-}
 
 int fwd_rows_per_stage(const grav_plan *p) {
     // ~16 KB of node weights per stage
@@ -577,5 +570,46 @@ int launch_fwd64_raw(Geo g, int ldw, const double *m, double *w, int rows_per_ch
 }
 
 int fwd64_stations_per_cta() { return kFwdThreads * kFwdT; }
+
+}  // namespace grav
+
+namespace grav {
+
+// The one constructor of a plan's Geo (both kernel files use it): every field,
+// the function table included, comes from the plan and its context.
+Geo make_geo(const grav_plan *p) {
+    Geo g;
+    g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
+    g.xe = p->d_xe; g.ye = p->d_ye; g.ze = p->d_ze;
+    g.N = p->N;
+    g.fn = p->ctx->d_fn;
+    return g;
+}
+
+int fn_table_size() { return kFnTableSize; }
+
+void fill_fn_table(double *t) {
+    for (int i = 0; i < kFnTableSize; ++i) t[i] = 0.0;
+    const long double grid = 4398046511104.0L;   // 2^42
+    auto split42 = [&](long double v, double &hi, double &lo) {
+        hi = (double)(nearbyintl(v * grid) / grid);
+        lo = (double)(v - (long double)hi);
+    };
+    for (int j = 0; j <= kFnLogJ; ++j) {
+        const long double F = 1.0L + (long double)j / kFnLogJ;
+        t[kFnLog + 3 * j] = (double)(1.0L / F);
+        split42(logl(F), t[kFnLog + 3 * j + 1], t[kFnLog + 3 * j + 2]);
+    }
+    split42(logl(2.0L), t[kFnLn2], t[kFnLn2 + 1]);
+    const long double half_pi = 2.0L * atanl(1.0L);
+    for (int j = 0; j <= kFnAtanJ; ++j) {
+        const long double a = atanl((long double)j / kFnAtanJ);
+        const long double b = half_pi - a;
+        t[kFnAtan + 4 * j] = (double)a;
+        t[kFnAtan + 4 * j + 1] = (double)(a - (long double)(double)a);
+        t[kFnAtan + 4 * j + 2] = (double)b;
+        t[kFnAtan + 4 * j + 3] = (double)(b - (long double)(double)b);
+    }
+}
 
 }  // namespace grav

@@ -17,6 +17,7 @@ struct Geo {
     int nx, ny, nz;
     const double *xe, *ye, *ze;   // device edges
     int64_t N;                    // stations
+    const double *fn = nullptr;   // device table of the FP64 log / atan (kFnTableSize doubles)
 };
 
 // Layout of the FP32 far-field operator (GRAV_MIXED).
@@ -71,6 +72,7 @@ struct grav_ctx {
     std::string last_error;
     int sm_count = 148;
     void *serve = nullptr;         // serving scheduler (serve.cpp)
+    double *d_fn = nullptr;        // FP64 log / atan table (fp64_kernels.cu, fill_fn_table)
 };
 
 namespace grav {
@@ -212,6 +214,12 @@ void launch_mixed_adj_finish(const grav_plan *p, const double *r, int depth_weig
 void launch_mixed_diag(const grav_plan *p, double *diag, cudaStream_t s);
 size_t mixed_scratch_bytes(const grav_plan *p);
 int mixed_adj_last_group(const grav_plan *p);
+// Device view of a plan's mesh, stations and function table.
+Geo make_geo(const grav_plan *p);
+// Host: fills the kFnTableSize-double table of the FP64 log / atan (long-double
+// logl / atanl values split into high and low doubles).
+void fill_fn_table(double *t);
+int fn_table_size();
 void launch_corner_fwd(const grav_plan *p, const double *m, cudaStream_t s);
 
 // vector kernels (cg_kernels.cu)

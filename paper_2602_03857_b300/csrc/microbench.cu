@@ -4,6 +4,7 @@
 // ALU rooflines of the operator kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <vector>
 
@@ -28,9 +29,10 @@ __device__ __forceinline__ float rsqrt_v(float x) {
 }
 
 // op: 0 rsqrt, 1 lg2, 2 ffma, 3 dfma, 4 packed fma.rn.f32x2 (counted as 2 FP32 FMAs),
-//     5 FP64 log, 6 FP64 atan, 7 FP64 sqrt, 8 FP64 division (CUDA's implementations)
+//     5 FP64 log, 6 FP64 atan, 7 FP64 sqrt, 8 FP64 division (CUDA's implementations),
+//     9 this library's table-driven log64, 10 its atan_ratio64 (tables in fn)
 template <int OP>
-__global__ void k_pipe(int iters, float seed, float *out, unsigned long long *clk) {
+__global__ void k_pipe(int iters, float seed, float *out, unsigned long long *clk, const double *fn) {
     const uint64_t t0 = globaltimer_ns();
     const long long c0 = clock64();
     if (OP == 4) {
@@ -58,6 +60,8 @@ __global__ void k_pipe(int iters, float seed, float *out, unsigned long long *cl
             for (int k = 0; k < kChains; ++k) {
                 if (OP == 5) a[k] = log(a[k]) + 2.5;
                 else if (OP == 6) a[k] = atan(a[k]) + 1.25;
+                else if (OP == 9) a[k] = log64(a[k], fn) + 2.5;
+                else if (OP == 10) a[k] = atan_ratio64(a[k], 1.0, fn) + 1.25;
                 else if (OP == 7) a[k] = sqrt(a[k]) + 1.5;
                 else a[k] = 3.0 / a[k] + 1.0;
             }
@@ -104,7 +108,7 @@ __global__ void k_pipe(int iters, float seed, float *out, unsigned long long *cl
 }
 
 template <int OP>
-int run_one(int sms, double *ops_per_s, double *clk_mhz) {
+int run_one(int sms, double *ops_per_s, double *clk_mhz, const double *fn = nullptr) {
     float *out = nullptr;
     unsigned long long *clk = nullptr;
     if (cudaMalloc(&out, 16) != cudaSuccess) return -1;
@@ -114,9 +118,9 @@ int run_one(int sms, double *ops_per_s, double *clk_mhz) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    k_pipe<OP><<<blocks, threads>>>(iters / 16, 1.5f, out, clk);   // warm-up
+    k_pipe<OP><<<blocks, threads>>>(iters / 16, 1.5f, out, clk, fn);   // warm-up
     cudaEventRecord(e0);
-    k_pipe<OP><<<blocks, threads>>>(iters, 1.5f, out, clk);
+    k_pipe<OP><<<blocks, threads>>>(iters, 1.5f, out, clk, fn);
     cudaEventRecord(e1);
     cudaEventSynchronize(e1);
     float ms = 0;
@@ -132,8 +136,40 @@ int run_one(int sms, double *ops_per_s, double *clk_mhz) {
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// out[i] = f(a[i], b[i]) for the self-check of the FP64 functions
+__global__ void k_eval_fn(int fn, const double *__restrict__ a, const double *__restrict__ b, double *__restrict__ out,
+                          int64_t n, const double *__restrict__ T) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v;
+        if (fn == 0) v = log64(a[i], T);
+        else if (fn == 1) v = atan_ratio64(a[i], b[i], T);
+        else if (fn == 2) v = log(a[i]);
+        else v = atan(a[i] / b[i]);
+        out[i] = v;
+    }
+}
+
 }  // namespace
 }  // namespace grav
+
+extern "C" int grav_eval_fn64(grav_ctx *ctx, int fn, const double *a, const double *b, double *out, int64_t n,
+                              grav_stream_t stream) {
+    using namespace grav;
+    if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
+    if (fn < 0 || fn > 3) return set_error(ctx, GRAV_EINVAL, "fn must be 0..3");
+    if (n < 0) return set_error(ctx, GRAV_EINVAL, "n must be >= 0");
+    if (n == 0) return GRAV_OK;
+    if (!a || !out || ((fn == 1 || fn == 3) && !b)) return set_error(ctx, GRAV_EINVAL, "NULL argument");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 148LL * 16);
+    k_eval_fn<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(fn, a, b, out, n, ctx->d_fn);
+    note_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    cudaSetDevice(prev);
+    return e == cudaSuccess ? GRAV_OK : cuda_error(ctx, e, "eval_fn64 launch");
+}
 
 extern "C" int grav_bench_pipes(int device, double *out) {
     using namespace grav;
@@ -157,6 +193,17 @@ extern "C" int grav_bench_pipes(int device, double *out) {
     rc |= run_one<6>(sms, &out[13], &out[14]);
     rc |= run_one<7>(sms, &out[15], &out[16]);
     rc |= run_one<8>(sms, &out[17], &out[18]);
+    std::vector<double> fh(fn_table_size());
+    fill_fn_table(fh.data());
+    double *fn = nullptr;
+    if (cudaMalloc(&fn, 8 * fh.size()) != cudaSuccess ||
+        cudaMemcpy(fn, fh.data(), 8 * fh.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        rc = -1;
+    } else {
+        rc |= run_one<9>(sms, &out[19], &out[20], fn);
+        rc |= run_one<10>(sms, &out[21], &out[22], fn);
+    }
+    if (fn) cudaFree(fn);
     cudaSetDevice(prev);
     return rc ? set_error(nullptr, GRAV_EDEVICE, "pipe microbenchmark failed") : GRAV_OK;
 }

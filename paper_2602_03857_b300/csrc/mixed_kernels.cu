@@ -650,7 +650,7 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
         double v = 0.0;
         if (ia >= 0 && ia <= g.nx && jb >= 0 && jb <= g.ny && c <= g.nz) {
             const double x = g.xe[ia] - xs, y = g.ye[jb] - ys, z = g.ze[c] - zs;
-            v = psi64(x, y, z, x * x, y * y, z * z);
+            v = psi64(x, y, z, x * x, y * y, z * z, g.fn);
         }
         P[t] = v;
     }
@@ -868,14 +868,6 @@ __global__ void __launch_bounds__(kMfThreads) k_mdiag(MixedGeo g, const float *_
 inline int grid_for(int64_t n, int threads, int cap = 148 * 32) {
     int64_t b = (n + threads - 1) / threads;
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
-}
-
-Geo make_geo(const grav_plan *p) {
-    Geo g;
-    g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
-    g.xe = p->d_xe; g.ye = p->d_ye; g.ze = p->d_ze;
-    g.N = p->N;
-    return g;
 }
 
 constexpr int kMfColsPerStage = 32;

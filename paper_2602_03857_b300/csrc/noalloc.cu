@@ -97,8 +97,9 @@ extern "C" int grav_forward_fp64_noalloc(const grav_mesh *mesh, const grav_surve
     const int64_t N = survey->n;
     const int ldw = (nx + 2) / 2 * 2;
     const int nrows = (ny + 1) * (nz + 1);
-    // scratch layout (in doubles): status | xe | ye | ze | w | partials
-    const size_t o_xe = 32;
+    // scratch layout (in doubles): status | FP64 log/atan table | xe | ye | ze | w | partials
+    const size_t o_fn = 32;
+    const size_t o_xe = o_fn + round32((size_t)fn_table_size());
     const size_t o_ye = o_xe + round32(nx + 1);
     const size_t o_ze = o_ye + round32(ny + 1);
     const size_t o_w = o_ze + round32(nz + 1);
@@ -124,7 +125,15 @@ extern "C" int grav_forward_fp64_noalloc(const grav_mesh *mesh, const grav_surve
     const cudaStream_t s = (cudaStream_t)stream;
     // the status word must start at zero; every other region is fully rewritten
     if ((e = cudaMemsetAsync(base, 0, 256, s)) != cudaSuccess) return cuda_error(nullptr, e, "status reset");
-    if ((e = cudaMemcpyAsync(base + o_xe, mesh->xe, 8ull * (nx + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+    // the function table is built once per process on the host and uploaded each call
+    static const std::vector<double> fn_host = [] {
+        std::vector<double> t(fn_table_size());
+        fill_fn_table(t.data());
+        return t;
+    }();
+    if ((e = cudaMemcpyAsync(base + o_fn, fn_host.data(), 8 * fn_host.size(), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(base + o_xe, mesh->xe, 8ull * (nx + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(base + o_ye, mesh->ye, 8ull * (ny + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(base + o_ze, mesh->ze, 8ull * (nz + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_error(nullptr, e, "edge upload");
@@ -132,6 +141,7 @@ extern "C" int grav_forward_fp64_noalloc(const grav_mesh *mesh, const grav_surve
     g.nx = nx; g.ny = ny; g.nz = nz;
     g.xe = base + o_xe; g.ye = base + o_ye; g.ze = base + o_ze;
     g.N = N;
+    g.fn = base + o_fn;
     launch_fwd64_raw(g, ldw, m, base + o_w, rows_per_chunk, nchunk, survey->x, survey->y, survey->z, base + o_part,
                      reinterpret_cast<int *>(base), s);
     launch_reduce_rows(base + o_part, nchunk, N, kGammaMgal, nullptr, 0.0, nullptr, d, s);

@@ -498,3 +498,23 @@ def test_outer_loop_reaches_dense_lu_minimiser(g, precond):
     assert res <= 1.5e-8 * np.linalg.norm(d)
     assert np.linalg.norm(y - ref["y"]) <= 1.01 * res / ref["lam"]
     assert info["true_rel_res"] <= 1e-8
+
+
+def test_empty_survey_one_shot_calls(g):
+    """n = 0 stations: forward is a no-op, G^T r = 0, the inversion returns
+    m_ref (the minimiser of Eq. 7 with no data term), and a plan is refused."""
+    mesh = synth.uniform_mesh(5, 4, 3, 10.0, 10.0, 10.0)
+    S = g.Survey(np.zeros(0), np.zeros(0), np.zeros(0))
+    empty = torch.zeros(0, dtype=torch.float64, device="cuda")
+    m = _dev(np.arange(mesh.ncells, dtype=np.float64))
+    for prec in ("fp64", "mixed"):
+        assert g.forward(m, mesh, S, precision=prec).numel() == 0
+        a = g.adjoint(empty, mesh, S, precision=prec)
+        assert a.shape == (mesh.ncells,) and not a.any()
+        mo, info = g.datainv(empty, mesh, S, precision=prec, m_ref=m)
+        assert torch.equal(mo, m) and info["converged"] and info["iters"] == 0
+        mo, info = g.datainv(empty, mesh, S, precision=prec)
+        assert not mo.any()
+    with pytest.raises(g.GravError) as e:
+        g.Plan(mesh, S)
+    assert e.value.code == g.GRAV_EINVAL
