@@ -40,6 +40,8 @@ import synth  # noqa: E402
 
 MUFU_PER_CLK_SM = 16          # reciprocal square roots per clock per SM (MUFU unit count)
 SM_MAX_MHZ = 2032.0
+DFMA_PER_CLK_SM = 1.65        # FP64 pipe operations per clock per SM (measured by grav_bench_pipes)
+FP64_OPS_PER_PSI = 98         # FP64 pipe operations per Eq. 2-3 evaluation (ncu, k_adj64 on 80x80x40)
 
 
 def parse():
@@ -295,9 +297,16 @@ def run_ours(args):
     adj_ms, adj_n = stages["adj_main"]
     dom = "fwd_main" if fwd_ms >= adj_ms else "adj_main"
     dms, dn = stages[dom]
-    pairs_launch = float(N) * M
-    achieved = pairs_launch / (dms / max(dn, 1) * 1e-3) / 1e9
-    peak = 148 * MUFU_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e9
+    if args.precision == "mixed":
+        units_launch = float(N) * M          # one MUFU rsqrt per (station, cell) pair
+        peak = 148 * MUFU_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e9
+        peak_basis = f"148 SMs x {MUFU_PER_CLK_SM} MUFU/clk x {SM_MAX_MHZ:.0f} MHz (MUFU unit count x max SM clock)"
+    else:
+        units_launch = float(N) * (wl.mesh.nx + 1) * (wl.mesh.ny + 1) * (wl.mesh.nz + 1)   # Psi per (station, node)
+        peak = 148 * DFMA_PER_CLK_SM * SM_MAX_MHZ * 1e6 / FP64_OPS_PER_PSI / 1e9
+        peak_basis = (f"148 SMs x {DFMA_PER_CLK_SM} FP64 ops/clk x {SM_MAX_MHZ:.0f} MHz / {FP64_OPS_PER_PSI} FP64 ops "
+                      "per Psi (ncu instruction count)")
+    achieved = units_launch / (dms / max(dn, 1) * 1e-3) / 1e9
     desc = plan.describe()
     kernel_name = desc["fwd_kernel"] if dom == "fwd_main" else desc["adj_kernel"]
     traffic = measured_traffic(kernel_name, args)
@@ -306,7 +315,7 @@ def run_ours(args):
             "frac": achieved / peak, "traffic": traffic,
             "traffic_note": "ncu dram__bytes_read+write per launch at full size (profiles/), null if the "
                             "kernel sources changed since the capture",
-            "peak_basis": f"148 SMs x {MUFU_PER_CLK_SM} MUFU/clk x {SM_MAX_MHZ:.0f} MHz (MUFU unit count x max SM clock)",
+            "peak_basis": peak_basis,
             "stage_ms_per_launch": {k: (v[0] / max(v[1], 1)) for k, v in stages.items()}}
 
     line = {
@@ -421,7 +430,7 @@ def run_serve(args):
     torch.cuda.synchronize()
     ctx = g.Context(0)
     ctx.serve_config(args.serve_slots)
-    opts = dict(precision="mixed", tol=1e-4, max_iter=500)
+    opts = dict(precision="mixed", tol=1e-4, max_iter=500, check_stations=16)
     t0 = time.perf_counter()
     ids = []
     for j, S, inp, out in prepared:
@@ -431,9 +440,12 @@ def run_serve(args):
         ids.append(ctx.submit(j.kind, j.mesh, S, inp, out, **opts))
     results = [ctx.wait(i, 3600.0) for i in ids]
     wall = time.perf_counter() - t0
-    lat, lat_f, lat_i, busy = [], [], [], []
+    lat, lat_f, lat_i, busy, errs = [], [], [], [], []
     pairs = 0.0
     for (j, S, inp, out), i in zip(prepared, ids):
+        e = ctx.poll(i)[1]["fp64_rel_err"]
+        if e >= 0:
+            errs.append(e)
         ts, tb, te = ctx.job_times(i)
         lat.append(te - ts)
         (lat_f if j.kind == "forward" else lat_i).append(te - ts)
@@ -449,6 +461,10 @@ def run_serve(args):
             "forward": {"n": len(lat_f), "p50_s": pct(lat_f, 50), "p99_s": pct(lat_f, 99)},
             "invert": {"n": len(lat_i), "p50_s": pct(lat_i, 50), "p99_s": pct(lat_i, 99)},
             "results": {str(k): results.count(k) for k in sorted(set(results))},
+            "fp64_rel_err": {"jobs_checked": len(errs), "stations_per_job": 16,
+                             "median": pct(errs, 50), "max": max(errs) if errs else None,
+                             "what": "max |mixed - FP64| / max |FP64| of each job's output (forward: d; "
+                                     "inversion: G m_out) at 16 stations"},
             "pairs_per_forward_pass_total": pairs, "data": "synthetic",
             "config": {"workload": "serving mix: 50k-500k cubic prisms (25-100 m), 1k-20k stations, "
                                    "block/dyke models, forward or inversion 50/50", "tol": 1e-4}}
@@ -471,7 +487,7 @@ def run_invert(args):
     d = g.forward(m, wl.mesh, S, precision=data_prec, near_cells=args.near_cells)
     torch.cuda.synchronize()
     opts = dict(precision=args.precision, near_cells=args.near_cells, tol=args.tol, max_iter=args.max_iter,
-                precond=args.precond)
+                precond=args.precond, check_stations=64)
     t0 = time.perf_counter()
     m_out, info = g.datainv(d, wl.mesh, S, **opts)
     torch.cuda.synchronize()
@@ -483,7 +499,8 @@ def run_invert(args):
             "converged": info["converged"], "true_rel_res": info["true_rel_res"], "lambda": info["lambda"],
             "cells": wl.mesh.ncells, "stations": wl.survey.n, "data_operator": data_prec,
             "rms_misfit_mgal": float(torch.sqrt(torch.mean(misfit * misfit))),
-            "rms_data_mgal": float(torch.sqrt(torch.mean(d * d))), "data": "synthetic"}
+            "rms_data_mgal": float(torch.sqrt(torch.mean(d * d))), "data": "synthetic",
+            "fp64_rel_err_of_predicted_data": info["fp64_rel_err"]}
     print(json.dumps(line), flush=True)
 
 

@@ -97,7 +97,7 @@ typedef struct {
 } grav_survey;
 
 typedef struct {
-    int precision;             /* GRAV_FP64 or GRAV_MIXED */
+    int precision;             /* GRAV_FP64, GRAV_MIXED or GRAV_MIXED_CORNER (forward only) */
     double z0;                 /* depth-weight offset (m): W^-2 = (zc + z0)^2, zc = cell-centre depth below ze[0] */
     double lambda_scale;       /* lambda = lambda_scale * trace(G W^-2 G^T) / N  (default 1e-2) */
     double lambda;             /* > 0: use this lambda instead of the trace rule */
@@ -113,6 +113,9 @@ typedef struct {
                                   updates y += alpha dy, dy from <= inner_max CG iterations on A dy = dd - A y,
                                   alpha by backtracking on the objective of Eq. 7; 0 = one CG solve (default) */
     int inner_max;             /* CG iterations per outer update (default 20) */
+    int check_stations;        /* mixed modes, > 0: state the error of the result against the FP64 operator
+                                  at this many evenly spaced stations (inversions: of G m_out; serving
+                                  forward jobs: of d), in grav_solve_info.fp64_rel_err; 0 = off (default) */
 } grav_options;
 
 typedef struct {
@@ -126,6 +129,8 @@ typedef struct {
     int outer;                 /* outer updates performed (outer_max > 0) */
     double alpha_min;          /* smallest accepted step length of the outer loop (1 if never backtracked) */
     int restarts;              /* single CG solve: restarts from the recomputed true residual */
+    double fp64_rel_err;       /* check_stations > 0: max |mixed - FP64| / max |FP64| over the checked stations;
+                                  -1 when not checked */
 } grav_solve_info;
 
 typedef struct grav_ctx grav_ctx;
@@ -134,7 +139,7 @@ typedef struct grav_plan grav_plan;
 /* Fills *opt with the defaults: GRAV_FP64, z0 = 50, lambda_scale = 1e-2,
  * lambda = 0, tol = 1e-6, max_iter = 1000, check_every = 0,
  * near_cells = 8, timeout_s = 3600, precond = 0, cache_g = 0, outer_max = 0,
- * inner_max = 20. */
+ * inner_max = 20, check_stations = 0. */
 void grav_options_default(grav_options *opt);
 
 /* Library version string (static storage). */
@@ -283,6 +288,16 @@ int grav_job_release(grav_ctx *ctx, uint64_t job_id);
  * for the GPU. */
 int grav_forward_fp64_noalloc(const grav_mesh *mesh, const grav_survey *survey, const double *m, double *d,
                               grav_stream_t stream);
+
+/* States the error of a product of this plan against the FP64 operator:
+ * d (DEVICE, survey n doubles) is compared at n_check evenly spaced stations
+ * (index floor(k n / n_check)) with G m evaluated in FP64 (Eq. 1-3, node
+ * shared) on those stations alone.  m: DEVICE, M doubles.  *max_abs_err and
+ * *rel_err (HOST; max |d - d64| and that over max |d64|) may be NULL.
+ * Synchronises `stream`.  Costs n_check / N of one FP64 forward product.
+ * 1 <= n_check <= n, else GRAV_EINVAL. */
+int grav_plan_check_fp64(grav_plan *plan, const double *m, const double *d, int n_check, double *max_abs_err,
+                         double *rel_err, grav_stream_t stream);
 
 /* ---- measurement ------------------------------------------------------------ */
 /* Total number of CUDA kernels this library has launched in the process

@@ -62,7 +62,7 @@ class grav_options(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("near_cells", ctypes.c_double), ("timeout_s", ctypes.c_double),
                 ("precond", ctypes.c_int), ("cache_g", ctypes.c_int), ("outer_max", ctypes.c_int),
-                ("inner_max", ctypes.c_int)]
+                ("inner_max", ctypes.c_int), ("check_stations", ctypes.c_int)]
 
 
 class grav_job(ctypes.Structure):
@@ -74,7 +74,7 @@ class grav_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("rel_res", ctypes.c_double),
                 ("true_rel_res", ctypes.c_double), ("lambda_", ctypes.c_double), ("trace", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("outer", ctypes.c_int), ("alpha_min", ctypes.c_double),
-                ("restarts", ctypes.c_int)]
+                ("restarts", ctypes.c_int), ("fp64_rel_err", ctypes.c_double)]
 
 
 def _sig(name, res, args):
@@ -117,6 +117,7 @@ _sig("grav_cancel", _i, [_vp, ctypes.c_uint64])
 _sig("grav_job_times", _i, [_vp, ctypes.c_uint64, _D, _D, _D])
 _sig("grav_job_release", _i, [_vp, ctypes.c_uint64])
 _sig("grav_eval_fn64", _i, [_vp, _i, _vp, _vp, _vp, ctypes.c_int64, _vp])
+_sig("grav_plan_check_fp64", _i, [_vp, _vp, _vp, _i, _D, _D, _vp])
 
 EXPORTED = [
     "grav_options_default", "grav_version", "grav_ctx_create", "grav_ctx_destroy", "grav_last_error",
@@ -124,7 +125,7 @@ EXPORTED = [
     "grav_plan_forward", "grav_plan_adjoint", "grav_plan_bytes", "grav_plan_destroy",
     "grav_launch_count", "grav_plan_timing", "grav_bench_pipes", "grav_plan_describe",
     "grav_serve_config", "grav_submit", "grav_poll", "grav_wait", "grav_cancel", "grav_job_times",
-    "grav_job_release", "grav_eval_fn64",
+    "grav_job_release", "grav_eval_fn64", "grav_plan_check_fp64",
 ]
 
 STAGES = ("fwd_main", "adj_main", "fwd_near", "adj_near")
@@ -233,7 +234,8 @@ class Context:
         info = grav_solve_info()
         self.check(_lib.grav_poll(self.h, ctypes.c_uint64(job_id), ctypes.byref(st), ctypes.byref(info)))
         return JOB_STATES[st.value], {"iters": info.iters, "converged": bool(info.converged),
-                                       "true_rel_res": info.true_rel_res, "lambda": info.lambda_}
+                                       "true_rel_res": info.true_rel_res, "lambda": info.lambda_,
+                                       "fp64_rel_err": info.fp64_rel_err}
 
     def wait(self, job_id: int, timeout_s: float = 600.0) -> int:
         """Job result code (GRAV_OK, GRAV_ENOTCONVERGED, GRAV_ECANCELED, ...) or GRAV_ETIMEDOUT."""
@@ -314,7 +316,7 @@ class Survey:
 
 def options(precision="fp64", z0=50.0, lambda_scale=1e-2, lam=0.0, tol=1e-6, max_iter=1000,
             check_every=0, near_cells=8.0, timeout_s=3600.0, precond="none", cache_g=False, outer_max=0,
-            inner_max=20) -> grav_options:
+            inner_max=20, check_stations=0) -> grav_options:
     o = grav_options()
     _lib.grav_options_default(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -324,6 +326,7 @@ def options(precision="fp64", z0=50.0, lambda_scale=1e-2, lam=0.0, tol=1e-6, max
     o.precond = {"none": 0, "jacobi": 1}[precond] if isinstance(precond, str) else int(precond)
     o.cache_g = int(bool(cache_g))
     o.outer_max, o.inner_max = int(outer_max), int(inner_max)
+    o.check_stations = int(check_stations)
     return o
 
 
@@ -396,7 +399,7 @@ def datainv(d, mesh, survey, m_ref=None, return_y=False, stream=None, ctx: Optio
     inf = {"iters": info.iters, "converged": bool(info.converged), "rel_res": info.rel_res,
            "true_rel_res": info.true_rel_res, "lambda": info.lambda_, "trace": info.trace,
            "seconds": info.seconds, "status": rc, "outer": info.outer, "alpha_min": info.alpha_min,
-           "restarts": info.restarts}
+           "restarts": info.restarts, "fp64_rel_err": info.fp64_rel_err}
     return (m, y, inf) if return_y else (m, inf)
 
 
@@ -431,6 +434,16 @@ class Plan:
         self.ctx.check(_lib.grav_plan_adjoint(self.h, r.data_ptr(), g.data_ptr(), int(bool(depth_weighted)),
                                               _stream(stream)))
         return g
+
+    def check_fp64(self, m, d, n_check=64, stream=None):
+        """(max |d - d64|, that / max |d64|) at n_check evenly spaced stations,
+        d64 = G m from the FP64 operator; d is this plan's product G m."""
+        m = _f64(m, self.mesh.ncells, "m")
+        d = _f64(d, self.survey.n, "d")
+        ea, er = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        self.ctx.check(_lib.grav_plan_check_fp64(self.h, m.data_ptr(), d.data_ptr(), int(n_check), ctypes.byref(ea),
+                                                 ctypes.byref(er), _stream(stream)))
+        return ea.value, er.value
 
     def describe(self) -> dict:
         """Launch configuration chosen for this plan (kernels, chunking, bytes)."""

@@ -102,6 +102,7 @@ int check_options(grav_ctx *ctx, const grav_options &o) {
     if (o.cache_g != 0 && o.cache_g != 1) return set_error(ctx, GRAV_EINVAL, "cache_g must be 0 or 1");
     if (o.outer_max < 0 || o.outer_max > 100000) return set_error(ctx, GRAV_EINVAL, "outer_max must lie in [0, 1e5]");
     if (o.outer_max > 0 && o.inner_max < 1) return set_error(ctx, GRAV_EINVAL, "inner_max must be >= 1");
+    if (o.check_stations < 0) return set_error(ctx, GRAV_EINVAL, "check_stations must be >= 0");
     return GRAV_OK;
 }
 
@@ -417,6 +418,46 @@ int plan_allocate(grav_plan *p, cudaStream_t s) {
     return GRAV_OK;
 }
 
+// FP64 check of a product d = G m of plan p at n_check evenly spaced stations:
+// a transient FP64 plan over those stations evaluates G m exactly (Eq. 1-3).
+int check_fp64(grav_plan *p, const double *m, const double *d, int n_check, double *max_abs, double *rel,
+               cudaStream_t s) {
+    grav_ctx *ctx = p->ctx;
+    if (n_check < 1 || n_check > p->N) return set_error(ctx, GRAV_EINVAL, "n_check must lie in [1, n]");
+    double *buf = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync((void **)&buf, 40ull * n_check, ctx->pool, s);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "check scratch");
+    double *sx = buf, *sy = buf + n_check, *sz = buf + 2 * n_check, *dg = buf + 3 * n_check, *d64 = buf + 4 * n_check;
+    launch_gather_check(p->sx, p->sy, p->sz, d, p->N, n_check, sx, sy, sz, dg, s);
+    grav_mesh mesh{p->nx, p->ny, p->nz, p->xe.data(), p->ye.data(), p->ze.data()};
+    grav_survey sub{n_check, sx, sy, sz};
+    grav_options o;
+    grav_options_default(&o);
+    o.z0 = p->opt.z0;
+    o.timeout_s = p->opt.timeout_s;
+    grav_plan *q = nullptr;
+    int rc = plan_create(ctx, &mesh, &sub, o, &q, s);
+    if (!rc) {
+        rc = plan_forward_ex(q, m, d64, nullptr, 0.0, s);
+        plan_destroy(q, s);
+    }
+    std::vector<double> h(2ull * n_check);
+    if (!rc) {
+        cudaMemcpyAsync(h.data(), dg, 16ull * n_check, cudaMemcpyDeviceToHost, s);
+        rc = read_status(ctx, s, p->opt.timeout_s);
+    }
+    cudaFreeAsync(buf, s);
+    if (rc) return rc;
+    double ea = 0.0, ma = 0.0;
+    for (int k = 0; k < n_check; ++k) {
+        ea = std::max(ea, std::fabs(h[k] - h[n_check + k]));
+        ma = std::max(ma, std::fabs(h[n_check + k]));
+    }
+    if (max_abs) *max_abs = ea;
+    if (rel) *rel = ma > 0 ? ea / ma : ea;
+    return GRAV_OK;
+}
+
 int plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const grav_options &o,
                 grav_plan **out, cudaStream_t s) {
     grav_plan *p = nullptr;
@@ -720,6 +761,13 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
         if ((rc = plan_adjoint_ex(p, y, m_out, 1, m_ref, s))) break;
         if (y_out) cudaMemcpyAsync(y_out, y, 8ull * N, cudaMemcpyDeviceToDevice, s);
         if ((rc = sync_scalars("cg finish"))) break;
+        double fp64_rel = -1.0;
+        if (o.check_stations > 0 && o.precision != GRAV_FP64) {
+            // the predicted data of the recovered model, mixed against FP64
+            if ((rc = plan_forward_ex(p, m_out, Ap, nullptr, 0.0, s))) break;
+            if ((rc = check_fp64(p, m_out, Ap, (int)std::min<int64_t>(o.check_stations, N), nullptr, &fp64_rel, s)))
+                break;
+        }
         if (info) {
             info->iters = iters;
             info->converged = converged ? 1 : 0;
@@ -728,6 +776,7 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             info->outer = outer_done;
             info->alpha_min = alpha_min;
             info->restarts = restarts;
+            info->fp64_rel_err = fp64_rel;
             info->true_rel_res = true_rel;
             info->lambda = lam;
             info->trace = trace;
@@ -770,6 +819,7 @@ void grav_options_default(grav_options *o) {
     o->cache_g = 0;
     o->outer_max = 0;
     o->inner_max = 20;
+    o->check_stations = 0;
 }
 
 const char *grav_version(void) { return "libgrav 0.1.0 (sm_103a)"; }
@@ -942,6 +992,15 @@ int grav_plan_timing(grav_plan *p, int enable, double *ms, int64_t *counts) {
     t.enabled = enable != 0;
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GRAV_OK : cuda_error(p->ctx, e, "stage timing");
+}
+
+int grav_plan_check_fp64(grav_plan *p, const double *m, const double *d, int n_check, double *max_abs_err,
+                         double *rel_err, grav_stream_t stream) {
+    if (!p) return set_error(nullptr, GRAV_EINVAL, "plan is NULL");
+    DeviceGuard g(p->ctx->device);
+    if (!is_device_ptr(m, p->ctx->device) || !is_device_ptr(d, p->ctx->device))
+        return set_error(p->ctx, GRAV_EINVAL, "m and d must be device pointers");
+    return check_fp64(p, m, d, n_check, max_abs_err, rel_err, (cudaStream_t)stream);
 }
 
 int grav_plan_destroy(grav_plan *p, grav_stream_t stream) {

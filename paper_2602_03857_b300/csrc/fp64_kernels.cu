@@ -586,6 +586,24 @@ Geo make_geo(const grav_plan *p) {
     return g;
 }
 
+__global__ void k_gather_check(const double *__restrict__ sx, const double *__restrict__ sy,
+                               const double *__restrict__ sz, const double *__restrict__ d, int64_t n, int n_check,
+                               double *ox, double *oy, double *oz, double *od) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_check) return;
+    const int64_t i = (int64_t)k * n / n_check;
+    ox[k] = sx[i];
+    oy[k] = sy[i];
+    oz[k] = sz[i];
+    od[k] = d[i];
+}
+
+void launch_gather_check(const double *sx, const double *sy, const double *sz, const double *d, int64_t n,
+                         int n_check, double *ox, double *oy, double *oz, double *od, cudaStream_t s) {
+    k_gather_check<<<(n_check + 127) / 128, 128, 0, s>>>(sx, sy, sz, d, n, n_check, ox, oy, oz, od);
+    note_launches(1);
+}
+
 int fn_table_size() { return kFnTableSize; }
 
 void fill_fn_table(double *t) {

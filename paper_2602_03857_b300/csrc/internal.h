@@ -214,6 +214,11 @@ void launch_mixed_adj_finish(const grav_plan *p, const double *r, int depth_weig
 void launch_mixed_diag(const grav_plan *p, double *diag, cudaStream_t s);
 size_t mixed_scratch_bytes(const grav_plan *p);
 int mixed_adj_last_group(const grav_plan *p);
+// out_{x,y,z}[k] = s{x,y,z}[i_k], out_d[k] = d[i_k], i_k = floor(k n / n_check)
+void launch_gather_check(const double *sx, const double *sy, const double *sz, const double *d, int64_t n,
+                         int n_check, double *ox, double *oy, double *oz, double *od, cudaStream_t s);
+int check_fp64(grav_plan *p, const double *m, const double *d, int n_check, double *max_abs, double *rel,
+               cudaStream_t s);
 // Device view of a plan's mesh, stations and function table.
 Geo make_geo(const grav_plan *p);
 // Host: fills the kFnTableSize-double table of the FP64 log / atan (long-double

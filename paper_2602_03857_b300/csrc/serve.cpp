@@ -9,6 +9,7 @@
 // plan, so its result is the same whether it runs alone or in the mix (the
 // kernels are deterministic).  Inversions check a cancel flag between CG
 // iteration chunks.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstdlib>
@@ -87,6 +88,10 @@ void run_job(Scheduler *s, Job *job, cudaStream_t stream) {
         if (d.kind == GRAV_JOB_FORWARD) {
             rc = plan_forward_ex(p, d.input, d.output, nullptr, 0.0, stream);
             if (rc == GRAV_OK) rc = read_status(ctx, stream, d.opt.timeout_s);
+            job->info.fp64_rel_err = -1.0;
+            if (rc == GRAV_OK && d.opt.check_stations > 0 && d.opt.precision != GRAV_FP64)
+                rc = check_fp64(p, d.input, d.output, (int)std::min<int64_t>(d.opt.check_stations, d.survey.n),
+                                nullptr, &job->info.fp64_rel_err, stream);
         } else {
             rc = solve_on_plan(p, d.input, d.m_ref, d.output, nullptr, &job->info, stream, &job->cancel);
         }
@@ -202,6 +207,12 @@ int grav_submit(grav_ctx *ctx, const grav_job *job, uint64_t *job_id) {
     size_t est = 0;
     if (rc == GRAV_OK) {
         est = p->bytes + (job->kind == GRAV_JOB_INVERT ? solve_bytes(p) : 0);
+        if (job->opt.check_stations > 0 && job->opt.precision != GRAV_FP64) {
+            // the FP64 check's transient plan: node weights, the adjoint's node-sized
+            // scratch (two arrays plus station-chunk partials), station arrays and partials
+            const size_t nodes = (size_t)(job->mesh.nx + 2) * (job->mesh.ny + 1) * (job->mesh.nz + 1);
+            est += 32 * nodes + 256ull * (size_t)job->opt.check_stations + (1u << 20);
+        }
         delete p;
         if (est > ctx->hbm_budget)
             rc = set_error(ctx, GRAV_ENOMEM, "job needs %.3f GB, more than the context budget %.3f GB", est / 1e9,

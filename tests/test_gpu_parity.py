@@ -518,3 +518,39 @@ def test_empty_survey_one_shot_calls(g):
     with pytest.raises(g.GravError) as e:
         g.Plan(mesh, S)
     assert e.value.code == g.GRAV_EINVAL
+
+
+def test_fp64_error_statement(g):
+    """check_fp64 / check_stations: the error a mixed result states against the
+    FP64 operator equals its error against the oracle at the same stations
+    (the FP64 operator matches the oracle to 1e-10), and is within 1e-5."""
+    wl = synth.make_workload("vslab_80x80x40")
+    S = g.Survey(wl.survey.x, wl.survey.y, wl.survey.z)
+    plan = g.Plan(wl.mesh, S, precision="mixed")
+    m = _dev(wl.m)
+    d = plan.forward(m)
+    n_check = 48
+    ea, er = plan.check_fp64(m, d, n_check)
+    idx = (np.arange(n_check) * wl.survey.n) // n_check
+    d_ref = oracle.forward(wl.mesh, wl.survey.subset(idx), wl.m)
+    dd = d.cpu().numpy()[idx]
+    assert abs(ea - np.abs(dd - d_ref).max()) <= 1e-10 * np.abs(d_ref).max()
+    assert 0 < er <= TOLMIX
+    plan.close()
+    p64 = g.Plan(wl.mesh, S)
+    assert p64.check_fp64(m, p64.forward(m), 16)[1] <= 1e-13
+    p64.close()
+    with pytest.raises(g.GravError):
+        plan2 = g.Plan(wl.mesh, S, precision="mixed")
+        try:
+            plan2.check_fp64(m, d, wl.survey.n + 1)
+        finally:
+            plan2.close()
+    # inversions state the error of their predicted data
+    blk = synth.make_workload("block_20x20x10")
+    S1 = g.Survey(blk.survey.x, blk.survey.y, blk.survey.z)
+    d1 = g.forward(_dev(blk.m), blk.mesh, S1)
+    _, info = g.datainv(d1, blk.mesh, S1, precision="mixed", tol=1e-6, check_stations=32)
+    assert 0 < info["fp64_rel_err"] <= TOLMIX
+    _, info = g.datainv(d1, blk.mesh, S1, precision="fp64", tol=1e-6, check_stations=32)
+    assert info["fp64_rel_err"] == -1.0

@@ -69,6 +69,14 @@ def test_mixed_batch_matches_solo_runs(g):
         for jid, (kind, mesh, S, inp, out, solo, opts) in zip(ids, jobs):
             assert torch.equal(out, solo), (kind, opts["precision"])
             assert ctx.poll(jid)[0] == "done"
+        # a mixed forward job asked to state its error against the FP64 operator
+        mesh, sv, m = _problem(20, 40, 30, 12, 800, 25.0)
+        S = g.Survey(sv.x, sv.y, sv.z)
+        out = torch.empty(sv.n, dtype=torch.float64, device="cuda")
+        jid = ctx.submit("forward", mesh, S, _dev(m), out, precision="mixed", check_stations=24)
+        assert ctx.wait(jid, 600.0) == g.GRAV_OK
+        err = ctx.poll(jid)[1]["fp64_rel_err"]
+        assert 0 < err <= 1e-5
         times = [ctx.job_times(j) for j in ids]
         assert all(t0 <= t1 <= t2 for t0, t1, t2 in times)
         overlaps = sum(1 for a in times for b in times if a is not b and a[1] < b[2] and b[1] < a[2])
