@@ -66,10 +66,13 @@ typedef struct CUstream_st *grav_stream_t;
 /* GRAV_FP64: Eq. 1-3 evaluated in FP64 once per (station, mesh node) and
  *   differenced across shared nodes (summation by parts of Eq. 1 + Eq. 5).
  * GRAV_MIXED: every cell contributes through an FP32 point-mass far-field term
- *   gamma rho V dz / R^3 with compensated (two-sum) accumulation; cells whose
- *   centre lies within near_cells cell widths of a station are corrected to
- *   the exact FP64 prism value (Eq. 1) for that station.  CG dots and step
- *   lengths stay in FP64.  Requires cubic cells (dx = dy = dz per cell).
+ *   gamma rho V dz / R^3 (times the box's quadrupole factor when the cells are
+ *   not cubes) with compensated (two-sum) accumulation; cells whose centre
+ *   lies within near_cells cell widths (width = the largest cell edge) of a
+ *   station are corrected to the exact FP64 prism value (Eq. 1) for that
+ *   station.  CG dots and step lengths stay in FP64.  Requires a uniform mesh
+ *   (constant dx, dy, dz; a x b x c cells with any a, b, c); GRAV_EINVAL
+ *   otherwise.
  */
 #define GRAV_FP64    0
 #define GRAV_MIXED   1

@@ -292,21 +292,23 @@ int plan_prepare(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey
     p->sx = survey->x; p->sy = survey->y; p->sz = survey->z;
     {
         const double a = p->xe[1] - p->xe[0];
+        const double b = p->ye[1] - p->ye[0];
         const double c = p->ze[1] - p->ze[0];
         auto uni = [&](const std::vector<double> &e, double h) {
             for (size_t i = 0; i + 1 < e.size(); ++i)
                 if (std::fabs((e[i + 1] - e[i]) - h) > 1e-9 * h) return false;
             return true;
         };
-        p->square = uni(p->xe, a) && uni(p->ye, a) && uni(p->ze, c);
-        p->cubic = p->square && std::fabs(a - c) <= 1e-9 * a;
+        p->uniform = uni(p->xe, a) && uni(p->ye, b) && uni(p->ze, c);
+        p->cubic = p->uniform && std::fabs(a - b) <= 1e-9 * a && std::fabs(a - c) <= 1e-9 * a;
         p->cell_a = a;
+        p->cell_b = b;
         p->cell_c = c;
     }
-    if (o.precision != GRAV_FP64 && !p->square) {
+    if (o.precision != GRAV_FP64 && !p->uniform) {
         delete p;
         return set_error(ctx, GRAV_EINVAL,
-                         "GRAV_MIXED needs a uniform mesh of square-based prisms (dx = dy everywhere, dz uniform)");
+                         "GRAV_MIXED needs a uniform mesh (constant dx, dy and dz; they may differ from each other)");
     }
     size_t bytes = 0;
     auto add = [&](size_t v) { bytes += (v + 255) / 256 * 256 + 256; };
@@ -327,13 +329,13 @@ int plan_prepare(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey
             if (p->c_nchunk > rows) bytes += (size_t)(p->c_nchunk - rows) * p->N * 8 + 256;
         }
     } else {
-        const double a = p->cell_a;
-        const double L = std::max(p->cell_a, p->cell_c);   // the window radius is k cell widths, width = largest edge
+        // the window radius is k cell widths, width = the largest cell edge
+        const double L = std::max(p->cell_a, std::max(p->cell_b, p->cell_c));
         const double k = o.near_cells;
         p->ng.radius_cells = k;
         p->ng.width = L;
-        p->ng.bx = (int)std::ceil(2.0 * k * L / a) + 1;
-        p->ng.by = p->ng.bx;
+        p->ng.bx = (int)std::ceil(2.0 * k * L / p->cell_a) + 1;
+        p->ng.by = (int)std::ceil(2.0 * k * L / p->cell_b) + 1;
         int bz = 0;
         for (int l = 0; l < p->nz; ++l)
             if (0.5 * (p->ze[l] + p->ze[l + 1]) - p->ze[0] < k * L) bz = l + 1;
@@ -944,7 +946,7 @@ int grav_plan_describe(const grav_plan *p, char *buf, size_t len) {
     } else {
         char adj[64];
         // template arguments as the compiled kernels carry them (the last one:
-        // quadrupole far field for square-based, non-cubic prisms)
+        // quadrupole far field for non-cubic prisms)
         const int quad = p->cubic ? 0 : 1;
         char fwd[64];
         snprintf(fwd, sizeof(fwd), "k_mfwd<8, %d>", quad);

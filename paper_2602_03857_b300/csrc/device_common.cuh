@@ -255,22 +255,33 @@ __device__ __forceinline__ f2_t far_pair_acc(f2_t zc, f2_t nzs, f2_t h2, f2_t w,
     return f2_fma(w, k, acc);
 }
 
-// Far-field term of a square-based prism (dx = dy = a, dz = c) to second
-// order: dz / R^3 * (1 + qc / R^2 * (9 - 15 dz^2 / R^2)) with qc = (a^2 - c^2) / 24
-// (the quadrupole of a uniform box; it vanishes for a cube).  qc = 0 gives
-// exactly far_kernel().
-__device__ __forceinline__ float far_kernel_q(float dz, float R2, float qc) {
+// Far-field term of a uniform a x b x c box to second order.  Averaging
+// K = dz / R^3 over the box adds (a^2 Kxx + b^2 Kyy + c^2 Kzz) / 24 (the
+// second moments a^2/12, b^2/12, c^2/12; K is harmonic, so the box's
+// quadrupole is all there is to this order), i.e. K times
+//   1 + (A dx^2 + B dy^2 + C dz^2) / R^4,
+//   A = (12a^2 - 3b^2 - 9c^2) / 24, B = (12b^2 - 3a^2 - 9c^2) / 24,
+//   C = (6c^2 - 3a^2 - 3b^2) / 24
+// (all three vanish for a cube).  ph = A dx^2 + B dy^2 is formed once per
+// (station, column) by far_ph(); qg = C.
+__device__ __forceinline__ float far_ph(float2 X, float2 Y, float xh, float xl, float yh, float yl, float qa,
+                                        float qb) {
+    const float dx = (X.x - xh) + (X.y - xl);
+    const float dy = (Y.x - yh) + (Y.y - yl);
+    return fmaf(qa * dx, dx, (qb * dy) * dy);
+}
+
+__device__ __forceinline__ float far_kernel_q(float dz, float R2, float qg, float ph) {
     const float rs = rsqrt_approx(R2);
     const float rs2 = rs * rs;
     const float k = (dz * rs) * rs2;
-    const float t = (dz * dz) * rs2;
-    const float u = fmaf(-15.0f, t, 9.0f);
-    const float f = fmaf(qc * rs2, u, 1.0f);
+    const float n = fmaf(qg, dz * dz, ph);
+    const float f = fmaf(n, rs2 * rs2, 1.0f);
     return k * f;
 }
 
 // The same for two pairs at once (same operations per half).
-__device__ __forceinline__ f2_t far_pair_acc_q(f2_t zc, f2_t nzs, f2_t h2, f2_t w, f2_t acc, f2_t qc) {
+__device__ __forceinline__ f2_t far_pair_acc_q(f2_t zc, f2_t nzs, f2_t h2, f2_t w, f2_t acc, f2_t qg, f2_t ph) {
     const f2_t dz = f2_add(zc, nzs);
     const f2_t R2 = f2_fma(dz, dz, h2);
     float r0, r1;
@@ -278,20 +289,19 @@ __device__ __forceinline__ f2_t far_pair_acc_q(f2_t zc, f2_t nzs, f2_t h2, f2_t 
     const f2_t rs = f2_pack(rsqrt_approx(r0), rsqrt_approx(r1));
     const f2_t rs2 = f2_mul(rs, rs);
     const f2_t k = f2_mul(f2_mul(dz, rs), rs2);
-    const f2_t t = f2_mul(f2_mul(dz, dz), rs2);
-    const f2_t u = f2_fma(f2_pack(-15.0f, -15.0f), t, f2_pack(9.0f, 9.0f));
-    const f2_t f = f2_fma(f2_mul(qc, rs2), u, f2_pack(1.0f, 1.0f));
+    const f2_t n = f2_fma(qg, f2_mul(dz, dz), ph);
+    const f2_t f = f2_fma(n, f2_mul(rs2, rs2), f2_pack(1.0f, 1.0f));
     return f2_fma(w, f2_mul(k, f), acc);
 }
 
 template <bool QUAD>
-__device__ __forceinline__ f2_t far_pair(f2_t zc, f2_t nzs, f2_t h2, f2_t w, f2_t acc, f2_t qc) {
-    return QUAD ? far_pair_acc_q(zc, nzs, h2, w, acc, qc) : far_pair_acc(zc, nzs, h2, w, acc);
+__device__ __forceinline__ f2_t far_pair(f2_t zc, f2_t nzs, f2_t h2, f2_t w, f2_t acc, f2_t qg, f2_t ph) {
+    return QUAD ? far_pair_acc_q(zc, nzs, h2, w, acc, qg, ph) : far_pair_acc(zc, nzs, h2, w, acc);
 }
 
 template <bool QUAD>
-__device__ __forceinline__ float far_k(float dz, float R2, float qc) {
-    return QUAD ? far_kernel_q(dz, R2, qc) : far_kernel(dz, R2);
+__device__ __forceinline__ float far_k(float dz, float R2, float qg, float ph) {
+    return QUAD ? far_kernel_q(dz, R2, qg, ph) : far_kernel(dz, R2);
 }
 
 // Knuth two-sum: (s, e) with s = fl(a + b), a + b = s + e exactly.

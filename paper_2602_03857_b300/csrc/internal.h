@@ -28,7 +28,7 @@ struct MixedGeo {
     const float *cy;              // [ny][2]
     const float *czc;             // [nzp] cell-centre depth (FP32), padded
     int64_t N;
-    float qc;                     // (a^2 - c^2) / 24: quadrupole coefficient of the a x a x c cells (0: cubes)
+    float qa, qb, qg;             // quadrupole coefficients A, B, C of the a x b x c cells (0 for cubes)
     const float *ex;              // [nx+1][2] x edges as (hi, lo) relative to x_ref (GRAV_MIXED_CORNER)
     const float *ey;              // [ny+1][2]
     const float *ez;              // [nz+1] edge depths (FP32)
@@ -96,8 +96,8 @@ struct grav_plan {
     int64_t N = 0, M = 0, Nn = 0;
     std::vector<double> xe, ye, ze;       // host copies
     bool cubic = false;
-    bool square = false;                  // uniform a x a x c cells (GRAV_MIXED)
-    double cell_a = 0, cell_c = 0;
+    bool uniform = false;                 // uniform a x b x c cells (needed by GRAV_MIXED)
+    double cell_a = 0, cell_b = 0, cell_c = 0;   // uniform cell size along x, y, z (when uniform)
     grav::Arena arena;
     size_t bytes = 0;
 

@@ -1,9 +1,10 @@
-// Mixed-precision prism-gravity operator (GRAV_MIXED), cubic cells.
+// Mixed-precision prism-gravity operator (GRAV_MIXED), uniform a x b x c cells.
 //
 // Far field (every cell, FP32): a uniform cube attracts like a point mass
 // at its centre up to a relative error O((a/R)^4) (its quadrupole moment
-// vanishes), so G_ik ~ gamma V dz / R^3.  One MUFU reciprocal square root
-// per (station, cell) pair; per-column FP32 sums are folded into a (hi, lo)
+// vanishes), so G_ik ~ gamma V dz / R^3; other boxes carry their quadrupole
+// factor (far_kernel_q, the QUAD instantiations).  One MUFU reciprocal square
+// root per (station, cell) pair; per-column FP32 sums are folded into a (hi, lo)
 // pair by Knuth's two-sum (compensated accumulation), partials are combined
 // in FP64 in a fixed order.
 //
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(kMfThreads, GRAV_MF_MINB) k_mfwd(MixedGeo g, c
         if (nst > 1) issue(1);
     }
     const int nl4 = g.nzp >> 2;
-    const f2_t qc2 = f2_pack(g.qc, g.qc);
+    const f2_t qg2 = f2_pack(g.qg, g.qg);
     for (int st = 0; st < nst; ++st) {
         const int buf = st & 1;
         if (threadIdx.x == 0) *flag = mbar_wait_bounded(&bar[buf], (st >> 1) & 1) ? 1 : 0;
@@ -193,12 +194,18 @@ __global__ void __launch_bounds__(kMfThreads, GRAV_MF_MINB) k_mfwd(MixedGeo g, c
             const float2 X = cxs[i], Y = cys[j];
             if (++i == g.nx) { i = 0; ++j; }
             // layer pairs (l, l+1) of this column share one packed f32x2 chain per station
-            f2_t h2p[T], cs2[T];
+            f2_t h2p[T], cs2[T], php[T];
 #pragma unroll
             for (int t = 0; t < T; ++t) {
                 const float h = far_h2(X, Y, xh[t], xl[t], yh[t], yl[t]);
                 h2p[t] = f2_pack(h, h);
                 cs2[t] = 0ull;
+                if (QUAD) {
+                    const float ph = far_ph(X, Y, xh[t], xl[t], yh[t], yl[t], g.qa, g.qb);
+                    php[t] = f2_pack(ph, ph);
+                } else {
+                    php[t] = 0ull;
+                }
             }
             const float4 *q4 = reinterpret_cast<const float4 *>(qb + (size_t)(col - ca) * g.nzp);
             const float4 *z4 = reinterpret_cast<const float4 *>(czs);
@@ -208,8 +215,8 @@ __global__ void __launch_bounds__(kMfThreads, GRAV_MF_MINB) k_mfwd(MixedGeo g, c
                 const f2_t z01 = f2_pack(z.x, z.y), z23 = f2_pack(z.z, z.w);
 #pragma unroll
                 for (int t = 0; t < T; ++t) {
-                    cs2[t] = far_pair<QUAD>(z01, nzs[t], h2p[t], q01, cs2[t], qc2);
-                    cs2[t] = far_pair<QUAD>(z23, nzs[t], h2p[t], q23, cs2[t], qc2);
+                    cs2[t] = far_pair<QUAD>(z01, nzs[t], h2p[t], q01, cs2[t], qg2, php[t]);
+                    cs2[t] = far_pair<QUAD>(z23, nzs[t], h2p[t], q23, cs2[t], qg2, php[t]);
                 }
             }
 #pragma unroll
@@ -313,11 +320,12 @@ __global__ void __launch_bounds__(kMaWarps * 32, MaMinBlocks<TZ>::value) k_madj(
                 const float4 P = pb[k];
                 const float2 Z = zb[k];
                 const float h2 = far_h2(X, Y, P.x, P.y, P.z, P.w);
+                const float ph = QUAD ? far_ph(X, Y, P.x, P.y, P.z, P.w, g.qa, g.qb) : 0.0f;
 #pragma unroll
                 for (int t = 0; t < TZ; ++t) {
                     const float dz = zc[t] - Z.x;
                     const float R2 = fmaf(dz, dz, h2);
-                    cs[t] = fmaf(Z.y, far_k<QUAD>(dz, R2, g.qc), cs[t]);
+                    cs[t] = fmaf(Z.y, far_k<QUAD>(dz, R2, g.qg, ph), cs[t]);
                 }
             }
 #pragma unroll
@@ -375,7 +383,7 @@ __device__ __forceinline__ void madj_bc_body(const MixedGeo &g, const float4 *__
     const float2 X = make_float2(g.cx[2 * i], g.cx[2 * i + 1]);
     const float2 Y = make_float2(g.cy[2 * j], g.cy[2 * j + 1]);
     static_assert(TZ % 2 == 0, "layer pairs");
-    const f2_t qc2 = f2_pack(g.qc, g.qc);
+    const f2_t qg2 = f2_pack(g.qg, g.qg);
     f2_t zcp[TZ / 2], cs2[TZ / 2];
     double acc[TZ];
 #pragma unroll
@@ -430,8 +438,13 @@ __device__ __forceinline__ void madj_bc_body(const MixedGeo &g, const float4 *__
                 const float2 Z = zb[k];
                 const float h = far_h2(X, Y, P.x, P.y, P.z, P.w);
                 const f2_t h2p = f2_pack(h, h), nz2 = f2_pack(-Z.x, -Z.x), w2 = f2_pack(Z.y, Z.y);
+                f2_t ph2 = 0ull;
+                if (QUAD) {
+                    const float ph = far_ph(X, Y, P.x, P.y, P.z, P.w, g.qa, g.qb);
+                    ph2 = f2_pack(ph, ph);
+                }
 #pragma unroll
-                for (int u = 0; u < TZ / 2; ++u) cs2[u] = far_pair<QUAD>(zcp[u], nz2, h2p, w2, cs2[u], qc2);
+                for (int u = 0; u < TZ / 2; ++u) cs2[u] = far_pair<QUAD>(zcp[u], nz2, h2p, w2, cs2[u], qg2, ph2);
             }
 #pragma unroll
             for (int u = 0; u < TZ / 2; ++u) {
@@ -615,11 +628,11 @@ __global__ void __launch_bounds__(kCfThreads) k_cfwd32(MixedGeo g, int ldw, cons
 // cell: dG = G_exact - G_far when the cell centre lies within the window
 // radius, else 0.  Also returns the near-field part of diag(G W^-2 G^T),
 // sum w2 (G_exact^2 - G_far^2), the box origin and the station's bin key.
-// The mesh is uniform cubic: x edges x0 + i a, y edges y0 + j a.
+// The mesh is uniform: x edges x0 + i a, y edges y0 + j b.
 // ---------------------------------------------------------------------------
 template <bool CORNER>
 __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
-    Geo g, MixedGeo mg, NearGeo ng, double x0, double y0, double a, double vol_mgal,
+    Geo g, MixedGeo mg, NearGeo ng, double x0, double y0, double a, double b, double vol_mgal,
     const double *__restrict__ sx, const double *__restrict__ sy, const double *__restrict__ sz,
     const double *__restrict__ w2, const float4 *__restrict__ st32, const float2 *__restrict__ stz,
     double *__restrict__ dG, int *__restrict__ st_i0, int *__restrict__ st_j0, double *__restrict__ diag_corr,
@@ -636,11 +649,11 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
     if (s >= g.N) return;   // warp-uniform
     const double xs = sx[s], ys = sy[s], zs = sz[s];
     const double lim = 1.0e9;
-    // window radius k * width in units of the horizontal cell size a (width =
-    // max(a, c), so the radius spans k * width / a >= k columns)
-    const double rad = ng.radius_cells * ng.width / a;
-    const double fx = fmin(fmax((xs - x0) / a - 0.5 - rad, -lim), lim);
-    const double fy = fmin(fmax((ys - y0) / a - 0.5 - rad, -lim), lim);
+    // window radius k * width in units of the cell sizes a (x) and b (y)
+    // (width = max(a, b, c), so the radius spans >= k columns on each axis)
+    const double rad = ng.radius_cells * ng.width;
+    const double fx = fmin(fmax((xs - x0) / a - 0.5 - rad / a, -lim), lim);
+    const double fy = fmin(fmax((ys - y0) / b - 0.5 - rad / b, -lim), lim);
     const int i0 = (int)floor(fx) + 1;
     const int j0 = (int)floor(fy) + 1;
     for (int t = lane; t < nnode; t += 32) {
@@ -704,9 +717,10 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
                     const float2 X = make_float2(mg.cx[2 * i], mg.cx[2 * i + 1]);
                     const float2 Y = make_float2(mg.cy[2 * j], mg.cy[2 * j + 1]);
                     const float h2 = far_h2(X, Y, S.x, S.y, S.z, S.w);
+                    const float ph = far_ph(X, Y, S.x, S.y, S.z, S.w, mg.qa, mg.qb);
                     const float dz = mg.czc[l] - zf;
                     const float R2 = fmaf(dz, dz, h2);
-                    gfar = vol_mgal * (double)far_kernel_q(dz, R2, mg.qc);
+                    gfar = vol_mgal * (double)far_kernel_q(dz, R2, mg.qg, ph);
                 }
                 val = gex - gfar;
                 dcorr += w2[l] * (gex * gex - gfar * gfar);
@@ -835,10 +849,11 @@ __global__ void __launch_bounds__(kMfThreads) k_mdiag(MixedGeo g, const float *_
         const int i = col % g.nx, j = col / g.nx;
         const float2 X = make_float2(g.cx[2 * i], g.cx[2 * i + 1]);
         const float2 Y = make_float2(g.cy[2 * j], g.cy[2 * j + 1]);
-        float h2[T], cs[T];
+        float h2[T], ph[T], cs[T];
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             h2[t] = far_h2(X, Y, xh[t], xl[t], yh[t], yl[t]);
+            ph[t] = QUAD ? far_ph(X, Y, xh[t], xl[t], yh[t], yl[t], g.qa, g.qb) : 0.0f;
             cs[t] = 0.f;
         }
         for (int l = 0; l < g.nz; ++l) {
@@ -846,7 +861,7 @@ __global__ void __launch_bounds__(kMfThreads) k_mdiag(MixedGeo g, const float *_
 #pragma unroll
             for (int t = 0; t < T; ++t) {
                 const float dz = zc - zs[t];
-                const float k = far_k<QUAD>(dz, fmaf(dz, dz, h2[t]), g.qc);
+                const float k = far_k<QUAD>(dz, fmaf(dz, dz, h2[t]), g.qg, ph[t]);
                 cs[t] = fmaf(wl, k * k, cs[t]);
             }
         }
@@ -1116,7 +1131,12 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
 
     p->mg.nx = nx; p->mg.ny = ny; p->mg.nz = nz; p->mg.nzp = nzp; p->mg.ncol = nx * ny;
     p->mg.cx = p->m_cx; p->mg.cy = p->m_cy; p->mg.czc = p->m_czc; p->mg.N = p->N;
-    p->mg.qc = p->cubic ? 0.0f : (float)((p->cell_a * p->cell_a - p->cell_c * p->cell_c) / 24.0);
+    {
+        const double a2 = p->cell_a * p->cell_a, b2 = p->cell_b * p->cell_b, c2 = p->cell_c * p->cell_c;
+        p->mg.qa = p->cubic ? 0.0f : (float)((12.0 * a2 - 3.0 * b2 - 9.0 * c2) / 24.0);
+        p->mg.qb = p->cubic ? 0.0f : (float)((12.0 * b2 - 3.0 * a2 - 9.0 * c2) / 24.0);
+        p->mg.qg = p->cubic ? 0.0f : (float)((6.0 * c2 - 3.0 * a2 - 3.0 * b2) / 24.0);
+    }
 
     cudaMemcpyAsync(p->m_cx, hcx.data(), 8ull * nx, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(p->m_cy, hcy.data(), 8ull * ny, cudaMemcpyHostToDevice, s);
@@ -1127,11 +1147,12 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
 
     const int nnode = (p->ng.bx + 1) * (p->ng.by + 1) * (p->ng.bz + 1);
     const size_t smem = (size_t)ns_warps * nnode * (corner ? 12 : 8);
-    const double vol_mgal = kGammaMgal * p->cell_a * p->cell_a * p->cell_c;
+    const double vol_mgal = kGammaMgal * p->cell_a * p->cell_b * p->cell_c;
     auto setup = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         kern<<<(unsigned)((p->N + ns_warps - 1) / ns_warps), ns_warps * 32, smem, s>>>(
-            make_geo(p), p->mg, p->ng, p->xe[0], p->ye[0], a, vol_mgal, p->sx, p->sy, p->sz, p->d_w2, p->st32,
+            make_geo(p), p->mg, p->ng, p->xe[0], p->ye[0], a, p->ye[1] - p->ye[0], vol_mgal, p->sx, p->sy, p->sz,
+            p->d_w2, p->st32,
             p->stz, p->dG, p->st_i0, p->st_j0, p->diag_corr, keys, vals, (unsigned)z.nbins);
     };
     if (corner) setup(k_near_setup<true>); else setup(k_near_setup<false>);
@@ -1148,7 +1169,7 @@ int mixed_adj_last_group(const grav_plan *p) { return p->m_adj_bc ? adj_tzl_bc(p
 size_t mfwd_smem(const grav_plan *p) { return mfwd_layout(p->mg, kMfColsPerStage).total; }
 
 void launch_mixed_prep_q(const grav_plan *p, const double *m, cudaStream_t s) {
-    const float scale = (float)(kGammaMgal * p->cell_a * p->cell_a * p->cell_c);
+    const float scale = (float)(kGammaMgal * p->cell_a * p->cell_b * p->cell_c);
     const int64_t total = (int64_t)p->mg.ncol * p->mg.nzp;
     k_prep_q<<<grid_for(total, 256), 256, 0, s>>>(p->mg, m, scale, p->qT);
     note_launches(1);
@@ -1259,7 +1280,7 @@ void launch_mixed_adj_finish(const grav_plan *p, const double *r, int depth_weig
     (void)r;
     k_madj_finish<<<grid_for(p->M, 256), 256, 0, s>>>(p->nx, p->ny, p->nz, std::min(p->ng.bz, p->nz), p->m_apart,
                                                       p->m_adj_nschunk,
-                                                      kGammaMgal * p->cell_a * p->cell_a * p->cell_c, p->m_cellacc,
+                                                      kGammaMgal * p->cell_a * p->cell_b * p->cell_c, p->m_cellacc,
                                                       depth_weighted ? p->d_w2 : nullptr, add, out);
     note_launches(1);
 }
@@ -1274,7 +1295,7 @@ void launch_mixed_diag(const grav_plan *p, double *diag, cudaStream_t s) {
         k_mdiag<kMfT, true><<<grid, kMfThreads, 0, s>>>(p->mg, p->m_w2f, p->st32, p->stz, p->m_fwd_cols_per_chunk,
                                                         p->m_part);
     note_launches(1);
-    const double v = kGammaMgal * p->cell_a * p->cell_a * p->cell_c;
+    const double v = kGammaMgal * p->cell_a * p->cell_b * p->cell_c;
     launch_reduce_rows(p->m_part, p->m_fwd_nchunk, p->N, v * v, nullptr, 0.0, p->diag_corr, diag, s);
 }
 

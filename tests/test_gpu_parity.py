@@ -237,20 +237,25 @@ def _mixed_definition(mesh, sv, G, cell, k):
     return np.where(R < k * cell, G, far)
 
 
-@pytest.mark.parametrize("shape,a,c,h,seed", [((30, 26, 14), 40.0, 20.0, 6.0, 11), ((21, 19, 9), 20.0, 30.0, 4.0, 12)])
-def test_mixed_square_prisms_vs_oracle(g, shape, a, c, h, seed, adjoint_layout):
-    """Non-cubic a x a x c cells: the far field carries the box's quadrupole
-    term, so the mixed operator still meets 1e-5 of max against the oracle, and
-    the kernels implement the definition (exact inside the window, corrected
-    point mass outside) at 1e-6."""
+@pytest.mark.parametrize("shape,a,b,c,h,seed", [((30, 26, 14), 40.0, 40.0, 20.0, 6.0, 11),
+                                                ((21, 19, 9), 20.0, 20.0, 30.0, 4.0, 12),
+                                                ((26, 35, 10), 30.0, 20.0, 25.0, 5.0, 13),
+                                                ((12, 48, 8), 50.0, 12.5, 20.0, 3.0, 14)])
+def test_mixed_noncubic_prisms_vs_oracle(g, shape, a, b, c, h, seed, adjoint_layout):
+    """Non-cubic a x b x c cells: the far field carries the box's quadrupole
+    factor 1 + (A dx^2 + B dy^2 + C dz^2) / R^4 (second moments a^2/12, b^2/12,
+    c^2/12 of the box in the Taylor expansion of dz / R^3), so the mixed
+    operator still meets 1e-5 of max against the oracle, and the kernels
+    implement that definition (exact inside the window of k * max(a, b, c),
+    corrected point mass outside) at 1e-6."""
     nx, ny, nz = shape
-    mesh = synth.uniform_mesh(nx, ny, nz, a, a, c)
+    mesh = synth.uniform_mesh(nx, ny, nz, a, b, c)
     rng = np.random.Generator(np.random.PCG64(60 + seed))
     m = synth.lognormal_background(mesh.ncells, 20.0, rng).reshape(nz, ny, nx)
     m[2:7, ny // 4: 3 * ny // 4, nx // 3: nx // 3 + 3] += 400.0
     m = m.ravel()
     n = 400
-    sv = synth.Survey(rng.uniform(0, nx * a, n), rng.uniform(0, ny * a, n), -rng.uniform(0.5, h, n))
+    sv = synth.Survey(rng.uniform(0, nx * a, n), rng.uniform(0, ny * b, n), -rng.uniform(0.5, h, n))
     S = g.Survey(sv.x, sv.y, sv.z)
     G = oracle.G_explicit(mesh, sv)
     d = g.forward(_dev(m), mesh, S, precision="mixed").cpu().numpy()
@@ -258,14 +263,17 @@ def test_mixed_square_prisms_vs_oracle(g, shape, a, c, h, seed, adjoint_layout):
     r = synth.random_vector(n, seed)
     at = g.adjoint(_dev(r), mesh, S, precision="mixed").cpu().numpy()
     assert _rel(at, G.T @ r) <= TOLMIX
-    L = max(a, c)
+    L = max(a, b, c)
     xc = 0.5 * (mesh.xe[:-1] + mesh.xe[1:]); yc = 0.5 * (mesh.ye[:-1] + mesh.ye[1:])
     zc = 0.5 * (mesh.ze[:-1] + mesh.ze[1:])
     Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
     DX = X.ravel()[None, :] - sv.x[:, None]; DY = Y.ravel()[None, :] - sv.y[:, None]
     DZ = Z.ravel()[None, :] - sv.z[:, None]
     R2 = DX ** 2 + DY ** 2 + DZ ** 2
-    far = 6.67430e-11 * 1e5 * a * a * c * DZ / R2 ** 1.5 * (1 + (a * a - c * c) / (24 * R2) * (9 - 15 * DZ ** 2 / R2))
+    qa = (12 * a * a - 3 * b * b - 9 * c * c) / 24
+    qb = (12 * b * b - 3 * a * a - 9 * c * c) / 24
+    qg = (6 * c * c - 3 * a * a - 3 * b * b) / 24
+    far = 6.67430e-11 * 1e5 * a * b * c * DZ / R2 ** 1.5 * (1 + (qa * DX ** 2 + qb * DY ** 2 + qg * DZ ** 2) / R2 ** 2)
     for k in (3.0, 5.0):
         Gk = np.where(R2 < (k * L) ** 2, G, far)
         dk = g.forward(_dev(m), mesh, S, precision="mixed", near_cells=k).cpu().numpy()
@@ -421,7 +429,7 @@ def test_error_paths(g):
     irregular, sv2, m2 = synth.small_random_problem(4, 4, 3, 10, seed=71, irregular=True)
     with pytest.raises(g.GravError) as e:
         g.forward(_dev(m2), irregular, g.Survey(sv2.x, sv2.y, sv2.z), precision="mixed")
-    assert e.value.code == g.GRAV_EINVAL and "square-based" in str(e.value)
+    assert e.value.code == g.GRAV_EINVAL and "uniform mesh" in str(e.value)
     with pytest.raises(g.GravError):
         g.forward(_dev(m), mesh, S, near_cells=0.2, precision="mixed")
     # host pointer for a device argument
