@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--invert", action="store_true", help="time one data-space inversion on --workload")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--max-iter", type=int, default=5000)
+    ap.add_argument("--reorth", type=int, default=1000,
+                    help="--invert: residuals kept for reorthogonalised CG (0 = plain CG)")
     ap.add_argument("--precond", default="none", choices=["none", "jacobi"])
     return ap.parse_args()
 
@@ -487,14 +489,15 @@ def run_invert(args):
     d = g.forward(m, wl.mesh, S, precision=data_prec, near_cells=args.near_cells)
     torch.cuda.synchronize()
     opts = dict(precision=args.precision, near_cells=args.near_cells, tol=args.tol, max_iter=args.max_iter,
-                precond=args.precond, check_stations=64)
+                precond=args.precond, check_stations=64, reorth=args.reorth)
     t0 = time.perf_counter()
     m_out, info = g.datainv(d, wl.mesh, S, **opts)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     misfit = g.forward(m_out, wl.mesh, S, precision=data_prec, near_cells=args.near_cells) - d
     line = {"metric": "inversion time to relative residual", "workload": args.workload,
-            "precision": args.precision, "precond": args.precond, "tol": args.tol, "seconds": wall,
+            "precision": args.precision, "precond": args.precond, "reorth": args.reorth, "tol": args.tol,
+            "seconds": wall,
             "iters": info["iters"],
             "converged": info["converged"], "true_rel_res": info["true_rel_res"], "lambda": info["lambda"],
             "cells": wl.mesh.ncells, "stations": wl.survey.n, "data_operator": data_prec,

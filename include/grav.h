@@ -116,6 +116,11 @@ typedef struct {
                                   updates y += alpha dy, dy from <= inner_max CG iterations on A dy = dd - A y,
                                   alpha by backtracking on the objective of Eq. 7; 0 = one CG solve (default) */
     int inner_max;             /* CG iterations per outer update (default 20) */
+    int reorth;                /* single CG solve without preconditioner (precond = 0, outer_max = 0): keep up
+                                  to this many normalised residuals (N*reorth*8 bytes of HBM, at most 4096)
+                                  and reorthogonalise every new residual against them (twice), which
+                                  restores the convergence CG loses to rounding on this system; 0 = plain
+                                  CG (default 1000) */
     int check_stations;        /* mixed modes, > 0: state the error of the result against the FP64 operator
                                   at this many evenly spaced stations (inversions: of G m_out; serving
                                   forward jobs: of d), in grav_solve_info.fp64_rel_err; 0 = off (default) */
@@ -142,7 +147,7 @@ typedef struct grav_plan grav_plan;
 /* Fills *opt with the defaults: GRAV_FP64, z0 = 50, lambda_scale = 1e-2,
  * lambda = 0, tol = 1e-6, max_iter = 1000, check_every = 0,
  * near_cells = 8, timeout_s = 3600, precond = 0, cache_g = 0, outer_max = 0,
- * inner_max = 20, check_stations = 0. */
+ * inner_max = 20, reorth = 1000, check_stations = 0. */
 void grav_options_default(grav_options *opt);
 
 /* Library version string (static storage). */

@@ -103,6 +103,8 @@ int check_options(grav_ctx *ctx, const grav_options &o) {
     if (o.outer_max < 0 || o.outer_max > 100000) return set_error(ctx, GRAV_EINVAL, "outer_max must lie in [0, 1e5]");
     if (o.outer_max > 0 && o.inner_max < 1) return set_error(ctx, GRAV_EINVAL, "inner_max must be >= 1");
     if (o.check_stations < 0) return set_error(ctx, GRAV_EINVAL, "check_stations must be >= 0");
+    if (o.reorth < 0 || o.reorth > kReorthMaxBasis)
+        return set_error(ctx, GRAV_EINVAL, "reorth must lie in [0, %d]", kReorthMaxBasis);
     return GRAV_OK;
 }
 
@@ -471,7 +473,17 @@ int plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey,
     return GRAV_OK;
 }
 
-size_t solve_bytes(const grav_plan *p) { return 8ull * (12 * p->N + p->M + kDotBlocks + kSCount) + 16 * 256; }
+// Basis vectors kept by the reorthogonalised CG (0: plain CG).
+int reorth_cap(const grav_plan *p) {
+    const grav_options &o = p->opt;
+    if (o.reorth <= 0 || o.precond != 0 || o.outer_max > 0) return 0;
+    return (int)std::min<int64_t>(o.reorth, (int64_t)o.max_iter + 1);
+}
+
+size_t solve_bytes(const grav_plan *p) {
+    const int cap = reorth_cap(p);
+    return 8ull * (12 * p->N + p->M + kDotBlocks + kSCount) + 16 * 256 + 8ull * cap * (p->N + 1) + 2 * 256;
+}
 
 void plan_destroy(grav_plan *p, cudaStream_t s) {
     if (!p) return;
@@ -536,6 +548,9 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
     double *fv = (double *)ar.take(8ull * N);
     double *dp = (double *)ar.take(8ull * kDotBlocks);
     double *sc = (double *)ar.take(8ull * kSCount);
+    const int cap = reorth_cap(p);
+    double *Qb = cap ? (double *)ar.take(8ull * cap * N) : nullptr;   // reorthogonalisation basis [cap][N]
+    double *cb = cap ? (double *)ar.take(8ull * cap) : nullptr;
     double *hsc = nullptr;
     cudaMallocHost((void **)&hsc, 8 * kSCount);
     cudaEvent_t ev;
@@ -690,6 +705,11 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             launch_dot(r, r, N, dp, sc + kSRR, s);
             cg_set_scalars(sc, o.tol * o.tol, kSRR, s);
         }
+        int kb = 0;   // basis vectors stored (reorthogonalised CG)
+        if (cap) {
+            cg_basis_append(Qb, r, N, sc, kSRR, s);
+            kb = 1;
+        }
         if ((rc = sync_scalars("cg start"))) break;
         if (hsc[kSFrozen] != 0.0) {
             converged = true;
@@ -716,8 +736,13 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
                         cg_beta(sc, it, kSResNew, s);
                         cg_update_p(pv, zv, N, sc, s);
                     } else {
+                        if (cap) cg_reorth(Qb, kb, N, r, cb, sc, s);
                         launch_dot(r, r, N, dp, sc + kSRRNew, s);
                         cg_beta(sc, it, kSRRNew, s);
+                        if (cap && kb < cap) {
+                            cg_basis_append(Qb + (size_t)kb * N, r, N, sc, kSRRNew, s);
+                            ++kb;
+                        }
                         cg_update_p(pv, r, N, sc, s);
                     }
                 }
@@ -755,6 +780,10 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             } else {
                 cudaMemcpyAsync(pv, r, 8ull * N, cudaMemcpyDeviceToDevice, s);
                 cg_restart(sc, 1, s);
+                if (cap) {   // a new Krylov space from the true residual
+                    cg_basis_append(Qb, r, N, sc, kSTmp, s);
+                    kb = 1;
+                }
             }
         }
         if (rc) break;
@@ -821,6 +850,7 @@ void grav_options_default(grav_options *o) {
     o->cache_g = 0;
     o->outer_max = 0;
     o->inner_max = 20;
+    o->reorth = 1000;
     o->check_stations = 0;
 }
 

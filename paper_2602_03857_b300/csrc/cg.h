@@ -34,5 +34,12 @@ void cg_set_scalars(double *sc, double tol2, int bb_slot, cudaStream_t s);
 void cg_restart(double *sc, int copy_rr, cudaStream_t s);
 void vec_mul(const double *a, const double *b, int64_t n, double *out, cudaStream_t s);
 void vec_jacobi_inv(const double *diag, double lam, int64_t n, double *out, cudaStream_t s);
+// Full reorthogonalisation of the CG residual against the stored basis Q
+// ([k][n], orthonormal rows): r -= Q^T (Q r), done twice; then
+// cg_basis_append: Q[k] = r / |r| with |r|^2 from sc[rr_slot].  Both are
+// no-ops once the CG state is frozen.  c: k doubles of scratch.
+constexpr int kReorthMaxBasis = 4096;
+void cg_reorth(const double *Q, int k, int64_t n, double *r, double *c, const double *sc, cudaStream_t s);
+void cg_basis_append(double *q_k, const double *r, int64_t n, const double *sc, int rr_slot, cudaStream_t s);
 
 }  // namespace grav

@@ -113,6 +113,49 @@ __global__ void k_cg_restart(double *__restrict__ sc, int copy_rr) {
     sc[kSFrozen] = (sc[kSTmp] <= sc[kSTol2] * sc[kSBB]) ? 1.0 : 0.0;
 }
 
+// c[j] = Q[j] . r, one CTA per basis vector, fixed reduction order
+__global__ void __launch_bounds__(kDotThreads) k_basis_coef(const double *__restrict__ Q, int64_t n,
+                                                            const double *__restrict__ r, double *__restrict__ c,
+                                                            const double *__restrict__ sc) {
+    if (sc[kSFrozen] != 0.0) return;
+    __shared__ double ws[kDotThreads / 32];
+    const double *q = Q + (int64_t)blockIdx.x * n;
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += kDotThreads) acc = fma(q[i], r[i], acc);
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kDotThreads / 32; ++w) t += ws[w];
+        c[blockIdx.x] = t;
+    }
+}
+
+// r[i] -= sum_j c[j] Q[j][i]  (coalesced across i; c staged in shared memory)
+__global__ void __launch_bounds__(256) k_basis_sub(const double *__restrict__ Q, int k, int64_t n,
+                                                   const double *__restrict__ c, double *__restrict__ r,
+                                                   const double *__restrict__ sc) {
+    if (sc[kSFrozen] != 0.0) return;
+    __shared__ double cs[kReorthMaxBasis];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = c[j];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int j = 0; j < k; ++j) acc = fma(cs[j], Q[(int64_t)j * n + i], acc);
+        r[i] -= acc;
+    }
+}
+
+__global__ void k_basis_append(double *__restrict__ q, const double *__restrict__ r, int64_t n,
+                               const double *__restrict__ sc, int rr_slot) {
+    if (sc[kSFrozen] != 0.0 || !(sc[rr_slot] > 0.0)) return;
+    const double inv = 1.0 / sqrt(sc[rr_slot]);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        q[i] = r[i] * inv;
+}
+
 inline int vgrid(int64_t n) {
     int64_t b = (n + 255) / 256;
     return (int)(b < 1 ? 1 : (b > 148 * 16 ? 148 * 16 : b));
@@ -150,6 +193,17 @@ void vec_mul(const double *a, const double *b, int64_t n, double *out, cudaStrea
 }
 void vec_jacobi_inv(const double *diag, double lam, int64_t n, double *out, cudaStream_t s) {
     k_jacobi_inv<<<vgrid(n), 256, 0, s>>>(diag, lam, n, out); note_launches(1);
+}
+void cg_reorth(const double *Q, int k, int64_t n, double *r, double *c, const double *sc, cudaStream_t s) {
+    if (k <= 0) return;
+    for (int pass = 0; pass < 2; ++pass) {   // "twice is enough"
+        k_basis_coef<<<k, kDotThreads, 0, s>>>(Q, n, r, c, sc);
+        k_basis_sub<<<vgrid(n), 256, 0, s>>>(Q, k, n, c, r, sc);
+    }
+    note_launches(4);
+}
+void cg_basis_append(double *q_k, const double *r, int64_t n, const double *sc, int rr_slot, cudaStream_t s) {
+    k_basis_append<<<vgrid(n), 256, 0, s>>>(q_k, r, n, sc, rr_slot); note_launches(1);
 }
 
 }  // namespace grav

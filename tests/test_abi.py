@@ -71,3 +71,11 @@ def test_binding_constants_match_header():
         if hasattr(g, name):
             assert getattr(g, name) == int(val), name
     assert g.PRECISIONS == {"fp64": 0, "mixed": 1, "mixed_corner": 2}
+
+
+def test_c_option_defaults(lib):
+    import paper_2602_03857_b300 as g
+    o = g.grav_options()
+    g._lib.grav_options_default(ctypes.byref(o))
+    assert o.precision == g.GRAV_FP64 and o.max_iter == 1000 and o.near_cells == 8.0
+    assert o.reorth == 1000 and o.check_stations == 0 and o.precond == 0 and o.outer_max == 0
