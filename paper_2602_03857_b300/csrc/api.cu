@@ -705,8 +705,9 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             launch_dot(r, r, N, dp, sc + kSRR, s);
             cg_set_scalars(sc, o.tol * o.tol, kSRR, s);
         }
-        int kb = 0;   // basis vectors stored (reorthogonalised CG)
-        if (cap) {
+        int kb = 0;            // basis vectors stored (reorthogonalised CG)
+        bool reo = cap > 0;    // reorthogonalise (first pass only; restarts run plain CG)
+        if (reo) {
             cg_basis_append(Qb, r, N, sc, kSRR, s);
             kb = 1;
         }
@@ -736,10 +737,10 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
                         cg_beta(sc, it, kSResNew, s);
                         cg_update_p(pv, zv, N, sc, s);
                     } else {
-                        if (cap) cg_reorth(Qb, kb, N, r, cb, sc, s);
+                        if (reo) cg_reorth(Qb, kb, N, r, cb, sc, s);
                         launch_dot(r, r, N, dp, sc + kSRRNew, s);
                         cg_beta(sc, it, kSRRNew, s);
-                        if (cap && kb < cap) {
+                        if (reo && kb < cap) {
                             cg_basis_append(Qb + (size_t)kb * N, r, N, sc, kSRRNew, s);
                             ++kb;
                         }
@@ -767,7 +768,7 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             if ((rc = sync_scalars("cg true residual"))) break;
             true_rel = hsc[kSBB] > 0 ? std::sqrt(hsc[kSTmp] / hsc[kSBB]) : 0.0;
             iters = (int)hsc[kSIters];   // iterations that updated y (no-ops after a freeze excluded)
-            if (true_rel <= o.tol || restarts >= 4 || it >= o.max_iter) {
+            if (true_rel <= o.tol || restarts >= 8 || it >= o.max_iter) {
                 converged = true_rel <= o.tol;
                 break;
             }
@@ -780,10 +781,12 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             } else {
                 cudaMemcpyAsync(pv, r, 8ull * N, cudaMemcpyDeviceToDevice, s);
                 cg_restart(sc, 1, s);
-                if (cap) {   // a new Krylov space from the true residual
-                    cg_basis_append(Qb, r, N, sc, kSTmp, s);
-                    kb = 1;
-                }
+                // Projecting the residual out of the stored span also removes the
+                // part that the operator's rounding puts there, which the iterate
+                // never sees; that gap between the recurrence and the true
+                // residual is what a restart finds.  The restart closes it with
+                // plain CG, which keeps every component of the residual.
+                reo = false;
             }
         }
         if (rc) break;
