@@ -223,6 +223,35 @@ def test_mixed_forward_adjoint_vs_oracle(g, shape, cell, h, seed, adjoint_layout
         assert np.abs(a - Gk.T @ r).max() <= 1e-6 * np.abs(Gk.T @ r).max(), k
 
 
+@pytest.mark.parametrize("shape,cells", [((1, 1, 1), (20.0, 20.0, 20.0)), ((7, 1, 1), (20.0, 20.0, 20.0)),
+                                         ((1, 9, 3), (15.0, 15.0, 15.0)), ((23, 19, 1), (30.0, 30.0, 30.0)),
+                                         ((9, 11, 2), (25.0, 10.0, 40.0)), ((13, 12, 17), (20.0, 20.0, 20.0)),
+                                         ((64, 1, 5), (10.0, 30.0, 10.0))])
+def test_mixed_degenerate_meshes_and_far_stations(g, shape, cells, adjoint_layout):
+    """Mixed mode on one-cell-wide, single-layer and ragged-layer meshes (nz = 1,
+    2, 17 against the 16-layer adjoint groups), rectangular cells, and stations
+    both above the mesh and far outside its footprint (empty near windows):
+    forward and depth-weighted adjoint within 1e-5 of max against the oracle."""
+    nx, ny, nz = shape
+    a, b, c = cells
+    mesh = synth.uniform_mesh(nx, ny, nz, a, b, c)
+    rng = np.random.Generator(np.random.PCG64(160 + nx + 7 * ny + 31 * nz))
+    m = rng.normal(0.0, 100.0, mesh.ncells) + 50.0
+    n = 97
+    X, Y = nx * a, ny * b
+    far = np.stack([rng.uniform(-20 * X - 500, 21 * X + 500, 24), rng.uniform(-20 * Y - 500, 21 * Y + 500, 24)])
+    sv = synth.Survey(np.concatenate([rng.uniform(-a, X + a, n - 24), far[0]]),
+                      np.concatenate([rng.uniform(-b, Y + b, n - 24), far[1]]),
+                      -rng.uniform(0.5, 12.0, n))
+    S = g.Survey(sv.x, sv.y, sv.z)
+    G = oracle.G_explicit(mesh, sv)
+    d = g.forward(_dev(m), mesh, S, precision="mixed").cpu().numpy()
+    assert _rel(d, G @ m) <= TOLMIX
+    r = synth.random_vector(n, 161)
+    at = g.adjoint(_dev(r), mesh, S, depth_weighted=True, precision="mixed").cpu().numpy()
+    assert _rel(at, oracle.depth_w2(mesh, 50.0) * (G.T @ r)) <= TOLMIX
+
+
 def _mixed_definition(mesh, sv, G, cell, k):
     """Dense matrix of the mixed approximation: G_ik from the oracle when the
     cell centre lies within k cell widths of station i, else the point mass
