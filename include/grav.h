@@ -202,6 +202,20 @@ int grav_datainv_solve(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *
                        const double *d, const double *m_ref, double *m_out, double *y_out,
                        grav_solve_info *info, const grav_options *opt, grav_stream_t stream);
 
+/* grav_datainv_solve with two additions (the paper has no counterpart; they
+ * serve checkpoint / resume and convergence records):
+ *   y0: DEVICE, n doubles, or NULL — CG starts from y = y0 instead of 0, e.g.
+ *       the y_out of an earlier call that stopped at max_iter (resume); the
+ *       tolerance stays relative to ||d - G m_ref||.
+ *   res_hist: DEVICE, res_hist_len doubles, or NULL — the single CG solve
+ *       writes its recurrence relative residual after iteration k into
+ *       res_hist[k] (k < res_hist_len); unused entries are -1.
+ * GRAV_EINVAL for host pointers or res_hist_len < 1 with res_hist given. */
+int grav_datainv_solve_ex(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey,
+                          const double *d, const double *m_ref, double *m_out, double *y_out,
+                          grav_solve_info *info, const grav_options *opt, grav_stream_t stream,
+                          const double *y0, double *res_hist, int res_hist_len);
+
 /* ---- reusable plans ------------------------------------------------------- */
 /* A plan holds one (mesh, survey, options) problem resident on the device:
  * the mesh edges, the station arrays' derived forms, the operator scratch and,

@@ -118,6 +118,9 @@ _sig("grav_job_times", _i, [_vp, ctypes.c_uint64, _D, _D, _D])
 _sig("grav_job_release", _i, [_vp, ctypes.c_uint64])
 _sig("grav_eval_fn64", _i, [_vp, _i, _vp, _vp, _vp, ctypes.c_int64, _vp])
 _sig("grav_plan_check_fp64", _i, [_vp, _vp, _vp, _i, _D, _D, _vp])
+_sig("grav_datainv_solve_ex", _i, [_vp, ctypes.POINTER(grav_mesh), ctypes.POINTER(grav_survey), _vp, _vp, _vp,
+                                   _vp, ctypes.POINTER(grav_solve_info), ctypes.POINTER(grav_options), _vp,
+                                   _vp, _vp, _i])
 
 EXPORTED = [
     "grav_options_default", "grav_version", "grav_ctx_create", "grav_ctx_destroy", "grav_last_error",
@@ -125,7 +128,7 @@ EXPORTED = [
     "grav_plan_forward", "grav_plan_adjoint", "grav_plan_bytes", "grav_plan_destroy",
     "grav_launch_count", "grav_plan_timing", "grav_bench_pipes", "grav_plan_describe",
     "grav_serve_config", "grav_submit", "grav_poll", "grav_wait", "grav_cancel", "grav_job_times",
-    "grav_job_release", "grav_eval_fn64", "grav_plan_check_fp64",
+    "grav_job_release", "grav_eval_fn64", "grav_plan_check_fp64", "grav_datainv_solve_ex",
 ]
 
 STAGES = ("fwd_main", "adj_main", "fwd_near", "adj_near")
@@ -382,25 +385,36 @@ def diag(mesh, survey, stream=None, ctx: Optional[Context] = None, **opts):
     return out, tr.value
 
 
-def datainv(d, mesh, survey, m_ref=None, return_y=False, stream=None, ctx: Optional[Context] = None, **opts):
-    """Data-space inversion (Eq. 10-11) by CG.  Returns (m, info) or (m, y, info)."""
+def datainv(d, mesh, survey, m_ref=None, return_y=False, stream=None, ctx: Optional[Context] = None, y0=None,
+            res_hist=False, **opts):
+    """Data-space inversion (Eq. 10-11) by CG.  Returns (m, info) or (m, y, info).
+    y0: start CG from this y (e.g. an earlier call's y; resume).  res_hist:
+    info["res_hist"] holds the recurrence relative residual per iteration."""
     torch = _torch()
     ctx = ctx or context()
     mesh, survey = Mesh.of(mesh), Survey.of(survey)
     d = _f64(d, survey.n, "d")
     mr = _f64(m_ref, mesh.ncells, "m_ref") if m_ref is not None else None
+    yi = _f64(y0, survey.n, "y0") if y0 is not None else None
     m = torch.empty(mesh.ncells, dtype=torch.float64, device=d.device)
     y = torch.empty(survey.n, dtype=torch.float64, device=d.device) if return_y else None
     info = grav_solve_info()
     o = options(**opts)
-    rc = ctx.check(_lib.grav_datainv_solve(ctx.h, ctypes.byref(mesh.c), ctypes.byref(survey.c), d.data_ptr(),
-                                           mr.data_ptr() if mr is not None else None, m.data_ptr(),
-                                           y.data_ptr() if y is not None else None, ctypes.byref(info),
-                                           ctypes.byref(o), _stream(stream)))
+    hist = torch.empty(max(1, o.max_iter), dtype=torch.float64, device=d.device) if res_hist else None
+    rc = ctx.check(_lib.grav_datainv_solve_ex(ctx.h, ctypes.byref(mesh.c), ctypes.byref(survey.c), d.data_ptr(),
+                                              mr.data_ptr() if mr is not None else None, m.data_ptr(),
+                                              y.data_ptr() if y is not None else None, ctypes.byref(info),
+                                              ctypes.byref(o), _stream(stream),
+                                              yi.data_ptr() if yi is not None else None,
+                                              hist.data_ptr() if hist is not None else None,
+                                              hist.numel() if hist is not None else 0))
     inf = {"iters": info.iters, "converged": bool(info.converged), "rel_res": info.rel_res,
            "true_rel_res": info.true_rel_res, "lambda": info.lambda_, "trace": info.trace,
            "seconds": info.seconds, "status": rc, "outer": info.outer, "alpha_min": info.alpha_min,
            "restarts": info.restarts, "fp64_rel_err": info.fp64_rel_err}
+    if hist is not None:
+        h = hist.cpu().numpy()
+        inf["res_hist"] = h[h >= 0]
     return (m, y, inf) if return_y else (m, inf)
 
 

@@ -220,6 +220,7 @@ size_t fp64_bytes(const grav_plan *p) {
 
 int plan_forward_ex(grav_plan *p, const double *m, double *d, const double *add, double add_scale,
                     cudaStream_t s) {
+    NvtxRange nv("grav::forward");
     if (p->cached) {
         launch_cached_fwd(p, m, add, add_scale, d, s);
     } else if (p->opt.precision == GRAV_FP64) {
@@ -242,6 +243,7 @@ int plan_forward_ex(grav_plan *p, const double *m, double *d, const double *add,
 
 int plan_adjoint_ex(grav_plan *p, const double *r, double *out, int depth_weighted, const double *add,
                     cudaStream_t s) {
+    NvtxRange nv("grav::adjoint");
     if (p->opt.precision == GRAV_MIXED_CORNER)
         return set_error(p->ctx, GRAV_EINVAL, "GRAV_MIXED_CORNER provides the forward product only");
     if (p->cached) {
@@ -258,6 +260,7 @@ int plan_adjoint_ex(grav_plan *p, const double *r, double *out, int depth_weight
 }
 
 int plan_diag(grav_plan *p, double *diag, cudaStream_t s) {
+    NvtxRange nv("grav::diag");
     if (p->opt.precision == GRAV_MIXED_CORNER)
         return set_error(p->ctx, GRAV_EINVAL, "GRAV_MIXED_CORNER provides the forward product only");
     if (p->cached) launch_cached_diag(p, diag, s);
@@ -464,6 +467,7 @@ int check_fp64(grav_plan *p, const double *m, const double *d, int n_check, doub
 
 int plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const grav_options &o,
                 grav_plan **out, cudaStream_t s) {
+    NvtxRange nv("grav::plan_create");
     grav_plan *p = nullptr;
     int rc = plan_prepare(ctx, mesh, survey, o, &p);
     if (rc) return rc;
@@ -518,7 +522,9 @@ int read_status(grav_ctx *ctx, cudaStream_t s, double timeout_s) {
 // Data-space CG: A = G W^-2 G^T + lambda I, y0 = 0, r0 = dd.
 // ---------------------------------------------------------------------------
 int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_out, double *y_out,
-                  grav_solve_info *info, cudaStream_t s, const std::atomic<int> *cancel) {
+                  grav_solve_info *info, cudaStream_t s, const std::atomic<int> *cancel, const double *y0,
+                  double *hist, int hist_len) {
+    NvtxRange nv("grav::solve");
     grav_ctx *ctx = p->ctx;
     const grav_options &o = p->opt;
     const double t0 = now_s();
@@ -564,6 +570,7 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
         cudaEventRecord(ev, s);
         return wait_event(ctx, ev, o.timeout_s, what);
     };
+    if (hist && hist_len > 0) vec_fill(hist, hist_len, -1.0, s);
     do {
         cudaMemsetAsync(sc, 0, 8 * kSCount, s);
         // dd = d - G m_ref
@@ -622,7 +629,8 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             //   d - G m = e0 + alpha e1, e0 = r + lam y, e1 = lam dy - A dy
             //   (m - m_ref)^T W_m^-1 (m - m_ref) = (y + alpha dy)^T (f0 + alpha f1),
             //   f0 = A y - lam y, f1 = A dy - lam dy.
-            vec_fill(yo, N, 0.0, s);
+            if (y0) cudaMemcpyAsync(yo, y0, 8ull * N, cudaMemcpyDeviceToDevice, s);
+            else vec_fill(yo, N, 0.0, s);
             launch_dot(dd, dd, N, dp, sc + kSTmp, s);
             if ((rc = sync_scalars("outer start"))) break;
             const double bb0 = hsc[kSTmp];
@@ -692,19 +700,29 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             iters = total_it;
             converged = true_rel <= o.tol;
         } else {
-        cudaMemcpyAsync(r, dd, 8ull * N, cudaMemcpyDeviceToDevice, s);
-        vec_fill(y, N, 0.0, s);
+        // start: y = y0 (or 0), r = dd - A y; convergence is relative to ||dd||
+        if (y0) {
+            cudaMemcpyAsync(y, y0, 8ull * N, cudaMemcpyDeviceToDevice, s);
+            if ((rc = plan_adjoint_ex(p, y, q, 1, nullptr, s))) break;
+            if ((rc = plan_forward_ex(p, q, Ap, y, lam, s))) break;
+            vec_axpby(1.0, dd, -1.0, Ap, N, r, s);
+        } else {
+            cudaMemcpyAsync(r, dd, 8ull * N, cudaMemcpyDeviceToDevice, s);
+            vec_fill(y, N, 0.0, s);
+        }
+        launch_dot(dd, dd, N, dp, sc + kSBB0, s);
         if (pc) {
             vec_mul(dinv, r, N, zv, s);
             cudaMemcpyAsync(pv, zv, 8ull * N, cudaMemcpyDeviceToDevice, s);
             launch_dot(r, zv, N, dp, sc + kSRR, s);
-            launch_dot(r, r, N, dp, sc + kSTmp, s);
-            cg_set_scalars(sc, o.tol * o.tol, kSTmp, s);
         } else {
-            cudaMemcpyAsync(pv, dd, 8ull * N, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(pv, r, 8ull * N, cudaMemcpyDeviceToDevice, s);
             launch_dot(r, r, N, dp, sc + kSRR, s);
-            cg_set_scalars(sc, o.tol * o.tol, kSRR, s);
         }
+        cg_set_scalars(sc, o.tol * o.tol, kSBB0, s);
+        // an iterate that already meets tol needs no iteration
+        launch_dot(r, r, N, dp, sc + kSTmp, s);
+        cg_restart(sc, 0, s);
         int kb = 0;            // basis vectors stored (reorthogonalised CG)
         bool reo = cap > 0;    // reorthogonalise (first pass only; restarts run plain CG)
         if (reo) {
@@ -734,12 +752,12 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
                         vec_mul(dinv, r, N, zv, s);
                         launch_dot(r, zv, N, dp, sc + kSRRNew, s);
                         launch_dot(r, r, N, dp, sc + kSResNew, s);
-                        cg_beta(sc, it, kSResNew, s);
+                        cg_beta(sc, it, kSResNew, s, hist, hist_len);
                         cg_update_p(pv, zv, N, sc, s);
                     } else {
                         if (reo) cg_reorth(Qb, kb, N, r, cb, sc, s);
                         launch_dot(r, r, N, dp, sc + kSRRNew, s);
-                        cg_beta(sc, it, kSRRNew, s);
+                        cg_beta(sc, it, kSRRNew, s, hist, hist_len);
                         if (reo && kb < cap) {
                             cg_basis_append(Qb + (size_t)kb * N, r, N, sc, kSRRNew, s);
                             ++kb;
@@ -1123,6 +1141,13 @@ int grav_diag(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, d
 int grav_datainv_solve(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const double *d,
                        const double *m_ref, double *m_out, double *y_out, grav_solve_info *info,
                        const grav_options *opt, grav_stream_t stream) {
+    return grav_datainv_solve_ex(ctx, mesh, survey, d, m_ref, m_out, y_out, info, opt, stream, nullptr, nullptr, 0);
+}
+
+int grav_datainv_solve_ex(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const double *d,
+                          const double *m_ref, double *m_out, double *y_out, grav_solve_info *info,
+                          const grav_options *opt, grav_stream_t stream, const double *y0, double *res_hist,
+                          int res_hist_len) {
     if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
     DeviceGuard g(ctx->device);
     int e0 = empty_survey(ctx, mesh, survey, opt);
@@ -1141,14 +1166,18 @@ int grav_datainv_solve(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *
         return e == cudaSuccess ? GRAV_OK : cuda_error(ctx, e, "inversion of an empty survey");
     }
     if (!is_device_ptr(d, ctx->device) || !is_device_ptr(m_out, ctx->device) ||
-        (m_ref && !is_device_ptr(m_ref, ctx->device)) || (y_out && !is_device_ptr(y_out, ctx->device)))
-        return set_error(ctx, GRAV_EINVAL, "d, m_out (and m_ref, y_out when given) must be device pointers");
+        (m_ref && !is_device_ptr(m_ref, ctx->device)) || (y_out && !is_device_ptr(y_out, ctx->device)) ||
+        (y0 && !is_device_ptr(y0, ctx->device)) || (res_hist && !is_device_ptr(res_hist, ctx->device)))
+        return set_error(ctx, GRAV_EINVAL,
+                         "d, m_out (and m_ref, y_out, y0, res_hist when given) must be device pointers");
+    if (res_hist_len < 0 || (res_hist && res_hist_len == 0))
+        return set_error(ctx, GRAV_EINVAL, "res_hist_len must be >= 1 when res_hist is given");
     if (info) std::memset(info, 0, sizeof(*info));
     const cudaStream_t s = (cudaStream_t)stream;
     grav_plan *p = nullptr;
     int rc = plan_create(ctx, mesh, survey, resolve(opt), &p, s);
     if (rc) return rc;
-    rc = solve_on_plan(p, d, m_ref, m_out, y_out, info, s, nullptr);
+    rc = solve_on_plan(p, d, m_ref, m_out, y_out, info, s, nullptr, y0, res_hist, res_hist ? res_hist_len : 0);
     plan_destroy(p, s);
     return rc;
 }

@@ -20,13 +20,15 @@ enum CgScalar : int {
     kSTmp = 10,
     kSResNew = 11, // r.r after the update (convergence test of the preconditioned CG)
     kSPhi = 12,    // 7 slots: dot products of the outer loop's line search
+    kSBB0 = 19,    // dd.dd when CG starts from a given y0
     kSCount = 24
 };
 
 void cg_alpha(double *sc, cudaStream_t s);
 void cg_update_yr(double *y, double *r, const double *p, const double *Ap, int64_t n, const double *sc,
                   cudaStream_t s);
-void cg_beta(double *sc, int it, int conv_slot, cudaStream_t s);
+// hist (may be null): hist[it] = sqrt(sc[conv_slot] / sc[kSBB]) for it < hist_len
+void cg_beta(double *sc, int it, int conv_slot, cudaStream_t s, double *hist = nullptr, int hist_len = 0);
 void cg_update_p(double *p, const double *r, int64_t n, const double *sc, cudaStream_t s);
 void vec_axpby(double a, const double *x, double b, const double *y, int64_t n, double *out, cudaStream_t s);
 void vec_fill(double *x, int64_t n, double v, cudaStream_t s);

@@ -56,7 +56,7 @@ __global__ void k_cg_update_yr(double *__restrict__ y, double *__restrict__ r, c
 
 // beta = rz_new / rz (rz = r.z, z = M^-1 r; z = r without preconditioner);
 // convergence on the residual norm held in conv_slot.
-__global__ void k_cg_beta(double *__restrict__ sc, int it, int conv_slot) {
+__global__ void k_cg_beta(double *__restrict__ sc, int it, int conv_slot, double *__restrict__ hist, int hist_len) {
     if (sc[kSFrozen] != 0.0) {
         sc[kSBeta] = 0.0;
         return;
@@ -65,6 +65,7 @@ __global__ void k_cg_beta(double *__restrict__ sc, int it, int conv_slot) {
     sc[kSBeta] = rz_new / sc[kSRR];
     sc[kSRR] = rz_new;
     sc[kSIters] = (double)(it + 1);
+    if (hist && it < hist_len) hist[it] = sqrt(sc[conv_slot] / sc[kSBB]);
     if (sc[conv_slot] <= sc[kSTol2] * sc[kSBB]) sc[kSFrozen] = 1.0;
 }
 
@@ -174,8 +175,8 @@ void cg_update_yr(double *y, double *r, const double *p, const double *Ap, int64
                   cudaStream_t s) {
     k_cg_update_yr<<<vgrid(n), 256, 0, s>>>(y, r, p, Ap, n, sc); note_launches(1);
 }
-void cg_beta(double *sc, int it, int conv_slot, cudaStream_t s) {
-    k_cg_beta<<<1, 1, 0, s>>>(sc, it, conv_slot); note_launches(1);
+void cg_beta(double *sc, int it, int conv_slot, cudaStream_t s, double *hist, int hist_len) {
+    k_cg_beta<<<1, 1, 0, s>>>(sc, it, conv_slot, hist, hist_len); note_launches(1);
 }
 void cg_update_p(double *p, const double *r, int64_t n, const double *sc, cudaStream_t s) {
     k_cg_update_p<<<vgrid(n), 256, 0, s>>>(p, r, n, sc); note_launches(1);

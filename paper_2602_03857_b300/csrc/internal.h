@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "grav.h"
 
 namespace grav {
@@ -169,8 +171,11 @@ int plan_adjoint_ex(grav_plan *p, const double *r, double *out, int depth_weight
                     cudaStream_t s);
 int plan_diag(grav_plan *p, double *diag, cudaStream_t s);
 int read_status(grav_ctx *ctx, cudaStream_t s, double timeout_s);
+// y0 (may be null): CG starts from y = y0; hist (may be null): the recurrence
+// relative residual after each iteration, hist_len entries (-1 when unused).
 int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_out, double *y_out,
-                  grav_solve_info *info, cudaStream_t s, const std::atomic<int> *cancel);
+                  grav_solve_info *info, cudaStream_t s, const std::atomic<int> *cancel,
+                  const double *y0 = nullptr, double *hist = nullptr, int hist_len = 0);
 
 // serving scheduler (serve.cpp)
 void serve_shutdown(grav_ctx *ctx);
@@ -219,6 +224,14 @@ void launch_gather_check(const double *sx, const double *sy, const double *sz, c
                          int n_check, double *ox, double *oy, double *oz, double *od, cudaStream_t s);
 int check_fp64(grav_plan *p, const double *m, const double *d, int n_check, double *max_abs, double *rel,
                cudaStream_t s);
+// Host-side NVTX range around a library stage (visible in Nsight timelines and
+// usable as an ncu --nvtx filter); costs nothing without a tool attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 // Device view of a plan's mesh, stations and function table.
 Geo make_geo(const grav_plan *p);
 // Host: fills the kFnTableSize-double table of the FP64 log / atan (long-double

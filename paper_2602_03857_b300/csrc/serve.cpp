@@ -76,6 +76,7 @@ bool head_admissible(Scheduler *s) {
 }
 
 void run_job(Scheduler *s, Job *job, cudaStream_t stream) {
+    NvtxRange nv(job->desc.kind == GRAV_JOB_FORWARD ? "grav::job_forward" : "grav::job_invert");
     grav_ctx *ctx = s->ctx;
     const grav_job &d = job->desc;
     grav_mesh mesh = d.mesh;

@@ -617,3 +617,30 @@ def test_reorthogonalised_cg(g, prec):
         assert np.linalg.norm(y - ref["y"]) <= 1.01 * res / ref["lam"]
         its[reorth] = info["iters"]
     assert its[1000] < its[0], its
+
+
+def test_resume_from_y0_and_residual_history(g):
+    """grav_datainv_solve_ex: a solve stopped at max_iter resumes from its y
+    (checkpoint/resume) and reaches the same minimiser; a converged y needs no
+    iteration; res_hist records the recurrence residual of every iteration."""
+    wl = synth.make_workload("block_20x20x10")
+    G = oracle.G_explicit(wl.mesh, wl.survey)
+    d = synth.add_noise(G @ wl.m, wl.noise_abs, wl.noise_rel, 3)
+    ref = oracle.invert_dense(wl.mesh, wl.survey, d, z0=50.0)
+    A = (G * ref["wm"]) @ G.T + ref["lam"] * np.eye(len(d))
+    S = g.Survey(wl.survey.x, wl.survey.y, wl.survey.z)
+    dd = _dev(d)
+    m1, y1, info1 = g.datainv(dd, wl.mesh, S, tol=1e-8, max_iter=15, return_y=True, res_hist=True)
+    assert info1["status"] == g.GRAV_ENOTCONVERGED and info1["iters"] == 15
+    h = info1["res_hist"]
+    assert len(h) == 15 and h[-1] < h[0]
+    m2, y2, info2 = g.datainv(dd, wl.mesh, S, tol=1e-8, max_iter=2000, return_y=True, y0=y1, res_hist=True)
+    assert info2["converged"]
+    y2n = y2.cpu().numpy()
+    res = np.linalg.norm(d - A @ y2n)
+    assert res <= 1.5e-8 * np.linalg.norm(d)
+    assert np.linalg.norm(y2n - ref["y"]) <= 1.01 * res / ref["lam"]
+    assert abs(info2["res_hist"][-1] - info2["rel_res"]) <= 1e-12 + 1e-6 * info2["rel_res"]
+    m3, info3 = g.datainv(dd, wl.mesh, S, tol=1e-6, max_iter=100, y0=y2)
+    assert info3["converged"] and info3["iters"] == 0
+    assert torch.allclose(m3, m2, rtol=0, atol=1e-9 * float(m2.abs().max()))
