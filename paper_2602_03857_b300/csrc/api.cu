@@ -229,6 +229,7 @@ int plan_forward_ex(grav_plan *p, const double *m, double *d, const double *add,
         launch_reduce_rows(p->part, p->f64_nchunk, p->N, kGammaMgal, add, add_scale, nullptr, d, s);
     } else if (p->opt.precision == GRAV_MIXED_CORNER) {
         launch_corner_fwd(p, m, s);
+        launch_mixed_prep_q(p, m, s);   // the near field reads q
         launch_mixed_near_fwd(p, m, s);
         launch_reduce_rows(p->cr_part, p->cr_nchunk, p->N, kGammaMgal, add, add_scale, p->near_corr, d, s);
     } else {

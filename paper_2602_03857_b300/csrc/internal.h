@@ -127,6 +127,7 @@ struct grav_plan {
     grav::NearGeo ng{};
     float *m_cx = nullptr, *m_cy = nullptr, *m_czc = nullptr;
     float *qT = nullptr;                  // [ncol][nzp] gamma*1e5*V*rho (FP32)
+    float *qN = nullptr;                  // [M] the same values in natural cell order (near field)
     float *m_w2f = nullptr;               // [nzp] (zc + z0)^2 in FP32
     float4 *st32 = nullptr;               // stations (xh, xl, yh, yl)
     float2 *stz = nullptr;                // stations (z, r)
@@ -135,7 +136,7 @@ struct grav_plan {
     int m_adj_bc = 0;                     // 1: broadcast adjoint layout (large meshes), 0: lanes split stations
     double *m_part = nullptr;             // [nchunk][N] forward partials (hi+lo in FP64)
     double *m_apart = nullptr;            // [nschunk][M] adjoint partials
-    double *dG = nullptr;                 // [N][slots] near-field correction (mGal per kg/m^3)
+    float *dG = nullptr;                  // [N][slots] near-field correction (mGal per kg/m^3), formed in FP64
     int *st_i0 = nullptr, *st_j0 = nullptr;   // box origin per station
     double *diag_corr = nullptr;          // [N] near-field correction of diag(G W^-2 G^T)
     int *bin_start = nullptr;             // [nbins+1]

@@ -88,6 +88,12 @@ __global__ void k_prep_q(MixedGeo g, const double *__restrict__ m, float scale, 
     }
 }
 
+// the same FP32 q in the cells' natural order (coalesced gathers of the near field)
+__global__ void k_prep_qn(int64_t M, const double *__restrict__ m, float scale, float *__restrict__ qn) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M; k += (int64_t)gridDim.x * blockDim.x)
+        qn[k] = (float)(scale * m[k]);
+}
+
 // stations: st32 = (xh, xl, yh, yl) of (x - xref, y - yref); stz = (z, r)
 __global__ void k_prep_stations(const double *__restrict__ x, const double *__restrict__ y,
                                 const double *__restrict__ z, int64_t n, double xref, double yref,
@@ -635,7 +641,7 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
     Geo g, MixedGeo mg, NearGeo ng, double x0, double y0, double a, double b, double vol_mgal,
     const double *__restrict__ sx, const double *__restrict__ sy, const double *__restrict__ sz,
     const double *__restrict__ w2, const float4 *__restrict__ st32, const float2 *__restrict__ stz,
-    double *__restrict__ dG, int *__restrict__ st_i0, int *__restrict__ st_j0, double *__restrict__ diag_corr,
+    float *__restrict__ dG, int *__restrict__ st_i0, int *__restrict__ st_j0, double *__restrict__ diag_corr,
     unsigned *__restrict__ keys, int *__restrict__ vals, unsigned key_sentinel) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -726,7 +732,9 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
                 dcorr += w2[l] * (gex * gex - gfar * gfar);
             }
         }
-        dG[s * ng.slots + t] = val;
+        // formed in FP64, stored in FP32 per unit q = gamma V rho (so the products
+        // use the FP32 q of the far field); relative rounding 6e-8
+        dG[s * ng.slots + t] = (float)(val / vol_mgal);
     }
     dcorr = warp_sum(dcorr);
     if (lane == 0) {
@@ -751,24 +759,64 @@ __global__ void k_bin_bounds(const unsigned *__restrict__ ks, int64_t n, int nbi
     }
 }
 
-// corr[s] = sum_slots dG[s][slot] * m[cell(s, slot)]   (warp per station)
-__global__ void k_near_fwd(int nx, int ny, int nz, NearGeo ng, int64_t N, const double *__restrict__ dG,
-                           const int *__restrict__ st_i0, const int *__restrict__ st_j0,
-                           const double *__restrict__ m, double *__restrict__ corr) {
+// corr[s] = sum_slots dGq[s][slot] * q[cell(s, slot)]   (warp per station),
+// q = gamma V rho in FP32 (the far field's values, in natural cell order).  Slot
+// t = a + bx (bj + by l); each lane walks t = lane, lane + 32, ... with
+// (a, bj, l) stepped incrementally (no divisions in the loop), four slots per
+// step so that their loads are independent.  Products and runs of 16 terms
+// are FP32 (FMA pipe), folded into an FP64 sum: the FP64 pipe (1/64 of the
+// FP32 rate on this GPU) does one addition per 16 terms instead of one FMA
+// per term.
+__global__ void __launch_bounds__(256) k_near_fwd(int nx, int ny, int nz, NearGeo ng, int64_t N,
+                                                  const float *__restrict__ dG, const int *__restrict__ st_i0,
+                                                  const int *__restrict__ st_j0, const float *__restrict__ qn,
+                                                  double *__restrict__ corr) {
     const int lane = threadIdx.x & 31;
     const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (s >= N) return;
     const int i0 = st_i0[s], j0 = st_j0[s];
+    const float *gs = dG + s * ng.slots;
+    const int qa = 32 % ng.bx, qr = 32 / ng.bx;
+    int a = lane % ng.bx;
+    const int r0 = lane / ng.bx;
+    int bj = r0 % ng.by, l = r0 / ng.by;
+    auto step = [&](int &a_, int &bj_, int &l_) {
+        a_ += qa;
+        int carry = qr;
+        if (a_ >= ng.bx) {
+            a_ -= ng.bx;
+            ++carry;
+        }
+        bj_ += carry;
+        while (bj_ >= ng.by) {
+            bj_ -= ng.by;
+            ++l_;
+        }
+    };
     double acc = 0.0;
-    for (int t = lane; t < ng.slots; t += 32) {
-        const int i = i0 + t % ng.bx;
-        const int j = j0 + (t / ng.bx) % ng.by;
-        const int l = t / (ng.bx * ng.by);
-        if (i >= 0 && i < nx && j >= 0 && j < ny && l < nz)
-            acc = fma(dG[s * ng.slots + t], m[i + (int64_t)nx * (j + (int64_t)ny * l)], acc);
+    float accf = 0.0f;
+    int run = 0;
+    for (int t = lane; t < ng.slots; t += 128) {
+        float g[4], q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + a, j = j0 + bj;
+            const bool ok = t + 32 * u < ng.slots && i >= 0 && i < nx && j >= 0 && j < ny && l < nz;
+            g[u] = ok ? gs[t + 32 * u] : 0.0f;
+            q[u] = ok ? qn[i + (int64_t)nx * (j + (int64_t)ny * l)] : 0.0f;
+            step(a, bj, l);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) accf = fmaf(g[u], q[u], accf);
+        if (++run == 4) {   // fold every 16 terms
+            acc += (double)accf;
+            accf = 0.0f;
+            run = 0;
+        }
     }
-    acc = warp_sum(acc);
-    if (lane == 0) corr[s] = acc;
+    acc += (double)accf;
+    const double v = warp_sum(acc);
+    if (lane == 0) corr[s] = v;
 }
 
 // out[k] = sum over stations whose window box holds cell k of dG * r, for the
@@ -777,11 +825,11 @@ __global__ void k_near_fwd(int nx, int ny, int nz, NearGeo ng, int64_t N, const 
 // y-by+1 .. y, and within one bin row the bins of the 32 columns are
 // consecutive keys, i.e. one contiguous range of the sorted station list.  For
 // each such station the lanes read one box row of dG (consecutive slots:
-// coalesced).  Per cell the stations are visited in (bin row, bin, station)
-// order: deterministic.
-__global__ void __launch_bounds__(256) k_near_adj(int nx, int ny, NearGeo ng, const double *__restrict__ dG,
+// coalesced).  Stations are fetched eight at a time (independent loads) and
+// accumulated in (bin row, bin, station) order: deterministic.
+__global__ void __launch_bounds__(256, 4) k_near_adj(int nx, int ny, NearGeo ng, const float *__restrict__ dG,
                                                   const int *__restrict__ bin_start, const int *__restrict__ bin_st,
-                                                  const int *__restrict__ st_i0, const double *__restrict__ r,
+                                                  const int *__restrict__ st_i0, const float2 *__restrict__ stz,
                                                   double *__restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
@@ -789,6 +837,7 @@ __global__ void __launch_bounds__(256) k_near_adj(int nx, int ny, NearGeo ng, co
     if (y >= ny) return;   // warp-uniform
     const int tx0 = blockIdx.x * 32;
     const int x = tx0 + lane;
+    const bool xin = x < nx;
     // shifted bin coordinates: sbi = i0 + bx - 1, sbj = j0 + by - 1
     const int sbi_lo = tx0;
     const int sbi_hi = min(ng.nbx - 1, tx0 + 31 + ng.bx - 1);
@@ -798,16 +847,30 @@ __global__ void __launch_bounds__(256) k_near_adj(int nx, int ny, NearGeo ng, co
         const int p0 = bin_start[sbi_lo + ng.nbx * sbj];
         const int p1 = bin_start[sbi_hi + ng.nbx * sbj + 1];
         const int64_t row = (int64_t)ng.bx * (b + (int64_t)ng.by * l);
-        for (int p = p0; p < p1; ++p) {
-            const int s = bin_st[p];
-            const int a = x - st_i0[s];
-            if (a >= 0 && a < ng.bx && x < nx) acc = fma(dG[(int64_t)s * ng.slots + row + a], r[s], acc);
+        // runs of up to 8 stations in FP32 (r as the FP32 copy in stz.y), folded
+        // into FP64; the run's loads are issued together (independent)
+        for (int p = p0; p < p1; p += 8) {
+            int sv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sv[u] = (p + u < p1) ? bin_st[p + u] : -1;
+            float g[8], rv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int a = sv[u] >= 0 ? x - st_i0[sv[u]] : -1;
+                const bool ok = a >= 0 && a < ng.bx && xin;
+                g[u] = ok ? dG[(int64_t)sv[u] * ng.slots + row + a] : 0.0f;
+                rv[u] = ok ? stz[sv[u]].y : 0.0f;
+            }
+            float accf = 0.0f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) accf = fmaf(g[u], rv[u], accf);
+            acc += (double)accf;
         }
     }
-    if (x < nx) out[x + (int64_t)nx * (y + (int64_t)ny * l)] = acc;
+    if (xin) out[x + (int64_t)nx * (y + (int64_t)ny * l)] = acc;
 }
 
-// out[k] = (vol * sum_c apart[c][k] + near[k] (top bz layers)) [* w2_l] [+ add[k]]
+// out[k] = vol * (sum_c apart[c][k] + near[k] (top bz layers)) [* w2_l] [+ add[k]]
 __global__ void k_madj_finish(int nx, int ny, int nz, int bz, const double *__restrict__ apart, int nschunk,
                               double vol, const double *__restrict__ near, const double *__restrict__ w2,
                               const double *__restrict__ add, double *__restrict__ out) {
@@ -817,8 +880,8 @@ __global__ void k_madj_finish(int nx, int ny, int nz, int bz, const double *__re
         const int l = (int)(k / plane);
         double s = 0.0;
         for (int c = 0; c < nschunk; ++c) s += apart[(int64_t)c * M + k];
-        s *= vol;
         if (l < bz) s += near[k];
+        s *= vol;
         if (w2) s *= w2[l];
         if (add) s += add[k];
         out[k] = s;
@@ -1005,10 +1068,11 @@ size_t mixed_scratch_bytes(const grav_plan *p) {
     auto add = [&](size_t v) { b += (v + 255) / 256 * 256 + 256; };
     add(8ull * p->nx); add(8ull * p->ny); add(4ull * nzp); add(4ull * nzp);   // cx, cy, czc, w2f
     add(4ull * p->nx * p->ny * nzp);                                       // qT
+    add(4ull * M);                                                          // qN
     add(16ull * (N + 2)); add(8ull * (N + 4));                             // st32, stz (padded)
     add(8ull * z.nchunk * N);                                               // m_part
     add(8ull * z.nschunk * M);                                              // m_apart
-    add(8ull * N * p->ng.slots);                                            // dG
+    add(4ull * N * p->ng.slots);                                            // dG (FP32)
     add(4ull * N); add(4ull * N);                                           // i0, j0
     add(8ull * N); add(8ull * N);                                           // diag_corr, near_corr
     add(8ull * p->nx * p->ny * lz);                                         // near adjoint
@@ -1070,6 +1134,7 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
     p->m_czc = (float *)take(p, 4ull * nzp);
     float *w2f = (float *)take(p, 4ull * nzp);
     p->qT = (float *)take(p, 4ull * nx * ny * nzp);
+    p->qN = (float *)take(p, 4ull * p->M);
     p->st32 = (float4 *)take(p, 16ull * (p->N + 2));
     p->stz = (float2 *)take(p, 8ull * (p->N + 4));
     p->m_fwd_cols_per_chunk = z.cols_per_chunk;
@@ -1081,7 +1146,7 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
     p->m_adj_bc = z.bc;
     p->m_part = (double *)take(p, 8ull * z.nchunk * p->N);
     p->m_apart = (double *)take(p, 8ull * z.nschunk * p->M);
-    p->dG = (double *)take(p, 8ull * p->N * p->ng.slots);
+    p->dG = (float *)take(p, 4ull * p->N * p->ng.slots);
     p->st_i0 = (int *)take(p, 4ull * p->N);
     p->st_j0 = (int *)take(p, 4ull * p->N);
     p->diag_corr = (double *)take(p, 8ull * p->N);
@@ -1172,7 +1237,8 @@ void launch_mixed_prep_q(const grav_plan *p, const double *m, cudaStream_t s) {
     const float scale = (float)(kGammaMgal * p->cell_a * p->cell_b * p->cell_c);
     const int64_t total = (int64_t)p->mg.ncol * p->mg.nzp;
     k_prep_q<<<grid_for(total, 256), 256, 0, s>>>(p->mg, m, scale, p->qT);
-    note_launches(1);
+    k_prep_qn<<<grid_for(p->M, 256), 256, 0, s>>>(p->M, m, scale, p->qN);
+    note_launches(2);
 }
 
 void launch_mixed_fwd(const grav_plan *p, cudaStream_t s) {
@@ -1207,8 +1273,9 @@ void launch_corner_fwd(const grav_plan *p, const double *m, cudaStream_t s) {
 void launch_mixed_near_fwd(const grav_plan *p, const double *m, cudaStream_t s) {
     const int64_t threads = p->N * 32;
     stage_begin(p, kStageFwdNear, s);
-    k_near_fwd<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(p->nx, p->ny, p->nz, p->ng, p->N, p->dG, p->st_i0,
-                                                                p->st_j0, m, p->near_corr);
+    (void)m;   // the near field reads the FP32 q that launch_mixed_prep_q formed from m
+    k_near_fwd<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(p->nx, p->ny, p->nz, p->ng, p->N, p->dG,
+                                                                p->st_i0, p->st_j0, p->qN, p->near_corr);
     stage_end(p, kStageFwdNear, s);
     note_launches(1);
 }
@@ -1269,7 +1336,7 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
     const int lz = std::min(p->ng.bz, p->nz);
     stage_begin(p, kStageAdjNear, s);
     dim3 gna((unsigned)((p->nx + 31) / 32), (unsigned)((p->ny + 7) / 8), (unsigned)lz);
-    k_near_adj<<<gna, 256, 0, s>>>(p->nx, p->ny, p->ng, p->dG, p->bin_start, p->bin_st, p->st_i0, r,
+    k_near_adj<<<gna, 256, 0, s>>>(p->nx, p->ny, p->ng, p->dG, p->bin_start, p->bin_st, p->st_i0, p->stz,
                                    p->m_cellacc);
     stage_end(p, kStageAdjNear, s);
     note_launches(2);
