@@ -350,6 +350,15 @@ int grav_plan_timing(grav_plan *plan, int enable, double *ms, int64_t *counts);
  * out: HOST, >= 23 doubles.  Per-clock rates per SM: rate / (MHz*1e6 * out[10]). */
 int grav_bench_pipes(int device, double *out);
 
+/* Self-check of the device-side failure path (the paper has no counterpart):
+ * launches one kernel whose bounded mbarrier wait cannot complete (nothing
+ * arrives), so it gives up after limit_ms (0 < limit_ms <= 1000), records the
+ * timeout bit in the context's status word and returns; the call then reads
+ * and clears the status word like every synchronising call.  Expected result:
+ * GRAV_EDEVICE with a "bounded device wait expired" message, the context still
+ * usable.  Synchronises `stream`. */
+int grav_selftest_wait(grav_ctx *ctx, double limit_ms, grav_stream_t stream);
+
 /* Self-check of the FP64 elementary functions inside Eq. 2-3 (the paper has
  * no counterpart): out[i] = f(a[i], b[i]) on ctx's device, with fn = 0 this
  * library's log(a), 1 its atan(a / b) (b > 0), 2 CUDA's log(a), 3 CUDA's

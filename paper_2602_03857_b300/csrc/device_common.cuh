@@ -57,14 +57,15 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t phase) {
     return ok != 0;
 }
 
-// Waits for `phase` of `bar` for at most kWaitLimitNs; returns false on
-// timeout (the caller records the status and leaves the kernel).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase) {
+// Waits for `phase` of `bar` for at most limit_ns (default kWaitLimitNs);
+// returns false on timeout (the caller records the status and leaves the
+// kernel).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, uint64_t limit_ns = kWaitLimitNs) {
     if (mbar_test(bar, phase)) return true;
     const uint64_t t0 = globaltimer_ns();
     while (true) {
         if (mbar_test(bar, phase)) return true;
-        if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
         __nanosleep(64);
     }
 }

@@ -149,8 +149,35 @@ __global__ void k_eval_fn(int fn, const double *__restrict__ a, const double *__
     }
 }
 
+// The failure path of every bounded mbarrier wait, exercised on purpose: an
+// mbarrier that expects one arrival which nothing makes; the wait gives up
+// after limit_ns, records kStatusMbarTimeout and the kernel returns.  No
+// asynchronous copy is in flight, so nothing outlives the kernel.
+__global__ void k_selftest_wait(int *status, uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    if (!mbar_wait_bounded(&bar, 0, limit_ns)) set_status(status, kStatusMbarTimeout);
+}
+
 }  // namespace
 }  // namespace grav
+
+extern "C" int grav_selftest_wait(grav_ctx *ctx, double limit_ms, grav_stream_t stream) {
+    using namespace grav;
+    if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
+    if (!(limit_ms > 0.0) || limit_ms > 1000.0) return set_error(ctx, GRAV_EINVAL, "limit_ms must lie in (0, 1000]");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    k_selftest_wait<<<1, 32, 0, (cudaStream_t)stream>>>(ctx->d_status, (uint64_t)(limit_ms * 1e6));
+    note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    int rc = e == cudaSuccess ? read_status(ctx, (cudaStream_t)stream, 60.0) : cuda_error(ctx, e, "selftest launch");
+    cudaSetDevice(prev);
+    return rc;
+}
 
 extern "C" int grav_eval_fn64(grav_ctx *ctx, int fn, const double *a, const double *b, double *out, int64_t n,
                               grav_stream_t stream) {
