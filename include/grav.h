@@ -346,8 +346,9 @@ int grav_plan_timing(grav_plan *plan, int enable, double *ms, int64_t *counts);
  * packed fma.rn.f32x2, [9] MHz, [10] SM count, then CUDA's FP64 functions:
  * [11] log/s, [12] MHz, [13] atan/s, [14] MHz, [15] sqrt/s, [16] MHz,
  * [17] divisions/s, [18] MHz, then this library's table-driven FP64 functions
- * used inside Eq. 2-3: [19] log/s, [20] MHz, [21] atan(a/b)/s, [22] MHz.
- * out: HOST, >= 23 doubles.  Per-clock rates per SM: rate / (MHz*1e6 * out[10]). */
+ * used inside Eq. 2-3: [19] log/s, [20] MHz, [21] atan(a/b)/s, [22] MHz, then
+ * MUFU [23] rcp/s, [24] MHz, [25] ex2/s, [26] MHz.
+ * out: HOST, >= 27 doubles.  Per-clock rates per SM: rate / (MHz*1e6 * out[10]). */
 int grav_bench_pipes(int device, double *out);
 
 /* Self-check of the device-side failure path (the paper has no counterpart):

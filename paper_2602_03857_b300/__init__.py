@@ -156,7 +156,7 @@ def launch_count() -> int:
 
 def bench_pipes(device: int = 0) -> dict:
     """Measured unit throughputs (per second) and SM clocks of the B300 pipes."""
-    out = (ctypes.c_double * 23)()
+    out = (ctypes.c_double * 27)()
     rc = _lib.grav_bench_pipes(int(device), out)
     if rc != GRAV_OK:
         raise GravError(rc, _lib.grav_last_error(None).decode())
@@ -164,7 +164,7 @@ def bench_pipes(device: int = 0) -> dict:
     r = {"sm_count": int(sms)}
     slots = [(name, 2 * k) for k, name in enumerate(("rsqrt", "lg2", "ffma", "dfma", "ffma_f32x2"))]
     slots += [(name, 11 + 2 * k) for k, name in enumerate(("log_f64", "atan_f64", "sqrt_f64", "div_f64",
-                                                            "log64_table", "atan_ratio64_table"))]
+                                                            "log64_table", "atan_ratio64_table", "rcp", "ex2"))]
     for name, i in slots:
         r[name + "_per_s"] = out[i]
         r[name + "_mhz"] = out[i + 1]

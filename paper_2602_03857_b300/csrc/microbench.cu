@@ -22,6 +22,18 @@ __device__ __forceinline__ float lg2_approx(float x) {
     return r;
 }
 
+__device__ __forceinline__ float rcp_v(float x) {
+    float r;
+    asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float ex2_v(float x) {
+    float r;
+    asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ float rsqrt_v(float x) {
     float r;
     asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -30,7 +42,8 @@ __device__ __forceinline__ float rsqrt_v(float x) {
 
 // op: 0 rsqrt, 1 lg2, 2 ffma, 3 dfma, 4 packed fma.rn.f32x2 (counted as 2 FP32 FMAs),
 //     5 FP64 log, 6 FP64 atan, 7 FP64 sqrt, 8 FP64 division (CUDA's implementations),
-//     9 this library's table-driven log64, 10 its atan_ratio64 (tables in fn)
+//     9 this library's table-driven log64, 10 its atan_ratio64 (tables in fn),
+//     11 MUFU rcp, 12 MUFU ex2
 template <int OP>
 __global__ void k_pipe(int iters, float seed, float *out, unsigned long long *clk, const double *fn) {
     const uint64_t t0 = globaltimer_ns();
@@ -51,7 +64,7 @@ __global__ void k_pipe(int iters, float seed, float *out, unsigned long long *cl
             s += lo + hi;
         }
         if (s == 12345.678f) out[0] = s;
-    } else if (OP >= 5) {
+    } else if (OP >= 5 && OP <= 10) {
         double a[kChains];
 #pragma unroll
         for (int k = 0; k < kChains; ++k) a[k] = 1.5 + seed + 0.001 * (threadIdx.x + k);
@@ -91,6 +104,8 @@ __global__ void k_pipe(int iters, float seed, float *out, unsigned long long *cl
             for (int k = 0; k < kChains; ++k) {
                 if (OP == 0) a[k] = rsqrt_v(a[k]);
                 else if (OP == 1) a[k] = lg2_approx(a[k] + 2.0f);
+                else if (OP == 11) a[k] = rcp_v(a[k] + 1.0f);
+                else if (OP == 12) a[k] = ex2_v(a[k] * -0.5f);
                 else a[k] = fmaf(a[k], 0.999999f, 1e-7f);
             }
         }
@@ -114,7 +129,7 @@ int run_one(int sms, double *ops_per_s, double *clk_mhz, const double *fn = null
     if (cudaMalloc(&out, 16) != cudaSuccess) return -1;
     if (cudaMalloc(&clk, 16) != cudaSuccess) return -1;
     const int blocks = sms * 8, threads = 256;
-    const int iters = (OP == 3) ? 256 : (OP >= 5 ? 16 : 4096);
+    const int iters = (OP == 3) ? 256 : (OP >= 5 && OP <= 10 ? 16 : 4096);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -230,6 +245,8 @@ extern "C" int grav_bench_pipes(int device, double *out) {
         rc |= run_one<9>(sms, &out[19], &out[20], fn);
         rc |= run_one<10>(sms, &out[21], &out[22], fn);
     }
+    rc |= run_one<11>(sms, &out[23], &out[24]);
+    rc |= run_one<12>(sms, &out[25], &out[26]);
     if (fn) cudaFree(fn);
     cudaSetDevice(prev);
     return rc ? set_error(nullptr, GRAV_EDEVICE, "pipe microbenchmark failed") : GRAV_OK;
