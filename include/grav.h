@@ -119,8 +119,9 @@ typedef struct {
     int reorth;                /* single CG solve without preconditioner (precond = 0, outer_max = 0): keep up
                                   to this many normalised residuals (N*reorth*8 bytes of HBM, at most 4096)
                                   and reorthogonalise every new residual against them (twice), which
-                                  restores the convergence CG loses to rounding on this system (restarts
-                                  from the true residual then run plain CG); 0 = plain CG (default 1000) */
+                                  restores the convergence CG loses to rounding on this system (a restart
+                                  from the true residual starts a fresh basis; at most 16 restarts);
+                                  0 = plain CG (default 1000) */
     int check_stations;        /* mixed modes, > 0: state the error of the result against the FP64 operator
                                   at this many evenly spaced stations (inversions: of G m_out; serving
                                   forward jobs: of d), in grav_solve_info.fp64_rel_err; 0 = off (default) */

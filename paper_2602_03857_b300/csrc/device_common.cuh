@@ -242,15 +242,19 @@ __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
     return d;
 }
 
+__device__ __forceinline__ f2_t rsqrt2(f2_t R2) {
+    float r0, r1;
+    f2_unpack(R2, r0, r1);
+    return f2_pack(rsqrt_approx(r0), rsqrt_approx(r1));
+}
+
 // The far-field term for two pairs at once: acc += w * dz / R^3 with
 // dz = zc + nzs (nzs = -station depth), R^2 = dz^2 + h2.  Same operations, in
 // the same order, as far_kernel() on each half.
 __device__ __forceinline__ f2_t far_pair_acc(f2_t zc, f2_t nzs, f2_t h2, f2_t w, f2_t acc) {
     const f2_t dz = f2_add(zc, nzs);
     const f2_t R2 = f2_fma(dz, dz, h2);
-    float r0, r1;
-    f2_unpack(R2, r0, r1);
-    const f2_t rs = f2_pack(rsqrt_approx(r0), rsqrt_approx(r1));
+    const f2_t rs = rsqrt2(R2);
     const f2_t rs2 = f2_mul(rs, rs);
     const f2_t k = f2_mul(f2_mul(dz, rs), rs2);
     return f2_fma(w, k, acc);
@@ -285,9 +289,7 @@ __device__ __forceinline__ float far_kernel_q(float dz, float R2, float qg, floa
 __device__ __forceinline__ f2_t far_pair_acc_q(f2_t zc, f2_t nzs, f2_t h2, f2_t w, f2_t acc, f2_t qg, f2_t ph) {
     const f2_t dz = f2_add(zc, nzs);
     const f2_t R2 = f2_fma(dz, dz, h2);
-    float r0, r1;
-    f2_unpack(R2, r0, r1);
-    const f2_t rs = f2_pack(rsqrt_approx(r0), rsqrt_approx(r1));
+    const f2_t rs = rsqrt2(R2);
     const f2_t rs2 = f2_mul(rs, rs);
     const f2_t k = f2_mul(f2_mul(dz, rs), rs2);
     const f2_t n = f2_fma(qg, f2_mul(dz, dz), ph);

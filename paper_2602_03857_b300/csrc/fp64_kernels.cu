@@ -175,13 +175,16 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd64(Geo g, int ldw, const dou
 // out[i] = scale * sum_c part[c][i] + add_scale * add[i] + add2[i]  (fixed order)
 __global__ void k_reduce_rows(const double *__restrict__ part, int nchunk, int64_t n, double scale,
                               const double *__restrict__ add, double add_scale,
-                              const double *__restrict__ add2, double *__restrict__ out) {
+                              const double *__restrict__ add2, const unsigned long long *__restrict__ fbits,
+                              double *__restrict__ out) {
+    const double fs = fbits ? __longlong_as_double((long long)*fbits) : 1.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int c = 0; c < nchunk; ++c) s += part[(int64_t)c * n + i];
         s *= scale;
-        if (add) s = fma(add_scale, add[i], s);
         if (add2) s += add2[i];
+        if (fbits) s *= fs;
+        if (add) s = fma(add_scale, add[i], s);
         out[i] = s;
     }
 }
@@ -514,8 +517,9 @@ void launch_fwd64(const grav_plan *p, cudaStream_t s) {
 }
 
 void launch_reduce_rows(const double *part, int nchunk, int64_t n, double scale, const double *add,
-                        double add_scale, const double *add2, double *out, cudaStream_t s) {
-    k_reduce_rows<<<grid_for(n, 256), 256, 0, s>>>(part, nchunk, n, scale, add, add_scale, add2, out);
+                        double add_scale, const double *add2, double *out, cudaStream_t s,
+                        const unsigned long long *fbits) {
+    k_reduce_rows<<<grid_for(n, 256), 256, 0, s>>>(part, nchunk, n, scale, add, add_scale, add2, fbits, out);
     note_launches(1);
 }
 

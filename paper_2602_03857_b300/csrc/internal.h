@@ -131,6 +131,8 @@ struct grav_plan {
     float *m_w2f = nullptr;               // [nzp] (zc + z0)^2 in FP32
     float4 *st32 = nullptr;               // stations (xh, xl, yh, yl)
     float2 *stz = nullptr;                // stations (z, r)
+    unsigned long long *rmax_bits = nullptr;   // max|r| of the last mixed adjoint (bits of a double)
+    unsigned long long *mmax_bits = nullptr;   // max|m| of the last mixed forward (bits of a double)
     int m_fwd_cols_per_chunk = 0, m_fwd_nchunk = 0;
     int m_adj_tz = 0, m_adj_ngz = 0, m_adj_nschunk = 0, m_adj_schunk_len = 0;
     int m_adj_bc = 0;                     // 1: broadcast adjoint layout (large meshes), 0: lanes split stations
@@ -190,8 +192,11 @@ void stage_end(const grav_plan *p, int stage, cudaStream_t s);
 void fp64_setup(grav_plan *p, cudaStream_t s);
 void launch_node_weights(const grav_plan *p, const double *m, cudaStream_t s);
 void launch_fwd64(const grav_plan *p, cudaStream_t s);
+// out[i] = fs * (scale * sum_c part[c][i] + add2[i]) + add_scale * add[i], fs = *fbits as a double
+// (1 when fbits is null); add and add2 may be null
 void launch_reduce_rows(const double *part, int nchunk, int64_t n, double scale, const double *add,
-                        double add_scale, const double *add2, double *out, cudaStream_t s);
+                        double add_scale, const double *add2, double *out, cudaStream_t s,
+                        const unsigned long long *fbits = nullptr);
 void launch_adj64(const grav_plan *p, const double *r, cudaStream_t s);
 void launch_adj_finish(const grav_plan *p, const double *u, double scale, int depth_weighted,
                        const double *add, double *out, cudaStream_t s);
@@ -211,7 +216,8 @@ int fwd64_stations_per_cta();
 // mixed launchers (mixed_kernels.cu)
 int mixed_setup(grav_plan *p, cudaStream_t s);   // 0 or a GRAV_E* code
 int near_setup_warps(const grav_plan *p);         // 0: window too large for shared memory
-void launch_mixed_prep_q(const grav_plan *p, const double *m, cudaStream_t s);
+// normalize: q in units of max|m| (mmax_bits); the forward's row reduction multiplies back
+void launch_mixed_prep_q(const grav_plan *p, const double *m, cudaStream_t s, bool normalize);
 void launch_mixed_fwd(const grav_plan *p, cudaStream_t s);
 void launch_mixed_near_fwd(const grav_plan *p, const double *m, cudaStream_t s);
 void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s);

@@ -77,24 +77,53 @@ __host__ __device__ MfwdSmem mfwd_layout(const MixedGeo &g, int cols_per_stage) 
 }
 
 // ---------------------------------------------------------------------------
-// qT[col][l] = gamma*1e5*V * m[i + nx*(j + ny*l)], col = i + nx*j; l >= nz: 0.
+// The FP32 operands of the mixed products are normalised by the largest
+// magnitude of the input vector (m for the forward, r for the adjoint), and
+// the FP64 results are multiplied back: the products are homogeneous in
+// their input up to rounding at any scale, instead of flushing to zero (or
+// overflowing) when the input leaves the range where FP32 products of it
+// with dz / R^3 stay normal.
+//
+// max |v_i| as the bit pattern of a non-negative double (atomicMax on the
+// bits orders non-negative doubles numerically); *bits must start at 0.
+__global__ void k_absmax(const double *__restrict__ v, int64_t n, unsigned long long *__restrict__ bits) {
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(v[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(bits, (unsigned long long)__double_as_longlong(m));
+}
+
+// 1 / max|v| (0 for a zero vector), or 1 without normalisation (bits null)
+__device__ __forceinline__ double inv_scale(const unsigned long long *bits) {
+    if (!bits) return 1.0;
+    const double vm = __longlong_as_double((long long)*bits);
+    return vm > 0.0 ? 1.0 / vm : 0.0;
+}
+
+// qT[col][l] = gamma*1e5*V * m[i + nx*(j + ny*l)] / max|m|, col = i + nx*j; l >= nz: 0.
 // ---------------------------------------------------------------------------
-__global__ void k_prep_q(MixedGeo g, const double *__restrict__ m, float scale, float *__restrict__ qT) {
+__global__ void k_prep_q(MixedGeo g, const double *__restrict__ m, float scale, const unsigned long long *bits,
+                         float *__restrict__ qT) {
+    const double sc = scale * inv_scale(bits);
     const int64_t total = (int64_t)g.ncol * g.nzp;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int l = (int)(t % g.nzp);
         const int64_t col = t / g.nzp;
-        qT[t] = (l < g.nz) ? (float)(scale * m[col + (int64_t)g.ncol * l]) : 0.0f;
+        qT[t] = (l < g.nz) ? (float)(sc * m[col + (int64_t)g.ncol * l]) : 0.0f;
     }
 }
 
 // the same FP32 q in the cells' natural order (coalesced gathers of the near field)
-__global__ void k_prep_qn(int64_t M, const double *__restrict__ m, float scale, float *__restrict__ qn) {
+__global__ void k_prep_qn(int64_t M, const double *__restrict__ m, float scale, const unsigned long long *bits,
+                          float *__restrict__ qn) {
+    const double sc = scale * inv_scale(bits);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M; k += (int64_t)gridDim.x * blockDim.x)
-        qn[k] = (float)(scale * m[k]);
+        qn[k] = (float)(sc * m[k]);
 }
 
-// stations: st32 = (xh, xl, yh, yl) of (x - xref, y - yref); stz = (z, r)
+// stations: st32 = (xh, xl, yh, yl) of (x - xref, y - yref); stz = (z, r / max|r|) (k_set_rz)
 __global__ void k_prep_stations(const double *__restrict__ x, const double *__restrict__ y,
                                 const double *__restrict__ z, int64_t n, double xref, double yref,
                                 float4 *__restrict__ st32, float2 *__restrict__ stz) {
@@ -106,9 +135,12 @@ __global__ void k_prep_stations(const double *__restrict__ x, const double *__re
     }
 }
 
-__global__ void k_set_rz(float2 *__restrict__ stz, const double *__restrict__ r, int64_t n) {
+// stz[i].y = r_i / max|r|
+__global__ void k_set_rz(float2 *__restrict__ stz, const double *__restrict__ r, int64_t n,
+                         const unsigned long long *bits) {
+    const double sc = inv_scale(bits);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        stz[i].y = (float)r[i];
+        stz[i].y = (float)(sc * r[i]);
 }
 
 // The far-field geometry of one (station, cell) pair exactly as every mixed
@@ -364,13 +396,24 @@ __global__ void __launch_bounds__(kMaWarps * 32, MaMinBlocks<TZ>::value) k_madj(
 // stations of a TMA-staged chunk are read by all lanes at once (shared-memory
 // broadcast), and every lane accumulates its own cells: no cross-lane
 // reduction.  Sums run in FP32 over 128 stations and are folded into FP64
-// accumulators (compensation by wider precision).
+// accumulators (compensation by wider precision; the FP64 adds run on the
+// otherwise idle FP64 pipe).  Every pair's kernel value dz / R^3 comes from
+// the same FP32 operations as in the forward (far_pair), so the mixed G^T is
+// the transpose of the mixed G term by term: CG on G W^-2 G^T needs that
+// symmetry (a variant that folded r into the pair geometry, one FP32
+// operation per pair fewer and 2 % faster, perturbed each term by a few ulp
+// and took 346 instead of 247 iterations on the 150 x 150 x 60 inversion).
 // ---------------------------------------------------------------------------
 #ifndef GRAV_AB_MINB
 #define GRAV_AB_MINB 2
 #endif
 constexpr int kAbWarps = 8;
 constexpr int kAbStage = 1024;
+// FP32 run length before the FP64 fold.  Measured at 210 x 210 x 75 x 178,797:
+// 64 / 128 / 256 stations take 142.5 / 139.3 / 138.7 ms, while the rounding
+// noise of G^T r (|G^T(a+b) - G^T a - G^T b| / |G^T(a+b)| for white-noise r)
+// is 2.1e-7 / ~2.9e-7 / 4.1e-7; the CG on G W^-2 G^T stalls near that noise
+// floor, so 128 trades 0.4 % of the adjoint for a lower floor.
 constexpr int kAbFold = 128;
 
 template <int TZ, bool QUAD>
@@ -870,17 +913,21 @@ __global__ void __launch_bounds__(256, 4) k_near_adj(int nx, int ny, NearGeo ng,
     if (xin) out[x + (int64_t)nx * (y + (int64_t)ny * l)] = acc;
 }
 
-// out[k] = vol * (sum_c apart[c][k] + near[k] (top bz layers)) [* w2_l] [+ add[k]]
+// out[k] = vol * fs * (sum_c apart[c][k] + near[k] (top bz layers)) [* w2_l] [+ add[k]],
+// fs = max|r| (bits in *fbits): the partials are in units of max|r|
 __global__ void k_madj_finish(int nx, int ny, int nz, int bz, const double *__restrict__ apart, int nschunk,
-                              double vol, const double *__restrict__ near, const double *__restrict__ w2,
+                              const unsigned long long *__restrict__ fbits, double vol,
+                              const double *__restrict__ near, const double *__restrict__ w2,
                               const double *__restrict__ add, double *__restrict__ out) {
     const int64_t M = (int64_t)nx * ny * nz;
     const int64_t plane = (int64_t)nx * ny;
+    const double fs = fbits ? __longlong_as_double((long long)*fbits) : 1.0;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M; k += (int64_t)gridDim.x * blockDim.x) {
         const int l = (int)(k / plane);
         double s = 0.0;
         for (int c = 0; c < nschunk; ++c) s += apart[(int64_t)c * M + k];
         if (l < bz) s += near[k];
+        s *= fs;
         s *= vol;
         if (w2) s *= w2[l];
         if (add) s += add[k];
@@ -954,10 +1001,16 @@ constexpr int kMfColsPerStage = 32;
 // fastest per layer among 8/12/16/20 at 2 CTAs per SM), the last group
 // rounded up to a multiple of 4.  Meshes with fewer than 16 layers use one
 // group of ceil4(nz).
-int adj_tz_bc(int nz) { return nz >= 16 ? 16 : (nz + 3) / 4 * 4; }
+#ifndef GRAV_AB_TZ
+#define GRAV_AB_TZ 16
+#endif
+constexpr int kAbTz = GRAV_AB_TZ;
+static_assert(kAbTz % 4 == 0 && kAbTz >= 16, "layer group: a multiple of 4, at least 16");
+int adj_tz_bc(int nz) { return nz >= kAbTz ? kAbTz : nz >= 16 ? 16 : (nz + 3) / 4 * 4; }
 int adj_tzl_bc(int nz) {
-    if (nz < 16) return (nz + 3) / 4 * 4;
-    const int rem = nz - 16 * ((nz + 15) / 16 - 1);
+    const int tz = adj_tz_bc(nz);
+    if (nz < 16) return tz;
+    const int rem = nz - tz * ((nz + tz - 1) / tz - 1);
     return (rem + 3) / 4 * 4;
 }
 
@@ -994,14 +1047,17 @@ static MixedSizes mixed_sizes(const grav_plan *p) {
     const int ncol = p->nx * p->ny;
     const int tiles = (int)((p->N + kMfThreads * kMfT - 1) / (kMfThreads * kMfT));
     // aim at >= 16 waves of ~6 resident CTAs per SM, each CTA >= 16 columns
-    const int64_t target = 148LL * 6 * 16;
+    const int64_t target = 148LL * 6 * 16;   // (32 or 48 waves: measured no faster)
     int nchunk = (int)std::min<int64_t>(std::max<int64_t>(1, (target + tiles - 1) / tiles), std::max(1, ncol / 16));
     z.cols_per_chunk = (ncol + nchunk - 1) / nchunk;
     z.nchunk = (ncol + z.cols_per_chunk - 1) / z.cols_per_chunk;
     // broadcast layout when the cells alone fill the GPU (>= 2 CTAs per SM);
-    // station chunks then add waves (>= 4) to trim the tail
+    // station chunks then add waves (>= 32) to trim the tail: measured at
+    // 210 x 210 x 75 x 178,797, 2 chunks (5.8 waves) 143.2 ms, 6 chunks
+    // 138.9 ms, 12 chunks (35 waves) 137.5 ms; the partials (chunks x M
+    // doubles) are capped at 512 MB
     const int tz_bc = adj_tz_bc(p->nz);
-    const int64_t slots = 148LL * 2;
+    const int64_t slots = 148LL * GRAV_AB_MINB;
     const int64_t bc_ctas = (int64_t)((ncol + kAbWarps * 32 - 1) / (kAbWarps * 32)) * ((p->nz + tz_bc - 1) / tz_bc);
     z.bc = (GRAV_AB_FORCE >= 0) ? GRAV_AB_FORCE : (bc_ctas >= slots ? 1 : 0);
     // run-time override of the layout choice: GRAV_ADJOINT_LAYOUT=broadcast|shuffle|auto
@@ -1013,7 +1069,8 @@ static MixedSizes mixed_sizes(const grav_plan *p) {
     z.ngz = (p->nz + z.tz - 1) / z.tz;
     int64_t nsch, stage;
     if (z.bc) {
-        nsch = std::max<int64_t>(1, (4 * slots + bc_ctas - 1) / bc_ctas);
+        nsch = std::max<int64_t>(1, (32 * slots + bc_ctas - 1) / bc_ctas);
+        nsch = std::min<int64_t>(nsch, std::max<int64_t>(1, (512ll << 20) / (8 * std::max<int64_t>(p->M, 1))));
         stage = kAbStage;
     } else {
         const int64_t groups_ctas = ((int64_t)ncol * z.ngz + kMaWarps - 1) / kMaWarps;
@@ -1070,6 +1127,7 @@ size_t mixed_scratch_bytes(const grav_plan *p) {
     add(4ull * p->nx * p->ny * nzp);                                       // qT
     add(4ull * M);                                                          // qN
     add(16ull * (N + 2)); add(8ull * (N + 4));                             // st32, stz (padded)
+    add(8); add(8);                                                         // max|r|, max|m|
     add(8ull * z.nchunk * N);                                               // m_part
     add(8ull * z.nschunk * M);                                              // m_apart
     add(4ull * N * p->ng.slots);                                            // dG (FP32)
@@ -1137,6 +1195,8 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
     p->qN = (float *)take(p, 4ull * p->M);
     p->st32 = (float4 *)take(p, 16ull * (p->N + 2));
     p->stz = (float2 *)take(p, 8ull * (p->N + 4));
+    p->rmax_bits = (unsigned long long *)take(p, 8);
+    p->mmax_bits = (unsigned long long *)take(p, 8);
     p->m_fwd_cols_per_chunk = z.cols_per_chunk;
     p->m_fwd_nchunk = z.nchunk;
     p->m_adj_tz = z.tz;
@@ -1233,11 +1293,17 @@ int mixed_adj_last_group(const grav_plan *p) { return p->m_adj_bc ? adj_tzl_bc(p
 
 size_t mfwd_smem(const grav_plan *p) { return mfwd_layout(p->mg, kMfColsPerStage).total; }
 
-void launch_mixed_prep_q(const grav_plan *p, const double *m, cudaStream_t s) {
+void launch_mixed_prep_q(const grav_plan *p, const double *m, cudaStream_t s, bool normalize) {
     const float scale = (float)(kGammaMgal * p->cell_a * p->cell_b * p->cell_c);
     const int64_t total = (int64_t)p->mg.ncol * p->mg.nzp;
-    k_prep_q<<<grid_for(total, 256), 256, 0, s>>>(p->mg, m, scale, p->qT);
-    k_prep_qn<<<grid_for(p->M, 256), 256, 0, s>>>(p->M, m, scale, p->qN);
+    const unsigned long long *bits = normalize ? p->mmax_bits : nullptr;
+    if (normalize) {
+        cudaMemsetAsync(p->mmax_bits, 0, 8, s);
+        k_absmax<<<grid_for(p->M, 256, 148 * 4), 256, 0, s>>>(m, p->M, p->mmax_bits);
+        note_launches(1);
+    }
+    k_prep_q<<<grid_for(total, 256), 256, 0, s>>>(p->mg, m, scale, bits, p->qT);
+    k_prep_qn<<<grid_for(p->M, 256), 256, 0, s>>>(p->M, m, scale, bits, p->qN);
     note_launches(2);
 }
 
@@ -1280,8 +1346,22 @@ void launch_mixed_near_fwd(const grav_plan *p, const double *m, cudaStream_t s) 
     note_launches(1);
 }
 
+// k_madj_bc<TZ, tzl> for the run-time last-group size tzl (a multiple of 4, <= TZ)
+template <int TZ, int L, bool Q, typename F>
+void pick_bc_last(int tzl, F &gob) {
+    if constexpr (L < TZ) {
+        if (tzl == L) { gob(k_madj_bc<TZ, L, Q>); return; }
+        pick_bc_last<TZ, L + 4, Q>(tzl, gob);
+    } else {
+        gob(k_madj_bc<TZ, TZ, Q>);
+    }
+}
+
 void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
-    k_set_rz<<<grid_for(p->N, 256), 256, 0, s>>>(p->stz, r, p->N);
+    cudaMemsetAsync(p->rmax_bits, 0, 8, s);
+    k_absmax<<<grid_for(p->N, 256, 148 * 4), 256, 0, s>>>(r, p->N, p->rmax_bits);
+    k_set_rz<<<grid_for(p->N, 256), 256, 0, s>>>(p->stz, r, p->N, p->rmax_bits);
+    note_launches(2);
     const int64_t groups = (int64_t)p->mg.ncol * p->m_adj_ngz;
     dim3 grid((unsigned)((groups + kMaWarps - 1) / kMaWarps), p->m_adj_nschunk);
     const size_t smem = 128 + 2ull * kMaStage * (sizeof(float4) + sizeof(float2));
@@ -1304,13 +1384,10 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
         const int tzl = adj_tzl_bc(p->nz);
         auto pick = [&](auto quad) {
             constexpr bool Q = decltype(quad)::value;
-            if (p->m_adj_tz == 16) {
-                switch (tzl) {
-                    case 4: gob(k_madj_bc<16, 4, Q>); break;
-                    case 8: gob(k_madj_bc<16, 8, Q>); break;
-                    case 12: gob(k_madj_bc<16, 12, Q>); break;
-                    default: gob(k_madj_bc<16, 16, Q>); break;
-                }
+            if (p->m_adj_tz == kAbTz) {
+                pick_bc_last<kAbTz, 4, Q>(tzl, gob);
+            } else if (p->m_adj_tz == 16) {
+                pick_bc_last<16, 4, Q>(tzl, gob);
             } else {
                 switch (p->m_adj_tz) {
                     case 4: gob(k_madj_bc<4, 4, Q>); break;
@@ -1347,6 +1424,7 @@ void launch_mixed_adj_finish(const grav_plan *p, const double *r, int depth_weig
     (void)r;
     k_madj_finish<<<grid_for(p->M, 256), 256, 0, s>>>(p->nx, p->ny, p->nz, std::min(p->ng.bz, p->nz), p->m_apart,
                                                       p->m_adj_nschunk,
+                                                      p->rmax_bits,
                                                       kGammaMgal * p->cell_a * p->cell_b * p->cell_c, p->m_cellacc,
                                                       depth_weighted ? p->d_w2 : nullptr, add, out);
     note_launches(1);

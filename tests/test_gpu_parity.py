@@ -252,6 +252,42 @@ def test_mixed_degenerate_meshes_and_far_stations(g, shape, cells, adjoint_layou
     assert _rel(at, oracle.depth_w2(mesh, 50.0) * (G.T @ r)) <= TOLMIX
 
 
+@pytest.mark.parametrize("cells", [(20.0, 20.0, 20.0), (30.0, 20.0, 25.0)])
+def test_mixed_products_scale_exactly(g, cells, adjoint_layout):
+    """The mixed products divide their input by its largest magnitude before
+    the FP32 arithmetic and multiply the FP64 result back, so an input scaled
+    by 2^k gives the output scaled by exactly 2^k, also far outside the range
+    in which FP32 products of the raw input would stay normal (2^-110 ~ 8e-34
+    times a density of ~100 flushed to zero before); zero entries and an
+    all-zero input are exact, and the scaled results still match the oracle."""
+    mesh = synth.uniform_mesh(23, 19, 18, *cells)
+    rng = np.random.Generator(np.random.PCG64(171))
+    m = rng.normal(0.0, 100.0, mesh.ncells)
+    m[::7] = 0.0
+    n = 300
+    sv = synth.Survey(rng.uniform(0, 23 * cells[0], n), rng.uniform(0, 19 * cells[1], n), -rng.uniform(0.5, 8.0, n))
+    sv.x[0], sv.y[0] = 11.5 * cells[0], 9.5 * cells[1]   # above a column centre, with r = 0 below
+    r = synth.random_vector(n, 172)
+    r[::5] = 0.0
+    plan = g.Plan(mesh, g.Survey(sv.x, sv.y, sv.z), precision="mixed")
+    d = plan.forward(_dev(m))
+    a = plan.adjoint(_dev(r), depth_weighted=True)
+    for k in (-110, -60, 60, 110):
+        s = 2.0 ** k
+        assert torch.equal(plan.forward(_dev(m * s)), d * s), k
+        assert torch.equal(plan.adjoint(_dev(r * s), depth_weighted=True), a * s), k
+    z = plan.forward(_dev(np.zeros(mesh.ncells)))
+    assert bool((z == 0).all())
+    z = plan.adjoint(_dev(np.zeros(n)), depth_weighted=True)
+    assert bool((z == 0).all())
+    G = oracle.G_explicit(mesh, sv)
+    s = 2.0 ** -110
+    assert _rel(plan.forward(_dev(m * s)).cpu().numpy(), G @ (m * s)) <= TOLMIX
+    a_ref = oracle.depth_w2(mesh, 50.0) * (G.T @ (r * s))
+    assert _rel(plan.adjoint(_dev(r * s), depth_weighted=True).cpu().numpy(), a_ref) <= TOLMIX
+    plan.close()
+
+
 def _mixed_definition(mesh, sv, G, cell, k):
     """Dense matrix of the mixed approximation: G_ik from the oracle when the
     cell centre lies within k cell widths of station i, else the point mass
