@@ -38,16 +38,20 @@ double now_s() {
 }
 
 // Polls `ev` until it completes or timeout_s elapses.
+// Polls the event until it completes or timeout_s passes.  The sleep between
+// polls is 1/16 of the time already waited (5 us .. 2 ms), so a wait ends at
+// most ~6 % (2 ms) after the event while long waits do not spin; a doubling
+// backoff instead overshot a 5.7 ms CG iteration by up to 2 ms.
 int wait_event(grav_ctx *ctx, cudaEvent_t ev, double timeout_s, const char *what) {
     const double t0 = now_s();
-    int sleep_us = 20;
     while (true) {
         const cudaError_t e = cudaEventQuery(ev);
         if (e == cudaSuccess) return GRAV_OK;
         if (e != cudaErrorNotReady) return cuda_error(ctx, e, what);
-        if (now_s() - t0 > timeout_s) return set_error(ctx, GRAV_ETIMEDOUT, "%s: timed out after %.1f s", what, timeout_s);
-        std::this_thread::sleep_for(std::chrono::microseconds(sleep_us));
-        sleep_us = std::min(sleep_us * 2, 2000);
+        const double el = now_s() - t0;
+        if (el > timeout_s) return set_error(ctx, GRAV_ETIMEDOUT, "%s: timed out after %.1f s", what, timeout_s);
+        const double us = std::min(2000.0, std::max(5.0, el * 1e6 / 16.0));
+        std::this_thread::sleep_for(std::chrono::microseconds((int64_t)us));
     }
 }
 
@@ -558,10 +562,13 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
     const int cap = reorth_cap(p);
     double *Qb = cap ? (double *)ar.take(8ull * cap * N) : nullptr;   // reorthogonalisation basis [cap][N]
     double *cb = cap ? (double *)ar.take(8ull * cap) : nullptr;
-    double *hsc = nullptr;
-    cudaMallocHost((void **)&hsc, 8 * kSCount);
-    cudaEvent_t ev;
+    double *hsc = nullptr;     // [0, kSCount): synchronous reads; then two slots of the CG pipeline
+    cudaMallocHost((void **)&hsc, 3 * 8 * kSCount);
+    double *hpipe = hsc + kSCount;
+    cudaEvent_t ev, evp[2];
     cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&evp[0], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&evp[1], cudaEventDisableTiming);
     int rc = GRAV_OK;
     double lam = o.lambda, trace = 0.0;
     int iters = 0;
@@ -741,38 +748,56 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
         // recomputed from y with the operator itself (r = dd - A y); if that
         // true residual is still above tol, CG restarts from it (p = r).
         for (restarts = 0;; ++restarts) {
-            while (!converged && it < o.max_iter) {
-                const int n_it = std::min(every, o.max_iter - it);
-                for (int k = 0; k < n_it; ++k, ++it) {
-                    if ((rc = plan_adjoint_ex(p, pv, q, 1, nullptr, s))) break;
-                    if ((rc = plan_forward_ex(p, q, Ap, pv, lam, s))) break;
-                    launch_dot(pv, Ap, N, dp, sc + kSPAp, s);
-                    cg_alpha(sc, s);
-                    cg_update_yr(y, r, pv, Ap, N, sc, s);
-                    if (pc) {
-                        vec_mul(dinv, r, N, zv, s);
-                        launch_dot(r, zv, N, dp, sc + kSRRNew, s);
-                        launch_dot(r, r, N, dp, sc + kSResNew, s);
-                        cg_beta(sc, it, kSResNew, s, hist, hist_len);
-                        cg_update_p(pv, zv, N, sc, s);
-                    } else {
-                        if (reo) cg_reorth(Qb, kb, N, r, cb, sc, s);
-                        launch_dot(r, r, N, dp, sc + kSRRNew, s);
-                        cg_beta(sc, it, kSRRNew, s, hist, hist_len);
-                        if (reo && kb < cap) {
-                            cg_basis_append(Qb + (size_t)kb * N, r, N, sc, kSRRNew, s);
-                            ++kb;
+            // Batches of `every` iterations are enqueued one ahead of the
+            // convergence check: while the host waits for the scalars of batch
+            // b (copied into a pinned slot of their own), batch b + 1 already
+            // runs, so the GPU does not idle on the host between batches.  An
+            // iteration after the device froze the state (converged or broken
+            // down) changes no vector, and the work after this loop is ordered
+            // behind it on the stream.
+            int queued = 0, head = 0;   // batches in flight; slot of the oldest
+            while (!converged) {
+                while (queued < 2 && it < o.max_iter) {
+                    const int n_it = std::min(every, o.max_iter - it);
+                    for (int k = 0; k < n_it; ++k, ++it) {
+                        if ((rc = plan_adjoint_ex(p, pv, q, 1, nullptr, s))) break;
+                        if ((rc = plan_forward_ex(p, q, Ap, pv, lam, s))) break;
+                        launch_dot(pv, Ap, N, dp, sc + kSPAp, s);
+                        cg_alpha(sc, s);
+                        cg_update_yr(y, r, pv, Ap, N, sc, s);
+                        if (pc) {
+                            vec_mul(dinv, r, N, zv, s);
+                            launch_dot(r, zv, N, dp, sc + kSRRNew, s);
+                            launch_dot(r, r, N, dp, sc + kSResNew, s);
+                            cg_beta(sc, it, kSResNew, s, hist, hist_len);
+                            cg_update_p(pv, zv, N, sc, s);
+                        } else {
+                            if (reo) cg_reorth(Qb, kb, N, r, cb, sc, s);
+                            launch_dot(r, r, N, dp, sc + kSRRNew, s);
+                            cg_beta(sc, it, kSRRNew, s, hist, hist_len);
+                            if (reo && kb < cap) {
+                                cg_basis_append(Qb + (size_t)kb * N, r, N, sc, kSRRNew, s);
+                                ++kb;
+                            }
+                            cg_update_p(pv, r, N, sc, s);
                         }
-                        cg_update_p(pv, r, N, sc, s);
                     }
+                    if (rc) break;
+                    const int slot = (head + queued) & 1;
+                    cudaMemcpyAsync(hpipe + (size_t)slot * kSCount, sc, 8 * kSCount, cudaMemcpyDeviceToHost, s);
+                    cudaEventRecord(evp[slot], s);
+                    ++queued;
                 }
-                if (rc) break;
-                if ((rc = sync_scalars("cg iteration"))) break;
-                if (hsc[kSFrozen] == 2.0) {
+                if (rc || queued == 0) break;
+                if ((rc = wait_event(ctx, evp[head], o.timeout_s, "cg iteration"))) break;
+                const double *hb = hpipe + (size_t)head * kSCount;
+                head ^= 1;
+                --queued;
+                if (hb[kSFrozen] == 2.0) {
                     rc = set_error(ctx, GRAV_EDEVICE, "CG breakdown: p.Ap <= 0 (operator not SPD in this precision)");
                     break;
                 }
-                if (hsc[kSFrozen] != 0.0) converged = true;
+                if (hb[kSFrozen] != 0.0) converged = true;
                 if (cancel && cancel->load()) {
                     rc = set_error(ctx, GRAV_ECANCELED, "solve cancelled");
                     break;
@@ -787,6 +812,7 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             if ((rc = sync_scalars("cg true residual"))) break;
             true_rel = hsc[kSBB] > 0 ? std::sqrt(hsc[kSTmp] / hsc[kSBB]) : 0.0;
             iters = (int)hsc[kSIters];   // iterations that updated y (no-ops after a freeze excluded)
+            it = iters;                  // the next cycle numbers its iterations after the real ones
             if (true_rel <= o.tol || restarts >= 16 || it >= o.max_iter) {
                 converged = true_rel <= o.tol;
                 break;
@@ -847,6 +873,8 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
     cudaFreeAsync(base, s);
     ctx->hbm_used -= bytes;
     cudaEventDestroy(ev);
+    cudaEventDestroy(evp[0]);
+    cudaEventDestroy(evp[1]);
     if (rc != GRAV_ETIMEDOUT) cudaStreamSynchronize(s);
     cudaFreeHost(hsc);
     if (info) info->seconds = now_s() - t0;
