@@ -173,20 +173,34 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd64(Geo g, int ldw, const dou
 }
 
 // out[i] = scale * sum_c part[c][i] + add_scale * add[i] + add2[i]  (fixed order)
-__global__ void k_reduce_rows(const double *__restrict__ part, int nchunk, int64_t n, double scale,
-                              const double *__restrict__ add, double add_scale,
-                              const double *__restrict__ add2, const unsigned long long *__restrict__ fbits,
-                              double *__restrict__ out) {
-    const double fs = fbits ? __longlong_as_double((long long)*fbits) : 1.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int c = 0; c < nchunk; ++c) s += part[(int64_t)c * n + i];
-        s *= scale;
-        if (add2) s += add2[i];
-        if (fbits) s *= fs;
-        if (add) s = fma(add_scale, add[i], s);
-        out[i] = s;
-    }
+// One CTA per 32 consecutive rows i: lane = row, the 8 warps split the
+// chunks c (warp w sums c = w, w + 8, ...; each load is 32 consecutive
+// doubles), then warp 0 adds the 8 warp sums in order: deterministic, and
+// parallel over chunks as well as rows (surveys of a few thousand stations
+// have thousands of forward chunks).
+constexpr int kRedWarps = 8;
+__global__ void __launch_bounds__(kRedWarps * 32) k_reduce_rows(const double *__restrict__ part, int nchunk, int64_t n,
+                                                              double scale, const double *__restrict__ add,
+                                                              double add_scale, const double *__restrict__ add2,
+                                                              const unsigned long long *__restrict__ fbits,
+                                                              double *__restrict__ out) {
+    __shared__ double ws[kRedWarps][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+    double s = 0.0;
+    if (i < n)
+        for (int c = warp; c < nchunk; c += kRedWarps) s += part[(int64_t)c * n + i];
+    ws[warp][lane] = s;
+    __syncthreads();
+    if (warp != 0 || i >= n) return;
+    s = ws[0][lane];
+#pragma unroll
+    for (int w = 1; w < kRedWarps; ++w) s += ws[w][lane];
+    s *= scale;
+    if (add2) s += add2[i];
+    if (fbits) s *= __longlong_as_double((long long)*fbits);
+    if (add) s = fma(add_scale, add[i], s);
+    out[i] = s;
 }
 
 // st4[s].w = r[s]
@@ -519,7 +533,9 @@ void launch_fwd64(const grav_plan *p, cudaStream_t s) {
 void launch_reduce_rows(const double *part, int nchunk, int64_t n, double scale, const double *add,
                         double add_scale, const double *add2, double *out, cudaStream_t s,
                         const unsigned long long *fbits) {
-    k_reduce_rows<<<grid_for(n, 256), 256, 0, s>>>(part, nchunk, n, scale, add, add_scale, add2, fbits, out);
+    if (n <= 0) return;
+    k_reduce_rows<<<(unsigned)((n + 31) / 32), kRedWarps * 32, 0, s>>>(part, nchunk, n, scale, add, add_scale, add2,
+                                                                      fbits, out);
     note_launches(1);
 }
 

@@ -283,9 +283,11 @@ __global__ void __launch_bounds__(kMfThreads, GRAV_MF_MINB) k_mfwd(MixedGeo g, c
 // Far-field adjoint: acc_k = sum_i r_i dz/R^3.  A warp owns TZ cells of one
 // column (layers lg*TZ ...); its lanes split the stations of the CTA's chunk
 // (x/y hi-lo and (z, r) staged in shared memory by two TMA bulk copies per
-// stage).  Each lane sums its stations of one stage in FP32, folds that stage
-// sum into (hi, lo) by two-sum, and at the end the 32 lane values are reduced
-// by a warp-shuffle butterfly in FP64 (fixed order: deterministic).
+// stage).  Layer pairs share one packed f32x2 chain per station (far_pair,
+// the forward's per-pair operations).  Each lane sums its stations of one
+// stage in FP32, folds that stage sum into (hi, lo) by two-sum, and at the
+// end the 32 lane values are reduced by a warp-shuffle butterfly in FP64
+// (fixed order: deterministic).
 // ---------------------------------------------------------------------------
 template <int TZ, bool QUAD>
 __global__ void __launch_bounds__(kMaWarps * 32, MaMinBlocks<TZ>::value) k_madj(MixedGeo g, const float4 *__restrict__ st32,
@@ -306,10 +308,15 @@ __global__ void __launch_bounds__(kMaWarps * 32, MaMinBlocks<TZ>::value) k_madj(
     const int i = col % g.nx, j = col / g.nx;
     const float2 X = make_float2(g.cx[2 * i], g.cx[2 * i + 1]);
     const float2 Y = make_float2(g.cy[2 * j], g.cy[2 * j + 1]);
-    float zc[TZ], hi[TZ], lo[TZ];
+    static_assert(TZ % 2 == 0, "layer pairs");
+    const f2_t qg2 = f2_pack(g.qg, g.qg);
+    f2_t zcp[TZ / 2];
+    float hi[TZ], lo[TZ];
+#pragma unroll
+    for (int u = 0; u < TZ / 2; ++u)
+        zcp[u] = f2_pack(g.czc[min(l0 + 2 * u, g.nzp - 1)], g.czc[min(l0 + 2 * u + 1, g.nzp - 1)]);
 #pragma unroll
     for (int t = 0; t < TZ; ++t) {
-        zc[t] = g.czc[min(l0 + t, g.nzp - 1)];
         hi[t] = 0.f; lo[t] = 0.f;
     }
     const int64_t s0 = (int64_t)blockIdx.y * schunk_len;
@@ -351,27 +358,32 @@ __global__ void __launch_bounds__(kMaWarps * 32, MaMinBlocks<TZ>::value) k_madj(
         const float4 *pb = sxy + buf * kMaStage;
         const float2 *zb = szr + buf * kMaStage;
         if (gvalid) {
-            float cs[TZ];
+            f2_t cs2[TZ / 2];
 #pragma unroll
-            for (int t = 0; t < TZ; ++t) cs[t] = 0.f;
+            for (int u = 0; u < TZ / 2; ++u) cs2[u] = 0ull;
             for (int k = lane; k < cnt; k += 32) {
                 const float4 P = pb[k];
                 const float2 Z = zb[k];
-                const float h2 = far_h2(X, Y, P.x, P.y, P.z, P.w);
-                const float ph = QUAD ? far_ph(X, Y, P.x, P.y, P.z, P.w, g.qa, g.qb) : 0.0f;
-#pragma unroll
-                for (int t = 0; t < TZ; ++t) {
-                    const float dz = zc[t] - Z.x;
-                    const float R2 = fmaf(dz, dz, h2);
-                    cs[t] = fmaf(Z.y, far_k<QUAD>(dz, R2, g.qg, ph), cs[t]);
+                const float h = far_h2(X, Y, P.x, P.y, P.z, P.w);
+                const f2_t h2p = f2_pack(h, h), nz2 = f2_pack(-Z.x, -Z.x), w2 = f2_pack(Z.y, Z.y);
+                f2_t ph2 = 0ull;
+                if (QUAD) {
+                    const float ph = far_ph(X, Y, P.x, P.y, P.z, P.w, g.qa, g.qb);
+                    ph2 = f2_pack(ph, ph);
                 }
+#pragma unroll
+                for (int u = 0; u < TZ / 2; ++u) cs2[u] = far_pair<QUAD>(zcp[u], nz2, h2p, w2, cs2[u], qg2, ph2);
             }
 #pragma unroll
-            for (int t = 0; t < TZ; ++t) {
-                float s, e;
-                two_sum(hi[t], cs[t], s, e);
-                hi[t] = s;
-                lo[t] += e;
+            for (int u = 0; u < TZ / 2; ++u) {
+                float a, b, s, e;
+                f2_unpack(cs2[u], a, b);
+                two_sum(hi[2 * u], a, s, e);
+                hi[2 * u] = s;
+                lo[2 * u] += e;
+                two_sum(hi[2 * u + 1], b, s, e);
+                hi[2 * u + 1] = s;
+                lo[2 * u + 1] += e;
             }
         }
         __syncthreads();
@@ -1014,18 +1026,35 @@ int adj_tzl_bc(int nz) {
     return (rem + 3) / 4 * 4;
 }
 
-int adj_tz(int nz) {
-    if (GRAV_MA_TZ == 8 || GRAV_MA_TZ == 12 || GRAV_MA_TZ == 15 || GRAV_MA_TZ == 16) return GRAV_MA_TZ;
-    // TZ in {8, 12, 15, 16} minimising (padded layers) x (measured time per layer
-    // slot, relative): 8 -> 1.018, 12 -> 0.990, 15 -> 1.000, 16 -> 1.070
-    // (B300, 210 x 210 x 75 cells x 178,797 stations, 2.03 GHz).
-    const int tzs[4] = {8, 12, 15, 16};
-    const double per_slot[4] = {1.018, 0.990, 1.000, 1.070};
+// Layer group of the shuffle adjoint layout (small meshes): TZ in
+// {8, 10, 12, 14, 16} minimising the modelled time
+//   waves x TZ x stations per chunk x CTAs per SM x per-layer cost(TZ),
+// waves = ceil(CTAs / (148 x CTAs per SM)) with the station chunking that
+// mixed_sizes() applies.  It accounts for padded layers (ceil(nz/TZ) TZ >= nz)
+// and for a nearly empty last wave.  Per-layer costs measured on the packed
+// kernel (17 serving-sized meshes, 1.7k-43.9k columns, 2k-20k stations):
+// 8 and 10: 1.03, 12 and 14: 1.00, 16: 0.96; the model's choice was within
+// 0.4 % of the best of the five on average (4.9 % at worst).
+int adj_tz(int nz, int ncol, int64_t N) {
+    if (GRAV_MA_TZ == 8 || GRAV_MA_TZ == 10 || GRAV_MA_TZ == 12 || GRAV_MA_TZ == 14 || GRAV_MA_TZ == 16)
+        return GRAV_MA_TZ;
+    const int tzs[5] = {8, 10, 12, 14, 16};
+    const double cost[5] = {1.03, 1.03, 1.00, 1.00, 0.96};
     int best = 8;
     double bc = 1e300;
-    for (int q = 0; q < 4; ++q) {
-        const double c = std::ceil(nz / (double)tzs[q]) * tzs[q] * per_slot[q];
-        if (c < bc) { bc = c; best = tzs[q]; }
+    for (int q = 0; q < 5; ++q) {
+        const int T = tzs[q];
+        const int minb = T <= 8 ? 3 : 2;   // MaMinBlocks<T>
+        const int64_t ngz = (nz + T - 1) / T;
+        const int64_t ctas = ((int64_t)ncol * ngz + kMaWarps - 1) / kMaWarps;
+        int64_t nsch = std::max<int64_t>(1, (148LL * 8 + ctas - 1) / ctas);
+        nsch = std::min<int64_t>(nsch, std::max<int64_t>(1, (N + kMaStage - 1) / kMaStage));
+        int64_t len = (N + nsch - 1) / nsch;
+        len = (len + kMaStage - 1) / kMaStage * kMaStage;
+        nsch = (N + len - 1) / len;
+        const int64_t waves = (ctas * nsch + 148LL * minb - 1) / (148LL * minb);
+        const double c = (double)waves * T * (double)std::min<int64_t>(len, N) * minb * cost[q];
+        if (c < bc) { bc = c; best = T; }
     }
     return best;
 }
@@ -1065,7 +1094,7 @@ static MixedSizes mixed_sizes(const grav_plan *p) {
         if (std::strcmp(env, "broadcast") == 0) z.bc = 1;
         else if (std::strcmp(env, "shuffle") == 0) z.bc = 0;
     }
-    z.tz = z.bc ? tz_bc : adj_tz(p->nz);
+    z.tz = z.bc ? tz_bc : adj_tz(p->nz, ncol, p->N);
     z.ngz = (p->nz + z.tz - 1) / z.tz;
     int64_t nsch, stage;
     if (z.bc) {
@@ -1402,8 +1431,9 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
             constexpr bool Q = decltype(quad)::value;
             switch (p->m_adj_tz) {
                 case 16: go(k_madj<16, Q>); break;
-                case 15: go(k_madj<15, Q>); break;
+                case 14: go(k_madj<14, Q>); break;
                 case 12: go(k_madj<12, Q>); break;
+                case 10: go(k_madj<10, Q>); break;
                 default: go(k_madj<8, Q>); break;
             }
         };
