@@ -140,6 +140,7 @@ struct grav_plan {
     double *m_apart = nullptr;            // [nschunk][M] adjoint partials
     float *dG = nullptr;                  // [N][slots] near-field correction (mGal per kg/m^3), formed in FP64
     int *st_i0 = nullptr, *st_j0 = nullptr;   // box origin per station
+    int *near_off = nullptr;              // [slots] cell offset of each window-box slot from the box origin
     double *diag_corr = nullptr;          // [N] near-field correction of diag(G W^-2 G^T)
     int *bin_start = nullptr;             // [nbins+1]
     int *bin_st = nullptr;                // [N] station indices sorted by bin

@@ -822,15 +822,49 @@ __global__ void k_bin_bounds(const unsigned *__restrict__ ks, int64_t n, int nbi
 // are FP32 (FMA pipe), folded into an FP64 sum: the FP64 pipe (1/64 of the
 // FP32 rate on this GPU) does one addition per 16 terms instead of one FMA
 // per term.
+//
+// Stations whose box lies inside the mesh (all but those near its edges) take
+// a fast path when the slot count is a multiple of 4: the table row streams
+// in 16-byte loads (read once, evict-first), the cell of each slot comes from
+// the plan's slot-offset table off[t] = a + nx (bj + ny l) (L1-resident), and
+// no slot needs a bounds check.
 __global__ void __launch_bounds__(256) k_near_fwd(int nx, int ny, int nz, NearGeo ng, int64_t N,
                                                   const float *__restrict__ dG, const int *__restrict__ st_i0,
-                                                  const int *__restrict__ st_j0, const float *__restrict__ qn,
-                                                  double *__restrict__ corr) {
+                                                  const int *__restrict__ st_j0, const int *__restrict__ off,
+                                                  const float *__restrict__ qn, double *__restrict__ corr) {
     const int lane = threadIdx.x & 31;
     const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (s >= N) return;
     const int i0 = st_i0[s], j0 = st_j0[s];
     const float *gs = dG + s * ng.slots;
+    if ((ng.slots & 3) == 0 && i0 >= 0 && i0 + ng.bx <= nx && j0 >= 0 && j0 + ng.by <= ny && ng.bz <= nz) {
+        const float4 *g4 = reinterpret_cast<const float4 *>(gs);
+        const int4 *o4 = reinterpret_cast<const int4 *>(off);
+        const float *qb = qn + i0 + (int64_t)nx * j0;
+        const int n4 = ng.slots >> 2;
+        double acc = 0.0;
+        for (int v = lane; v < n4; v += 64) {   // 8 slots per lane and step, loads issued together
+            const bool two = v + 32 < n4;
+            const float4 G0 = __ldcs(g4 + v);
+            const int4 O0 = __ldg(o4 + v);
+            const float4 G1 = two ? __ldcs(g4 + v + 32) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int4 O1 = two ? __ldg(o4 + v + 32) : make_int4(0, 0, 0, 0);
+            const float q0 = qb[O0.x], q1 = qb[O0.y], q2 = qb[O0.z], q3 = qb[O0.w];
+            const float q4 = qb[O1.x], q5 = qb[O1.y], q6 = qb[O1.z], q7 = qb[O1.w];
+            float accf = G0.x * q0;
+            accf = fmaf(G0.y, q1, accf);
+            accf = fmaf(G0.z, q2, accf);
+            accf = fmaf(G0.w, q3, accf);
+            accf = fmaf(G1.x, q4, accf);
+            accf = fmaf(G1.y, q5, accf);
+            accf = fmaf(G1.z, q6, accf);
+            accf = fmaf(G1.w, q7, accf);
+            acc += (double)accf;   // FP32 runs of 8 terms folded into FP64
+        }
+        const double v = warp_sum(acc);
+        if (lane == 0) corr[s] = v;
+        return;
+    }
     const int qa = 32 % ng.bx, qr = 32 / ng.bx;
     int a = lane % ng.bx;
     const int r0 = lane / ng.bx;
@@ -1161,6 +1195,7 @@ size_t mixed_scratch_bytes(const grav_plan *p) {
     add(8ull * z.nschunk * M);                                              // m_apart
     add(4ull * N * p->ng.slots);                                            // dG (FP32)
     add(4ull * N); add(4ull * N);                                           // i0, j0
+    add(4ull * p->ng.slots);                                                // slot -> cell offset
     add(8ull * N); add(8ull * N);                                           // diag_corr, near_corr
     add(8ull * p->nx * p->ny * lz);                                         // near adjoint
     add(4ull * N); add(4ull * N); add(4ull * N); add(4ull * N);             // keys, keys_sorted, vals, bin_st
@@ -1238,6 +1273,7 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
     p->dG = (float *)take(p, 4ull * p->N * p->ng.slots);
     p->st_i0 = (int *)take(p, 4ull * p->N);
     p->st_j0 = (int *)take(p, 4ull * p->N);
+    p->near_off = (int *)take(p, 4ull * p->ng.slots);
     p->diag_corr = (double *)take(p, 8ull * p->N);
     p->near_corr = (double *)take(p, 8ull * p->N);
     const int64_t lz = std::min(p->ng.bz, nz);
@@ -1292,6 +1328,15 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
         p->mg.qg = p->cubic ? 0.0f : (float)((6.0 * c2 - 3.0 * a2 - 3.0 * b2) / 24.0);
     }
 
+    {
+        // slot t = a + bx (bj + by l) of a station's window box -> cell offset from its box origin
+        std::vector<int> hoff(p->ng.slots);
+        for (int l = 0; l < p->ng.bz; ++l)
+            for (int bj = 0; bj < p->ng.by; ++bj)
+                for (int a = 0; a < p->ng.bx; ++a)
+                    hoff[a + p->ng.bx * (bj + p->ng.by * l)] = a + nx * (bj + ny * l);
+        cudaMemcpyAsync(p->near_off, hoff.data(), 4ull * p->ng.slots, cudaMemcpyHostToDevice, s);
+    }
     cudaMemcpyAsync(p->m_cx, hcx.data(), 8ull * nx, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(p->m_cy, hcy.data(), 8ull * ny, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(p->m_czc, hcz.data(), 4ull * nzp, cudaMemcpyHostToDevice, s);
@@ -1370,7 +1415,8 @@ void launch_mixed_near_fwd(const grav_plan *p, const double *m, cudaStream_t s) 
     stage_begin(p, kStageFwdNear, s);
     (void)m;   // the near field reads the FP32 q that launch_mixed_prep_q formed from m
     k_near_fwd<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(p->nx, p->ny, p->nz, p->ng, p->N, p->dG,
-                                                                p->st_i0, p->st_j0, p->qN, p->near_corr);
+                                                                p->st_i0, p->st_j0, p->near_off, p->qN,
+                                                                p->near_corr);
     stage_end(p, kStageFwdNear, s);
     note_launches(1);
 }
