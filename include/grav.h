@@ -70,9 +70,12 @@ typedef struct CUstream_st *grav_stream_t;
  *   not cubes) with compensated (two-sum) accumulation; cells whose centre
  *   lies within near_cells cell widths (width = the largest cell edge) of a
  *   station are corrected to the exact FP64 prism value (Eq. 1) for that
- *   station.  CG dots and step lengths stay in FP64.  Requires a uniform mesh
- *   (constant dx, dy, dz; a x b x c cells with any a, b, c); GRAV_EINVAL
- *   otherwise.
+ *   station.  CG dots and step lengths stay in FP64.  The input vector (m for
+ *   the forward, r for the adjoint) is divided by its largest magnitude before
+ *   the FP32 arithmetic and the FP64 result multiplied back, so a product
+ *   scales exactly with a power-of-two scaling of its input at any magnitude.
+ *   Requires a uniform mesh (constant dx, dy, dz; a x b x c cells with any
+ *   a, b, c); GRAV_EINVAL otherwise.
  */
 #define GRAV_FP64    0
 #define GRAV_MIXED   1
@@ -81,7 +84,8 @@ typedef struct CUstream_st *grav_stream_t;
  *   node (node-shared) plus the same FP64 near-window correction as
  *   GRAV_MIXED.  Forward product only (grav_forward / grav_plan_forward); it
  *   exists to measure that scheme's error, which FP32 cancellation of the
- *   corner differences makes far larger than GRAV_MIXED's (see DESIGN). */
+ *   corner differences makes far larger than GRAV_MIXED's (2.8e-5 against
+ *   7.3e-7 of max|d| on an 80 x 80 x 40 mesh of 50 m cells, 6,561 stations). */
 #define GRAV_MIXED_CORNER 2
 
 /* ---- descriptors ---------------------------------------------------------- */

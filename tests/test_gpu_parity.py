@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
 same seeded inputs.
 
-Tolerances (stated in the spec requirement and restated here):
+Tolerances of the product's accuracy requirement:
   FP64 mode:  |d_gpu - d_oracle| <= 1e-10 * max|d_oracle|   (same for G^T r)
   mixed mode: |d_gpu - d_oracle| <= 1e-5  * max|d_oracle|
 Sizes span several CTA tiles with ragged tails; edge cases cover n = 1,
