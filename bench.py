@@ -66,7 +66,10 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=5000)
     ap.add_argument("--reorth", type=int, default=1000,
                     help="--invert: residuals kept for reorthogonalised CG (0 = plain CG)")
-    ap.add_argument("--precond", default="none", choices=["none", "jacobi"])
+    ap.add_argument("--precond", default="none", choices=["none", "jacobi", "nystrom"])
+    ap.add_argument("--nys-rank", type=int, default=0, help="--precond nystrom: sketch size (0: automatic)")
+    ap.add_argument("--nys-coarsen", type=int, default=0,
+                    help="--precond nystrom: coarsening factor per axis (0: automatic)")
     return ap.parse_args()
 
 
@@ -509,7 +512,8 @@ def run_invert(args):
     d = g.forward(m, wl.mesh, S, precision=data_prec, near_cells=args.near_cells)
     torch.cuda.synchronize()
     opts = dict(precision=args.precision, near_cells=args.near_cells, tol=args.tol, max_iter=args.max_iter,
-                precond=args.precond, check_stations=64, reorth=args.reorth)
+                precond=args.precond, check_stations=64, reorth=args.reorth, nys_rank=args.nys_rank,
+                nys_coarsen=args.nys_coarsen)
     t0 = time.perf_counter()
     m_out, info = g.datainv(d, wl.mesh, S, **opts)
     torch.cuda.synchronize()
@@ -517,6 +521,7 @@ def run_invert(args):
     misfit = g.forward(m_out, wl.mesh, S, precision=data_prec, near_cells=args.near_cells) - d
     line = {"metric": "inversion time to relative residual", "workload": args.workload,
             "precision": args.precision, "precond": args.precond, "reorth": args.reorth, "tol": args.tol,
+            "nys_rank": args.nys_rank if args.precond == "nystrom" else None,
             "seconds": wall,
             "iters": info["iters"],
             "converged": info["converged"], "true_rel_res": info["true_rel_res"], "lambda": info["lambda"],

@@ -113,7 +113,10 @@ typedef struct {
     int check_every;           /* host convergence check period in iterations (0 = automatic) */
     double near_cells;         /* GRAV_MIXED near-field radius in cell widths (default 8) */
     double timeout_s;          /* bound on every host wait of a call (default 3600 s) */
-    int precond;               /* CG preconditioner: 0 none, 1 Jacobi, diag(G W^-2 G^T + lambda I)^-1 (default 0) */
+    int precond;               /* CG preconditioner: 0 none, 1 Jacobi, diag(G W^-2 G^T + lambda I)^-1, 2 randomized
+                                  Nystrom (Frangella, Tropp and Udell 2023) of G W^-2 G^T from nys_rank products
+                                  with the operator on a mesh coarsened nys_coarsen times per axis (uniform
+                                  meshes; single CG solve; N*(nys_rank + reorth)*8 extra bytes) (default 0) */
     int cache_g;               /* GRAV_FP64 only: 1 = build G explicitly once (FP64, N*M*8 bytes) when it fits the
                                   context budget and stream it for every product; 0 = always recompute (default 0) */
     int outer_max;             /* > 0: the paper's outer model-update loop (Section 2.2): at most outer_max
@@ -129,6 +132,10 @@ typedef struct {
     int check_stations;        /* mixed modes, > 0: state the error of the result against the FP64 operator
                                   at this many evenly spaced stations (inversions: of G m_out; serving
                                   forward jobs: of d), in grav_solve_info.fp64_rel_err; 0 = off (default) */
+    int nys_rank;              /* precond = 2: sketch size ell (products with the coarse operator), 1..8192;
+                                  0 = automatic, N / 60 clamped to [100, 3000] (default 0) */
+    int nys_coarsen;           /* precond = 2: coarsening factor per axis of the sketch operator, 1..8;
+                                  0 = automatic, min(4, min(nx, ny, nz) / 8), at least 1 (default 0) */
 } grav_options;
 
 typedef struct {

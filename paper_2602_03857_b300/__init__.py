@@ -62,7 +62,8 @@ class grav_options(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("near_cells", ctypes.c_double), ("timeout_s", ctypes.c_double),
                 ("precond", ctypes.c_int), ("cache_g", ctypes.c_int), ("outer_max", ctypes.c_int),
-                ("inner_max", ctypes.c_int), ("reorth", ctypes.c_int), ("check_stations", ctypes.c_int)]
+                ("inner_max", ctypes.c_int), ("reorth", ctypes.c_int), ("check_stations", ctypes.c_int),
+                ("nys_rank", ctypes.c_int), ("nys_coarsen", ctypes.c_int)]
 
 
 class grav_job(ctypes.Structure):
@@ -320,18 +321,19 @@ class Survey:
 
 def options(precision="fp64", z0=50.0, lambda_scale=1e-2, lam=0.0, tol=1e-6, max_iter=1000,
             check_every=0, near_cells=8.0, timeout_s=3600.0, precond="none", cache_g=False, outer_max=0,
-            inner_max=20, reorth=1000, check_stations=0) -> grav_options:
+            inner_max=20, reorth=1000, check_stations=0, nys_rank=0, nys_coarsen=0) -> grav_options:
     o = grav_options()
     _lib.grav_options_default(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.z0, o.lambda_scale, o.lambda_ = float(z0), float(lambda_scale), float(lam)
     o.tol, o.max_iter, o.check_every = float(tol), int(max_iter), int(check_every)
     o.near_cells, o.timeout_s = float(near_cells), float(timeout_s)
-    o.precond = {"none": 0, "jacobi": 1}[precond] if isinstance(precond, str) else int(precond)
+    o.precond = {"none": 0, "jacobi": 1, "nystrom": 2}[precond] if isinstance(precond, str) else int(precond)
     o.cache_g = int(bool(cache_g))
     o.outer_max, o.inner_max = int(outer_max), int(inner_max)
     o.reorth = int(reorth)
     o.check_stations = int(check_stations)
+    o.nys_rank, o.nys_coarsen = int(nys_rank), int(nys_coarsen)
     return o
 
 

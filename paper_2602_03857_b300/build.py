@@ -35,7 +35,7 @@ def nvcc() -> str:
 
 
 def _flags(ptxas_verbose: bool = False):
-    f = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I" + INCLUDE, "-I" + CSRC,
+    f = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-fopenmp", "-I" + INCLUDE, "-I" + CSRC,
          "--expt-relaxed-constexpr", "-Xcudafe", "--diag_suppress=177"] + ARCH
     f += [x for x in os.environ.get("GRAV_NVCC_DEFINES", "").split() if x.startswith("-D")]
     if ptxas_verbose:
@@ -77,7 +77,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
                 if r.returncode != 0:
                     raise RuntimeError(f"nvcc failed on {cmd[2] if cmd[1] == '-c' else cmd[4]}")
     if relink or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        cmd = [nvcc(), "-shared", "-o", LIB + ".tmp"] + objs + ARCH + ["-Xcompiler", "-fPIC"]
+        cmd = [nvcc(), "-shared", "-o", LIB + ".tmp"] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lcublas", "-lgomp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)

@@ -37,7 +37,6 @@ double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// Polls `ev` until it completes or timeout_s elapses.
 // Polls the event until it completes or timeout_s passes.  The sleep between
 // polls is 1/16 of the time already waited (5 us .. 2 ms), so a wait ends at
 // most ~6 % (2 ms) after the event while long waits do not spin; a doubling
@@ -102,7 +101,12 @@ int check_options(grav_ctx *ctx, const grav_options &o) {
     if (!(o.near_cells >= 1.0 && o.near_cells <= 16.0))
         return set_error(ctx, GRAV_EINVAL, "near_cells must lie in [1, 16]");
     if (!(o.timeout_s > 0)) return set_error(ctx, GRAV_EINVAL, "timeout_s must be > 0");
-    if (o.precond != 0 && o.precond != 1) return set_error(ctx, GRAV_EINVAL, "precond must be 0 (none) or 1 (Jacobi)");
+    if (o.precond < 0 || o.precond > 2)
+        return set_error(ctx, GRAV_EINVAL, "precond must be 0 (none), 1 (Jacobi) or 2 (Nystrom)");
+    if (o.precond == 2 && (o.nys_rank < 0 || o.nys_rank > 8192))
+        return set_error(ctx, GRAV_EINVAL, "nys_rank must lie in [0 (automatic), 8192]");
+    if (o.precond == 2 && (o.nys_coarsen < 0 || o.nys_coarsen > 8))
+        return set_error(ctx, GRAV_EINVAL, "nys_coarsen must lie in [0 (automatic), 8]");
     if (o.cache_g != 0 && o.cache_g != 1) return set_error(ctx, GRAV_EINVAL, "cache_g must be 0 or 1");
     if (o.outer_max < 0 || o.outer_max > 100000) return set_error(ctx, GRAV_EINVAL, "outer_max must lie in [0, 1e5]");
     if (o.outer_max > 0 && o.inner_max < 1) return set_error(ctx, GRAV_EINVAL, "inner_max must be >= 1");
@@ -133,6 +137,10 @@ int empty_survey(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey
 }
 
 }  // namespace
+
+int host_wait(grav_ctx *ctx, cudaEvent_t ev, double timeout_s, const char *what) {
+    return wait_event(ctx, ev, timeout_s, what);
+}
 
 void note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
@@ -485,13 +493,15 @@ int plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey,
 // Basis vectors kept by the reorthogonalised CG (0: plain CG).
 int reorth_cap(const grav_plan *p) {
     const grav_options &o = p->opt;
-    if (o.reorth <= 0 || o.precond != 0 || o.outer_max > 0) return 0;
+    if (o.reorth <= 0 || o.precond == 1 || o.outer_max > 0) return 0;
     return (int)std::min<int64_t>(o.reorth, (int64_t)o.max_iter + 1);
 }
 
 size_t solve_bytes(const grav_plan *p) {
     const int cap = reorth_cap(p);
-    return 8ull * (12 * p->N + p->M + kDotBlocks + kSCount) + 16 * 256 + 8ull * cap * (p->N + 1) + 2 * 256;
+    // reorthogonalisation: one basis, two (residuals and preconditioned residuals) with precond = 2
+    const size_t bases = (p->opt.precond == 2 ? 2ull : 1ull) * cap * p->N;
+    return 8ull * (12 * p->N + p->M + kDotBlocks + kSCount) + 16 * 256 + 8ull * (bases + cap) + 3 * 256;
 }
 
 void plan_destroy(grav_plan *p, cudaStream_t s) {
@@ -562,6 +572,8 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
     const int cap = reorth_cap(p);
     double *Qb = cap ? (double *)ar.take(8ull * cap * N) : nullptr;   // reorthogonalisation basis [cap][N]
     double *cb = cap ? (double *)ar.take(8ull * cap) : nullptr;
+    double *Wb = (cap && o.precond == 2) ? (double *)ar.take(8ull * cap * N) : nullptr;   // M^-1 Qb rows
+    NysState ns;
     double *hsc = nullptr;     // [0, kSCount): synchronous reads; then two slots of the CG pipeline
     cudaMallocHost((void **)&hsc, 3 * 8 * kSCount);
     double *hpipe = hsc + kSCount;
@@ -590,8 +602,8 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
         }
         // lambda = lambda_scale * trace(G W^-2 G^T) / N; the diagonal also feeds
         // the Jacobi preconditioner M = diag(G W^-2 G^T + lambda I)
-        const bool pc = o.precond == 1;
-        if (!(lam > 0) || pc) {
+        const bool jac = o.precond == 1, nys = o.precond == 2, pc = jac || nys;
+        if (!(lam > 0) || jac) {
             if ((rc = plan_diag(p, dinv, s))) break;
             if (!(lam > 0)) {
                 launch_dot(dinv, nullptr, N, dp, sc + kSTrace, s);
@@ -603,8 +615,14 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
                     break;
                 }
             }
-            if (pc) vec_jacobi_inv(dinv, lam, N, dinv, s);
+            if (jac) vec_jacobi_inv(dinv, lam, N, dinv, s);
         }
+        if (nys && (rc = nys_build(p, lam, o.nys_rank, o.nys_coarsen, 0x243F6A8885A308D3ull, &ns, s))) break;
+        // z = M^-1 r: Jacobi or the Nystrom preconditioner
+        auto apply_prec = [&](const double *rv, double *z) {
+            if (nys) nys_apply(ns, rv, z, s);
+            else vec_mul(dinv, rv, N, z, s);
+        };
         double true_rel = 0.0;
         // one CG iteration on A x = b with x in `xv`, residual `rv`, direction pv
         auto cg_step = [&](double *xv, double *rv, int it_global) -> int {
@@ -615,7 +633,7 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             cg_alpha(sc, s);
             cg_update_yr(xv, rv, pv, Ap, N, sc, s);
             if (pc) {
-                vec_mul(dinv, rv, N, zv, s);
+                apply_prec(rv, zv);
                 launch_dot(rv, zv, N, dp, sc + kSRRNew, s);
                 launch_dot(rv, rv, N, dp, sc + kSResNew, s);
                 cg_beta(sc, it_global, kSResNew, s);
@@ -720,7 +738,7 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
         }
         launch_dot(dd, dd, N, dp, sc + kSBB0, s);
         if (pc) {
-            vec_mul(dinv, r, N, zv, s);
+            apply_prec(r, zv);
             cudaMemcpyAsync(pv, zv, 8ull * N, cudaMemcpyDeviceToDevice, s);
             launch_dot(r, zv, N, dp, sc + kSRR, s);
         } else {
@@ -733,10 +751,13 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
         cg_restart(sc, 0, s);
         int kb = 0;            // basis vectors stored (reorthogonalised CG)
         const bool reo = cap > 0;   // reorthogonalise (every restart starts a fresh basis)
-        if (reo) {
+        // first basis vector: r / sqrt(r.z) (and z / sqrt(r.z) with the Nystrom preconditioner)
+        auto basis_start = [&]() {
             cg_basis_append(Qb, r, N, sc, kSRR, s);
+            if (Wb) cg_basis_append(Wb, zv, N, sc, kSRR, s);
             kb = 1;
-        }
+        };
+        if (reo) basis_start();
         if ((rc = sync_scalars("cg start"))) break;
         if (hsc[kSFrozen] != 0.0) {
             converged = true;
@@ -766,10 +787,18 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
                         cg_alpha(sc, s);
                         cg_update_yr(y, r, pv, Ap, N, sc, s);
                         if (pc) {
-                            vec_mul(dinv, r, N, zv, s);
+                            // precond = 2: the residual is made orthogonal to the earlier ones in
+                            // the M^-1 inner product (r -= V (W^T r), twice) before z = M^-1 r
+                            if (reo) cg_reorth2(Wb, Qb, kb, N, r, cb, sc, s);
+                            apply_prec(r, zv);
                             launch_dot(r, zv, N, dp, sc + kSRRNew, s);
                             launch_dot(r, r, N, dp, sc + kSResNew, s);
                             cg_beta(sc, it, kSResNew, s, hist, hist_len);
+                            if (reo && kb < cap) {
+                                cg_basis_append(Qb + (size_t)kb * N, r, N, sc, kSRRNew, s);
+                                cg_basis_append(Wb + (size_t)kb * N, zv, N, sc, kSRRNew, s);
+                                ++kb;
+                            }
                             cg_update_p(pv, zv, N, sc, s);
                         } else {
                             if (reo) cg_reorth(Qb, kb, N, r, cb, sc, s);
@@ -819,10 +848,11 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             }
             converged = false;
             if (pc) {
-                vec_mul(dinv, r, N, zv, s);
+                apply_prec(r, zv);
                 cudaMemcpyAsync(pv, zv, 8ull * N, cudaMemcpyDeviceToDevice, s);
                 launch_dot(r, zv, N, dp, sc + kSRR, s);
                 cg_restart(sc, 0, s);
+                if (reo) basis_start();
             } else {
                 cudaMemcpyAsync(pv, r, 8ull * N, cudaMemcpyDeviceToDevice, s);
                 cg_restart(sc, 1, s);
@@ -835,11 +865,7 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
                 // Measured against plain CG after the restart: 539 instead of 688
                 // iterations at 210 x 210 x 75 x 178,797, 230 instead of 241 on
                 // the noisy 80 x 80 x 40 slab, equal where no restart happens.
-                if (reo) {
-                    kb = 0;
-                    cg_basis_append(Qb, r, N, sc, kSRR, s);
-                    kb = 1;
-                }
+                if (reo) basis_start();
             }
         }
         if (rc) break;
@@ -870,6 +896,7 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
         }
         rc = read_status(ctx, s, o.timeout_s);
     } while (false);
+    nys_free(p, &ns, s);
     cudaFreeAsync(base, s);
     ctx->hbm_used -= bytes;
     cudaEventDestroy(ev);
@@ -910,6 +937,8 @@ void grav_options_default(grav_options *o) {
     o->inner_max = 20;
     o->reorth = 1000;
     o->check_stations = 0;
+    o->nys_rank = 0;
+    o->nys_coarsen = 0;
 }
 
 const char *grav_version(void) { return "libgrav 0.1.0 (sm_103a)"; }

@@ -43,5 +43,10 @@ void vec_jacobi_inv(const double *diag, double lam, int64_t n, double *out, cuda
 constexpr int kReorthMaxBasis = 4096;
 void cg_reorth(const double *Q, int k, int64_t n, double *r, double *c, const double *sc, cudaStream_t s);
 void cg_basis_append(double *q_k, const double *r, int64_t n, const double *sc, int rr_slot, cudaStream_t s);
+// Preconditioned variant: r -= V^T (W r), twice, with V[j] = r_j / sqrt(r_j.z_j)
+// and W[j] = z_j / sqrt(r_j.z_j) (z = M^-1 r): makes r orthogonal to the earlier
+// residuals in the M^-1 inner product.
+void cg_reorth2(const double *W, const double *V, int k, int64_t n, double *r, double *c, const double *sc,
+                cudaStream_t s);
 
 }  // namespace grav

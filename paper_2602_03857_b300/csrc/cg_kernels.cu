@@ -203,6 +203,15 @@ void cg_reorth(const double *Q, int k, int64_t n, double *r, double *c, const do
     }
     note_launches(4);
 }
+void cg_reorth2(const double *W, const double *V, int k, int64_t n, double *r, double *c, const double *sc,
+                cudaStream_t s) {
+    if (k <= 0) return;
+    for (int pass = 0; pass < 2; ++pass) {
+        k_basis_coef<<<k, kDotThreads, 0, s>>>(W, n, r, c, sc);
+        k_basis_sub<<<vgrid(n), 256, 0, s>>>(V, k, n, c, r, sc);
+    }
+    note_launches(4);
+}
 void cg_basis_append(double *q_k, const double *r, int64_t n, const double *sc, int rr_slot, cudaStream_t s) {
     k_basis_append<<<vgrid(n), 256, 0, s>>>(q_k, r, n, sc, rr_slot); note_launches(1);
 }

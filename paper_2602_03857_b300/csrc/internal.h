@@ -181,6 +181,25 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
                   grav_solve_info *info, cudaStream_t s, const std::atomic<int> *cancel,
                   const double *y0 = nullptr, double *hist = nullptr, int hist_len = 0);
 
+// Randomized Nystrom preconditioner of G W^-2 G^T + lambda I (nystrom.cu):
+// Y_nu (N x ell), the Cholesky factor L of the ell x ell Woodbury matrix,
+// scratch t, the cuBLAS handle and the device block holding them.
+struct NysState {
+    int ell = 0;
+    int64_t N = 0;
+    double mu = 0.0, nu = 0.0;
+    double *Y = nullptr, *L = nullptr, *t = nullptr;
+    void *blas = nullptr;
+    char *mem = nullptr;
+    size_t bytes = 0;
+};
+size_t nys_bytes(int64_t N, int ell);
+int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState *st, cudaStream_t s);
+void nys_apply(const NysState &st, const double *r, double *z, cudaStream_t s);
+void nys_free(grav_plan *p, NysState *st, cudaStream_t s);
+// bounded host wait for an event (GRAV_ETIMEDOUT after timeout_s)
+int host_wait(grav_ctx *ctx, cudaEvent_t ev, double timeout_s, const char *what);
+
 // serving scheduler (serve.cpp)
 void serve_shutdown(grav_ctx *ctx);
 
