@@ -424,6 +424,16 @@ def extras(args, g, torch, wl, plan, d, line):
         "iters": info["iters"], "true_rel_res": info["true_rel_res"],
         "fp64_rel_err_of_predicted_data": info["fp64_rel_err"],
         "what": "one grav_datainv_solve call: plan set-up, trace, reorthogonalised CG, recovery"}
+    t0 = time.perf_counter()
+    mm, info = g.datainv(d3, wl3.mesh, S3, precision="mixed", tol=1e-6, max_iter=5000, check_stations=64,
+                         precond="nystrom")
+    torch.cuda.synchronize()
+    line["inversion_to_1e-6_150x150x60_nystrom"] = {
+        "workload": "dipdyke_150x150x60", "precision": "mixed", "seconds": time.perf_counter() - t0,
+        "iters": info["iters"], "true_rel_res": info["true_rel_res"],
+        "fp64_rel_err_of_predicted_data": info["fp64_rel_err"],
+        "what": "as above with the randomized Nystrom preconditioner (automatic rank and coarsening; sketch "
+                "included)"}
 
 
 def run_serve(args):
