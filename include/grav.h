@@ -133,9 +133,11 @@ typedef struct {
                                   at this many evenly spaced stations (inversions: of G m_out; serving
                                   forward jobs: of d), in grav_solve_info.fp64_rel_err; 0 = off (default) */
     int nys_rank;              /* precond = 2: sketch size ell (products with the coarse operator), 1..8192;
-                                  0 = automatic, N / 60 clamped to [100, 3000] (default 0) */
+                                  0 = automatic: GRAV_MIXED N / 60 clamped to [100, 3000], GRAV_FP64
+                                  min(3000, N / 2) (default 0) */
     int nys_coarsen;           /* precond = 2: coarsening factor per axis of the sketch operator, 1..8;
-                                  0 = automatic, min(4, min(nx, ny, nz) / 8), at least 1 (default 0) */
+                                  0 = automatic, min(4 (GRAV_MIXED) or 2 (GRAV_FP64), min(nx, ny, nz) / 8),
+                                  at least 1 (default 0) */
 } grav_options;
 
 typedef struct {

@@ -116,12 +116,21 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
     NvtxRange nv("grav::nystrom_build");
     const int64_t N = p->N;
     if (!p->uniform) return set_error(ctx, GRAV_EINVAL, "precond = 2 (Nystrom) needs a mesh of uniform cells");
-    // automatic sizes (0): rank N / 60 in [100, 3000]; coarsening min(4, smallest cell count / 8).
-    // Measured at 210 x 210 x 75 cells x 178,797 stations (inversion to 1e-6, mixed):
-    // (rank, coarsening) (1000, 2) 99.9 s, (2000, 3) 74.6 s, (3000, 3) 85.0 s, (3000, 4) 70.5 s,
-    // against 153 s without a preconditioner.
-    if (ell <= 0) ell = (int)std::min<int64_t>(3000, std::max<int64_t>(100, (N + 30) / 60));
-    if (cf <= 0) cf = std::max(1, std::min(4, std::min(p->nx, std::min(p->ny, p->nz)) / 8));
+    // Automatic sizes (0).  The sketch products run on the mixed coarse
+    // operator, so their cost relative to one CG iteration is ~1/cf^3 in mixed
+    // mode but ~1/(600 cf^3) in FP64 mode, where a large sketch is nearly free.
+    //   mixed: rank N / 60 in [100, 3000], coarsening min(4, smallest cell count / 8);
+    //   FP64:  rank min(3000, N / 2), coarsening min(2, smallest cell count / 8).
+    // Measured (inversion to 1e-6; without a preconditioner in brackets):
+    //   210 x 210 x 75 cells x 178,797 stations, mixed: (rank, coarsening) (1000, 2)
+    //   99.9 s, (2000, 3) 74.6 s, (3000, 3) 85.0 s, (3000, 4) 70.5 s [153 s];
+    //   80 x 80 x 40 x 6,561, FP64: (109, 4) 119 s, (1500, 2) 30.4 s, (3000, 2) 24.4 s [99 s].
+    const bool f64 = p->opt.precision == GRAV_FP64;
+    const int mmin = std::min(p->nx, std::min(p->ny, p->nz));
+    if (ell <= 0)
+        ell = f64 ? (int)std::min<int64_t>(3000, std::max<int64_t>(1, N / 2))
+                  : (int)std::min<int64_t>(3000, std::max<int64_t>(100, (N + 30) / 60));
+    if (cf <= 0) cf = std::max(1, std::min(f64 ? 2 : 4, mmin / 8));
     ell = (int)std::min<int64_t>(ell, N);
     if (ell < 1 || cf < 1) return set_error(ctx, GRAV_EINVAL, "Nystrom rank and coarsening must be >= 1");
     *st = NysState{};
