@@ -23,7 +23,7 @@
 //   with one ell x ell Cholesky factor T = L L^T (on the host).  Applying it
 //   costs two GEMVs with the N x ell matrix Y_nu and two triangular solves.
 //
-// cuBLAS supplies the two ell x ell GEMMs and the GEMV / TRSV of the
+// cuBLAS supplies the ell x ell GEMM and rank-k update and the GEMV / TRSV of the
 // application (plain library dense algebra); the sketch products are this
 // library's operator kernels.
 #include <cublas_v2.h>
@@ -223,10 +223,11 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
         k_axpby_n<<<grid_n(N * ell), 256, 0, s>>>(1.0, st->Y, st->nu, Om, N * ell);   // Y_nu
         note_launches(1);
         const double one = 1.0, zero = 0.0;
+        // M = Omega^T Y_nu (full), Y_nu^T Y_nu (lower triangle only: symmetric rank-k update)
         if (cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, ell, ell, (int)N, &one, Om, (int)N, st->Y, (int)N, &zero, Mm,
                         ell) != CUBLAS_STATUS_SUCCESS ||
-            cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, ell, ell, (int)N, &one, st->Y, (int)N, st->Y, (int)N, &zero, YY,
-                        ell) != CUBLAS_STATUS_SUCCESS) {
+            cublasDsyrk(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, ell, (int)N, &one, st->Y, (int)N, &zero, YY, ell) !=
+                CUBLAS_STATUS_SUCCESS) {
             rc = set_error(ctx, GRAV_EDEVICE, "cuBLAS GEMM failed in the Nystrom set-up");
             break;
         }
@@ -234,12 +235,13 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
         cudaMemcpyAsync(hYY.data(), YY, 8ull * ell * ell, cudaMemcpyDeviceToHost, s);
         cudaEventRecord(ev, s);
         if ((rc = host_wait(ctx, ev, p->opt.timeout_s, "Nystrom Gram matrices"))) break;
-        // T = mu sym(M) + sym(Y^T Y) (column-major results; symmetric, so row-major reads agree)
+        // T = mu sym(M) + Y^T Y (column-major results; the rank-k update filled
+        // the lower triangle, (i, j) with i >= j at i + ell j)
         std::vector<double> T((size_t)ell * ell);
         for (int i = 0; i < ell; ++i)
             for (int j = 0; j < ell; ++j) {
                 const size_t ij = (size_t)i + (size_t)ell * j, ji = (size_t)j + (size_t)ell * i;
-                T[(size_t)i * ell + j] = st->mu * 0.5 * (hM[ij] + hM[ji]) + 0.5 * (hYY[ij] + hYY[ji]);
+                T[(size_t)i * ell + j] = st->mu * 0.5 * (hM[ij] + hM[ji]) + (i >= j ? hYY[ij] : hYY[ji]);
             }
         if (!cholesky_rowmajor(T, ell)) {
             rc = set_error(ctx, GRAV_EDEVICE, "Nystrom matrix T is not positive definite (rank %d)", ell);
