@@ -116,7 +116,9 @@ typedef struct {
     int precond;               /* CG preconditioner: 0 none, 1 Jacobi, diag(G W^-2 G^T + lambda I)^-1, 2 randomized
                                   Nystrom (Frangella, Tropp and Udell 2023) of G W^-2 G^T from nys_rank products
                                   with the operator on a mesh coarsened nys_coarsen times per axis (uniform
-                                  meshes; single CG solve; N*(nys_rank + reorth)*8 extra bytes) (default 0) */
+                                  meshes; single CG solve; N*(nys_rank + reorth)*8 extra bytes, and during
+                                  the set-up 8*N*nys_rank bytes more plus one block of the explicit coarse
+                                  operator of at most 4 GB) (default 0) */
     int cache_g;               /* GRAV_FP64 only: 1 = build G explicitly once (FP64, N*M*8 bytes) when it fits the
                                   context budget and stream it for every product; 0 = always recompute (default 0) */
     int outer_max;             /* > 0: the paper's outer model-update loop (Section 2.2): at most outer_max
@@ -136,8 +138,8 @@ typedef struct {
                                   0 = automatic: GRAV_MIXED N / 60 clamped to [100, 3000], GRAV_FP64
                                   min(3000, N / 2) (default 0) */
     int nys_coarsen;           /* precond = 2: coarsening factor per axis of the sketch operator, 1..8;
-                                  0 = automatic, min(4 (GRAV_MIXED) or 2 (GRAV_FP64), min(nx, ny, nz) / 8),
-                                  at least 1 (default 0) */
+                                  0 = automatic: GRAV_MIXED min(3, min(nx, ny, nz) / 8), at least 1;
+                                  GRAV_FP64 1 (default 0) */
 } grav_options;
 
 typedef struct {

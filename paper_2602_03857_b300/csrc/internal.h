@@ -182,7 +182,7 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
                   const double *y0 = nullptr, double *hist = nullptr, int hist_len = 0);
 
 // Randomized Nystrom preconditioner of G W^-2 G^T + lambda I (nystrom.cu):
-// Y_nu (N x ell), the Cholesky factor L of the ell x ell Woodbury matrix,
+// Y (N x ell), the Cholesky factor L of the ell x ell Woodbury matrix,
 // scratch t, the cuBLAS handle and the device block holding them.
 struct NysState {
     int ell = 0;
@@ -194,6 +194,8 @@ struct NysState {
     size_t bytes = 0;
 };
 size_t nys_bytes(int64_t N, int ell);
+void nys_sizes(const grav_plan *p, int *ell, int *cf);   // resolves the automatic (0) rank and coarsening
+size_t nys_peak_bytes(const grav_plan *p);               // persistent + set-up HBM of nys_build
 int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState *st, cudaStream_t s);
 void nys_apply(const NysState &st, const double *r, double *z, cudaStream_t s);
 void nys_free(grav_plan *p, NysState *st, cudaStream_t s);

@@ -15,17 +15,32 @@
 //   carries K's leading eigenvectors.
 // * Omega is Gaussian scaled by 1/sqrt(N) (no orthonormalisation: for
 //   N >> ell its columns are already nearly orthonormal, and K_hat does not
-//   depend on a change of basis of Omega's range); Y_nu = Y + nu Omega with
-//   nu = sqrt(N) eps ||Y||_F keeps Omega^T Y_nu positive definite.
-// * P^-1 by the Woodbury identity applied to K_hat = Y_nu M^-1 Y_nu^T,
-//   M = Omega^T Y_nu:  (mu I + Y_nu M^-1 Y_nu^T)^-1 r
-//     = (r - Y_nu T^-1 Y_nu^T r) / mu,  T = mu M + Y_nu^T Y_nu,  mu = lambda - nu,
+//   depend on a change of basis of Omega's range).
+// * With K_c = B B^T and Z = B^T Omega, the Nystrom approximation
+//   K Omega (Omega^T K Omega)^-1 Omega^T K is Y M^-1 Y^T with Y = B Z and
+//   M = Z^T Z.  M is formed as a Gram matrix (positive semidefinite whatever
+//   the rounding of Z), and K_hat = Y (M + nu I)^-1 Y^T is positive
+//   semidefinite for any Y; the shift nu (1e-3 lambda, raised if the
+//   factorisation needs it) only shrinks K_hat in directions whose Rayleigh
+//   quotient is far below lambda, where P is lambda I either way.  (The
+//   published method shifts Y by nu Omega instead; with FP32 products the
+//   Gram form is what keeps T positive definite when ell is a large share
+//   of N.)
+// * P^-1 by the Woodbury identity applied to K_hat:
+//     (lambda I + Y M_nu^-1 Y^T)^-1 r = (r - Y T^-1 Y^T r) / lambda,
+//     T = lambda M_nu + Y^T Y,
 //   with one ell x ell Cholesky factor T = L L^T (on the host).  Applying it
-//   costs two GEMVs with the N x ell matrix Y_nu and two triangular solves.
+//   costs two GEMVs with the N x ell matrix Y and two triangular solves.
+// * The ell sketch products Y = K_c Omega share every pair term: the coarse
+//   operator is formed explicitly, one block of cells at a time, as
+//   B = G_c W_c^-1 / cf^(3/2) in FP32 (K_c = B B^T; far term plus the coarse
+//   plan's near-field table, the entries the coarse mixed operator applies),
+//   and Y = sum_b B_b (B_b^T Omega) by two FP32 GEMMs per block.  One pair
+//   evaluation then serves all ell columns instead of one, and the products
+//   run at the FP32 GEMM rate.
 //
-// cuBLAS supplies the ell x ell GEMM and rank-k update and the GEMV / TRSV of the
-// application (plain library dense algebra); the sketch products are this
-// library's operator kernels.
+// cuBLAS supplies the GEMMs and the GEMV / TRSV of the application (plain
+// library dense algebra).
 #include <cublas_v2.h>
 #include <cuda_runtime.h>
 
@@ -34,6 +49,7 @@
 #include <vector>
 
 #include "cg.h"
+#include "device_common.cuh"
 #include "internal.h"
 
 namespace grav {
@@ -48,26 +64,78 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     return x ^ (x >> 31);
 }
 
-// out[i] = scale * N(0, 1) from the Box-Muller transform of two uniforms
-// drawn from counters 2i and 2i+1 of the stream `seed` (deterministic).
-__global__ void k_randn(double *__restrict__ out, int64_t n, uint64_t seed, double scale) {
+// out[i] = scale * N(0, 1) (rounded to FP32) from the Box-Muller transform of
+// two uniforms drawn from counters 2i and 2i+1 of the stream `seed`
+// (deterministic).
+__global__ void k_randn32(float *__restrict__ out, int64_t n, uint64_t seed, double scale) {
     const double two_pi = 6.283185307179586476925286766559;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t a = splitmix64(seed ^ (2ull * (uint64_t)i));
         const uint64_t b = splitmix64(seed ^ (2ull * (uint64_t)i + 1ull));
         const double u1 = ((double)(a >> 11) + 1.0) * 0x1.0p-53;   // (0, 1]
         const double u2 = (double)(b >> 11) * 0x1.0p-53;           // [0, 1)
-        out[i] = scale * sqrt(-2.0 * log(u1)) * cos(two_pi * u2);
+        out[i] = (float)(scale * sqrt(-2.0 * log(u1)) * cos(two_pi * u2));
     }
 }
 
-// y = a * y + b * x
-__global__ void k_axpby_n(double a, double *__restrict__ y, double b, const double *__restrict__ x, int64_t n) {
+inline unsigned grid_n(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 148LL * 32)); }
+
+__global__ void k_widen(const float *__restrict__ x, double *__restrict__ y, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = a * y[i] + b * x[i];
+        y[i] = (double)x[i];
 }
 
-inline unsigned grid_n(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 148LL * 32)); }
+// Explicit block of the scaled coarse operator B = G_c W_c^-1 / cf^(3/2)
+// (K_c = B B^T), cells c0 <= c < c0 + cb in natural order, column-major
+// B[(c - c0) N + s] (FP32).  The far part is the mixed operator's own FP32
+// point-mass (+ quadrupole) term of the pair; fac[l] = gamma V (zc_l + z0) / cf^1.5.
+constexpr int kNysCells = 16;   // cells per thread
+
+template <bool QUAD>
+__global__ void __launch_bounds__(256) k_nys_far(MixedGeo g, const float4 *__restrict__ st32,
+                                                 const float2 *__restrict__ stz, int64_t N, int64_t c0, int cb,
+                                                 const float *__restrict__ fac, float *__restrict__ B) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const float4 S = st32[s];
+    const float zs = stz[s].x;
+    const int k0 = blockIdx.y * kNysCells, k1 = min(cb, k0 + kNysCells);
+    for (int k = k0; k < k1; ++k) {
+        const int64_t c = c0 + k;
+        const int col = (int)(c % g.ncol), l = (int)(c / g.ncol);
+        const int i = col % g.nx, j = col / g.nx;
+        const float2 X = make_float2(g.cx[2 * i], g.cx[2 * i + 1]);
+        const float2 Y = make_float2(g.cy[2 * j], g.cy[2 * j + 1]);
+        const float dx = (X.x - S.x) + (X.y - S.y);
+        const float dy = (Y.x - S.z) + (Y.y - S.w);
+        const float h2 = fmaf(dx, dx, dy * dy);
+        const float ph = QUAD ? far_ph(X, Y, S.x, S.y, S.z, S.w, g.qa, g.qb) : 0.0f;
+        const float dz = g.czc[l] - zs;
+        const float R2 = fmaf(dz, dz, h2);
+        B[(int64_t)k * N + s] = far_k<QUAD>(dz, R2, g.qg, ph) * fac[l];
+    }
+}
+
+// Adds the near-field correction table of the coarse plan (exact prism minus
+// the far term, per unit gamma V) to the block; one warp per station, each
+// (station, cell) pair is touched by one lane only.
+__global__ void __launch_bounds__(256) k_nys_near(int nx, int ny, int nz, NearGeo ng, int64_t N,
+                                                  const float *__restrict__ dG, const int *__restrict__ st_i0,
+                                                  const int *__restrict__ st_j0, int64_t c0, int cb,
+                                                  const float *__restrict__ fac, float *__restrict__ B) {
+    const int lane = threadIdx.x & 31;
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= N) return;
+    const int i0 = st_i0[s], j0 = st_j0[s];
+    for (int t = lane; t < ng.slots; t += 32) {
+        const int i = i0 + t % ng.bx, j = j0 + (t / ng.bx) % ng.by, l = t / (ng.bx * ng.by);
+        if (i < 0 || i >= nx || j < 0 || j >= ny || l >= nz) continue;
+        const int64_t k = (int64_t)i + (int64_t)nx * (j + (int64_t)ny * l) - c0;
+        if (k < 0 || k >= cb) continue;
+        const float d = dG[s * ng.slots + t];
+        if (d != 0.0f) B[k * N + s] += d * fac[l];
+    }
+}
 
 // sum_k a[k] b[k], k < n, in four interleaved partial sums
 inline double dot4(const double *a, const double *b, int n) {
@@ -106,9 +174,41 @@ bool cholesky_rowmajor(std::vector<double> &A, int n) {
 
 }  // namespace
 
+// Automatic sizes (0).  The sketch costs 4 N M_c ell FP32 GEMM flops plus an
+// FP64 Gram of ell^2 (N + M_c); a CG iteration costs two products with the
+// fine operator, ~0.3 s (mixed) or ~0.9 s (FP64) at the sizes below, so FP64
+// solves sketch the uncoarsened operator.
+//   mixed: rank N / 60 in [100, 3000], coarsening min(3, smallest cell count / 8);
+//   FP64:  rank min(3000, N / 2), coarsening 1.
+// Measured (inversion to 1e-6; without a preconditioner in brackets):
+//   210 x 210 x 75 cells x 178,797 stations, mixed, rank 2980, coarsening 2 / 3 / 4:
+//   96 / 103 / 122 iterations, 49.2 / 37.9 / 40.4 s [539, 153 s];
+//   80 x 80 x 40 x 6,561, FP64, rank 3000, coarsening 1 / 2: 13 / 26 iterations,
+//   16.1 / 23.6 s [128, 99 s].
+void nys_sizes(const grav_plan *p, int *ell, int *cf) {
+    const bool f64 = p->opt.precision == GRAV_FP64;
+    const int64_t N = p->N;
+    const int mmin = std::min(p->nx, std::min(p->ny, p->nz));
+    if (*ell <= 0)
+        *ell = f64 ? (int)std::min<int64_t>(3000, std::max<int64_t>(1, N / 2))
+                   : (int)std::min<int64_t>(3000, std::max<int64_t>(100, (N + 30) / 60));
+    if (*cf <= 0) *cf = f64 ? 1 : std::max(1, std::min(3, mmin / 8));
+    *ell = (int)std::min<int64_t>(*ell, N);
+}
+
 size_t nys_bytes(int64_t N, int ell) {
-    // persistent part: Y_nu (N x ell), L (ell x ell), t (ell)
+    // persistent part: Y (N x ell), L (ell x ell), t (ell)
     return 8ull * ((size_t)N * ell + (size_t)ell * ell + ell) + 3 * 256;
+}
+
+size_t nys_peak_bytes(const grav_plan *p) {
+    int ell = p->opt.nys_rank, cf = p->opt.nys_coarsen;
+    nys_sizes(p, &ell, &cf);
+    if (ell < 1 || cf < 1) return 0;
+    const int64_t N = p->N;
+    const int64_t Mc = (int64_t)((p->nx + cf - 1) / cf) * ((p->ny + cf - 1) / cf) * ((p->nz + cf - 1) / cf);
+    const int64_t cb = std::min<int64_t>({Mc, (1ll << 30) / N, (1ll << 27) / ell, 65535ll * kNysCells});
+    return nys_bytes(N, ell) + 8ull * N * ell + 16ull * ell * ell + 4ull * cb * N + 12ull * cb * ell + (1u << 20);
 }
 
 int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState *st, cudaStream_t s) {
@@ -116,22 +216,7 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
     NvtxRange nv("grav::nystrom_build");
     const int64_t N = p->N;
     if (!p->uniform) return set_error(ctx, GRAV_EINVAL, "precond = 2 (Nystrom) needs a mesh of uniform cells");
-    // Automatic sizes (0).  The sketch products run on the mixed coarse
-    // operator, so their cost relative to one CG iteration is ~1/cf^3 in mixed
-    // mode but ~1/(600 cf^3) in FP64 mode, where a large sketch is nearly free.
-    //   mixed: rank N / 60 in [100, 3000], coarsening min(4, smallest cell count / 8);
-    //   FP64:  rank min(3000, N / 2), coarsening min(2, smallest cell count / 8).
-    // Measured (inversion to 1e-6; without a preconditioner in brackets):
-    //   210 x 210 x 75 cells x 178,797 stations, mixed: (rank, coarsening) (1000, 2)
-    //   99.9 s, (2000, 3) 74.6 s, (3000, 3) 85.0 s, (3000, 4) 70.5 s [153 s];
-    //   80 x 80 x 40 x 6,561, FP64: (109, 4) 119 s, (1500, 2) 30.4 s, (3000, 2) 24.4 s [99 s].
-    const bool f64 = p->opt.precision == GRAV_FP64;
-    const int mmin = std::min(p->nx, std::min(p->ny, p->nz));
-    if (ell <= 0)
-        ell = f64 ? (int)std::min<int64_t>(3000, std::max<int64_t>(1, N / 2))
-                  : (int)std::min<int64_t>(3000, std::max<int64_t>(100, (N + 30) / 60));
-    if (cf <= 0) cf = std::max(1, std::min(f64 ? 2 : 4, mmin / 8));
-    ell = (int)std::min<int64_t>(ell, N);
+    nys_sizes(p, &ell, &cf);
     if (ell < 1 || cf < 1) return set_error(ctx, GRAV_EINVAL, "Nystrom rank and coarsening must be >= 1");
     *st = NysState{};
     st->ell = ell;
@@ -157,12 +242,22 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
     const int64_t Mc = (int64_t)nxc * nyc * nzc;
     // persistent block
     st->bytes = nys_bytes(N, ell);
-    // temporary block: Omega (N x ell), q (Mc), M and Y^T Y (ell x ell each), dot partials, scalar
-    const size_t tmp_bytes = 8ull * ((size_t)N * ell + Mc + 2ull * ell * ell + kDotBlocks + 8) + 5 * 256;
-    if (ctx->hbm_used.load() + st->bytes + tmp_bytes > ctx->hbm_budget) {
+    // temporary block: Omega and Y (FP32, N x ell), M and Y^T Y (ell x ell),
+    // the FP32 layer factors, then a cell block of B (N x cb, FP32) and
+    // Z_b = B_b^T Omega (cb x ell, FP32 and FP64) sized to what the budget
+    // leaves (cb <= 2^30 / N: one block at most 4 GB)
+    const size_t fixed_bytes = 8ull * N * ell + 16ull * ell * ell + 4ull * nzc + 6 * 256;
+    const size_t used = ctx->hbm_used.load() + st->bytes + fixed_bytes;
+    const size_t left = ctx->hbm_budget > used ? ctx->hbm_budget - used : 0;
+    int64_t cb = std::min<int64_t>({Mc, (1ll << 30) / N, (1ll << 27) / ell, 65535ll * kNysCells,
+                                    (int64_t)(left / (4ull * N + 12ull * ell))});
+    if (cb < std::min<int64_t>(Mc, 64)) {
         plan_destroy(cp, s);
         return set_error(ctx, GRAV_ENOMEM, "Nystrom preconditioner (rank %d) exceeds the HBM budget", ell);
     }
+    const int64_t nblk = (Mc + cb - 1) / cb;
+    cb = (Mc + nblk - 1) / nblk;   // equal blocks
+    const size_t tmp_bytes = fixed_bytes + 4ull * cb * N + 12ull * cb * ell + 3 * 256;
     char *tmp = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync((void **)&st->mem, st->bytes, ctx->pool, s);
     if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void **)&tmp, tmp_bytes, ctx->pool, s);
@@ -180,15 +275,22 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
     st->t = (double *)pa.take(8ull * ell);
     Arena ta;
     ta.base = tmp; ta.size = tmp_bytes;
-    double *Om = (double *)ta.take(8ull * N * ell);
-    double *qc = (double *)ta.take(8ull * Mc);
+    float *Om32 = (float *)ta.take(4ull * N * ell);
+    float *Y32 = (float *)ta.take(4ull * N * ell);
     double *Mm = (double *)ta.take(8ull * ell * ell);
-    double *YY = (double *)ta.take(8ull * ell * ell);
-    double *dp = (double *)ta.take(8ull * kDotBlocks);
-    double *sc = (double *)ta.take(64);
+    double *Gy = (double *)ta.take(8ull * ell * ell);
+    float *fac = (float *)ta.take(4ull * nzc);
+    float *Bb = (float *)ta.take(4ull * N * cb);
+    float *Zb = (float *)ta.take(4ull * cb * ell);
+    double *Zd = (double *)ta.take(8ull * cb * ell);
+    // fac[l] = gamma V_c (zc_l + z0) / cf^(3/2): K ~ G_c W_c^-2 G_c^T / cf^3 = B B^T
+    std::vector<float> hfac(nzc);
+    const double vol_mgal = kGammaMgal * cp->cell_a * cp->cell_b * cp->cell_c;
+    for (int l = 0; l < nzc; ++l)
+        hfac[l] = (float)(vol_mgal * (0.5 * (zc[l] + zc[l + 1]) - zc[0] + p->opt.z0) / std::pow((double)cf, 1.5));
+    cudaMemcpyAsync(fac, hfac.data(), 4ull * nzc, cudaMemcpyHostToDevice, s);
     cublasHandle_t h = nullptr;
-    std::vector<double> hM((size_t)ell * ell), hYY((size_t)ell * ell);
-    double *hs = nullptr;
+    std::vector<double> hM((size_t)ell * ell), hG((size_t)ell * ell);
     cudaEvent_t ev = nullptr;
     do {
         if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) {
@@ -197,53 +299,64 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
         }
         st->blas = h;
         cublasSetStream(h, s);
-        // Omega ~ N(0, 1/N); Y = K_c Omega column by column (depth-weighted adjoint, then forward)
-        k_randn<<<grid_n(N * ell), 256, 0, s>>>(Om, N * ell, seed, 1.0 / std::sqrt((double)N));
+        cublasSetMathMode(h, CUBLAS_DEFAULT_MATH);   // FP32 GEMMs in FP32 (no TF32)
+        k_randn32<<<grid_n(N * ell), 256, 0, s>>>(Om32, N * ell, seed, 1.0 / std::sqrt((double)N));
         note_launches(1);
-        for (int j = 0; j < ell && !rc; ++j) {
-            rc = plan_adjoint_ex(cp, Om + (size_t)j * N, qc, 1, nullptr, s);
-            if (!rc) rc = plan_forward_ex(cp, qc, st->Y + (size_t)j * N, nullptr, 0.0, s);
+        // per cell block: B_b; Z_b = B_b^T Omega; Y += B_b Z_b; M += Z_b^T Z_b (FP64)
+        const float onef = 1.0f, zerof = 0.0f;
+        const double one = 1.0, zero = 0.0;
+        for (int64_t b = 0; b < nblk && !rc; ++b) {
+            const int64_t c0 = b * cb;
+            const int nb = (int)std::min<int64_t>(cb, Mc - c0);
+            dim3 gf((unsigned)((N + 255) / 256), (unsigned)((nb + kNysCells - 1) / kNysCells));
+            if (cp->cubic)
+                k_nys_far<false><<<gf, 256, 0, s>>>(cp->mg, cp->st32, cp->stz, N, c0, nb, fac, Bb);
+            else
+                k_nys_far<true><<<gf, 256, 0, s>>>(cp->mg, cp->st32, cp->stz, N, c0, nb, fac, Bb);
+            k_nys_near<<<(unsigned)((N * 32 + 255) / 256), 256, 0, s>>>(nxc, nyc, nzc, cp->ng, N, cp->dG, cp->st_i0,
+                                                                      cp->st_j0, c0, nb, fac, Bb);
+            const float betaf = b ? 1.0f : 0.0f;
+            const double beta = b ? 1.0 : 0.0;
+            bool ok = cublasSgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, nb, ell, (int)N, &onef, Bb, (int)N, Om32, (int)N,
+                                  &zerof, Zb, nb) == CUBLAS_STATUS_SUCCESS;
+            ok = ok && cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, ell, nb, &onef, Bb, (int)N, Zb, nb, &betaf,
+                                   Y32, (int)N) == CUBLAS_STATUS_SUCCESS;
+            k_widen<<<grid_n((int64_t)nb * ell), 256, 0, s>>>(Zb, Zd, (int64_t)nb * ell);
+            note_launches(3);
+            ok = ok && cublasDsyrk(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, ell, nb, &one, Zd, nb, &beta, Mm, ell) ==
+                           CUBLAS_STATUS_SUCCESS;
+            if (!ok) rc = set_error(ctx, GRAV_EDEVICE, "cuBLAS failed in the Nystrom sketch");
         }
         if (rc) break;
-        const double inv_c3 = 1.0 / ((double)cf * cf * cf);
-        k_axpby_n<<<grid_n(N * ell), 256, 0, s>>>(inv_c3, st->Y, 0.0, Om, N * ell);
-        launch_dot(st->Y, st->Y, N * ell, dp, sc, s);
+        k_widen<<<grid_n(N * ell), 256, 0, s>>>(Y32, st->Y, N * ell);
         note_launches(1);
-        cudaMallocHost((void **)&hs, 64);
-        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        cudaMemcpyAsync(hs, sc, 8, cudaMemcpyDeviceToHost, s);
-        cudaEventRecord(ev, s);
-        if ((rc = host_wait(ctx, ev, p->opt.timeout_s, "Nystrom sketch"))) break;
-        st->nu = std::sqrt((double)N) * 2.220446049250313e-16 * std::sqrt(std::max(hs[0], 0.0));
-        st->mu = lam - st->nu;
-        if (!(st->mu > 0.0) || !std::isfinite(st->mu)) {
-            rc = set_error(ctx, GRAV_EDEVICE, "Nystrom shift %g not below lambda %g", st->nu, lam);
-            break;
-        }
-        k_axpby_n<<<grid_n(N * ell), 256, 0, s>>>(1.0, st->Y, st->nu, Om, N * ell);   // Y_nu
-        note_launches(1);
-        const double one = 1.0, zero = 0.0;
-        // M = Omega^T Y_nu (full), Y_nu^T Y_nu (lower triangle only: symmetric rank-k update)
-        if (cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, ell, ell, (int)N, &one, Om, (int)N, st->Y, (int)N, &zero, Mm,
-                        ell) != CUBLAS_STATUS_SUCCESS ||
-            cublasDsyrk(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, ell, (int)N, &one, st->Y, (int)N, &zero, YY, ell) !=
-                CUBLAS_STATUS_SUCCESS) {
-            rc = set_error(ctx, GRAV_EDEVICE, "cuBLAS GEMM failed in the Nystrom set-up");
+        if (cublasDsyrk(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, ell, (int)N, &one, st->Y, (int)N, &zero, Gy, ell) !=
+            CUBLAS_STATUS_SUCCESS) {
+            rc = set_error(ctx, GRAV_EDEVICE, "cuBLAS SYRK failed in the Nystrom set-up");
             break;
         }
         cudaMemcpyAsync(hM.data(), Mm, 8ull * ell * ell, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(hYY.data(), YY, 8ull * ell * ell, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(hG.data(), Gy, 8ull * ell * ell, cudaMemcpyDeviceToHost, s);
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         cudaEventRecord(ev, s);
         if ((rc = host_wait(ctx, ev, p->opt.timeout_s, "Nystrom Gram matrices"))) break;
-        // T = mu sym(M) + Y^T Y (column-major results; the rank-k update filled
-        // the lower triangle, (i, j) with i >= j at i + ell j)
+        // T = mu (M + nu I) + Y^T Y, row-major lower triangle (both Gram
+        // matrices are column-major lower: element (i, j), i >= j, at i + ell j).
+        // nu starts at 1e-3 lambda and grows tenfold (to at most 10 lambda)
+        // while the factorisation finds a non-positive pivot.
+        st->mu = lam;
         std::vector<double> T((size_t)ell * ell);
-        for (int i = 0; i < ell; ++i)
-            for (int j = 0; j < ell; ++j) {
-                const size_t ij = (size_t)i + (size_t)ell * j, ji = (size_t)j + (size_t)ell * i;
-                T[(size_t)i * ell + j] = st->mu * 0.5 * (hM[ij] + hM[ji]) + (i >= j ? hYY[ij] : hYY[ji]);
-            }
-        if (!cholesky_rowmajor(T, ell)) {
+        bool factored = false;
+        for (double nu = 1e-3 * lam; !factored && nu <= 10.0 * lam * 1.0000001; nu *= 10.0) {
+            for (int i = 0; i < ell; ++i)
+                for (int j = 0; j <= i; ++j) {
+                    const size_t cij = (size_t)i + (size_t)ell * j;
+                    T[(size_t)i * ell + j] = lam * (hM[cij] + (i == j ? nu : 0.0)) + hG[cij];
+                }
+            st->nu = nu;
+            factored = cholesky_rowmajor(T, ell);
+        }
+        if (!factored) {
             rc = set_error(ctx, GRAV_EDEVICE, "Nystrom matrix T is not positive definite (rank %d)", ell);
             break;
         }
@@ -256,7 +369,6 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
         rc = host_wait(ctx, ev, p->opt.timeout_s, "Nystrom factor upload");
     } while (false);
     if (ev) cudaEventDestroy(ev);
-    if (hs) cudaFreeHost(hs);
     cudaFreeAsync(tmp, s);
     ctx->hbm_used -= tmp_bytes;
     plan_destroy(cp, s);

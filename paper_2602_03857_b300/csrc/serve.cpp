@@ -208,8 +208,8 @@ int grav_submit(grav_ctx *ctx, const grav_job *job, uint64_t *job_id) {
     size_t est = 0;
     if (rc == GRAV_OK) {
         est = p->bytes + (job->kind == GRAV_JOB_INVERT ? solve_bytes(p) : 0);
-        if (job->kind == GRAV_JOB_INVERT && p->opt.precond == 2)   // Nystrom factors (the coarse plan is transient)
-            est += nys_bytes(p->N, (int)std::min<int64_t>(p->opt.nys_rank, p->N));
+        if (job->kind == GRAV_JOB_INVERT && p->opt.precond == 2)   // Nystrom factors and set-up scratch
+            est += nys_peak_bytes(p);
         if (job->opt.check_stations > 0 && job->opt.precision != GRAV_FP64) {
             // the FP64 check's transient plan: node weights, the adjoint's node-sized
             // scratch (two arrays plus station-chunk partials), station arrays and partials
