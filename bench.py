@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--near-cells", type=float, default=8.0)
     ap.add_argument("--no-extras", action="store_true", help="skip fp64/inversion/cpu extras")
+    ap.add_argument("--no-bench-inversion", action="store_true",
+                    help="extras without the inversion of the bench workload itself (~40 s at paper scale)")
     ap.add_argument("--cpu-stations", type=int, default=16)
     ap.add_argument("--cpu-cells", type=int, default=48)
     ap.add_argument("--serve", action="store_true",
@@ -434,6 +436,22 @@ def extras(args, g, torch, wl, plan, d, line):
         "fp64_rel_err_of_predicted_data": info["fp64_rel_err"],
         "what": "as above with the randomized Nystrom preconditioner (automatic rank and coarsening; sketch "
                 "included)"}
+    if args.precision == "mixed" and not args.no_bench_inversion:
+        # the bench workload itself (210 x 210 x 75 cells x 178,797 stations by default):
+        # data = the last timed forward product (mixed operator), Nystrom-preconditioned CG
+        S0 = g.Survey(wl.survey.x, wl.survey.y, wl.survey.z)
+        dd = d.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mm, info = g.datainv(dd, wl.mesh, S0, precision="mixed", near_cells=args.near_cells, tol=1e-6,
+                             max_iter=5000, check_stations=64, precond="nystrom")
+        torch.cuda.synchronize()
+        line["inversion_to_1e-6_" + args.workload + "_nystrom"] = {
+            "workload": args.workload, "precision": "mixed", "seconds": time.perf_counter() - t0,
+            "iters": info["iters"], "converged": info["converged"], "true_rel_res": info["true_rel_res"],
+            "fp64_rel_err_of_predicted_data": info["fp64_rel_err"],
+            "what": "one grav_datainv_solve call on the bench workload (data: its mixed forward product), "
+                    "Nystrom-preconditioned, sketch and plan set-up included"}
 
 
 def run_serve(args):
