@@ -384,6 +384,19 @@ int grav_selftest_wait(grav_ctx *ctx, double limit_ms, grav_stream_t stream);
 int grav_eval_fn64(grav_ctx *ctx, int fn, const double *a, const double *b, double *out, int64_t n,
                    grav_stream_t stream);
 
+/* Self-check of the randomized Nystrom preconditioner's sketch operator
+ * (precond = 2; not in the paper): Y = K_c X with K_c = G_c W_c^-2 G_c^T / c^3
+ * the depth-weighted operator of the mesh coarsened c x c x c (cells of c
+ * times the size, same origin and stations; GRAV_MIXED far term plus an FP64-
+ * formed near-field table within 3 coarse cells), applied the way the sketch
+ * applies it: explicit FP32 blocks of G_c W_c^-1 c^-3/2 and two FP32 GEMMs.
+ * X, Y: DEVICE, column-major n x k doubles (X is rounded to FP32).  mesh must
+ * be uniform; opt gives z0 (NULL: defaults).  1 <= coarsen <= 8, k >= 1, else
+ * GRAV_EINVAL.  Synchronises `stream`. */
+int grav_nystrom_coarse_apply(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, int coarsen,
+                              const double *X, int k, double *Y, const grav_options *opt,
+                              grav_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

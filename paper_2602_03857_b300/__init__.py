@@ -120,6 +120,8 @@ _sig("grav_job_release", _i, [_vp, ctypes.c_uint64])
 _sig("grav_eval_fn64", _i, [_vp, _i, _vp, _vp, _vp, ctypes.c_int64, _vp])
 _sig("grav_plan_check_fp64", _i, [_vp, _vp, _vp, _i, _D, _D, _vp])
 _sig("grav_selftest_wait", _i, [_vp, ctypes.c_double, _vp])
+_sig("grav_nystrom_coarse_apply", _i, [_vp, ctypes.POINTER(grav_mesh), ctypes.POINTER(grav_survey), _i, _vp, _i,
+                                       _vp, ctypes.POINTER(grav_options), _vp])
 _sig("grav_datainv_solve_ex", _i, [_vp, ctypes.POINTER(grav_mesh), ctypes.POINTER(grav_survey), _vp, _vp, _vp,
                                    _vp, ctypes.POINTER(grav_solve_info), ctypes.POINTER(grav_options), _vp,
                                    _vp, _vp, _i])
@@ -131,6 +133,7 @@ EXPORTED = [
     "grav_launch_count", "grav_plan_timing", "grav_bench_pipes", "grav_plan_describe",
     "grav_serve_config", "grav_submit", "grav_poll", "grav_wait", "grav_cancel", "grav_job_times",
     "grav_job_release", "grav_eval_fn64", "grav_plan_check_fp64", "grav_datainv_solve_ex", "grav_selftest_wait",
+    "grav_nystrom_coarse_apply",
 ]
 
 STAGES = ("fwd_main", "adj_main", "fwd_near", "adj_near")
@@ -386,6 +389,24 @@ def diag(mesh, survey, stream=None, ctx: Optional[Context] = None, **opts):
     ctx.check(_lib.grav_diag(ctx.h, ctypes.byref(mesh.c), ctypes.byref(survey.c), out.data_ptr(), ctypes.byref(tr),
                              ctypes.byref(o), _stream(stream)))
     return out, tr.value
+
+
+def nystrom_coarse_apply(X, mesh, survey, coarsen, stream=None, ctx: Optional[Context] = None, **opts):
+    """K_c X (n x k) with the explicit coarse operator of the Nystrom sketch
+    (mesh coarsened `coarsen` times per axis); X: (n, k) or (n,) float64."""
+    torch = _torch()
+    ctx = ctx or context()
+    mesh, survey = Mesh.of(mesh), Survey.of(survey)
+    X = torch.as_tensor(X, dtype=torch.float64, device="cuda")
+    vec = X.dim() == 1
+    Xc = X.reshape(survey.n, -1).t().contiguous()   # column-major n x k = row-major k x n
+    Y = torch.empty_like(Xc)
+    o = options(**opts)
+    ctx.check(_lib.grav_nystrom_coarse_apply(ctx.h, ctypes.byref(mesh.c), ctypes.byref(survey.c), int(coarsen),
+                                             Xc.data_ptr(), Xc.shape[0], Y.data_ptr(), ctypes.byref(o),
+                                             _stream(stream)))
+    Y = Y.t()
+    return Y.reshape(-1) if vec else Y
 
 
 def datainv(d, mesh, survey, m_ref=None, return_y=False, stream=None, ctx: Optional[Context] = None, y0=None,

@@ -1204,6 +1204,25 @@ int grav_diag(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, d
     return rc;
 }
 
+int grav_nystrom_coarse_apply(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, int coarsen,
+                              const double *X, int k, double *Y, const grav_options *opt,
+                              grav_stream_t stream) {
+    if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    if (k < 1 || coarsen < 1 || coarsen > 8) return set_error(ctx, GRAV_EINVAL, "need k >= 1 and coarsen in [1, 8]");
+    if (!is_device_ptr(X, ctx->device) || !is_device_ptr(Y, ctx->device))
+        return set_error(ctx, GRAV_EINVAL, "X and Y must be device pointers");
+    const grav_options o = resolve(opt);
+    grav_plan *p = nullptr;
+    int rc = plan_prepare(ctx, mesh, survey, o, &p);   // geometry only: no device allocation
+    if (rc) return rc;
+    const cudaStream_t s = (cudaStream_t)stream;
+    rc = nys_coarse_apply(p, coarsen, X, k, Y, s);
+    if (!rc) rc = read_status(ctx, s, o.timeout_s);
+    delete p;
+    return rc;
+}
+
 int grav_datainv_solve(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const double *d,
                        const double *m_ref, double *m_out, double *y_out, grav_solve_info *info,
                        const grav_options *opt, grav_stream_t stream) {

@@ -196,6 +196,8 @@ struct NysState {
 size_t nys_bytes(int64_t N, int ell);
 void nys_sizes(const grav_plan *p, int *ell, int *cf);   // resolves the automatic (0) rank and coarsening
 size_t nys_peak_bytes(const grav_plan *p);               // persistent + set-up HBM of nys_build
+// Y = K_c X (N x k, device, column-major) with the explicit coarse operator of the sketch
+int nys_coarse_apply(grav_plan *p, int cf, const double *X, int k, double *Y, cudaStream_t s);
 int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState *st, cudaStream_t s);
 void nys_apply(const NysState &st, const double *r, double *z, cudaStream_t s);
 void nys_free(grav_plan *p, NysState *st, cudaStream_t s);

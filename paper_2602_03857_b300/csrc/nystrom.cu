@@ -80,6 +80,11 @@ __global__ void k_randn32(float *__restrict__ out, int64_t n, uint64_t seed, dou
 
 inline unsigned grid_n(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 148LL * 32)); }
 
+__global__ void k_narrow(const double *__restrict__ x, float *__restrict__ y, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+
 __global__ void k_widen(const float *__restrict__ x, double *__restrict__ y, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = (double)x[i];
@@ -211,6 +216,143 @@ size_t nys_peak_bytes(const grav_plan *p) {
     return nys_bytes(N, ell) + 8ull * N * ell + 16ull * ell * ell + 4ull * cb * N + 12ull * cb * ell + (1u << 20);
 }
 
+namespace {
+
+// The plan of p's mesh coarsened cf x cf x cf (cells cf a x cf b x cf c of
+// the same origin; it may reach past the fine mesh by less than one coarse
+// cell on each axis), mixed precision with a near window of 3 cells, same
+// stations and z0.
+int coarse_plan(grav_plan *p, int cf, grav_plan **cp, cudaStream_t s) {
+    const int nxc = (p->nx + cf - 1) / cf, nyc = (p->ny + cf - 1) / cf, nzc = (p->nz + cf - 1) / cf;
+    std::vector<double> xc(nxc + 1), yc(nyc + 1), zc(nzc + 1);
+    for (int i = 0; i <= nxc; ++i) xc[i] = p->xe[0] + (double)i * cf * p->cell_a;
+    for (int j = 0; j <= nyc; ++j) yc[j] = p->ye[0] + (double)j * cf * p->cell_b;
+    for (int l = 0; l <= nzc; ++l) zc[l] = p->ze[0] + (double)l * cf * p->cell_c;
+    const grav_mesh cm{nxc, nyc, nzc, xc.data(), yc.data(), zc.data()};
+    const grav_survey sv{p->N, p->sx, p->sy, p->sz};
+    grav_options oc;
+    grav_options_default(&oc);
+    oc.precision = GRAV_MIXED;
+    oc.near_cells = 3.0;
+    oc.z0 = p->opt.z0;
+    oc.timeout_s = p->opt.timeout_s;
+    return plan_create(p->ctx, &cm, &sv, oc, cp, s);
+}
+
+// Y32 = K_c X32 = B (B^T X32) (N x k, FP32, column-major) with B = G_c W_c^-1
+// / cf^(3/2) formed explicitly one block of cells at a time (FP32, at most
+// 4 GB); when M is given, M (k x k, FP64, lower triangle) = Z^T Z with
+// Z = B^T X32 (each block's Z_b widened to FP64, exact).  Scratch comes from
+// the context's pool and the context's HBM budget.
+int coarse_products(grav_plan *cp, int cf, double z0, const float *X32, int k, float *Y32, double *M,
+                    cublasHandle_t h, cudaStream_t s) {
+    grav_ctx *ctx = cp->ctx;
+    const int64_t N = cp->N, Mc = cp->M;
+    const int nzc = cp->nz;
+    const size_t used = ctx->hbm_used.load() + 4ull * nzc + 4 * 256;
+    const size_t left = ctx->hbm_budget > used ? ctx->hbm_budget - used : 0;
+    int64_t cb = std::min<int64_t>({Mc, (1ll << 30) / N, (1ll << 27) / k, 65535ll * kNysCells,
+                                    (int64_t)(left / (4ull * N + (M ? 12ull : 4ull) * k))});
+    if (cb < std::min<int64_t>(Mc, 64))
+        return set_error(ctx, GRAV_ENOMEM, "explicit coarse operator block (%d columns) exceeds the HBM budget", k);
+    const int64_t nblk = (Mc + cb - 1) / cb;
+    cb = (Mc + nblk - 1) / nblk;   // equal blocks
+    const size_t bytes = 4ull * nzc + 4ull * cb * N + (M ? 12ull : 4ull) * cb * k + 4 * 256;
+    char *mem = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync((void **)&mem, bytes, ctx->pool, s);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "explicit coarse operator block");
+    ctx->hbm_used += bytes;
+    Arena ta;
+    ta.base = mem; ta.size = bytes;
+    float *fac = (float *)ta.take(4ull * nzc);
+    float *Bb = (float *)ta.take(4ull * N * cb);
+    float *Zb = (float *)ta.take(4ull * cb * k);
+    double *Zd = M ? (double *)ta.take(8ull * cb * k) : nullptr;
+    // fac[l] = gamma V_c (zc_l + z0) / cf^(3/2): K ~ G_c W_c^-2 G_c^T / cf^3 = B B^T
+    std::vector<float> hfac(nzc);
+    const double vol_mgal = kGammaMgal * cp->cell_a * cp->cell_b * cp->cell_c;
+    for (int l = 0; l < nzc; ++l)
+        hfac[l] = (float)(vol_mgal * (0.5 * (cp->ze[l] + cp->ze[l + 1]) - cp->ze[0] + z0) / std::pow((double)cf, 1.5));
+    cudaMemcpyAsync(fac, hfac.data(), 4ull * nzc, cudaMemcpyHostToDevice, s);
+    int rc = GRAV_OK;
+    const float onef = 1.0f, zerof = 0.0f;
+    const double one = 1.0;
+    for (int64_t b = 0; b < nblk && !rc; ++b) {
+        const int64_t c0 = b * cb;
+        const int nb = (int)std::min<int64_t>(cb, Mc - c0);
+        dim3 gf((unsigned)((N + 255) / 256), (unsigned)((nb + kNysCells - 1) / kNysCells));
+        if (cp->cubic)
+            k_nys_far<false><<<gf, 256, 0, s>>>(cp->mg, cp->st32, cp->stz, N, c0, nb, fac, Bb);
+        else
+            k_nys_far<true><<<gf, 256, 0, s>>>(cp->mg, cp->st32, cp->stz, N, c0, nb, fac, Bb);
+        k_nys_near<<<(unsigned)((N * 32 + 255) / 256), 256, 0, s>>>(cp->nx, cp->ny, nzc, cp->ng, N, cp->dG, cp->st_i0,
+                                                                  cp->st_j0, c0, nb, fac, Bb);
+        note_launches(2);
+        const float betaf = b ? 1.0f : 0.0f;
+        const double beta = b ? 1.0 : 0.0;
+        bool ok = cublasSgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, nb, k, (int)N, &onef, Bb, (int)N, X32, (int)N, &zerof, Zb,
+                              nb) == CUBLAS_STATUS_SUCCESS;
+        ok = ok && cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, k, nb, &onef, Bb, (int)N, Zb, nb, &betaf, Y32,
+                               (int)N) == CUBLAS_STATUS_SUCCESS;
+        if (M) {
+            k_widen<<<grid_n((int64_t)nb * k), 256, 0, s>>>(Zb, Zd, (int64_t)nb * k);
+            note_launches(1);
+            ok = ok && cublasDsyrk(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, k, nb, &one, Zd, nb, &beta, M, k) ==
+                           CUBLAS_STATUS_SUCCESS;
+        }
+        if (!ok) rc = set_error(ctx, GRAV_EDEVICE, "cuBLAS failed in the explicit coarse products");
+    }
+    cudaFreeAsync(mem, s);
+    ctx->hbm_used -= bytes;
+    return rc;
+}
+
+}  // namespace
+
+int nys_coarse_apply(grav_plan *p, int cf, const double *X, int k, double *Y, cudaStream_t s) {
+    grav_ctx *ctx = p->ctx;
+    if (!p->uniform) return set_error(ctx, GRAV_EINVAL, "the coarse operator needs a mesh of uniform cells");
+    if (cf < 1 || cf > 8 || k < 1) return set_error(ctx, GRAV_EINVAL, "coarsening must lie in [1, 8] and k >= 1");
+    const int64_t N = p->N;
+    grav_plan *cp = nullptr;
+    int rc = coarse_plan(p, cf, &cp, s);
+    if (rc) return rc;
+    const size_t bytes = 8ull * N * k + 2 * 256;
+    char *mem = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync((void **)&mem, bytes, ctx->pool, s);
+    if (e != cudaSuccess) {
+        plan_destroy(cp, s);
+        return cuda_error(ctx, e, "coarse operator vectors");
+    }
+    ctx->hbm_used += bytes;
+    Arena ta;
+    ta.base = mem; ta.size = bytes;
+    float *X32 = (float *)ta.take(4ull * N * k);
+    float *Y32 = (float *)ta.take(4ull * N * k);
+    k_narrow<<<grid_n(N * k), 256, 0, s>>>(X, X32, N * k);
+    note_launches(1);
+    cublasHandle_t h = nullptr;
+    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) {
+        rc = set_error(ctx, GRAV_EDEVICE, "cublasCreate failed");
+    } else {
+        cublasSetStream(h, s);
+        cublasSetMathMode(h, CUBLAS_DEFAULT_MATH);
+        rc = coarse_products(cp, cf, p->opt.z0, X32, k, Y32, nullptr, h, s);
+        if (!rc) {
+            k_widen<<<grid_n(N * k), 256, 0, s>>>(Y32, Y, N * k);
+            note_launches(1);
+        }
+    }
+    cudaFreeAsync(mem, s);
+    ctx->hbm_used -= bytes;
+    plan_destroy(cp, s);
+    if (h) {
+        cudaStreamSynchronize(s);
+        cublasDestroy(h);
+    }
+    return rc;
+}
+
 int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState *st, cudaStream_t s) {
     grav_ctx *ctx = p->ctx;
     NvtxRange nv("grav::nystrom_build");
@@ -221,43 +363,17 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
     *st = NysState{};
     st->ell = ell;
     st->N = N;
-    // coarse mesh: cf x cf x cf cells of the same origin (it may reach past
-    // the fine mesh by less than one coarse cell on each axis)
-    const int nxc = (p->nx + cf - 1) / cf, nyc = (p->ny + cf - 1) / cf, nzc = (p->nz + cf - 1) / cf;
-    std::vector<double> xc(nxc + 1), yc(nyc + 1), zc(nzc + 1);
-    for (int i = 0; i <= nxc; ++i) xc[i] = p->xe[0] + (double)i * cf * p->cell_a;
-    for (int j = 0; j <= nyc; ++j) yc[j] = p->ye[0] + (double)j * cf * p->cell_b;
-    for (int l = 0; l <= nzc; ++l) zc[l] = p->ze[0] + (double)l * cf * p->cell_c;
-    const grav_mesh cm{nxc, nyc, nzc, xc.data(), yc.data(), zc.data()};
-    const grav_survey sv{N, p->sx, p->sy, p->sz};
-    grav_options oc;
-    grav_options_default(&oc);
-    oc.precision = GRAV_MIXED;
-    oc.near_cells = 3.0;
-    oc.z0 = p->opt.z0;
-    oc.timeout_s = p->opt.timeout_s;
     grav_plan *cp = nullptr;
-    int rc = plan_create(ctx, &cm, &sv, oc, &cp, s);
+    int rc = coarse_plan(p, cf, &cp, s);
     if (rc) return rc;
-    const int64_t Mc = (int64_t)nxc * nyc * nzc;
-    // persistent block
+    // persistent block; temporary block: Omega and Y (FP32, N x ell), M and
+    // Y^T Y (ell x ell); the explicit blocks take what the budget leaves
     st->bytes = nys_bytes(N, ell);
-    // temporary block: Omega and Y (FP32, N x ell), M and Y^T Y (ell x ell),
-    // the FP32 layer factors, then a cell block of B (N x cb, FP32) and
-    // Z_b = B_b^T Omega (cb x ell, FP32 and FP64) sized to what the budget
-    // leaves (cb <= 2^30 / N: one block at most 4 GB)
-    const size_t fixed_bytes = 8ull * N * ell + 16ull * ell * ell + 4ull * nzc + 6 * 256;
-    const size_t used = ctx->hbm_used.load() + st->bytes + fixed_bytes;
-    const size_t left = ctx->hbm_budget > used ? ctx->hbm_budget - used : 0;
-    int64_t cb = std::min<int64_t>({Mc, (1ll << 30) / N, (1ll << 27) / ell, 65535ll * kNysCells,
-                                    (int64_t)(left / (4ull * N + 12ull * ell))});
-    if (cb < std::min<int64_t>(Mc, 64)) {
+    const size_t tmp_bytes = 8ull * N * ell + 16ull * ell * ell + 4 * 256;
+    if (ctx->hbm_used.load() + st->bytes + tmp_bytes > ctx->hbm_budget) {
         plan_destroy(cp, s);
         return set_error(ctx, GRAV_ENOMEM, "Nystrom preconditioner (rank %d) exceeds the HBM budget", ell);
     }
-    const int64_t nblk = (Mc + cb - 1) / cb;
-    cb = (Mc + nblk - 1) / nblk;   // equal blocks
-    const size_t tmp_bytes = fixed_bytes + 4ull * cb * N + 12ull * cb * ell + 3 * 256;
     char *tmp = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync((void **)&st->mem, st->bytes, ctx->pool, s);
     if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void **)&tmp, tmp_bytes, ctx->pool, s);
@@ -279,16 +395,6 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
     float *Y32 = (float *)ta.take(4ull * N * ell);
     double *Mm = (double *)ta.take(8ull * ell * ell);
     double *Gy = (double *)ta.take(8ull * ell * ell);
-    float *fac = (float *)ta.take(4ull * nzc);
-    float *Bb = (float *)ta.take(4ull * N * cb);
-    float *Zb = (float *)ta.take(4ull * cb * ell);
-    double *Zd = (double *)ta.take(8ull * cb * ell);
-    // fac[l] = gamma V_c (zc_l + z0) / cf^(3/2): K ~ G_c W_c^-2 G_c^T / cf^3 = B B^T
-    std::vector<float> hfac(nzc);
-    const double vol_mgal = kGammaMgal * cp->cell_a * cp->cell_b * cp->cell_c;
-    for (int l = 0; l < nzc; ++l)
-        hfac[l] = (float)(vol_mgal * (0.5 * (zc[l] + zc[l + 1]) - zc[0] + p->opt.z0) / std::pow((double)cf, 1.5));
-    cudaMemcpyAsync(fac, hfac.data(), 4ull * nzc, cudaMemcpyHostToDevice, s);
     cublasHandle_t h = nullptr;
     std::vector<double> hM((size_t)ell * ell), hG((size_t)ell * ell);
     cudaEvent_t ev = nullptr;
@@ -302,34 +408,11 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
         cublasSetMathMode(h, CUBLAS_DEFAULT_MATH);   // FP32 GEMMs in FP32 (no TF32)
         k_randn32<<<grid_n(N * ell), 256, 0, s>>>(Om32, N * ell, seed, 1.0 / std::sqrt((double)N));
         note_launches(1);
-        // per cell block: B_b; Z_b = B_b^T Omega; Y += B_b Z_b; M += Z_b^T Z_b (FP64)
-        const float onef = 1.0f, zerof = 0.0f;
-        const double one = 1.0, zero = 0.0;
-        for (int64_t b = 0; b < nblk && !rc; ++b) {
-            const int64_t c0 = b * cb;
-            const int nb = (int)std::min<int64_t>(cb, Mc - c0);
-            dim3 gf((unsigned)((N + 255) / 256), (unsigned)((nb + kNysCells - 1) / kNysCells));
-            if (cp->cubic)
-                k_nys_far<false><<<gf, 256, 0, s>>>(cp->mg, cp->st32, cp->stz, N, c0, nb, fac, Bb);
-            else
-                k_nys_far<true><<<gf, 256, 0, s>>>(cp->mg, cp->st32, cp->stz, N, c0, nb, fac, Bb);
-            k_nys_near<<<(unsigned)((N * 32 + 255) / 256), 256, 0, s>>>(nxc, nyc, nzc, cp->ng, N, cp->dG, cp->st_i0,
-                                                                      cp->st_j0, c0, nb, fac, Bb);
-            const float betaf = b ? 1.0f : 0.0f;
-            const double beta = b ? 1.0 : 0.0;
-            bool ok = cublasSgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, nb, ell, (int)N, &onef, Bb, (int)N, Om32, (int)N,
-                                  &zerof, Zb, nb) == CUBLAS_STATUS_SUCCESS;
-            ok = ok && cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, ell, nb, &onef, Bb, (int)N, Zb, nb, &betaf,
-                                   Y32, (int)N) == CUBLAS_STATUS_SUCCESS;
-            k_widen<<<grid_n((int64_t)nb * ell), 256, 0, s>>>(Zb, Zd, (int64_t)nb * ell);
-            note_launches(3);
-            ok = ok && cublasDsyrk(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, ell, nb, &one, Zd, nb, &beta, Mm, ell) ==
-                           CUBLAS_STATUS_SUCCESS;
-            if (!ok) rc = set_error(ctx, GRAV_EDEVICE, "cuBLAS failed in the Nystrom sketch");
-        }
-        if (rc) break;
+        // Y = K_c Omega and M = Z^T Z, Z = B^T Omega
+        if ((rc = coarse_products(cp, cf, p->opt.z0, Om32, ell, Y32, Mm, h, s))) break;
         k_widen<<<grid_n(N * ell), 256, 0, s>>>(Y32, st->Y, N * ell);
         note_launches(1);
+        const double one = 1.0, zero = 0.0;
         if (cublasDsyrk(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, ell, (int)N, &one, st->Y, (int)N, &zero, Gy, ell) !=
             CUBLAS_STATUS_SUCCESS) {
             rc = set_error(ctx, GRAV_EDEVICE, "cuBLAS SYRK failed in the Nystrom set-up");
