@@ -105,10 +105,10 @@ __global__ void __launch_bounds__(256) k_nys_far(MixedGeo g, const float4 *__res
     const float4 S = st32[s];
     const float zs = stz[s].x;
     const int k0 = blockIdx.y * kNysCells, k1 = min(cb, k0 + kNysCells);
+    // (i, j, l) of cell c0 + k0, then stepped along x (meshes hold at most 2^30 cells)
+    const int c = (int)(c0 + k0);
+    int l = c / g.ncol, i = (c - l * g.ncol) % g.nx, j = (c - l * g.ncol) / g.nx;
     for (int k = k0; k < k1; ++k) {
-        const int64_t c = c0 + k;
-        const int col = (int)(c % g.ncol), l = (int)(c / g.ncol);
-        const int i = col % g.nx, j = col / g.nx;
         const float2 X = make_float2(g.cx[2 * i], g.cx[2 * i + 1]);
         const float2 Y = make_float2(g.cy[2 * j], g.cy[2 * j + 1]);
         const float dx = (X.x - S.x) + (X.y - S.y);
@@ -118,6 +118,13 @@ __global__ void __launch_bounds__(256) k_nys_far(MixedGeo g, const float4 *__res
         const float dz = g.czc[l] - zs;
         const float R2 = fmaf(dz, dz, h2);
         B[(int64_t)k * N + s] = far_k<QUAD>(dz, R2, g.qg, ph) * fac[l];
+        if (++i == g.nx) {
+            i = 0;
+            if (++j == g.ny) {
+                j = 0;
+                ++l;
+            }
+        }
     }
 }
 
