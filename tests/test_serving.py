@@ -4,6 +4,8 @@
   mesh and survey sizes) submitted together to a 3-slot scheduler gives, for
   every job, bitwise the same output as the same job run alone through the
   one-shot calls, and at least two jobs overlap in time.
+* Nystrom-preconditioned inversion jobs (precond = 2) in such a mix give the
+  results they give alone, within 1e-9 of max |m|.
 * Host-side failure paths, none of which faults the GPU: cancelling a queued
   and a running job, a bounded wait that times out, an unknown job id, a job
   larger than the context's HBM budget, and CG stopping at max_iter.
@@ -81,6 +83,47 @@ def test_mixed_batch_matches_solo_runs(g):
         assert all(t0 <= t1 <= t2 for t0, t1, t2 in times)
         overlaps = sum(1 for a in times for b in times if a is not b and a[1] < b[2] and b[1] < a[2])
         assert overlaps > 0, "no two jobs ran at the same time"
+    finally:
+        ctx.close()
+
+
+def test_nystrom_inversions_in_the_mix_match_solo_runs(g):
+    """precond = 2 inversion jobs (each builds its own sketch, cuBLAS handle and
+    host Cholesky factor in its worker thread) submitted with a forward job to a
+    3-slot scheduler: each result equals the same job run alone within 1e-9 of
+    max |m| (the set-up is deterministic: counter-based Omega, fixed-order
+    factorisation), and the preconditioned jobs converge."""
+    solo_ctx = g.context()
+    specs = [("invert", "mixed", (40, 36, 12, 900, 50.0)), ("invert", "fp64", (16, 14, 8, 200, 30.0)),
+             ("forward", "mixed", (60, 50, 20, 2000, 40.0)), ("invert", "mixed", (30, 30, 16, 600, 20.0))]
+    jobs = []
+    for q, (kind, prec, shape) in enumerate(specs):
+        mesh, sv, m = _problem(40 + q, *shape)
+        S = g.Survey(sv.x, sv.y, sv.z)
+        if kind == "forward":
+            opts = dict(precision=prec)
+            inp = _dev(m)
+            solo = g.forward(inp, mesh, S, ctx=solo_ctx, **opts)
+            out = torch.full((sv.n,), float("nan"), dtype=torch.float64, device="cuda")
+        else:
+            opts = dict(precision=prec, tol=1e-8 if prec == "fp64" else 1e-5, max_iter=3000, precond="nystrom")
+            inp = g.forward(_dev(m), mesh, S, ctx=solo_ctx, precision="fp64")
+            solo, info = g.datainv(inp, mesh, S, ctx=solo_ctx, **opts)
+            assert info["converged"], info
+            out = torch.full((mesh.ncells,), float("nan"), dtype=torch.float64, device="cuda")
+        jobs.append((kind, mesh, S, inp, out, solo, opts))
+    torch.cuda.synchronize()
+    ctx = g.Context(0)
+    try:
+        ctx.serve_config(3)
+        ids = [ctx.submit(kind, mesh, S, inp, out, **opts) for kind, mesh, S, inp, out, solo, opts in jobs]
+        for jid in ids:
+            assert ctx.wait(jid, 600.0) == g.GRAV_OK
+        for jid, (kind, mesh, S, inp, out, solo, opts) in zip(ids, jobs):
+            state, info = ctx.poll(jid)
+            assert state == "done"
+            scale = float(solo.abs().max())
+            assert float((out - solo).abs().max()) <= 1e-9 * scale, (kind, opts["precision"])
     finally:
         ctx.close()
 
