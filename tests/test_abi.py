@@ -79,3 +79,15 @@ def test_c_option_defaults(lib):
     g._lib.grav_options_default(ctypes.byref(o))
     assert o.precision == g.GRAV_FP64 and o.max_iter == 1000 and o.near_cells == 8.0
     assert o.reorth == 1000 and o.check_stations == 0 and o.precond == 0 and o.outer_max == 0
+
+
+def test_preconditioner_options_without_gpu(lib):
+    import paper_2602_03857_b300 as g
+    o = g.options(precond="nystrom", nys_rank=120, nys_coarsen=2)
+    assert (o.precond, o.nys_rank, o.nys_coarsen) == (2, 120, 2)
+    assert g.options(precond="jacobi").precond == 1 and g.options().precond == 0
+    c = g.grav_options()
+    g._lib.grav_options_default(ctypes.byref(c))
+    assert c.nys_rank == 0 and c.nys_coarsen == 0   # automatic sizes
+    with pytest.raises(KeyError):
+        g.options(precond="ilu")
