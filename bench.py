@@ -340,7 +340,7 @@ def run_ours(args):
         "clocks": clk.summary(),
         "plan_setup_s": setup_s, "plan_bytes": plan.nbytes,
     }
-    if rank == 0 and not args.no_extras:
+    if ws == 1 and not args.no_extras:   # the CPU baseline and the extras run at N = 1 only
         extras(args, g, torch, wl, plan, d, line)
     plan.close()
     if rank == 0:
