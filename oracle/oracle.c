@@ -32,7 +32,9 @@
  * share: the point-mass limit, an independent Gauss-Legendre Newton
  * integral, the on-axis solid-angle closed form (and its Bouguer-slab limit),
  * superposition, symmetry, z-mirror, finite-difference check of the mixed
- * third derivative of Psi, and the exact transpose.
+ * third derivative of Psi, the exact transpose, and the x/y edge assignment
+ * and cell ordering k = i + nx (j + ny l), one cell at a time on a mesh with
+ * nx != ny and unequal spacings against the Newton integral of that cell's box.
  */
 #include <math.h>
 #include <stddef.h>

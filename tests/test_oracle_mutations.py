@@ -17,7 +17,8 @@ import numpy as np
 import pytest
 
 import oracle
-from tests.test_oracle_pins import _newton_gl, _on_axis, _prism_mp
+from tests.test_oracle_pins import (ASYM_ST, ASYM_XE, ASYM_YE, ASYM_ZE, _newton_gl, _on_axis, _prism_mp,
+                                    asym_expected)
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
 
@@ -36,6 +37,16 @@ MUTANTS = {
     "depth_weight_top_edge": ("double zc = 0.5 * (ze[l] + ze[l + 1]) - ze[0];",
                               "double zc = ze[l] - ze[0];"),
     "z_index_shift": ("ze[l] - sz, ze[l + 1] - sz);", "ze[l] - sz, ze[l] + (ze[1] - ze[0]) - sz);"),
+    # the edge arrays swapped, the station's coordinates not (swapping both is
+    # no mistake: Psi and hence g_z are symmetric under x <-> y)
+    "swap_xy_edges": ("oracle_prism(xe[i] - sx, xe[i + 1] - sx,\n                        ye[j] - sy, ye[j + 1] - sy,",
+                      "oracle_prism(ye[j] - sx, ye[j + 1] - sx,\n                        xe[i] - sy, xe[i + 1] - sy,"),
+    "swap_station_xy": ("oracle_prism(xe[i] - sx, xe[i + 1] - sx,\n                        ye[j] - sy, ye[j + 1] - sy,",
+                        "oracle_prism(xe[i] - sy, xe[i + 1] - sy,\n                        ye[j] - sx, ye[j + 1] - sx,"),
+    "forward_cell_order_y_fastest": ("size_t k = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * l);",
+                                     "size_t k = (size_t)j + (size_t)ny * ((size_t)i + (size_t)nx * l);"),
+    "adjoint_cell_order_y_fastest": ("int i = (int)(k % nx);\n        int j = (int)((k / nx) % ny);",
+                                     "int j = (int)(k % ny);\n        int i = (int)((k / ny) % nx);"),
 }
 
 
@@ -53,6 +64,7 @@ def _build(src_text, tmpdir, name):
     lib.oracle_prism.argtypes = [d] * 6
     P = ctypes.POINTER(d)
     lib.oracle_adjoint.argtypes = [ctypes.c_int] * 3 + [P] * 3 + [ctypes.c_int] + [P] * 3 + [P, P, ctypes.c_int, d]
+    lib.oracle_forward.argtypes = [ctypes.c_int] * 3 + [P] * 3 + [ctypes.c_int] + [P] * 3 + [P, P]
     return lib
 
 
@@ -95,6 +107,28 @@ def _pins_fail(lib):
         expect.append(g * (0.5 * (ze[l] + ze[l + 1]) + 50.0) ** 2)
     if not np.allclose(out, expect, rtol=1e-9):
         failed.append("depth_weighted_adjoint")
+    # x/y edge assignment and cell ordering: one cell at a time (forward) and
+    # one station at a time (adjoint) on the asymmetric 3 x 2 x 2 mesh
+    ref = asym_expected()
+    xe, ye, ze = ASYM_XE.copy(), ASYM_YE.copy(), ASYM_ZE.copy()
+    sx, sy, sz = (np.ascontiguousarray(ASYM_ST[:, c]) for c in range(3))
+    ns, M = ref.shape
+    G_fwd = np.zeros((ns, M))
+    for k in range(M):
+        m = np.zeros(M); m[k] = 1.0
+        d = np.zeros(ns)
+        lib.oracle_forward(3, 2, 2, P(xe), P(ye), P(ze), ns, P(sx), P(sy), P(sz), P(m), P(d))
+        G_fwd[:, k] = d
+    if not np.allclose(G_fwd, ref, rtol=1e-11, atol=0):
+        failed.append("horizontal_geometry_forward")
+    G_adj = np.zeros((ns, M))
+    for s in range(ns):
+        r = np.zeros(ns); r[s] = 1.0
+        out = np.zeros(M)
+        lib.oracle_adjoint(3, 2, 2, P(xe), P(ye), P(ze), ns, P(sx), P(sy), P(sz), P(r), P(out), 0, 50.0)
+        G_adj[s] = out
+    if not np.allclose(G_adj, ref, rtol=1e-11, atol=0):
+        failed.append("horizontal_geometry_adjoint")
     return failed
 
 

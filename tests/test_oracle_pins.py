@@ -6,6 +6,7 @@ quadrature of Newton's integral, an algebraic identity of the paper
 dropped term of Eq. 2, a wrong parity sign in Eq. 1, a swapped coordinate, a
 wrong depth-weight index, a transposed G) fails at least one of them.
 """
+import functools
 import json
 import math
 import os
@@ -247,6 +248,60 @@ def test_transpose_and_dot():
     assert np.allclose(gtrw, wm * (G.T @ r), rtol=1e-12, atol=1e-12 * np.abs(gtrw).max())
     diag = oracle.diag_GWG(mesh, sv, 50.0)
     assert np.allclose(diag, (G * G) @ wm, rtol=1e-12)
+
+
+# --- horizontal geometry: x/y edge assignment and the cell ordering --------
+
+# A mesh with nx != ny, unequal x, y and z spacings and x0 != y0, seen from
+# stations that sit off every axis of symmetry: swapping the x and y edges,
+# the station's x and y, or the order of i and j in k changes every value.
+ASYM_XE = -37.0 + np.array([0.0, 10.0, 20.0, 30.0])
+ASYM_YE = 112.0 + np.array([0.0, 25.0, 50.0])
+ASYM_ZE = np.array([0.0, 15.0, 35.0])
+ASYM_ST = np.array([[-57.0, 172.0, -30.0], [8.0, 97.0, -40.0], [-32.0, 122.0, -25.0], [-9.0, 149.0, -33.0]])
+
+
+@functools.lru_cache(maxsize=1)
+def asym_expected():
+    """G[s, k] of the asymmetric mesh from the Newton integral of each cell's
+    explicit box [xe_i, xe_i+1] x [ye_j, ye_j+1] x [ze_l, ze_l+1], with
+    k = i + nx (j + ny l) (x fastest), by Gauss-Legendre (no Psi)."""
+    nx, ny, nz = len(ASYM_XE) - 1, len(ASYM_YE) - 1, len(ASYM_ZE) - 1
+    G = np.zeros((len(ASYM_ST), nx * ny * nz))
+    for s, (sx, sy, sz) in enumerate(ASYM_ST):
+        for l in range(nz):
+            for j in range(ny):
+                for i in range(nx):
+                    k = i + nx * (j + ny * l)
+                    G[s, k] = GAMMA * 1e5 * _newton_gl(ASYM_XE[i] - sx, ASYM_XE[i + 1] - sx,
+                                                       ASYM_YE[j] - sy, ASYM_YE[j + 1] - sy,
+                                                       ASYM_ZE[l] - sz, ASYM_ZE[l + 1] - sz)
+    return G
+
+
+def test_horizontal_geometry_and_cell_order_one_cell_at_a_time():
+    """One non-zero cell at a time: the oracle's forward, adjoint and explicit
+    G reproduce the Newton integral of that cell's own box at off-axis
+    stations (Eq. 1 and Eq. 4-6, cell k = i + nx (j + ny l)).  This fixes the
+    x/y edge assignment and the (i, j, l) -> k ordering, which the symmetric
+    pins above cannot see."""
+    mesh = synth.Mesh(ASYM_XE.copy(), ASYM_YE.copy(), ASYM_ZE.copy())
+    sv = synth.Survey(ASYM_ST[:, 0].copy(), ASYM_ST[:, 1].copy(), ASYM_ST[:, 2].copy())
+    ref = asym_expected()
+    assert mesh.ncells == ref.shape[1] == 12
+    for k in range(mesh.ncells):
+        m = np.zeros(mesh.ncells)
+        m[k] = 1.0
+        d = oracle.forward(mesh, sv, m)
+        assert np.allclose(d, ref[:, k], rtol=1e-11, atol=0), k
+    for s in range(sv.n):
+        r = np.zeros(sv.n)
+        r[s] = 1.0
+        assert np.allclose(oracle.adjoint(mesh, sv, r), ref[s], rtol=1e-11, atol=0), s
+    assert np.allclose(oracle.G_explicit(mesh, sv), ref, rtol=1e-11, atol=0)
+    # the values really differ under the mistakes this pin is for
+    swapped = ref.reshape(sv.n, 2, 2, 3).transpose(0, 1, 3, 2).reshape(sv.n, -1)
+    assert np.abs(swapped - ref).max() > 1e-3 * np.abs(ref).max()
 
 
 def test_depth_weight_indexing():
