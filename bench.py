@@ -16,7 +16,8 @@ oracle timed on the host cores (cpu_baseline), the mixed-vs-FP64-oracle error
 on the oracle's sample stations, FP64-mode throughput on the 80 x 80 x 40
 workload, the error of the literal FP32 corner-term scheme there (against the
 FP64 mode, beside the mixed scheme's), and the inversion time to relative
-residual 1e-6 (mixed and FP64).
+residual 1e-6 (mixed and FP64), and a bounded replay of the serving stream
+(first 64 jobs).
 Under torchrun (N > 1) every rank runs an independent replica (the operator
 is single-GPU; replicas only) and `value` is the total over ranks.
 """
@@ -167,9 +168,14 @@ def run_reference(args):
         pps, sec, th, _, _, _ = oracle_sample(wl, args.cpu_stations, args.cpu_cells, seed=s)
         vals.append(pps)
     v = statistics.median(vals)
+    sample_pairs = args.cpu_stations * wl.mesh.ncells + args.cpu_cells * wl.survey.n
     line = {
         "impl": "reference", "metric": "prism-station pairs/s for G.m and G^T r", "value": v, "unit": "pairs/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": pairs_step / v * 1e3,
+        "ms_per_step_basis": (f"extrapolated: one full step is {pairs_step:.4g} pairs at the measured rate; each "
+                              f"timed step ran a sample of {sample_pairs:.4g} pairs "
+                              f"({sample_pairs / v * 1e3:.0f} ms)"),
+        "sample_pairs_per_step": sample_pairs, "sample_ms_per_step": sample_pairs / v * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "cells": wl.mesh.ncells, "stations": wl.survey.n},
         "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": th, "kind": "oracle",
@@ -436,6 +442,28 @@ def extras(args, g, torch, wl, plan, d, line):
         "fp64_rel_err_of_predicted_data": info["fp64_rel_err"],
         "what": "as above with the randomized Nystrom preconditioner (automatic rank and coarsening; sketch "
                 "included)"}
+    # inversion time to 1e-6 at 80 x 80 x 40 cells x 6,561 stations, FP64 against mixed
+    # (data: the FP64 forward of the slab model plus 1 % + 0.01 mGal seeded noise)
+    d2 = g.forward(torch.tensor(wl2.m, device="cuda"), wl2.mesh, S2, precision="fp64").cpu().numpy()
+    d2 = torch.tensor(synth.add_noise(d2, wl2.noise_abs, wl2.noise_rel, 0), device="cuda")
+    vs = {}
+    for prec, pc in (("fp64", "nystrom"), ("mixed", "none")):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mm, info = g.datainv(d2, wl2.mesh, S2, precision=prec, tol=1e-6, max_iter=5000, precond=pc,
+                             check_stations=64 if prec == "mixed" else 0)
+        torch.cuda.synchronize()
+        vs[prec] = {"seconds": time.perf_counter() - t0, "precond": pc, "iters": info["iters"],
+                    "converged": info["converged"], "true_rel_res": info["true_rel_res"]}
+        if prec == "mixed":
+            vs[prec]["fp64_rel_err_of_predicted_data"] = info["fp64_rel_err"]
+    line["inversion_to_1e-6_vslab_80x80x40"] = {
+        "workload": "vslab_80x80x40", **vs, "fp64_over_mixed_seconds": vs["fp64"]["seconds"] / vs["mixed"]["seconds"],
+        "what": "one grav_datainv_solve call each (plan set-up, trace, CG to a true relative residual of 1e-6, "
+                "recovery); the FP64 solve takes the Nystrom preconditioner (sketch included), without it it "
+                "needs ~100 s"}
+    # the serving loop on the first 64 jobs of the seeded request stream
+    line["serving_64_jobs"] = serve_replay(g, torch, 64, 20.0, 8)
     if args.precision == "mixed" and not args.no_bench_inversion:
         # the bench workload itself (210 x 210 x 75 cells x 178,797 stations by default):
         # data = the last timed forward product (mixed operator), Nystrom-preconditioned CG
@@ -455,14 +483,18 @@ def extras(args, g, torch, wl, plan, d, line):
 
 
 def run_serve(args):
-    """Request-loop benchmark: jobs arrive at their seeded Poisson times (rate
-    args.serve_rate), each a forward or an inversion (mixed precision, CG
-    tolerance 1e-4 as in the paper's inner CG) on its own mesh and survey;
-    latency = completion - submission (steady clock inside libgrav)."""
     import torch
     import paper_2602_03857_b300 as g
     torch.cuda.set_device(0)
-    jobs = synth.serving_jobs(args.serve_jobs, args.serve_rate, seed=0)
+    print(json.dumps(serve_replay(g, torch, args.serve_jobs, args.serve_rate, args.serve_slots)), flush=True)
+
+
+def serve_replay(g, torch, n_jobs, rate, slots):
+    """Request-loop benchmark: jobs arrive at their seeded Poisson times (rate
+    `rate`), each a forward or an inversion (mixed precision, CG tolerance
+    1e-4 as in the paper's inner CG) on its own mesh and survey; latency =
+    completion - submission (steady clock inside libgrav)."""
+    jobs = synth.serving_jobs(n_jobs, rate, seed=0)
     prepared = []
     for j in jobs:
         S = g.Survey(j.survey.x, j.survey.y, j.survey.z)
@@ -475,7 +507,7 @@ def run_serve(args):
         prepared.append((j, S, inp, out))
     torch.cuda.synchronize()
     ctx = g.Context(0)
-    ctx.serve_config(args.serve_slots)
+    ctx.serve_config(slots)
     opts = dict(precision="mixed", tol=1e-4, max_iter=500, check_stations=16)
     t0 = time.perf_counter()
     ids = []
@@ -506,7 +538,7 @@ def run_serve(args):
     ctx.close()
     pct = lambda v, q: float(np.percentile(np.array(v), q)) if v else None
     line = {"metric": "serving latency and throughput (mixed precision)", "jobs": len(jobs),
-            "arrival_rate_hz": args.serve_rate, "slots": args.serve_slots, "wall_s": wall,
+            "arrival_rate_hz": rate, "slots": slots, "wall_s": wall,
             "throughput_jobs_per_s": len(jobs) / wall,
             "offered_load_jobs_per_s": len(jobs) / max(j.arrival_s for j in jobs),
             "p50_latency_s": pct(lat, 50), "p99_latency_s": pct(lat, 99),
@@ -521,7 +553,7 @@ def run_serve(args):
             "achieved_pairs_per_s": pairs_done / wall, "data": "synthetic",
             "config": {"workload": "serving mix: 50k-500k cubic prisms (25-100 m), 1k-20k stations, "
                                    "block/dyke models, forward or inversion 50/50", "tol": 1e-4}}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_invert(args):

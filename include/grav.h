@@ -65,6 +65,8 @@ typedef struct CUstream_st *grav_stream_t;
 /* ---- precision modes ------------------------------------------------------ */
 /* GRAV_FP64: Eq. 1-3 evaluated in FP64 once per (station, mesh node) and
  *   differenced across shared nodes (summation by parts of Eq. 1 + Eq. 5).
+ *   Needs nx+1 <= 8528 (a row of node weights is staged in shared memory);
+ *   GRAV_EINVAL otherwise.
  * GRAV_MIXED: every cell contributes through an FP32 point-mass far-field term
  *   gamma rho V dz / R^3 (times the box's quadrupole factor when the cells are
  *   not cubes) with compensated (two-sum) accumulation; cells whose centre
@@ -317,7 +319,14 @@ int grav_job_release(grav_ctx *ctx, uint64_t job_id);
  * loads the library until the process exits.  Problems whose node weights
  * ((ny+1)(nz+1)(nx+1 rounded up to even) doubles) plus one partial per
  * station do not fit are rejected with GRAV_EINVAL and a message naming the
- * sizes.  Every call shares that array and keeps the previous call's
+ * sizes, as are meshes above 2^30 cells or 2^30 nodes and meshes with
+ * nx+1 > 8528 (one row of node weights is staged in shared memory); all of
+ * these are rejected before anything is enqueued.
+ *
+ * Device failure: the kernel's waits on its copies are bounded; if one runs
+ * out, the product is incomplete and every entry of d is set to NaN (no host
+ * synchronisation is needed to see it: check d).  GRAV_OK only means that
+ * the work was enqueued.  Every call shares that array and keeps the previous call's
  * contents, so calls that overlap on the GPU (different streams, threads or
  * processes' contexts on the same device without ordering) race and give
  * wrong results: order them on one stream.  The first call on each device

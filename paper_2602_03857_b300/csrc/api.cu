@@ -323,6 +323,13 @@ int plan_prepare(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey
         p->cell_b = b;
         p->cell_c = c;
     }
+    if (o.precision == GRAV_FP64 && p->nx + 1 > fwd64_max_nodes_x()) {
+        delete p;
+        return set_error(ctx, GRAV_EINVAL,
+                         "GRAV_FP64 stages one row of nx+1 node weights in shared memory: nx+1 must be <= %d "
+                         "(got %d)",
+                         fwd64_max_nodes_x(), mesh->nx + 1);
+    }
     if (o.precision != GRAV_FP64 && !p->uniform) {
         delete p;
         return set_error(ctx, GRAV_EINVAL,

@@ -20,6 +20,7 @@ namespace {
 
 constexpr int kFwdThreads = 128;
 constexpr int kFwdT = 2;            // stations per thread
+constexpr int kFwdSmemLimit = 200 * 1024;   // dynamic shared memory k_fwd64 may use
 constexpr int kAdjWarps = 8;        // warps per CTA in the adjoint
 constexpr int kAdjTZ = 8;           // node levels per warp
 constexpr int kAdjStage = 256;      // stations per TMA stage
@@ -515,7 +516,7 @@ void launch_node_weights(const grav_plan *p, const double *m, cudaStream_t s) {
 
 void fp64_setup(grav_plan *p, cudaStream_t s) {
     k_init_st4<<<grid_for(p->N, 256), 256, 0, s>>>(p->st4, p->sx, p->sy, p->sz, p->N);
-    cudaFuncSetAttribute(k_fwd64<kFwdT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_fwd64<kFwdT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmemLimit);
 }
 
 void launch_fwd64(const grav_plan *p, cudaStream_t s) {
@@ -577,11 +578,13 @@ namespace grav {
 int launch_fwd64_raw(Geo g, int ldw, const double *m, double *w, int rows_per_chunk, int nchunk,
                      const double *sx, const double *sy, const double *sz, double *part, int *status,
                      cudaStream_t s) {
+    if (cudaFuncSetAttribute(k_fwd64<kFwdT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmemLimit) !=
+        cudaSuccess)
+        return -1;
     const int64_t total = (int64_t)(g.ny + 1) * (g.nz + 1) * ldw;
     k_node_weights<<<grid_for(total, 256), 256, 0, s>>>(g.nx, g.ny, g.nz, ldw, m, w);
     const int rps = std::max(1, std::min(rows_per_chunk, (16384 / 8) / ldw));
     const size_t smem = 128 + (size_t)ldw * 8 + 2ull * rps * ldw * 8;
-    cudaFuncSetAttribute(k_fwd64<kFwdT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     const int tiles = (int)((g.N + kFwdThreads * kFwdT - 1) / (kFwdThreads * kFwdT));
     dim3 grid(tiles, nchunk);
     k_fwd64<kFwdT><<<grid, kFwdThreads, smem, s>>>(g, ldw, w, rows_per_chunk, rps, sx, sy, sz, part, status);
@@ -590,6 +593,10 @@ int launch_fwd64_raw(Geo g, int ldw, const double *m, double *w, int rows_per_ch
 }
 
 int fwd64_stations_per_cta() { return kFwdThreads * kFwdT; }
+
+// 128 bytes of barriers + the x-edge row + two stage buffers of >= 1 row
+// (rows of ldw doubles, ldw = nx+1 rounded up to even).
+int fwd64_max_nodes_x() { return (kFwdSmemLimit - 128) / 24 / 2 * 2; }
 
 }  // namespace grav
 

@@ -232,10 +232,15 @@ void launch_cached_diag(const grav_plan *p, double *diag, cudaStream_t s);
 void launch_cached_adj(const grav_plan *p, const double *r, int depth_weighted, const double *add, double *out,
                        cudaStream_t s);
 size_t fwd64_smem_bytes(const grav_plan *p);
+// Returns the number of kernels launched, or -1 (nothing launched) when the
+// forward kernel's shared-memory limit cannot be set.
 int launch_fwd64_raw(Geo g, int ldw, const double *m, double *w, int rows_per_chunk, int nchunk,
                      const double *sx, const double *sy, const double *sz, double *part, int *status,
                      cudaStream_t s);
 int fwd64_stations_per_cta();
+// Largest nx+1 whose padded node row (with the two stage buffers of one row
+// each) fits k_fwd64's 200 KB dynamic shared memory.
+int fwd64_max_nodes_x();
 
 // mixed launchers (mixed_kernels.cu)
 int mixed_setup(grav_plan *p, cudaStream_t s);   // 0 or a GRAV_E* code

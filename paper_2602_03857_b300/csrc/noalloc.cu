@@ -69,6 +69,17 @@ bool edges_ok(const double *e, int n) {
 
 inline size_t round32(size_t v) { return (v + 31) / 32 * 32; }   // 256-byte granularity in doubles
 
+// A bounded wait in k_fwd64 that ran out leaves its CTA's partial sums
+// unwritten (the array keeps an earlier call's values there), so the whole
+// product is void: every d_i becomes NaN.  The status word was cleared at the
+// start of this call on the same stream.
+__global__ void k_void_on_status(const int *__restrict__ status, double *__restrict__ d, int64_t n) {
+    if (*status == 0) return;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        d[i] = nan;
+}
+
 }  // namespace
 }  // namespace grav
 
@@ -80,6 +91,13 @@ extern "C" int grav_forward_fp64_noalloc(const grav_mesh *mesh, const grav_surve
     if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || mesh->nx > (1 << 20) || mesh->ny > (1 << 20) ||
         mesh->nz > (1 << 16))
         return set_error(nullptr, GRAV_EINVAL, "mesh sizes must lie in [1, 2^20] x [1, 2^20] x [1, 2^16]");
+    if ((int64_t)mesh->nx * mesh->ny * mesh->nz > ((int64_t)1 << 30) ||
+        (int64_t)(mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1) > ((int64_t)1 << 30))
+        return set_error(nullptr, GRAV_EINVAL, "mesh too large: at most 2^30 cells and 2^30 nodes");
+    if (mesh->nx + 1 > fwd64_max_nodes_x())
+        return set_error(nullptr, GRAV_EINVAL,
+                         "nx+1 must be <= %d (one row of node weights is staged in shared memory; got %d)",
+                         fwd64_max_nodes_x(), mesh->nx + 1);
     if (!mesh->xe || !mesh->ye || !mesh->ze || !edges_ok(mesh->xe, mesh->nx) || !edges_ok(mesh->ye, mesh->ny) ||
         !edges_ok(mesh->ze, mesh->nz))
         return set_error(nullptr, GRAV_EINVAL, "mesh edges must be finite and strictly increasing");
@@ -96,19 +114,22 @@ extern "C" int grav_forward_fp64_noalloc(const grav_mesh *mesh, const grav_surve
     const int nx = mesh->nx, ny = mesh->ny, nz = mesh->nz;
     const int64_t N = survey->n;
     const int ldw = (nx + 2) / 2 * 2;
-    const int nrows = (ny + 1) * (nz + 1);
+    // (ny+1)(nz+1) <= 2^30 by the node cap above; the products below are size_t
+    const int64_t nrows64 = (int64_t)(ny + 1) * (nz + 1);
     // scratch layout (in doubles): status | FP64 log/atan table | xe | ye | ze | w | partials
     const size_t o_fn = 32;
     const size_t o_xe = o_fn + round32((size_t)fn_table_size());
-    const size_t o_ye = o_xe + round32(nx + 1);
-    const size_t o_ze = o_ye + round32(ny + 1);
-    const size_t o_w = o_ze + round32(nz + 1);
-    const size_t o_part = o_w + round32((size_t)nrows * ldw);
-    if (o_part + (size_t)N > kStaticScratchDoubles)
+    const size_t o_ye = o_xe + round32((size_t)nx + 1);
+    const size_t o_ze = o_ye + round32((size_t)ny + 1);
+    const size_t o_w = o_ze + round32((size_t)nz + 1);
+    const size_t w_doubles = (size_t)nrows64 * (size_t)ldw;
+    if (w_doubles > kStaticScratchDoubles || o_w + round32(w_doubles) + (size_t)N > kStaticScratchDoubles)
         return set_error(nullptr, GRAV_EINVAL,
                          "problem too large for the %zu MiB static scratch: node weights need %.1f MiB and the "
                          "partial sums at least %.1f MiB",
-                         kStaticScratchBytes >> 20, (double)nrows * ldw * 8 / 1048576.0, (double)N * 8 / 1048576.0);
+                         kStaticScratchBytes >> 20, (double)w_doubles * 8 / 1048576.0, (double)N * 8 / 1048576.0);
+    const size_t o_part = o_w + round32(w_doubles);
+    const int nrows = (int)nrows64;   // fits: the node weights fit 64 MiB
     // chunking: as many node-row chunks as fill the GPU, capped by what fits
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
@@ -142,9 +163,13 @@ extern "C" int grav_forward_fp64_noalloc(const grav_mesh *mesh, const grav_surve
     g.xe = base + o_xe; g.ye = base + o_ye; g.ze = base + o_ze;
     g.N = N;
     g.fn = base + o_fn;
-    launch_fwd64_raw(g, ldw, m, base + o_w, rows_per_chunk, nchunk, survey->x, survey->y, survey->z, base + o_part,
-                     reinterpret_cast<int *>(base), s);
+    int *status = reinterpret_cast<int *>(base);
+    if (launch_fwd64_raw(g, ldw, m, base + o_w, rows_per_chunk, nchunk, survey->x, survey->y, survey->z,
+                         base + o_part, status, s) < 0)
+        return cuda_error(nullptr, cudaGetLastError(), "noalloc forward: shared-memory limit of k_fwd64");
     launch_reduce_rows(base + o_part, nchunk, N, kGammaMgal, nullptr, 0.0, nullptr, d, s);
+    k_void_on_status<<<(unsigned)std::min<int64_t>((N + 255) / 256, (int64_t)sms * 8), 256, 0, s>>>(status, d, N);
+    note_launches(1);
     e = cudaGetLastError();
     return e == cudaSuccess ? GRAV_OK : cuda_error(nullptr, e, "noalloc forward launch");
 }
