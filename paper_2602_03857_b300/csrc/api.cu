@@ -366,6 +366,7 @@ int plan_prepare(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey
             if (0.5 * (p->ze[l] + p->ze[l + 1]) - p->ze[0] < k * L) bz = l + 1;
         p->ng.bz = std::max(1, bz);
         p->ng.slots = p->ng.bx * p->ng.by * p->ng.bz;
+        p->ng.ld = (p->ng.slots + 3) / 4 * 4;
         p->ng.nbx = p->nx + p->ng.bx - 1;
         p->ng.nby = p->ny + p->ng.by - 1;
         bytes += mixed_scratch_bytes(p);

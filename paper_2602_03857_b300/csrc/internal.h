@@ -41,6 +41,8 @@ struct MixedGeo {
 struct NearGeo {
     int bx, by, bz;
     int slots;                    // bx * by * bz
+    int ld;                       // table row stride in floats: slots rounded up to a multiple of 4
+                                  // (16-byte rows for TMA bulk copies and float4 loads; pad entries 0)
     double radius_cells;          // near_cells
     double width;                 // cell width the radius is measured in: max(a, c)
     int nbx, nby;                 // bin grid: i0 + (bx-1) in [0, nbx)
@@ -146,6 +148,8 @@ struct grav_plan {
     int *bin_st = nullptr;                // [N] station indices sorted by bin
     double *near_corr = nullptr;          // [N] forward near-field correction scratch
     double *m_cellacc = nullptr;          // [M] adjoint scratch
+    double *near_tpart = nullptr;         // per station tile: FP64 near adjoint sums over its cell region
+    int near_adj_rows = 0;                // 1: station-streaming near adjoint (k_near_adj_rows)
     float *cr_w32 = nullptr;              // GRAV_MIXED_CORNER: node weights, FP32 rows of cr_ldw
     double *cr_part = nullptr;            // [cr_nchunk][N] row-chunk partials of the corner forward
     int cr_ldw = 0, cr_rows_per_chunk = 0, cr_nchunk = 0;

@@ -789,8 +789,9 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
         }
         // formed in FP64, stored in FP32 per unit q = gamma V rho (so the products
         // use the FP32 q of the far field); relative rounding 6e-8
-        dG[s * ng.slots + t] = (float)(val / vol_mgal);
+        dG[s * ng.ld + t] = (float)(val / vol_mgal);
     }
+    if (lane < ng.ld - ng.slots) dG[s * ng.ld + ng.slots + lane] = 0.0f;   // row padding
     dcorr = warp_sum(dcorr);
     if (lane == 0) {
         diag_corr[s] = dcorr;
@@ -824,10 +825,10 @@ __global__ void k_bin_bounds(const unsigned *__restrict__ ks, int64_t n, int nbi
 // per term.
 //
 // Stations whose box lies inside the mesh (all but those near its edges) take
-// a fast path when the slot count is a multiple of 4: the table row streams
-// in 16-byte loads (read once, evict-first), the cell of each slot comes from
-// the plan's slot-offset table off[t] = a + nx (bj + ny l) (L1-resident), and
-// no slot needs a bounds check.
+// a fast path: the table row (padded to a multiple of 4 floats) streams in
+// 16-byte loads (read once, evict-first), the cell of each slot comes from the
+// plan's slot-offset table off[t] = a + nx (bj + ny l) (L1-resident), and no
+// slot needs a bounds check.
 __global__ void __launch_bounds__(256) k_near_fwd(int nx, int ny, int nz, NearGeo ng, int64_t N,
                                                   const float *__restrict__ dG, const int *__restrict__ st_i0,
                                                   const int *__restrict__ st_j0, const int *__restrict__ off,
@@ -836,12 +837,13 @@ __global__ void __launch_bounds__(256) k_near_fwd(int nx, int ny, int nz, NearGe
     const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (s >= N) return;
     const int i0 = st_i0[s], j0 = st_j0[s];
-    const float *gs = dG + s * ng.slots;
-    if ((ng.slots & 3) == 0 && i0 >= 0 && i0 + ng.bx <= nx && j0 >= 0 && j0 + ng.by <= ny && ng.bz <= nz) {
+    const float *gs = dG + s * ng.ld;
+    if (i0 >= 0 && i0 + ng.bx <= nx && j0 >= 0 && j0 + ng.by <= ny && ng.bz <= nz) {
+        // padded slots hold dG = 0 and offset 0 (the box origin, inside the mesh)
         const float4 *g4 = reinterpret_cast<const float4 *>(gs);
         const int4 *o4 = reinterpret_cast<const int4 *>(off);
         const float *qb = qn + i0 + (int64_t)nx * j0;
-        const int n4 = ng.slots >> 2;
+        const int n4 = ng.ld >> 2;
         double acc = 0.0;
         for (int v = lane; v < n4; v += 64) {   // 8 slots per lane and step, loads issued together
             const bool two = v + 32 < n4;
@@ -947,7 +949,7 @@ __global__ void __launch_bounds__(256, 4) k_near_adj(int nx, int ny, NearGeo ng,
             for (int u = 0; u < 8; ++u) {
                 const int a = sv[u] >= 0 ? x - st_i0[sv[u]] : -1;
                 const bool ok = a >= 0 && a < ng.bx && xin;
-                g[u] = ok ? dG[(int64_t)sv[u] * ng.slots + row + a] : 0.0f;
+                g[u] = ok ? dG[(int64_t)sv[u] * ng.ld + row + a] : 0.0f;
                 rv[u] = ok ? stz[sv[u]].y : 0.0f;
             }
             float accf = 0.0f;
@@ -957,6 +959,193 @@ __global__ void __launch_bounds__(256, 4) k_near_adj(int nx, int ny, NearGeo ng,
         }
     }
     if (xin) out[x + (int64_t)nx * (y + (int64_t)ny * l)] = acc;
+}
+
+// Near-field adjoint, station-streaming form (the default when its shared
+// memory fits).  out[k] = sum over stations s whose window box holds cell k of
+// dG[s][slot(s, k)] * r_s, for the top lz layers.
+//
+// CTA = tile of kNaTile x kNaTile station bins (box origins i0, j0); the boxes
+// of its stations cover a region of RX x RY x lz cells, RX = kNaTile + bx - 1.
+// Each station's table row (ld floats, contiguous, 16-byte padded) is copied
+// whole into shared memory by one 1D TMA bulk copy through an ns-stage ring
+// completed on mbarriers, so the table is read from HBM exactly once and in
+// full rows (the cell-tiled form below reads box rows of 17 floats split over
+// 32-column tiles and fetches about twice the table).  Thread t owns slots
+// t, t + 256, ...: slot u of station s adds dG * r into region cell
+// base(s) + roff[u].  The slots of one station map to distinct cells and a
+// barrier separates consecutive stations, so every cell receives its terms in
+// station order (bitwise deterministic).  Terms are summed in FP32 in shared
+// memory and folded into an FP64 region sum every kNaFold stations (a cell
+// sees at most kNaFold FP32 terms between folds).  Each CTA stores its region
+// sums to tpart[tile]; k_near_adj_gather adds, per cell, the tiles whose
+// region holds it, in tile order.
+constexpr int kNaTile = 8;
+constexpr int kNaThreads = 256;
+constexpr int kNaFold = 16;
+constexpr int kNaMaxStages = 12;
+constexpr size_t kNaSmemBudget = 110 * 1024;   // two CTAs per SM
+static_assert(8 * kNaMaxStages + 8 <= 128 && 128 + 4 * (2 * kNaTile + 1) <= 256, "near adjoint header");
+
+struct NearAdjShape {
+    bool ok = false;
+    int RX = 0, RY = 0, lz = 0, RC = 0, ns = 0, ntx = 0, nty = 0;
+    size_t o_roff = 0, o_sb = 0, o_acc32 = 0, o_acc64 = 0, o_stage = 0, smem = 0;
+};
+
+static NearAdjShape near_adj_shape(const grav_plan *p) {
+    NearAdjShape z;
+    z.RX = kNaTile + p->ng.bx - 1;
+    z.RY = kNaTile + p->ng.by - 1;
+    z.lz = std::min(p->ng.bz, p->nz);
+    z.RC = z.RX * z.RY * z.lz;
+    z.ntx = (p->ng.nbx + kNaTile - 1) / kNaTile;
+    z.nty = (p->ng.nby + kNaTile - 1) / kNaTile;
+    z.o_roff = 256;                                           // header: mbarriers, flags, row table
+    z.o_sb = align_up(z.o_roff + 4ull * p->ng.ld, 16);       // roff[ld]
+    z.o_acc32 = z.o_sb + 2ull * 4 * kNaMaxStages;             // sbase[], srv[]
+    z.o_acc64 = align_up(z.o_acc32 + 4ull * z.RC, 16);
+    z.o_stage = align_up(z.o_acc64 + 8ull * z.RC, 128);
+    const size_t row = 4ull * p->ng.ld;
+    const int ns = z.o_stage + 2 * row <= kNaSmemBudget ? (int)((kNaSmemBudget - z.o_stage) / row) : 0;
+    z.ns = std::min(ns, kNaMaxStages);
+    z.smem = z.o_stage + (size_t)z.ns * row;
+    z.ok = z.ns >= 2 && p->ng.ld % 4 == 0;
+    return z;
+}
+
+__global__ void __launch_bounds__(kNaThreads) k_near_adj_rows(
+    NearGeo ng, int RX, int RY, int lz, int ns, int ntx, uint32_t o_roff, uint32_t o_sb, uint32_t o_acc32,
+    uint32_t o_acc64, uint32_t o_stage, const float *__restrict__ dG, const int *__restrict__ bin_start,
+    const int *__restrict__ bin_st, const int *__restrict__ st_i0, const int *__restrict__ st_j0,
+    const float2 *__restrict__ stz, double *__restrict__ tpart, int *status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // header (256 bytes): mbarriers [0, 96), flags [96, 104), row table [128, 196)
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);                      // [ns], ns <= 12
+    volatile int *flag = reinterpret_cast<volatile int *>(smem_raw + 8 * kNaMaxStages);   // [2]
+    int *rowinfo = reinterpret_cast<int *>(smem_raw + 128);                       // [2 kNaTile + 1]
+    int *roff = reinterpret_cast<int *>(smem_raw + o_roff);
+    int *sbase = reinterpret_cast<int *>(smem_raw + o_sb);
+    float *srv = reinterpret_cast<float *>(smem_raw + o_sb + 4 * kNaMaxStages);
+    float *acc32 = reinterpret_cast<float *>(smem_raw + o_acc32);
+    double *acc64 = reinterpret_cast<double *>(smem_raw + o_acc64);
+    float *stage = reinterpret_cast<float *>(smem_raw + o_stage);
+    const int tid = threadIdx.x;
+    const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
+    const int I0 = tx * kNaTile, J0 = ty * kNaTile;
+    const int RC = RX * RY * lz;
+
+    // slot u = a + bx (b + by l) -> region offset a + RX (b + RY l); padding and
+    // layers below the mesh (l >= lz) take no cell
+    for (int u = tid; u < ng.ld; u += kNaThreads) {
+        int v = -1;
+        if (u < ng.slots) {
+            const int a = u % ng.bx, b = (u / ng.bx) % ng.by, l = u / (ng.bx * ng.by);
+            if (l < lz) v = a + RX * (b + RY * l);
+        }
+        roff[u] = v;
+    }
+    for (int c = tid; c < RC; c += kNaThreads) {
+        acc32[c] = 0.0f;
+        acc64[c] = 0.0;
+    }
+    // station ranges of the tile's bin rows: rowinfo[r] = first position in
+    // bin_st, rowinfo[kNaTile + 1 + r] = stations before row r (prefix)
+    if (tid == 0) {
+        int q = 0;
+        const int i1 = min(I0 + kNaTile, ng.nbx);
+        for (int r = 0; r < kNaTile; ++r) {
+            const int sbj = J0 + r;
+            int p0 = 0, p1 = 0;
+            if (sbj < ng.nby) {
+                p0 = bin_start[I0 + ng.nbx * sbj];
+                p1 = bin_start[i1 + ng.nbx * sbj];
+            }
+            rowinfo[r] = p0;
+            rowinfo[kNaTile + r] = q;
+            q += p1 - p0;
+        }
+        rowinfo[2 * kNaTile] = q;
+        for (int k = 0; k < ns; ++k) mbar_init(&full[k], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int Q = rowinfo[2 * kNaTile];
+    const uint32_t row_bytes = 4u * (uint32_t)ng.ld;
+
+    // thread 0: station q's row into stage q % ns, its region base and r
+    auto issue = [&](int q) {
+        int r = 0;
+        while (r + 1 < kNaTile && rowinfo[kNaTile + r + 1] <= q) ++r;
+        const int sidx = bin_st[rowinfo[r] + (q - rowinfo[kNaTile + r])];
+        const int ri = st_i0[sidx] + ng.bx - 1 - I0;
+        const int rj = st_j0[sidx] + ng.by - 1 - J0;
+        const int k = q % ns;
+        sbase[k] = (ri >= 0 && ri < kNaTile && rj >= 0 && rj < kNaTile) ? ri + RX * rj : -1;
+        srv[k] = stz[sidx].y;
+        mbar_arrive_expect_tx(&full[k], row_bytes);
+        tma_load_1d(stage + (size_t)k * ng.ld, dG + (int64_t)sidx * ng.ld, row_bytes, &full[k]);
+    };
+    if (tid == 0)
+        for (int q = 0; q < min(Q, ns); ++q) issue(q);
+
+    for (int q = 0; q < Q; ++q) {
+        const int k = q % ns;
+        if (tid == 0) flag[q & 1] = mbar_wait_bounded(&full[k], (uint32_t)((q / ns) & 1)) ? 1 : 0;
+        __syncthreads();   // also orders station q-1's shared-memory sums before station q's
+        if (!flag[q & 1]) {
+            if (tid == 0) {
+                set_status(status, kStatusMbarTimeout);
+                for (int u = q + 1; u < min(Q, max(q - 1 + ns, ns)); ++u)   // copies still in flight
+                    (void)mbar_wait_bounded(&full[u % ns], (uint32_t)((u / ns) & 1));
+            }
+            return;
+        }
+        if (tid == 0 && q >= 1 && q - 1 + ns < Q) {   // stage (q-1) % ns was read before the barrier
+            fence_proxy_async_smem();
+            issue(q - 1 + ns);
+        }
+        const int base = sbase[k];
+        const float rv = srv[k];
+        if (base >= 0 && rv != 0.0f) {
+            const float *gr = stage + (size_t)k * ng.ld;
+            for (int u = tid; u < ng.ld; u += kNaThreads) {
+                const int o = roff[u];
+                if (o >= 0) acc32[base + o] = fmaf(gr[u], rv, acc32[base + o]);
+            }
+        }
+        if ((q + 1) % kNaFold == 0 || q + 1 == Q) {
+            __syncthreads();
+            for (int c = tid; c < RC; c += kNaThreads) {
+                acc64[c] += (double)acc32[c];
+                acc32[c] = 0.0f;
+            }
+        }
+    }
+    __syncthreads();
+    double *dst = tpart + (size_t)blockIdx.x * RC;
+    for (int c = tid; c < RC; c += kNaThreads) dst[c] = acc64[c];
+}
+
+// out[x + nx (y + ny l)] = sum over the station tiles (tx, ty) whose region holds
+// the cell, ty then tx ascending (fixed order).
+__global__ void k_near_adj_gather(int nx, int ny, int lz, int bx, int by, int RX, int RY, int ntx,
+                                  const double *__restrict__ tpart, double *__restrict__ out) {
+    const int64_t total = (int64_t)nx * ny * lz;
+    const int64_t RC = (int64_t)RX * RY * lz;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(k % nx);
+        const int y = (int)((k / nx) % ny);
+        const int l = (int)(k / ((int64_t)nx * ny));
+        double s = 0.0;
+        for (int ty = y / kNaTile; ty <= (y + by - 1) / kNaTile; ++ty)
+            for (int tx = x / kNaTile; tx <= (x + bx - 1) / kNaTile; ++tx) {
+                const int ri = x - (tx * kNaTile - bx + 1), rj = y - (ty * kNaTile - by + 1);
+                s += tpart[(int64_t)(ty * ntx + tx) * RC + ri + (int64_t)RX * (rj + (int64_t)RY * l)];
+            }
+        out[k] = s;
+    }
 }
 
 // out[k] = vol * fs * (sum_c apart[c][k] + near[k] (top bz layers)) [* w2_l] [+ add[k]],
@@ -1193,11 +1382,15 @@ size_t mixed_scratch_bytes(const grav_plan *p) {
     add(8); add(8);                                                         // max|r|, max|m|
     add(8ull * z.nchunk * N);                                               // m_part
     add(8ull * z.nschunk * M);                                              // m_apart
-    add(4ull * N * p->ng.slots);                                            // dG (FP32)
+    add(4ull * N * p->ng.ld);                                               // dG (FP32, padded rows)
     add(4ull * N); add(4ull * N);                                           // i0, j0
-    add(4ull * p->ng.slots);                                                // slot -> cell offset
+    add(4ull * p->ng.ld);                                                   // slot -> cell offset
     add(8ull * N); add(8ull * N);                                           // diag_corr, near_corr
     add(8ull * p->nx * p->ny * lz);                                         // near adjoint
+    {
+        const NearAdjShape na = near_adj_shape(p);
+        if (na.ok) add(8ull * na.ntx * na.nty * na.RC);                     // per-tile near sums
+    }
     add(4ull * N); add(4ull * N); add(4ull * N); add(4ull * N);             // keys, keys_sorted, vals, bin_st
     add(4ull * (z.nbins + 2));                                              // bin_start
     add(z.cub_temp);
@@ -1270,14 +1463,20 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
     p->m_adj_bc = z.bc;
     p->m_part = (double *)take(p, 8ull * z.nchunk * p->N);
     p->m_apart = (double *)take(p, 8ull * z.nschunk * p->M);
-    p->dG = (float *)take(p, 4ull * p->N * p->ng.slots);
+    p->dG = (float *)take(p, 4ull * p->N * p->ng.ld);
     p->st_i0 = (int *)take(p, 4ull * p->N);
     p->st_j0 = (int *)take(p, 4ull * p->N);
-    p->near_off = (int *)take(p, 4ull * p->ng.slots);
+    p->near_off = (int *)take(p, 4ull * p->ng.ld);
     p->diag_corr = (double *)take(p, 8ull * p->N);
     p->near_corr = (double *)take(p, 8ull * p->N);
     const int64_t lz = std::min(p->ng.bz, nz);
     p->m_cellacc = (double *)take(p, 8ull * nx * ny * lz);
+    {
+        const NearAdjShape na = near_adj_shape(p);
+        const char *ev = std::getenv("GRAV_NEAR_ADJ");   // "tiles": the cell-tiled form below
+        p->near_adj_rows = na.ok && !(ev && std::strcmp(ev, "tiles") == 0);
+        if (p->near_adj_rows) p->near_tpart = (double *)take(p, 8ull * na.ntx * na.nty * na.RC);
+    }
     unsigned *keys = (unsigned *)take(p, 4ull * p->N);
     unsigned *keys_sorted = (unsigned *)take(p, 4ull * p->N);
     int *vals = (int *)take(p, 4ull * p->N);
@@ -1330,12 +1529,12 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
 
     {
         // slot t = a + bx (bj + by l) of a station's window box -> cell offset from its box origin
-        std::vector<int> hoff(p->ng.slots);
+        std::vector<int> hoff(p->ng.ld, 0);   // padding slots: offset 0
         for (int l = 0; l < p->ng.bz; ++l)
             for (int bj = 0; bj < p->ng.by; ++bj)
                 for (int a = 0; a < p->ng.bx; ++a)
                     hoff[a + p->ng.bx * (bj + p->ng.by * l)] = a + nx * (bj + ny * l);
-        cudaMemcpyAsync(p->near_off, hoff.data(), 4ull * p->ng.slots, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(p->near_off, hoff.data(), 4ull * p->ng.ld, cudaMemcpyHostToDevice, s);
     }
     cudaMemcpyAsync(p->m_cx, hcx.data(), 8ull * nx, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(p->m_cy, hcy.data(), 8ull * ny, cudaMemcpyHostToDevice, s);
@@ -1488,9 +1687,22 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
     stage_end(p, kStageAdjMain, s);
     const int lz = std::min(p->ng.bz, p->nz);
     stage_begin(p, kStageAdjNear, s);
-    dim3 gna((unsigned)((p->nx + 31) / 32), (unsigned)((p->ny + 7) / 8), (unsigned)lz);
-    k_near_adj<<<gna, 256, 0, s>>>(p->nx, p->ny, p->ng, p->dG, p->bin_start, p->bin_st, p->st_i0, p->stz,
-                                   p->m_cellacc);
+    if (p->near_adj_rows) {
+        const NearAdjShape na = near_adj_shape(p);
+        cudaFuncSetAttribute(k_near_adj_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)na.smem);
+        k_near_adj_rows<<<(unsigned)(na.ntx * na.nty), kNaThreads, na.smem, s>>>(
+            p->ng, na.RX, na.RY, na.lz, na.ns, na.ntx, (uint32_t)na.o_roff, (uint32_t)na.o_sb,
+            (uint32_t)na.o_acc32, (uint32_t)na.o_acc64, (uint32_t)na.o_stage, p->dG, p->bin_start, p->bin_st,
+            p->st_i0, p->st_j0, p->stz, p->near_tpart, p->ctx->d_status);
+        const int64_t cells = (int64_t)p->nx * p->ny * lz;
+        k_near_adj_gather<<<grid_for(cells, 256), 256, 0, s>>>(p->nx, p->ny, lz, p->ng.bx, p->ng.by, na.RX, na.RY,
+                                                               na.ntx, p->near_tpart, p->m_cellacc);
+        note_launches(1);
+    } else {
+        dim3 gna((unsigned)((p->nx + 31) / 32), (unsigned)((p->ny + 7) / 8), (unsigned)lz);
+        k_near_adj<<<gna, 256, 0, s>>>(p->nx, p->ny, p->ng, p->dG, p->bin_start, p->bin_st, p->st_i0, p->stz,
+                                       p->m_cellacc);
+    }
     stage_end(p, kStageAdjNear, s);
     note_launches(2);
 }

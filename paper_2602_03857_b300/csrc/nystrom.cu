@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256) k_nys_near(int nx, int ny, int nz, NearGe
         if (i < 0 || i >= nx || j < 0 || j >= ny || l >= nz) continue;
         const int64_t k = (int64_t)i + (int64_t)nx * (j + (int64_t)ny * l) - c0;
         if (k < 0 || k >= cb) continue;
-        const float d = dG[s * ng.slots + t];
+        const float d = dG[s * ng.ld + t];
         if (d != 0.0f) B[k * N + s] += d * fac[l];
     }
 }
