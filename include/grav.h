@@ -255,14 +255,27 @@ int grav_plan_destroy(grav_plan *plan, grav_stream_t stream);
 /* A context runs a scheduler with K slots (default 4, or GRAV_SERVE_SLOTS in
  * the environment, or grav_serve_config before the first submit).  Each slot
  * is a host worker thread with its own non-blocking CUDA stream.  Submitted
- * jobs wait in a FIFO queue; a free slot takes the head job as soon as the
- * job's device footprint (its plan, plus the CG vectors for an inversion)
- * fits in the context's HBM budget next to the jobs already running.  Jobs
+ * jobs wait in a queue; a free slot takes the oldest job as soon as the job's
+ * device footprint (its plan, plus the CG vectors for an inversion) fits in
+ * the context's HBM budget next to the jobs already running.  When the oldest
+ * job does not fit, the first later job that does may start instead
+ * (backfill), at most 8 times before the oldest job is served first.  Jobs
  * therefore start while others are still on the GPU and their kernels
- * overlap on the device.  Each job builds its own plan, and every kernel is
- * deterministic, so a job's result is bitwise the same alone and in a mix.
- * The serving entry points are the request-loop counterpart of the paper's
- * single inversion run (Section 3.1); the paper has no serving layer. */
+ * overlap on the device.
+ *
+ * Plans stay resident: a finished job leaves its plan (mesh tables, station
+ * arrays, near-field table, the trace of G W^-2 G^T) in a cache of idle plans,
+ * and a later job with the same mesh edges, the same survey arrays (device
+ * pointers and n) holding the same values (a 64-bit fingerprint of x, y, z is
+ * taken on the device when the job starts), and the same precision, z0,
+ * near_cells and cache_g runs on it without building one.  Idle plans count
+ * against the HBM budget and are released, least recently used first, when
+ * an admission needs the memory or the cache exceeds its entry limit.  Every
+ * kernel is deterministic and a reused plan holds the same tables, so a
+ * job's result is bitwise the same alone, in a mix, and on a fresh or a
+ * resident plan.  The serving entry points are the request-loop counterpart
+ * of the paper's single inversion run (Section 3.1); the paper has no serving
+ * layer. */
 #define GRAV_JOB_FORWARD   0   /* output d = G input */
 #define GRAV_JOB_INVERT    1   /* output m from data `input`, as grav_datainv_solve */
 
@@ -301,6 +314,18 @@ int grav_cancel(grav_ctx *ctx, uint64_t job_id);
 int grav_job_times(grav_ctx *ctx, uint64_t job_id, double *t_submit, double *t_start, double *t_end);
 /* Forgets a finished job's record (GRAV_EBUSY while queued or running). */
 int grav_job_release(grav_ctx *ctx, uint64_t job_id);
+/* Plan of a job: *plan_reused = 1 if it ran on a resident plan; *setup_s =
+ * host wall time of building its plan (0 when reused); *footprint = the
+ * device bytes its admission reserved.  Any pointer may be NULL. */
+int grav_job_plan(grav_ctx *ctx, uint64_t job_id, int *plan_reused, double *setup_s, size_t *footprint);
+/* At most max_plans idle plans stay resident (0..1024, default 16; 0 turns
+ * the plan cache off).  May be called at any time; excess plans are released
+ * at the next admission or job end. */
+int grav_serve_plan_cache(grav_ctx *ctx, int max_plans);
+/* Plans built and reused by the scheduler so far, idle plans resident now and
+ * their device bytes.  Any pointer may be NULL. */
+int grav_serve_stats(grav_ctx *ctx, int64_t *plans_built, int64_t *plans_reused, int *plans_resident,
+                     size_t *bytes_resident);
 
 /* ---- forward product without device allocation --------------------------- */
 /* The paper has no counterpart to this entry point.  It serves callers that

@@ -117,6 +117,10 @@ _sig("grav_wait", _i, [_vp, ctypes.c_uint64, ctypes.c_double])
 _sig("grav_cancel", _i, [_vp, ctypes.c_uint64])
 _sig("grav_job_times", _i, [_vp, ctypes.c_uint64, _D, _D, _D])
 _sig("grav_job_release", _i, [_vp, ctypes.c_uint64])
+_sig("grav_job_plan", _i, [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), _D, ctypes.POINTER(ctypes.c_size_t)])
+_sig("grav_serve_plan_cache", _i, [_vp, _i])
+_sig("grav_serve_stats", _i, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)])
 _sig("grav_eval_fn64", _i, [_vp, _i, _vp, _vp, _vp, ctypes.c_int64, _vp])
 _sig("grav_plan_check_fp64", _i, [_vp, _vp, _vp, _i, _D, _D, _vp])
 _sig("grav_selftest_wait", _i, [_vp, ctypes.c_double, _vp])
@@ -132,7 +136,7 @@ EXPORTED = [
     "grav_plan_forward", "grav_plan_adjoint", "grav_plan_bytes", "grav_plan_destroy",
     "grav_launch_count", "grav_plan_timing", "grav_bench_pipes", "grav_plan_describe",
     "grav_serve_config", "grav_submit", "grav_poll", "grav_wait", "grav_cancel", "grav_job_times",
-    "grav_job_release", "grav_eval_fn64", "grav_plan_check_fp64", "grav_datainv_solve_ex", "grav_selftest_wait",
+    "grav_job_release", "grav_job_plan", "grav_serve_plan_cache", "grav_serve_stats", "grav_eval_fn64", "grav_plan_check_fp64", "grav_datainv_solve_ex", "grav_selftest_wait",
     "grav_nystrom_coarse_apply",
 ]
 
@@ -257,6 +261,23 @@ class Context:
         self.check(_lib.grav_job_times(self.h, ctypes.c_uint64(job_id), ctypes.byref(a), ctypes.byref(b),
                                        ctypes.byref(c)))
         return a.value, b.value, c.value
+
+    def job_plan(self, job_id: int) -> dict:
+        """Whether the job ran on a resident plan, its plan set-up time and its reserved footprint."""
+        r, t, b = ctypes.c_int(0), ctypes.c_double(0), ctypes.c_size_t(0)
+        self.check(_lib.grav_job_plan(self.h, ctypes.c_uint64(job_id), ctypes.byref(r), ctypes.byref(t),
+                                      ctypes.byref(b)))
+        return {"plan_reused": bool(r.value), "setup_s": t.value, "footprint": int(b.value)}
+
+    def plan_cache(self, max_plans: int):
+        """At most max_plans idle plans stay resident (0 turns the plan cache off)."""
+        self.check(_lib.grav_serve_plan_cache(self.h, int(max_plans)))
+
+    def serve_stats(self) -> dict:
+        a, b, c, d = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int(0), ctypes.c_size_t(0)
+        self.check(_lib.grav_serve_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+        return {"plans_built": a.value, "plans_reused": b.value, "plans_resident": c.value,
+                "bytes_resident": int(d.value)}
 
     def release(self, job_id: int):
         self.check(_lib.grav_job_release(self.h, ctypes.c_uint64(job_id)))

@@ -611,12 +611,18 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
         // lambda = lambda_scale * trace(G W^-2 G^T) / N; the diagonal also feeds
         // the Jacobi preconditioner M = diag(G W^-2 G^T + lambda I)
         const bool jac = o.precond == 1, nys = o.precond == 2, pc = jac || nys;
-        if (!(lam > 0) || jac) {
+        if (!(lam > 0) && !jac && p->trace_cache > 0) {
+            // a resident plan (serving) keeps the trace of its first solve: the
+            // same deterministic value, without another diagonal pass
+            trace = p->trace_cache;
+            lam = o.lambda_scale * trace / (double)N;
+        } else if (!(lam > 0) || jac) {
             if ((rc = plan_diag(p, dinv, s))) break;
             if (!(lam > 0)) {
                 launch_dot(dinv, nullptr, N, dp, sc + kSTrace, s);
                 if ((rc = sync_scalars("trace"))) break;
                 trace = hsc[kSTrace];
+                if (trace > 0 && std::isfinite(trace)) p->trace_cache = trace;
                 lam = o.lambda_scale * trace / (double)N;
                 if (!(lam > 0) || !std::isfinite(lam)) {
                     rc = set_error(ctx, GRAV_EDEVICE, "lambda from the trace is not positive (trace %g)", trace);

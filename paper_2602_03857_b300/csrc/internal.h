@@ -154,6 +154,8 @@ struct grav_plan {
     double *cr_part = nullptr;            // [cr_nchunk][N] row-chunk partials of the corner forward
     int cr_ldw = 0, cr_rows_per_chunk = 0, cr_nchunk = 0;
 
+    double trace_cache = 0.0;             // trace(G W^-2 G^T) of an earlier solve on this plan (0: none)
+
     // CG / diag scratch
     double *diag = nullptr;               // [N]
     double *vec = nullptr;                // CG vectors

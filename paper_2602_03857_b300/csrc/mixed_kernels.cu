@@ -987,10 +987,12 @@ constexpr int kNaMaxStages = 12;
 constexpr size_t kNaSmemBudget = 110 * 1024;   // two CTAs per SM
 static_assert(8 * kNaMaxStages + 8 <= 128 && 128 + 4 * (2 * kNaTile + 1) <= 256, "near adjoint header");
 
+constexpr int kNaMeta = 256;     // station metadata ring (prefetched 128 stations ahead)
+
 struct NearAdjShape {
     bool ok = false;
     int RX = 0, RY = 0, lz = 0, RC = 0, ns = 0, ntx = 0, nty = 0;
-    size_t o_roff = 0, o_sb = 0, o_acc32 = 0, o_acc64 = 0, o_stage = 0, smem = 0;
+    size_t o_roff = 0, o_sb = 0, o_meta = 0, o_acc32 = 0, o_acc64 = 0, o_stage = 0, smem = 0;
 };
 
 static NearAdjShape near_adj_shape(const grav_plan *p) {
@@ -1003,7 +1005,8 @@ static NearAdjShape near_adj_shape(const grav_plan *p) {
     z.nty = (p->ng.nby + kNaTile - 1) / kNaTile;
     z.o_roff = 256;                                           // header: mbarriers, flags, row table
     z.o_sb = align_up(z.o_roff + 4ull * p->ng.ld, 16);       // roff[ld]
-    z.o_acc32 = z.o_sb + 2ull * 4 * kNaMaxStages;             // sbase[], srv[]
+    z.o_meta = z.o_sb + 2ull * 4 * kNaMaxStages;              // sbase[], srv[]
+    z.o_acc32 = z.o_meta + 3ull * 4 * kNaMeta;                // station ring: index, base, r
     z.o_acc64 = align_up(z.o_acc32 + 4ull * z.RC, 16);
     z.o_stage = align_up(z.o_acc64 + 8ull * z.RC, 128);
     const size_t row = 4ull * p->ng.ld;
@@ -1015,8 +1018,8 @@ static NearAdjShape near_adj_shape(const grav_plan *p) {
 }
 
 __global__ void __launch_bounds__(kNaThreads) k_near_adj_rows(
-    NearGeo ng, int RX, int RY, int lz, int ns, int ntx, uint32_t o_roff, uint32_t o_sb, uint32_t o_acc32,
-    uint32_t o_acc64, uint32_t o_stage, const float *__restrict__ dG, const int *__restrict__ bin_start,
+    NearGeo ng, int RX, int RY, int lz, int ns, int ntx, uint32_t o_roff, uint32_t o_sb, uint32_t o_meta,
+    uint32_t o_acc32, uint32_t o_acc64, uint32_t o_stage, const float *__restrict__ dG, const int *__restrict__ bin_start,
     const int *__restrict__ bin_st, const int *__restrict__ st_i0, const int *__restrict__ st_j0,
     const float2 *__restrict__ stz, double *__restrict__ tpart, int *status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1027,6 +1030,9 @@ __global__ void __launch_bounds__(kNaThreads) k_near_adj_rows(
     int *roff = reinterpret_cast<int *>(smem_raw + o_roff);
     int *sbase = reinterpret_cast<int *>(smem_raw + o_sb);
     float *srv = reinterpret_cast<float *>(smem_raw + o_sb + 4 * kNaMaxStages);
+    int *msidx = reinterpret_cast<int *>(smem_raw + o_meta);          // [kNaMeta]
+    int *mbase = msidx + kNaMeta;                                      // [kNaMeta]
+    float *mrv = reinterpret_cast<float *>(mbase + kNaMeta);          // [kNaMeta]
     float *acc32 = reinterpret_cast<float *>(smem_raw + o_acc32);
     double *acc64 = reinterpret_cast<double *>(smem_raw + o_acc64);
     float *stage = reinterpret_cast<float *>(smem_raw + o_stage);
@@ -1073,19 +1079,38 @@ __global__ void __launch_bounds__(kNaThreads) k_near_adj_rows(
     const int Q = rowinfo[2 * kNaTile];
     const uint32_t row_bytes = 4u * (uint32_t)ng.ld;
 
-    // thread 0: station q's row into stage q % ns, its region base and r
+    // station metadata (table row, region base, FP32 r) for stations [u0, u1),
+    // into ring slot u % kNaMeta, one station per thread: the dependent global
+    // loads run in parallel and ahead of the copies that need them
+    auto fetch_meta = [&](int u0, int u1) {
+        const int u = u0 + tid;
+        if (u < u1) {
+            int r = 0;
+            while (r + 1 < kNaTile && rowinfo[kNaTile + r + 1] <= u) ++r;
+            const int sidx = bin_st[rowinfo[r] + (u - rowinfo[kNaTile + r])];
+            const int ri = st_i0[sidx] + ng.bx - 1 - I0;
+            const int rj = st_j0[sidx] + ng.by - 1 - J0;
+            const int slot = u % kNaMeta;
+            msidx[slot] = sidx;
+            mbase[slot] = (ri >= 0 && ri < kNaTile && rj >= 0 && rj < kNaTile) ? ri + RX * rj : -1;
+            mrv[slot] = stz[sidx].y;
+        }
+    };
+    // thread 0: station q's row into stage q % ns, with its region base and r
     auto issue = [&](int q) {
-        int r = 0;
-        while (r + 1 < kNaTile && rowinfo[kNaTile + r + 1] <= q) ++r;
-        const int sidx = bin_st[rowinfo[r] + (q - rowinfo[kNaTile + r])];
-        const int ri = st_i0[sidx] + ng.bx - 1 - I0;
-        const int rj = st_j0[sidx] + ng.by - 1 - J0;
-        const int k = q % ns;
-        sbase[k] = (ri >= 0 && ri < kNaTile && rj >= 0 && rj < kNaTile) ? ri + RX * rj : -1;
-        srv[k] = stz[sidx].y;
+        const int k = q % ns, slot = q % kNaMeta;
+        const int sidx = msidx[slot];
+        sbase[k] = mbase[slot];
+        srv[k] = mrv[slot];
         mbar_arrive_expect_tx(&full[k], row_bytes);
         tma_load_1d(stage + (size_t)k * ng.ld, dG + (int64_t)sidx * ng.ld, row_bytes, &full[k]);
     };
+    static_assert(kNaMeta == kNaThreads, "one metadata slot per thread");
+    auto fetch_meta_half = [&](int u0, int u1) {
+        if (tid < kNaMeta / 2) fetch_meta(u0, u1);
+    };
+    fetch_meta(0, min(Q, kNaMeta));
+    __syncthreads();
     if (tid == 0)
         for (int q = 0; q < min(Q, ns); ++q) issue(q);
 
@@ -1105,6 +1130,9 @@ __global__ void __launch_bounds__(kNaThreads) k_near_adj_rows(
             fence_proxy_async_smem();
             issue(q - 1 + ns);
         }
+        // refill half of the metadata ring: slots of stations [q + 128, q + 256) held
+        // stations [q - 128, q), all issued (ns <= 12); read after >= 1 more barrier
+        if (q % (kNaMeta / 2) == 0 && q > 0) fetch_meta_half(q + kNaMeta / 2, min(Q, q + kNaMeta));
         const int base = sbase[k];
         const float rv = srv[k];
         if (base >= 0 && rv != 0.0f) {
@@ -1691,7 +1719,7 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
         const NearAdjShape na = near_adj_shape(p);
         cudaFuncSetAttribute(k_near_adj_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)na.smem);
         k_near_adj_rows<<<(unsigned)(na.ntx * na.nty), kNaThreads, na.smem, s>>>(
-            p->ng, na.RX, na.RY, na.lz, na.ns, na.ntx, (uint32_t)na.o_roff, (uint32_t)na.o_sb,
+            p->ng, na.RX, na.RY, na.lz, na.ns, na.ntx, (uint32_t)na.o_roff, (uint32_t)na.o_sb, (uint32_t)na.o_meta,
             (uint32_t)na.o_acc32, (uint32_t)na.o_acc64, (uint32_t)na.o_stage, p->dG, p->bin_start, p->bin_st,
             p->st_i0, p->st_j0, p->stz, p->near_tpart, p->ctx->d_status);
         const int64_t cells = (int64_t)p->nx * p->ny * lz;

@@ -224,3 +224,103 @@ def test_cancel_timeout_and_errors(g):
         assert e.value.code == g.GRAV_ENOMEM
     finally:
         small.close()
+
+
+def test_backfill_and_resident_plans(g):
+    """Admission by footprint with backfill, and resident plans.
+
+    Two inversions L1, L2 on one mesh and survey (different data) and a small
+    forward job S are submitted in the order L1, L2, S to a context whose HBM
+    budget (2 f_L - 1, f the reserved footprints) holds L1 + S and L1's
+    resident plan + L2, but not L1 + L2.  L2 must wait for L1's memory; S,
+    behind it in the queue, starts at once and finishes before L2 starts
+    (strict FIFO would hold it behind L2).  L2 then runs on the plan L1 left
+    resident.  Every output equals the same job run through the one-shot
+    calls, bitwise."""
+    mesh, sv, m = _problem(60, 70, 60, 24, 4000, 25.0)
+    S_big = g.Survey(sv.x, sv.y, sv.z)
+    d1 = oracle.forward(mesh, sv, m)
+    d2 = d1 * 0.5 + synth.random_vector(sv.n, 61, 0.01)
+    smesh, ssv, sm = _problem(62, 20, 18, 8, 300, 25.0)
+    S_small = g.Survey(ssv.x, ssv.y, ssv.z)
+    inv = dict(precision="mixed", tol=1e-6, max_iter=3000)
+    solo_ctx = g.context()
+    ref1, _ = g.datainv(_dev(d1), mesh, S_big, ctx=solo_ctx, **inv)
+    ref2, _ = g.datainv(_dev(d2), mesh, S_big, ctx=solo_ctx, **inv)
+    refs = g.forward(_dev(sm), smesh, S_small, ctx=solo_ctx, precision="mixed")
+    # footprints, measured by the scheduler itself on a roomy context
+    probe = g.Context(0)
+    try:
+        probe.plan_cache(0)
+        o = torch.empty(mesh.ncells, dtype=torch.float64, device="cuda")
+        a = probe.submit("invert", mesh, S_big, _dev(d1), o, **inv)
+        os_ = torch.empty(ssv.n, dtype=torch.float64, device="cuda")
+        b = probe.submit("forward", smesh, S_small, _dev(sm), os_, precision="mixed")
+        assert probe.wait(a, 600.0) == g.GRAV_OK and probe.wait(b, 600.0) == g.GRAV_OK
+        f_big, f_small = probe.job_plan(a)["footprint"], probe.job_plan(b)["footprint"]
+    finally:
+        probe.close()
+    assert f_small < f_big // 4
+    ctx = g.Context(0, hbm_budget=2 * f_big - 1)
+    try:
+        ctx.serve_config(3)
+        out1 = torch.full((mesh.ncells,), float("nan"), dtype=torch.float64, device="cuda")
+        out2 = torch.full((mesh.ncells,), float("nan"), dtype=torch.float64, device="cuda")
+        outs = torch.full((ssv.n,), float("nan"), dtype=torch.float64, device="cuda")
+        j1 = ctx.submit("invert", mesh, S_big, _dev(d1), out1, **inv)
+        j2 = ctx.submit("invert", mesh, S_big, _dev(d2), out2, **inv)
+        js = ctx.submit("forward", smesh, S_small, _dev(sm), outs, precision="mixed")
+        for j in (j1, j2, js):
+            assert ctx.wait(j, 600.0) == g.GRAV_OK
+        t1, t2, ts = ctx.job_times(j1), ctx.job_times(j2), ctx.job_times(js)
+        assert t2[1] >= t1[2], "L2 started before L1 released its memory"
+        assert ts[1] < t2[1] and ts[2] <= t2[1], "the small job did not backfill ahead of L2"
+        assert ctx.job_plan(j2)["plan_reused"] and not ctx.job_plan(j1)["plan_reused"]
+        assert ctx.job_plan(j2)["setup_s"] == 0.0
+        assert torch.equal(out1, ref1) and torch.equal(out2, ref2) and torch.equal(outs, refs)
+    finally:
+        ctx.close()
+
+
+def test_resident_plan_stream_and_changed_survey(g):
+    """An inversion stream on one survey through one slot builds one plan and
+    reuses it; each result equals its one-shot run bitwise and the first one
+    passes the oracle check.  Changing the survey's values in place (same
+    device arrays) makes the next job build a fresh plan, whose result is the
+    one-shot result for the new stations."""
+    mesh, sv, m = _problem(70, 30, 26, 10, 700, 30.0)
+    S = g.Survey(sv.x, sv.y, sv.z)
+    d = oracle.forward(mesh, sv, m)
+    opts = dict(precision="fp64", tol=1e-8, max_iter=3000)
+    solo_ctx = g.context()
+    ctx = g.Context(0)
+    try:
+        ctx.serve_config(1)
+        datas = [d] + [d + synth.random_vector(sv.n, 71 + k, 0.005) for k in range(3)]
+        ids, outs = [], []
+        for dk in datas:
+            out = torch.full((mesh.ncells,), float("nan"), dtype=torch.float64, device="cuda")
+            ids.append(ctx.submit("invert", mesh, S, _dev(dk), out, **opts))
+            outs.append(out)
+        for j in ids:
+            assert ctx.wait(j, 600.0) == g.GRAV_OK
+        st = ctx.serve_stats()
+        assert st["plans_built"] == 1 and st["plans_reused"] == 3 and st["plans_resident"] == 1
+        assert [ctx.job_plan(j)["plan_reused"] for j in ids] == [False, True, True, True]
+        for dk, out in zip(datas, outs):
+            ref, _ = g.datainv(_dev(dk), mesh, S, ctx=solo_ctx, **opts)
+            assert torch.equal(out, ref)
+        _oracle_check("invert", "fp64", mesh, sv, _dev(datas[0]), outs[0], opts["tol"])
+        # same arrays, new values: no reuse, and the result follows the new survey
+        S.z.sub_(1.5)
+        sv2 = synth.Survey(sv.x, sv.y, sv.z - 1.5)
+        out = torch.full((mesh.ncells,), float("nan"), dtype=torch.float64, device="cuda")
+        j = ctx.submit("invert", mesh, S, _dev(d), out, **opts)
+        assert ctx.wait(j, 600.0) == g.GRAV_OK
+        assert not ctx.job_plan(j)["plan_reused"]
+        ref, _ = g.datainv(_dev(d), mesh, S, ctx=solo_ctx, **opts)
+        assert torch.equal(out, ref)
+        assert ctx.serve_stats()["plans_built"] == 2
+        _oracle_check("invert", "fp64", mesh, sv2, _dev(d), out, opts["tol"])
+    finally:
+        ctx.close()
