@@ -70,6 +70,31 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase,
     }
 }
 
+// As mbar_wait_bounded, but polling with mbarrier.try_wait (the hardware
+// suspends the thread until the phase completes or a short system time limit
+// passes) instead of test_wait + __nanosleep: for pipelines whose consumer
+// spends little time per stage, where a sleep quantum would dominate.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_spin_bounded(uint64_t *bar, uint32_t phase,
+                                                       uint64_t limit_ns = kWaitLimitNs) {
+    if (mbar_try_wait(bar, phase)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (true) {
+        if (mbar_try_wait(bar, phase)) return true;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
+}
+
 // 1D bulk copy global -> shared, completing on `bar` (TMA, no tensor map).
 // dst and src must be 16-byte aligned and bytes a multiple of 16.
 __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {

@@ -976,23 +976,25 @@ __global__ void __launch_bounds__(256, 4) k_near_adj(int nx, int ny, NearGeo ng,
 // base(s) + roff[u].  The slots of one station map to distinct cells and a
 // barrier separates consecutive stations, so every cell receives its terms in
 // station order (bitwise deterministic).  Terms are summed in FP32 in shared
-// memory and folded into an FP64 region sum every kNaFold stations (a cell
-// sees at most kNaFold FP32 terms between folds).  Each CTA stores its region
-// sums to tpart[tile]; k_near_adj_gather adds, per cell, the tiles whose
-// region holds it, in tile order.
+// memory and folded every kNaFold stations into the CTA's FP64 region sums,
+// tpart[tile] in global memory (a cell sees at most kNaFold FP32 terms
+// between folds); k_near_adj_gather adds, per cell, the tiles whose region
+// holds it, in tile order.
 constexpr int kNaTile = 8;
 constexpr int kNaThreads = 256;
 constexpr int kNaFold = 16;
 constexpr int kNaMaxStages = 12;
-constexpr size_t kNaSmemBudget = 110 * 1024;   // two CTAs per SM
+constexpr size_t kNaSmemBudget = 74 * 1024;    // three CTAs per SM
 static_assert(8 * kNaMaxStages + 8 <= 128 && 128 + 4 * (2 * kNaTile + 1) <= 256, "near adjoint header");
 
 constexpr int kNaMeta = 256;     // station metadata ring (prefetched 128 stations ahead)
 
+constexpr int kNaMaxKs = 20;      // slots per thread the streaming form handles (rows up to 5120 floats)
+
 struct NearAdjShape {
     bool ok = false;
-    int RX = 0, RY = 0, lz = 0, RC = 0, ns = 0, ntx = 0, nty = 0;
-    size_t o_roff = 0, o_sb = 0, o_meta = 0, o_acc32 = 0, o_acc64 = 0, o_stage = 0, smem = 0;
+    int RX = 0, RY = 0, lz = 0, RC = 0, ns = 0, ntx = 0, nty = 0, ks = 0;
+    size_t o_sb = 0, o_meta = 0, o_acc32 = 0, o_stage = 0, smem = 0;
 };
 
 static NearAdjShape near_adj_shape(const grav_plan *p) {
@@ -1003,23 +1005,24 @@ static NearAdjShape near_adj_shape(const grav_plan *p) {
     z.RC = z.RX * z.RY * z.lz;
     z.ntx = (p->ng.nbx + kNaTile - 1) / kNaTile;
     z.nty = (p->ng.nby + kNaTile - 1) / kNaTile;
-    z.o_roff = 256;                                           // header: mbarriers, flags, row table
-    z.o_sb = align_up(z.o_roff + 4ull * p->ng.ld, 16);       // roff[ld]
+    z.o_sb = 256;                                             // after the header: mbarriers, flags, row table
     z.o_meta = z.o_sb + 2ull * 4 * kNaMaxStages;              // sbase[], srv[]
     z.o_acc32 = z.o_meta + 3ull * 4 * kNaMeta;                // station ring: index, base, r
-    z.o_acc64 = align_up(z.o_acc32 + 4ull * z.RC, 16);
-    z.o_stage = align_up(z.o_acc64 + 8ull * z.RC, 128);
+    z.o_stage = align_up(z.o_acc32 + 4ull * z.RC, 128);
     const size_t row = 4ull * p->ng.ld;
     const int ns = z.o_stage + 2 * row <= kNaSmemBudget ? (int)((kNaSmemBudget - z.o_stage) / row) : 0;
     z.ns = std::min(ns, kNaMaxStages);
     z.smem = z.o_stage + (size_t)z.ns * row;
-    z.ok = z.ns >= 2 && p->ng.ld % 4 == 0;
+    const int need = (p->ng.ld + kNaThreads - 1) / kNaThreads;
+    z.ks = need <= 4 ? 4 : need <= 8 ? 8 : need <= 12 ? 12 : need <= 16 ? 16 : kNaMaxKs;
+    z.ok = z.ns >= 2 && p->ng.ld % 4 == 0 && need <= kNaMaxKs;
     return z;
 }
 
+template <int KS>
 __global__ void __launch_bounds__(kNaThreads) k_near_adj_rows(
-    NearGeo ng, int RX, int RY, int lz, int ns, int ntx, uint32_t o_roff, uint32_t o_sb, uint32_t o_meta,
-    uint32_t o_acc32, uint32_t o_acc64, uint32_t o_stage, const float *__restrict__ dG, const int *__restrict__ bin_start,
+    NearGeo ng, int RX, int RY, int lz, int ns, int ntx, uint32_t o_sb, uint32_t o_meta,
+    uint32_t o_acc32, uint32_t o_stage, const float *__restrict__ dG, const int *__restrict__ bin_start,
     const int *__restrict__ bin_st, const int *__restrict__ st_i0, const int *__restrict__ st_j0,
     const float2 *__restrict__ stz, double *__restrict__ tpart, int *status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1027,30 +1030,35 @@ __global__ void __launch_bounds__(kNaThreads) k_near_adj_rows(
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);                      // [ns], ns <= 12
     volatile int *flag = reinterpret_cast<volatile int *>(smem_raw + 8 * kNaMaxStages);   // [2]
     int *rowinfo = reinterpret_cast<int *>(smem_raw + 128);                       // [2 kNaTile + 1]
-    int *roff = reinterpret_cast<int *>(smem_raw + o_roff);
     int *sbase = reinterpret_cast<int *>(smem_raw + o_sb);
     float *srv = reinterpret_cast<float *>(smem_raw + o_sb + 4 * kNaMaxStages);
     int *msidx = reinterpret_cast<int *>(smem_raw + o_meta);          // [kNaMeta]
     int *mbase = msidx + kNaMeta;                                      // [kNaMeta]
     float *mrv = reinterpret_cast<float *>(mbase + kNaMeta);          // [kNaMeta]
     float *acc32 = reinterpret_cast<float *>(smem_raw + o_acc32);
-    double *acc64 = reinterpret_cast<double *>(smem_raw + o_acc64);
     float *stage = reinterpret_cast<float *>(smem_raw + o_stage);
     const int tid = threadIdx.x;
     const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
     const int I0 = tx * kNaTile, J0 = ty * kNaTile;
     const int RC = RX * RY * lz;
 
-    // slot u = a + bx (b + by l) -> region offset a + RX (b + RY l); padding and
-    // layers below the mesh (l >= lz) take no cell
-    for (int u = tid; u < ng.ld; u += kNaThreads) {
+    // this thread's slots u = tid + 256 k: u = a + bx (b + by l) -> region
+    // offset a + RX (b + RY l), kept in registers; padding and layers below
+    // the mesh (l >= lz) take no cell (-1)
+    int ro[KS];
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+        const int u = tid + kNaThreads * k;
         int v = -1;
         if (u < ng.slots) {
             const int a = u % ng.bx, b = (u / ng.bx) % ng.by, l = u / (ng.bx * ng.by);
             if (l < lz) v = a + RX * (b + RY * l);
         }
-        roff[u] = v;
+        ro[k] = v;
     }
+    // the CTA's FP64 region sums live in its own block of tpart (L2-resident);
+    // thread t alone folds into cells t, t + 256, ..., so the order is fixed
+    double *acc64 = tpart + (size_t)blockIdx.x * RC;
     for (int c = tid; c < RC; c += kNaThreads) {
         acc32[c] = 0.0f;
         acc64[c] = 0.0;
@@ -1116,7 +1124,7 @@ __global__ void __launch_bounds__(kNaThreads) k_near_adj_rows(
 
     for (int q = 0; q < Q; ++q) {
         const int k = q % ns;
-        if (tid == 0) flag[q & 1] = mbar_wait_bounded(&full[k], (uint32_t)((q / ns) & 1)) ? 1 : 0;
+        if (tid == 0) flag[q & 1] = mbar_wait_spin_bounded(&full[k], (uint32_t)((q / ns) & 1)) ? 1 : 0;
         __syncthreads();   // also orders station q-1's shared-memory sums before station q's
         if (!flag[q & 1]) {
             if (tid == 0) {
@@ -1136,11 +1144,17 @@ __global__ void __launch_bounds__(kNaThreads) k_near_adj_rows(
         const int base = sbase[k];
         const float rv = srv[k];
         if (base >= 0 && rv != 0.0f) {
-            const float *gr = stage + (size_t)k * ng.ld;
-            for (int u = tid; u < ng.ld; u += kNaThreads) {
-                const int o = roff[u];
-                if (o >= 0) acc32[base + o] = fmaf(gr[u], rv, acc32[base + o]);
-            }
+            // a station's slots are distinct cells: all loads first, then the
+            // stores (independent, so their latencies overlap)
+            const float *gr = stage + (size_t)k * ng.ld + tid;
+            float gv[KS], av[KS];
+#pragma unroll
+            for (int j = 0; j < KS; ++j) gv[j] = ro[j] >= 0 ? gr[kNaThreads * j] : 0.0f;
+#pragma unroll
+            for (int j = 0; j < KS; ++j) av[j] = ro[j] >= 0 ? acc32[base + ro[j]] : 0.0f;
+#pragma unroll
+            for (int j = 0; j < KS; ++j)
+                if (ro[j] >= 0) acc32[base + ro[j]] = fmaf(gv[j], rv, av[j]);
         }
         if ((q + 1) % kNaFold == 0 || q + 1 == Q) {
             __syncthreads();
@@ -1150,9 +1164,6 @@ __global__ void __launch_bounds__(kNaThreads) k_near_adj_rows(
             }
         }
     }
-    __syncthreads();
-    double *dst = tpart + (size_t)blockIdx.x * RC;
-    for (int c = tid; c < RC; c += kNaThreads) dst[c] = acc64[c];
 }
 
 // out[x + nx (y + ny l)] = sum over the station tiles (tx, ty) whose region holds
@@ -1717,11 +1728,20 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
     stage_begin(p, kStageAdjNear, s);
     if (p->near_adj_rows) {
         const NearAdjShape na = near_adj_shape(p);
-        cudaFuncSetAttribute(k_near_adj_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)na.smem);
-        k_near_adj_rows<<<(unsigned)(na.ntx * na.nty), kNaThreads, na.smem, s>>>(
-            p->ng, na.RX, na.RY, na.lz, na.ns, na.ntx, (uint32_t)na.o_roff, (uint32_t)na.o_sb, (uint32_t)na.o_meta,
-            (uint32_t)na.o_acc32, (uint32_t)na.o_acc64, (uint32_t)na.o_stage, p->dG, p->bin_start, p->bin_st,
-            p->st_i0, p->st_j0, p->stz, p->near_tpart, p->ctx->d_status);
+        auto go = [&](auto kern) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)na.smem);
+            kern<<<(unsigned)(na.ntx * na.nty), kNaThreads, na.smem, s>>>(
+                p->ng, na.RX, na.RY, na.lz, na.ns, na.ntx, (uint32_t)na.o_sb, (uint32_t)na.o_meta,
+                (uint32_t)na.o_acc32, (uint32_t)na.o_stage, p->dG, p->bin_start, p->bin_st,
+                p->st_i0, p->st_j0, p->stz, p->near_tpart, p->ctx->d_status);
+        };
+        switch (na.ks) {
+            case 4: go(k_near_adj_rows<4>); break;
+            case 8: go(k_near_adj_rows<8>); break;
+            case 12: go(k_near_adj_rows<12>); break;
+            case 16: go(k_near_adj_rows<16>); break;
+            default: go(k_near_adj_rows<kNaMaxKs>); break;
+        }
         const int64_t cells = (int64_t)p->nx * p->ny * lz;
         k_near_adj_gather<<<grid_for(cells, 256), 256, 0, s>>>(p->nx, p->ny, lz, p->ng.bx, p->ng.by, na.RX, na.RY,
                                                                na.ntx, p->near_tpart, p->m_cellacc);
