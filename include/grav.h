@@ -431,6 +431,18 @@ int grav_nystrom_coarse_apply(grav_ctx *ctx, const grav_mesh *mesh, const grav_s
                               const double *X, int k, double *Y, const grav_options *opt,
                               grav_stream_t stream);
 
+/* Self-check of the dense kernels behind the Nystrom preconditioner (not in
+ * the paper), on ctx's device, enqueued on `stream`:
+ *   op 0: C (+)= A B, FP32, A(m, k) = A[k + lda m]  (C float, m-fastest: C[m + ldc n])
+ *   op 1: C (+)= A B, FP32, A(m, k) = A[m + lda k]
+ *         (ops 0-1: B(k, n) = B[k + ldb n]; M x N output, inner dimension K)
+ *   op 2: C (+)= A^T A, lower triangle only (C double, C[i + N j], i >= j, i, j < N),
+ *         A(k, i) = A[k + lda i], k < K; exact FP32 products, double-float sums.
+ * accumulate = 1 adds to C.  All pointers DEVICE, 16-byte aligned; lda, ldb,
+ * ldc, K (and M for ops 0-1) multiples of 4; GRAV_EINVAL otherwise. */
+int grav_dense_check(grav_ctx *ctx, int op, int M, int N, int K, const float *A, int64_t lda, const float *B,
+                     int64_t ldb, void *C, int64_t ldc, int accumulate, grav_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

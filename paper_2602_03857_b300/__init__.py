@@ -126,6 +126,8 @@ _sig("grav_plan_check_fp64", _i, [_vp, _vp, _vp, _i, _D, _D, _vp])
 _sig("grav_selftest_wait", _i, [_vp, ctypes.c_double, _vp])
 _sig("grav_nystrom_coarse_apply", _i, [_vp, ctypes.POINTER(grav_mesh), ctypes.POINTER(grav_survey), _i, _vp, _i,
                                        _vp, ctypes.POINTER(grav_options), _vp])
+_sig("grav_dense_check", _i, [_vp, _i, _i, _i, _i, _vp, ctypes.c_int64, _vp, ctypes.c_int64, _vp, ctypes.c_int64, _i,
+                             _vp])
 _sig("grav_datainv_solve_ex", _i, [_vp, ctypes.POINTER(grav_mesh), ctypes.POINTER(grav_survey), _vp, _vp, _vp,
                                    _vp, ctypes.POINTER(grav_solve_info), ctypes.POINTER(grav_options), _vp,
                                    _vp, _vp, _i])
@@ -137,7 +139,7 @@ EXPORTED = [
     "grav_launch_count", "grav_plan_timing", "grav_bench_pipes", "grav_plan_describe",
     "grav_serve_config", "grav_submit", "grav_poll", "grav_wait", "grav_cancel", "grav_job_times",
     "grav_job_release", "grav_job_plan", "grav_serve_plan_cache", "grav_serve_stats", "grav_eval_fn64", "grav_plan_check_fp64", "grav_datainv_solve_ex", "grav_selftest_wait",
-    "grav_nystrom_coarse_apply",
+    "grav_nystrom_coarse_apply", "grav_dense_check",
 ]
 
 STAGES = ("fwd_main", "adj_main", "fwd_near", "adj_near")

@@ -77,7 +77,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
                 if r.returncode != 0:
                     raise RuntimeError(f"nvcc failed on {cmd[2] if cmd[1] == '-c' else cmd[4]}")
     if relink or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        cmd = [nvcc(), "-shared", "-o", LIB + ".tmp"] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lcublas", "-lgomp"]
+        cmd = [nvcc(), "-shared", "-o", LIB + ".tmp"] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lgomp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)

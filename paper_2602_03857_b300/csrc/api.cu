@@ -1237,6 +1237,23 @@ int grav_nystrom_coarse_apply(grav_ctx *ctx, const grav_mesh *mesh, const grav_s
     return rc;
 }
 
+int grav_dense_check(grav_ctx *ctx, int op, int M, int N, int K, const float *A, int64_t lda, const float *B,
+                     int64_t ldb, void *C, int64_t ldc, int accumulate, grav_stream_t stream) {
+    if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    if (op < 0 || op > 2 || M < 0 || N < 0 || K < 0) return set_error(ctx, GRAV_EINVAL, "bad op or size");
+    if (!is_device_ptr(A, ctx->device) || !is_device_ptr(C, ctx->device) ||
+        (op < 2 && !is_device_ptr(B, ctx->device)))
+        return set_error(ctx, GRAV_EINVAL, "A, B and C must be device pointers");
+    const cudaStream_t s = (cudaStream_t)stream;
+    int rc = op < 2 ? launch_sgemm(op == 0, M, N, K, A, lda, B, ldb, (float *)C, ldc, accumulate != 0, s)
+                    : launch_gram_df(N, K, A, lda, (double *)C, accumulate != 0, s);
+    if (rc) return set_error(ctx, GRAV_EINVAL, "unsupported layout (leading dimensions, K, M multiples of 4, "
+                                               "16-byte aligned pointers)");
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GRAV_OK : cuda_error(ctx, e, "dense kernel launch");
+}
+
 int grav_datainv_solve(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey, const double *d,
                        const double *m_ref, double *m_out, double *y_out, grav_solve_info *info,
                        const grav_options *opt, grav_stream_t stream) {

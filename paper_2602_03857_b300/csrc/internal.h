@@ -192,10 +192,13 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
 // scratch t, the cuBLAS handle and the device block holding them.
 struct NysState {
     int ell = 0;
-    int64_t N = 0;
+    int64_t N = 0, ldy = 0;               // ldy: N rounded up to a multiple of 4
     double mu = 0.0, nu = 0.0;
-    double *Y = nullptr, *L = nullptr, *t = nullptr;
-    void *blas = nullptr;
+    float *Y = nullptr;                   // Y = K_c Omega, ldy x ell, column-major (FP32 values)
+    double *Linv = nullptr;               // L^-1, ell x ell column-major, lower (T = L L^T)
+    double *t = nullptr, *u = nullptr, *v = nullptr;   // [ell] application scratch
+    float *vh = nullptr, *vl = nullptr;   // [ell] v as FP32 pairs
+    float *rh = nullptr, *rl = nullptr;   // [ldy] r as FP32 pairs
     char *mem = nullptr;
     size_t bytes = 0;
 };
@@ -281,6 +284,21 @@ Geo make_geo(const grav_plan *p);
 void fill_fn_table(double *t);
 int fn_table_size();
 void launch_corner_fwd(const grav_plan *p, const double *m, cudaStream_t s);
+
+// dense kernels of the Nystrom preconditioner (dense_kernels.cu).  Return -1
+// (nothing launched) when the layout requirements are not met.
+// C (+)= A B in FP32: A(m, k) = A[k + lda m] (a_kmajor) or A[m + lda k];
+// B(k, n) = B[k + ldb n]; C(m, n) = C[m + ldc n].  lda, ldb, ldc, K, M
+// multiples of 4, bases 16-byte aligned.
+int launch_sgemm(bool a_kmajor, int M, int N, int K, const float *A, int64_t lda, const float *B, int64_t ldb,
+                 float *C, int64_t ldc, bool accumulate, cudaStream_t s);
+// G (+)= X^T X (lower triangle, G[i + n j], i >= j) for X[k + ldx i], k < K,
+// i < n; exact FP32 products, double-float sums.  ldx, K multiples of 4.
+int launch_gram_df(int n, int K, const float *X, int64_t ldx, double *G, bool accumulate, cudaStream_t s);
+// z = (r - Y Linv^T Linv Y^T r) / mu  (Y FP32 [ldy][ell], Linv FP64 lower)
+void launch_nys_apply(const float *Y, int64_t ldy, int64_t n, int ell, const double *Linv, double mu,
+                      const double *r, double *z, float *rh, float *rl, double *t, double *u, double *v, float *vh,
+                      float *vl, cudaStream_t s);
 
 // vector kernels (cg_kernels.cu)
 void launch_dot(const double *a, const double *b, int64_t n, double *partials, double *out, cudaStream_t s);

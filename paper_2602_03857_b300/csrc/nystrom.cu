@@ -29,19 +29,27 @@
 // * P^-1 by the Woodbury identity applied to K_hat:
 //     (lambda I + Y M_nu^-1 Y^T)^-1 r = (r - Y T^-1 Y^T r) / lambda,
 //     T = lambda M_nu + Y^T Y,
-//   with one ell x ell Cholesky factor T = L L^T (on the host).  Applying it
-//   costs two GEMVs with the N x ell matrix Y and two triangular solves.
+//   with one ell x ell Cholesky factor T = L L^T and its inverse L^-1 (on
+//   the host, ell^3 / 2 flops; ell <= 8192).  Applying it costs two GEMVs
+//   with the N x ell matrix Y and two triangular products with L^-1
+//   (T^-1 = L^-T L^-1).  Y holds FP32 values (the sketch products are FP32),
+//   so Y is kept in FP32 and the GEMVs take exact FP32 products of Y with
+//   the FP32-pair split of the FP64 vector, summed in double-float
+//   arithmetic: half the bytes of an FP64 Y and no FP64-pipe work.  The
+//   application is the symmetric W W^T form, W = Y L^-T, on the stored numbers.
 // * The ell sketch products Y = K_c Omega share every pair term: the coarse
 //   operator is formed explicitly, one block of cells at a time, as
 //   B = G_c W_c^-1 / cf^(3/2) in FP32 (K_c = B B^T; far term plus the coarse
 //   plan's near-field table, the entries the coarse mixed operator applies),
 //   and Y = sum_b B_b (B_b^T Omega) by two FP32 GEMMs per block.  One pair
 //   evaluation then serves all ell columns instead of one, and the products
-//   run at the FP32 GEMM rate.
+//   run at the FP32 GEMM rate.  The Gram matrices M = Z^T Z and Y^T Y take
+//   exact FP32 products summed in double-float arithmetic on the FP32 pipe
+//   (FP64-class sums at the FP32 rate; this GPU's FP64 pipe runs at 1/64 of it).
 //
-// cuBLAS supplies the GEMMs and the GEMV / TRSV of the application (plain
-// library dense algebra).
-#include <cublas_v2.h>
+// All dense products are this library's own kernels (dense_kernels.cu).
+// Vectors of N stations are stored with a leading dimension ldy = N rounded
+// up to a multiple of 4 (16-byte columns); the padding rows hold zeros.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -64,42 +72,55 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     return x ^ (x >> 31);
 }
 
-// out[i] = scale * N(0, 1) (rounded to FP32) from the Box-Muller transform of
-// two uniforms drawn from counters 2i and 2i+1 of the stream `seed`
-// (deterministic).
-__global__ void k_randn32(float *__restrict__ out, int64_t n, uint64_t seed, double scale) {
+// out[s + ld j] = scale * N(0, 1) (rounded to FP32) for s < n, j < k, from
+// the Box-Muller transform of two uniforms drawn from counters 2i and 2i+1,
+// i = s + n j, of the stream `seed` (deterministic); padding rows s >= n are 0.
+__global__ void k_randn32(float *__restrict__ out, int64_t n, int64_t ld, int k, uint64_t seed, double scale) {
     const double two_pi = 6.283185307179586476925286766559;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t a = splitmix64(seed ^ (2ull * (uint64_t)i));
-        const uint64_t b = splitmix64(seed ^ (2ull * (uint64_t)i + 1ull));
+    const int64_t total = ld * k;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = q % ld, j = q / ld;
+        if (s >= n) {
+            out[q] = 0.0f;
+            continue;
+        }
+        const uint64_t i = (uint64_t)(s + n * j);
+        const uint64_t a = splitmix64(seed ^ (2ull * i));
+        const uint64_t b = splitmix64(seed ^ (2ull * i + 1ull));
         const double u1 = ((double)(a >> 11) + 1.0) * 0x1.0p-53;   // (0, 1]
         const double u2 = (double)(b >> 11) * 0x1.0p-53;           // [0, 1)
-        out[i] = (float)(scale * sqrt(-2.0 * log(u1)) * cos(two_pi * u2));
+        out[q] = (float)(scale * sqrt(-2.0 * log(u1)) * cos(two_pi * u2));
     }
 }
 
 inline unsigned grid_n(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 148LL * 32)); }
 
-__global__ void k_narrow(const double *__restrict__ x, float *__restrict__ y, int64_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = (float)x[i];
+// y[s + ldy j] = x[s + n j] rounded to FP32 (s < n; padding rows 0), j < k
+__global__ void k_narrow(const double *__restrict__ x, int64_t n, int k, float *__restrict__ y, int64_t ldy) {
+    const int64_t total = ldy * k;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = q % ldy, j = q / ldy;
+        y[q] = s < n ? (float)x[s + n * j] : 0.0f;
+    }
 }
 
-__global__ void k_widen(const float *__restrict__ x, double *__restrict__ y, int64_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = (double)x[i];
+// y[s + n j] = x[s + ldx j] (s < n, j < k)
+__global__ void k_widen(const float *__restrict__ x, int64_t ldx, int64_t n, int k, double *__restrict__ y) {
+    const int64_t total = n * k;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x)
+        y[q] = (double)x[q % n + ldx * (q / n)];
 }
 
 // Explicit block of the scaled coarse operator B = G_c W_c^-1 / cf^(3/2)
 // (K_c = B B^T), cells c0 <= c < c0 + cb in natural order, column-major
-// B[(c - c0) N + s] (FP32).  The far part is the mixed operator's own FP32
+// B[(c - c0) ldb + s] (FP32).  The far part is the mixed operator's own FP32
 // point-mass (+ quadrupole) term of the pair; fac[l] = gamma V (zc_l + z0) / cf^1.5.
 constexpr int kNysCells = 16;   // cells per thread
 
 template <bool QUAD>
 __global__ void __launch_bounds__(256) k_nys_far(MixedGeo g, const float4 *__restrict__ st32,
-                                                 const float2 *__restrict__ stz, int64_t N, int64_t c0, int cb,
-                                                 const float *__restrict__ fac, float *__restrict__ B) {
+                                                 const float2 *__restrict__ stz, int64_t N, int64_t ldb, int64_t c0,
+                                                 int cb, const float *__restrict__ fac, float *__restrict__ B) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
     const float4 S = st32[s];
@@ -117,7 +138,7 @@ __global__ void __launch_bounds__(256) k_nys_far(MixedGeo g, const float4 *__res
         const float ph = QUAD ? far_ph(X, Y, S.x, S.y, S.z, S.w, g.qa, g.qb) : 0.0f;
         const float dz = g.czc[l] - zs;
         const float R2 = fmaf(dz, dz, h2);
-        B[(int64_t)k * N + s] = far_k<QUAD>(dz, R2, g.qg, ph) * fac[l];
+        B[(int64_t)k * ldb + s] = far_k<QUAD>(dz, R2, g.qg, ph) * fac[l];
         if (++i == g.nx) {
             i = 0;
             if (++j == g.ny) {
@@ -131,7 +152,7 @@ __global__ void __launch_bounds__(256) k_nys_far(MixedGeo g, const float4 *__res
 // Adds the near-field correction table of the coarse plan (exact prism minus
 // the far term, per unit gamma V) to the block; one warp per station, each
 // (station, cell) pair is touched by one lane only.
-__global__ void __launch_bounds__(256) k_nys_near(int nx, int ny, int nz, NearGeo ng, int64_t N,
+__global__ void __launch_bounds__(256) k_nys_near(int nx, int ny, int nz, NearGeo ng, int64_t N, int64_t ldb,
                                                   const float *__restrict__ dG, const int *__restrict__ st_i0,
                                                   const int *__restrict__ st_j0, int64_t c0, int cb,
                                                   const float *__restrict__ fac, float *__restrict__ B) {
@@ -145,7 +166,7 @@ __global__ void __launch_bounds__(256) k_nys_near(int nx, int ny, int nz, NearGe
         const int64_t k = (int64_t)i + (int64_t)nx * (j + (int64_t)ny * l) - c0;
         if (k < 0 || k >= cb) continue;
         const float d = dG[s * ng.ld + t];
-        if (d != 0.0f) B[k * N + s] += d * fac[l];
+        if (d != 0.0f) B[k * ldb + s] += d * fac[l];
     }
 }
 
@@ -184,6 +205,27 @@ bool cholesky_rowmajor(std::vector<double> &A, int n) {
     return true;
 }
 
+// Inverse of the lower triangular factor: Li (column-major, Li[i + n j],
+// zeros above the diagonal) from L (row-major lower, as cholesky_rowmajor
+// leaves it), by forward substitution on each unit vector (columns in
+// parallel): Li_jj = 1 / L_jj, Li_ij = -(sum_{j <= k < i} L_ik Li_kj) / L_ii.
+void tri_inverse_lower(const std::vector<double> &L, int n, std::vector<double> &Li) {
+    Li.assign((size_t)n * n, 0.0);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int j = 0; j < n; ++j) {
+        double *x = &Li[(size_t)n * j];
+        x[j] = 1.0 / L[(size_t)j * n + j];
+        for (int i = j + 1; i < n; ++i) {
+            const double *Lr = &L[(size_t)i * n];
+            double acc = 0.0;
+            for (int k = j; k < i; ++k) acc += Lr[k] * x[k];
+            x[i] = -acc / Lr[i];
+        }
+    }
+}
+
+inline int64_t pad4(int64_t v) { return (v + 3) / 4 * 4; }
+
 }  // namespace
 
 // Automatic sizes (0).  The sketch costs 4 N M_c ell FP32 GEMM flops plus an
@@ -210,18 +252,29 @@ void nys_sizes(const grav_plan *p, int *ell, int *cf) {
 }
 
 size_t nys_bytes(int64_t N, int ell) {
-    // persistent part: Y (N x ell), L (ell x ell), t (ell)
-    return 8ull * ((size_t)N * ell + (size_t)ell * ell + ell) + 3 * 256;
+    // persistent part: Y (FP32, ldy x ell), L^-1 (ell x ell), t, u, v (ell doubles),
+    // vh, vl (ell floats), rh, rl (ldy floats)
+    const size_t ldy = (size_t)pad4(N);
+    return 4ull * ldy * ell + 8ull * ell * ell + 24ull * ell + 8ull * ell + 8ull * ldy + 9 * 256;
+}
+
+// Explicit-block width: cells per block of the coarse operator (multiple of 4).
+static int64_t block_cells(int64_t Mc, int64_t ldy, int k, size_t left) {
+    int64_t cb = std::min<int64_t>({Mc, (1ll << 30) / ldy, (1ll << 27) / k, 65535ll * kNysCells,
+                                    (int64_t)(left / (4ull * ldy + 4ull * k + 64))});
+    return cb;
 }
 
 size_t nys_peak_bytes(const grav_plan *p) {
     int ell = p->opt.nys_rank, cf = p->opt.nys_coarsen;
     nys_sizes(p, &ell, &cf);
     if (ell < 1 || cf < 1) return 0;
-    const int64_t N = p->N;
+    const int64_t ldy = pad4(p->N);
     const int64_t Mc = (int64_t)((p->nx + cf - 1) / cf) * ((p->ny + cf - 1) / cf) * ((p->nz + cf - 1) / cf);
-    const int64_t cb = std::min<int64_t>({Mc, (1ll << 30) / N, (1ll << 27) / ell, 65535ll * kNysCells});
-    return nys_bytes(N, ell) + 8ull * N * ell + 16ull * ell * ell + 4ull * cb * N + 12ull * cb * ell + (1u << 20);
+    const int64_t cb = pad4(std::min<int64_t>({Mc, (1ll << 30) / ldy, (1ll << 27) / ell, 65535ll * kNysCells}));
+    // persistent + Omega (FP32) + the two Gram matrices + one explicit block and Z_b
+    return nys_bytes(p->N, ell) + 4ull * ldy * ell + 16ull * ell * ell + 4ull * cb * ldy + 4ull * cb * ell +
+           (1u << 20);
 }
 
 namespace {
@@ -247,25 +300,25 @@ int coarse_plan(grav_plan *p, int cf, grav_plan **cp, cudaStream_t s) {
     return plan_create(p->ctx, &cm, &sv, oc, cp, s);
 }
 
-// Y32 = K_c X32 = B (B^T X32) (N x k, FP32, column-major) with B = G_c W_c^-1
-// / cf^(3/2) formed explicitly one block of cells at a time (FP32, at most
-// 4 GB); when M is given, M (k x k, FP64, lower triangle) = Z^T Z with
-// Z = B^T X32 (each block's Z_b widened to FP64, exact).  Scratch comes from
-// the context's pool and the context's HBM budget.
+// Y32 = K_c X32 = B (B^T X32) (ldy x k, FP32, column-major; rows >= N of X32
+// must be 0) with B = G_c W_c^-1 / cf^(3/2) formed explicitly one block of
+// cells at a time (FP32, at most 4 GB); when M is given, M (k x k, FP64,
+// lower triangle) = Z^T Z with Z = B^T X32 (exact FP32 products, double-float
+// sums).  Scratch comes from the context's pool and the context's HBM budget.
 int coarse_products(grav_plan *cp, int cf, double z0, const float *X32, int k, float *Y32, double *M,
-                    cublasHandle_t h, cudaStream_t s) {
+                    cudaStream_t s) {
     grav_ctx *ctx = cp->ctx;
-    const int64_t N = cp->N, Mc = cp->M;
+    const int64_t N = cp->N, Mc = cp->M, ldy = pad4(N);
     const int nzc = cp->nz;
     const size_t used = ctx->hbm_used.load() + 4ull * nzc + 4 * 256;
     const size_t left = ctx->hbm_budget > used ? ctx->hbm_budget - used : 0;
-    int64_t cb = std::min<int64_t>({Mc, (1ll << 30) / N, (1ll << 27) / k, 65535ll * kNysCells,
-                                    (int64_t)(left / (4ull * N + (M ? 12ull : 4ull) * k))});
+    int64_t cb = block_cells(Mc, ldy, k, left);
     if (cb < std::min<int64_t>(Mc, 64))
         return set_error(ctx, GRAV_ENOMEM, "explicit coarse operator block (%d columns) exceeds the HBM budget", k);
     const int64_t nblk = (Mc + cb - 1) / cb;
     cb = (Mc + nblk - 1) / nblk;   // equal blocks
-    const size_t bytes = 4ull * nzc + 4ull * cb * N + (M ? 12ull : 4ull) * cb * k + 4 * 256;
+    const int64_t cbp = pad4(cb);   // GEMM inner dimension, zero columns at the end
+    const size_t bytes = 4ull * nzc + 4ull * cbp * ldy + 4ull * cbp * k + 4 * 256;
     char *mem = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync((void **)&mem, bytes, ctx->pool, s);
     if (e != cudaSuccess) return cuda_error(ctx, e, "explicit coarse operator block");
@@ -273,9 +326,8 @@ int coarse_products(grav_plan *cp, int cf, double z0, const float *X32, int k, f
     Arena ta;
     ta.base = mem; ta.size = bytes;
     float *fac = (float *)ta.take(4ull * nzc);
-    float *Bb = (float *)ta.take(4ull * N * cb);
-    float *Zb = (float *)ta.take(4ull * cb * k);
-    double *Zd = M ? (double *)ta.take(8ull * cb * k) : nullptr;
+    float *Bb = (float *)ta.take(4ull * ldy * cbp);
+    float *Zb = (float *)ta.take(4ull * cbp * k);
     // fac[l] = gamma V_c (zc_l + z0) / cf^(3/2): K ~ G_c W_c^-2 G_c^T / cf^3 = B B^T
     std::vector<float> hfac(nzc);
     const double vol_mgal = kGammaMgal * cp->cell_a * cp->cell_b * cp->cell_c;
@@ -283,32 +335,24 @@ int coarse_products(grav_plan *cp, int cf, double z0, const float *X32, int k, f
         hfac[l] = (float)(vol_mgal * (0.5 * (cp->ze[l] + cp->ze[l + 1]) - cp->ze[0] + z0) / std::pow((double)cf, 1.5));
     cudaMemcpyAsync(fac, hfac.data(), 4ull * nzc, cudaMemcpyHostToDevice, s);
     int rc = GRAV_OK;
-    const float onef = 1.0f, zerof = 0.0f;
-    const double one = 1.0;
     for (int64_t b = 0; b < nblk && !rc; ++b) {
         const int64_t c0 = b * cb;
         const int nb = (int)std::min<int64_t>(cb, Mc - c0);
+        // zero block: padding rows (stations >= N) and columns (cells >= nb) stay 0
+        cudaMemsetAsync(Bb, 0, 4ull * ldy * cbp, s);
         dim3 gf((unsigned)((N + 255) / 256), (unsigned)((nb + kNysCells - 1) / kNysCells));
         if (cp->cubic)
-            k_nys_far<false><<<gf, 256, 0, s>>>(cp->mg, cp->st32, cp->stz, N, c0, nb, fac, Bb);
+            k_nys_far<false><<<gf, 256, 0, s>>>(cp->mg, cp->st32, cp->stz, N, ldy, c0, nb, fac, Bb);
         else
-            k_nys_far<true><<<gf, 256, 0, s>>>(cp->mg, cp->st32, cp->stz, N, c0, nb, fac, Bb);
-        k_nys_near<<<(unsigned)((N * 32 + 255) / 256), 256, 0, s>>>(cp->nx, cp->ny, nzc, cp->ng, N, cp->dG, cp->st_i0,
-                                                                  cp->st_j0, c0, nb, fac, Bb);
+            k_nys_far<true><<<gf, 256, 0, s>>>(cp->mg, cp->st32, cp->stz, N, ldy, c0, nb, fac, Bb);
+        k_nys_near<<<(unsigned)((N * 32 + 255) / 256), 256, 0, s>>>(cp->nx, cp->ny, nzc, cp->ng, N, ldy, cp->dG,
+                                                                  cp->st_i0, cp->st_j0, c0, nb, fac, Bb);
         note_launches(2);
-        const float betaf = b ? 1.0f : 0.0f;
-        const double beta = b ? 1.0 : 0.0;
-        bool ok = cublasSgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, nb, k, (int)N, &onef, Bb, (int)N, X32, (int)N, &zerof, Zb,
-                              nb) == CUBLAS_STATUS_SUCCESS;
-        ok = ok && cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, k, nb, &onef, Bb, (int)N, Zb, nb, &betaf, Y32,
-                               (int)N) == CUBLAS_STATUS_SUCCESS;
-        if (M) {
-            k_widen<<<grid_n((int64_t)nb * k), 256, 0, s>>>(Zb, Zd, (int64_t)nb * k);
-            note_launches(1);
-            ok = ok && cublasDsyrk(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, k, nb, &one, Zd, nb, &beta, M, k) ==
-                           CUBLAS_STATUS_SUCCESS;
-        }
-        if (!ok) rc = set_error(ctx, GRAV_EDEVICE, "cuBLAS failed in the explicit coarse products");
+        // Z_b = B_b^T X32 (cbp x k), Y32 (+)= B_b Z_b, M (+)= Z_b^T Z_b
+        bool ok = launch_sgemm(true, (int)cbp, k, (int)ldy, Bb, ldy, X32, ldy, Zb, cbp, false, s) == 0;
+        ok = ok && launch_sgemm(false, (int)ldy, k, (int)cbp, Bb, ldy, Zb, cbp, Y32, ldy, b > 0, s) == 0;
+        if (M) ok = ok && launch_gram_df(k, (int)cbp, Zb, cbp, M, b > 0, s) == 0;
+        if (!ok) rc = set_error(ctx, GRAV_EINVAL, "explicit coarse products: unsupported layout");
     }
     cudaFreeAsync(mem, s);
     ctx->hbm_used -= bytes;
@@ -321,11 +365,11 @@ int nys_coarse_apply(grav_plan *p, int cf, const double *X, int k, double *Y, cu
     grav_ctx *ctx = p->ctx;
     if (!p->uniform) return set_error(ctx, GRAV_EINVAL, "the coarse operator needs a mesh of uniform cells");
     if (cf < 1 || cf > 8 || k < 1) return set_error(ctx, GRAV_EINVAL, "coarsening must lie in [1, 8] and k >= 1");
-    const int64_t N = p->N;
+    const int64_t N = p->N, ldy = pad4(N);
     grav_plan *cp = nullptr;
     int rc = coarse_plan(p, cf, &cp, s);
     if (rc) return rc;
-    const size_t bytes = 8ull * N * k + 2 * 256;
+    const size_t bytes = 8ull * ldy * k + 2 * 256;
     char *mem = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync((void **)&mem, bytes, ctx->pool, s);
     if (e != cudaSuccess) {
@@ -335,49 +379,39 @@ int nys_coarse_apply(grav_plan *p, int cf, const double *X, int k, double *Y, cu
     ctx->hbm_used += bytes;
     Arena ta;
     ta.base = mem; ta.size = bytes;
-    float *X32 = (float *)ta.take(4ull * N * k);
-    float *Y32 = (float *)ta.take(4ull * N * k);
-    k_narrow<<<grid_n(N * k), 256, 0, s>>>(X, X32, N * k);
+    float *X32 = (float *)ta.take(4ull * ldy * k);
+    float *Y32 = (float *)ta.take(4ull * ldy * k);
+    k_narrow<<<grid_n(ldy * k), 256, 0, s>>>(X, N, k, X32, ldy);
     note_launches(1);
-    cublasHandle_t h = nullptr;
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) {
-        rc = set_error(ctx, GRAV_EDEVICE, "cublasCreate failed");
-    } else {
-        cublasSetStream(h, s);
-        cublasSetMathMode(h, CUBLAS_DEFAULT_MATH);
-        rc = coarse_products(cp, cf, p->opt.z0, X32, k, Y32, nullptr, h, s);
-        if (!rc) {
-            k_widen<<<grid_n(N * k), 256, 0, s>>>(Y32, Y, N * k);
-            note_launches(1);
-        }
+    rc = coarse_products(cp, cf, p->opt.z0, X32, k, Y32, nullptr, s);
+    if (!rc) {
+        k_widen<<<grid_n(N * k), 256, 0, s>>>(Y32, ldy, N, k, Y);
+        note_launches(1);
     }
     cudaFreeAsync(mem, s);
     ctx->hbm_used -= bytes;
     plan_destroy(cp, s);
-    if (h) {
-        cudaStreamSynchronize(s);
-        cublasDestroy(h);
-    }
     return rc;
 }
 
 int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState *st, cudaStream_t s) {
     grav_ctx *ctx = p->ctx;
     NvtxRange nv("grav::nystrom_build");
-    const int64_t N = p->N;
+    const int64_t N = p->N, ldy = pad4(N);
     if (!p->uniform) return set_error(ctx, GRAV_EINVAL, "precond = 2 (Nystrom) needs a mesh of uniform cells");
     nys_sizes(p, &ell, &cf);
     if (ell < 1 || cf < 1) return set_error(ctx, GRAV_EINVAL, "Nystrom rank and coarsening must be >= 1");
     *st = NysState{};
     st->ell = ell;
     st->N = N;
+    st->ldy = ldy;
     grav_plan *cp = nullptr;
     int rc = coarse_plan(p, cf, &cp, s);
     if (rc) return rc;
-    // persistent block; temporary block: Omega and Y (FP32, N x ell), M and
-    // Y^T Y (ell x ell); the explicit blocks take what the budget leaves
+    // persistent block; temporary block: Omega (FP32, ldy x ell), M and Y^T Y
+    // (ell x ell FP64); the explicit blocks take what the budget leaves
     st->bytes = nys_bytes(N, ell);
-    const size_t tmp_bytes = 8ull * N * ell + 16ull * ell * ell + 4 * 256;
+    const size_t tmp_bytes = 4ull * ldy * ell + 16ull * ell * ell + 4 * 256;
     if (ctx->hbm_used.load() + st->bytes + tmp_bytes > ctx->hbm_budget) {
         plan_destroy(cp, s);
         return set_error(ctx, GRAV_ENOMEM, "Nystrom preconditioner (rank %d) exceeds the HBM budget", ell);
@@ -394,36 +428,33 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
     ctx->hbm_used += st->bytes + tmp_bytes;
     Arena pa;
     pa.base = st->mem; pa.size = st->bytes;
-    st->Y = (double *)pa.take(8ull * N * ell);
-    st->L = (double *)pa.take(8ull * ell * ell);
+    st->Y = (float *)pa.take(4ull * ldy * ell);
+    st->Linv = (double *)pa.take(8ull * ell * ell);
     st->t = (double *)pa.take(8ull * ell);
+    st->u = (double *)pa.take(8ull * ell);
+    st->v = (double *)pa.take(8ull * ell);
+    st->vh = (float *)pa.take(4ull * ell);
+    st->vl = (float *)pa.take(4ull * ell);
+    st->rh = (float *)pa.take(4ull * ldy);
+    st->rl = (float *)pa.take(4ull * ldy);
     Arena ta;
     ta.base = tmp; ta.size = tmp_bytes;
-    float *Om32 = (float *)ta.take(4ull * N * ell);
-    float *Y32 = (float *)ta.take(4ull * N * ell);
+    float *Om32 = (float *)ta.take(4ull * ldy * ell);
     double *Mm = (double *)ta.take(8ull * ell * ell);
     double *Gy = (double *)ta.take(8ull * ell * ell);
-    cublasHandle_t h = nullptr;
     std::vector<double> hM((size_t)ell * ell), hG((size_t)ell * ell);
     cudaEvent_t ev = nullptr;
     do {
-        if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) {
-            rc = set_error(ctx, GRAV_EDEVICE, "cublasCreate failed");
+        if (pa.overflow || ta.overflow) {
+            rc = set_error(ctx, GRAV_EDEVICE, "Nystrom scratch layout");
             break;
         }
-        st->blas = h;
-        cublasSetStream(h, s);
-        cublasSetMathMode(h, CUBLAS_DEFAULT_MATH);   // FP32 GEMMs in FP32 (no TF32)
-        k_randn32<<<grid_n(N * ell), 256, 0, s>>>(Om32, N * ell, seed, 1.0 / std::sqrt((double)N));
+        k_randn32<<<grid_n(ldy * ell), 256, 0, s>>>(Om32, N, ldy, ell, seed, 1.0 / std::sqrt((double)N));
         note_launches(1);
         // Y = K_c Omega and M = Z^T Z, Z = B^T Omega
-        if ((rc = coarse_products(cp, cf, p->opt.z0, Om32, ell, Y32, Mm, h, s))) break;
-        k_widen<<<grid_n(N * ell), 256, 0, s>>>(Y32, st->Y, N * ell);
-        note_launches(1);
-        const double one = 1.0, zero = 0.0;
-        if (cublasDsyrk(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, ell, (int)N, &one, st->Y, (int)N, &zero, Gy, ell) !=
-            CUBLAS_STATUS_SUCCESS) {
-            rc = set_error(ctx, GRAV_EDEVICE, "cuBLAS SYRK failed in the Nystrom set-up");
+        if ((rc = coarse_products(cp, cf, p->opt.z0, Om32, ell, st->Y, Mm, s))) break;
+        if (launch_gram_df(ell, (int)ldy, st->Y, ldy, Gy, false, s) != 0) {
+            rc = set_error(ctx, GRAV_EINVAL, "Nystrom Gram matrix: unsupported layout");
             break;
         }
         cudaMemcpyAsync(hM.data(), Mm, 8ull * ell * ell, cudaMemcpyDeviceToHost, s);
@@ -451,11 +482,9 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
             rc = set_error(ctx, GRAV_EDEVICE, "Nystrom matrix T is not positive definite (rank %d)", ell);
             break;
         }
-        // column-major lower factor for cuBLAS: Lc(i, j) = L[i][j] for i >= j
-        std::vector<double> Lc((size_t)ell * ell, 0.0);
-        for (int j = 0; j < ell; ++j)
-            for (int i = j; i < ell; ++i) Lc[(size_t)i + (size_t)ell * j] = T[(size_t)i * ell + j];
-        cudaMemcpyAsync(st->L, Lc.data(), 8ull * ell * ell, cudaMemcpyHostToDevice, s);
+        std::vector<double> Li;
+        tri_inverse_lower(T, ell, Li);
+        cudaMemcpyAsync(st->Linv, Li.data(), 8ull * ell * ell, cudaMemcpyHostToDevice, s);
         cudaEventRecord(ev, s);
         rc = host_wait(ctx, ev, p->opt.timeout_s, "Nystrom factor upload");
     } while (false);
@@ -468,20 +497,11 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
 }
 
 void nys_apply(const NysState &st, const double *r, double *z, cudaStream_t s) {
-    cublasHandle_t h = (cublasHandle_t)st.blas;
-    cublasSetStream(h, s);
-    const double one = 1.0, zero = 0.0, mone = -1.0, inv_mu = 1.0 / st.mu;
-    const int n = (int)st.N, ell = st.ell;
-    cublasDgemv(h, CUBLAS_OP_T, n, ell, &one, st.Y, n, r, 1, &zero, st.t, 1);   // t = Y^T r
-    cublasDtrsv(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, ell, st.L, ell, st.t, 1);
-    cublasDtrsv(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, ell, st.L, ell, st.t, 1);
-    cudaMemcpyAsync(z, r, 8ull * st.N, cudaMemcpyDeviceToDevice, s);
-    cublasDgemv(h, CUBLAS_OP_N, n, ell, &mone, st.Y, n, st.t, 1, &one, z, 1);    // z = r - Y t
-    cublasDscal(h, n, &inv_mu, z, 1);
+    launch_nys_apply(st.Y, st.ldy, st.N, st.ell, st.Linv, st.mu, r, z, st.rh, st.rl, st.t, st.u, st.v, st.vh, st.vl,
+                     s);
 }
 
 void nys_free(grav_plan *p, NysState *st, cudaStream_t s) {
-    if (st->blas) cublasDestroy((cublasHandle_t)st->blas);
     if (st->mem) {
         cudaFreeAsync(st->mem, s);
         p->ctx->hbm_used -= st->bytes;

@@ -841,3 +841,66 @@ def test_nystrom_pcg_reaches_dense_lu_minimiser(g, prec, rank, cf):
         assert np.linalg.norm(y - ref["y"]) <= 1.01 * res / ref["lam"], pc
         its[pc] = info["iters"]
     assert its["nystrom"] < its["jacobi"], its
+
+
+# ------------------------------------------------ dense kernels (Nystrom) ---
+
+def test_dense_kernels_sgemm_and_gram(g):
+    """The preconditioner's dense kernels against float64 products of the same
+    FP32 inputs, on ragged sizes (partial 128 x 128 / 64 x 64 tiles, K not a
+    multiple of the 16-deep slices).  SGEMM (FP32 sums of K terms): within the
+    recursive-summation bound (K + 2) u (|A| |B|), u = 2^-24.  Gram (exact
+    products, double-float sums): within 1e-13 of (|X|^T |X|).  Accumulation
+    adds to C; a leading dimension that is not a multiple of 4 is refused."""
+    ctx = g.context()
+    rng = np.random.default_rng(31)
+    u = 2.0 ** -24
+
+    def run(op, M, N, K, A, lda, B, ldb, C, ldc, acc):
+        rc = g._lib.grav_dense_check(ctx.h, op, M, N, K, A.data_ptr(), lda,
+                                     B.data_ptr() if B is not None else None, ldb, C.data_ptr(), ldc, acc,
+                                     g._stream(None))
+        return rc
+
+    for op, M, N, K in ((0, 132, 77, 1000), (1, 260, 130, 52), (0, 4, 1, 4), (1, 388, 257, 1028)):
+        lda = K + 4 if op == 0 else M + 8
+        a_cols = M if op == 0 else K
+        A = rng.standard_normal((a_cols, lda)).astype(np.float32)   # row = one column of the col-major array
+        ldb = K + 8
+        B = rng.standard_normal((N, ldb)).astype(np.float32)
+        ldc = M + 4
+        C0 = rng.standard_normal((N, ldc)).astype(np.float32)
+        Am = A[:, :K].astype(np.float64) if op == 0 else A[:, :M].T.astype(np.float64)   # Am[m, k]
+        Bm = B[:, :K].T.astype(np.float64)                                             # Bm[k, n]
+        ref = Am @ Bm
+        bound = (K + 2) * u * (np.abs(Am) @ np.abs(Bm))
+        for acc in (0, 1):
+            At, Bt, Ct = (torch.tensor(x, device="cuda") for x in (A, B, C0))
+            assert run(op, M, N, K, At, lda, Bt, ldb, Ct, ldc, acc) == g.GRAV_OK
+            got = Ct.cpu().numpy()[:, :M].T.astype(np.float64)
+            want = ref + (C0[:, :M].T.astype(np.float64) if acc else 0.0)
+            assert np.all(np.abs(got - want) <= bound + (np.abs(C0[:, :M].T) * u * 2 if acc else 0.0)), (op, M, N, K)
+            # untouched padding columns of C
+            assert np.array_equal(Ct.cpu().numpy()[:, M:], C0[:, M:])
+    # Gram: G = X^T X, lower triangle
+    for n, K in ((150, 1004), (64, 16), (5, 4)):
+        ldx = K + 4
+        X = rng.standard_normal((n, ldx)).astype(np.float32)
+        Xm = X[:, :K].T.astype(np.float64)
+        ref = Xm.T @ Xm
+        scale = np.abs(Xm).T @ np.abs(Xm)
+        Gt = torch.full((n, n), 7.0, dtype=torch.float64, device="cuda")   # G[i + n j] -> row j, column i
+        Xt = torch.tensor(X, device="cuda")
+        assert run(2, 0, n, K, Xt, ldx, None, 0, Gt, n, 0) == g.GRAV_OK
+        got = Gt.cpu().numpy().T           # got[i, j]
+        low = np.tril(np.ones((n, n), bool))
+        assert np.all(np.abs(got - ref)[low] <= 1e-13 * scale[low]), (n, K)
+        assert np.all(got[~low] == 7.0)    # the upper triangle is not written
+        assert run(2, 0, n, K, Xt, ldx, None, 0, Gt, n, 1) == g.GRAV_OK
+        got2 = Gt.cpu().numpy().T
+        assert np.all(np.abs(got2 - 2 * ref)[low] <= 2e-13 * scale[low])
+    # refused layouts: nothing launched
+    A = torch.zeros((8, 10), dtype=torch.float32, device="cuda")
+    C = torch.zeros((8, 8), dtype=torch.float32, device="cuda")
+    assert run(0, 8, 8, 8, A, 10, A, 10, C, 8, 0) == g.GRAV_EINVAL
+    assert run(1, 6, 8, 8, A, 8, A, 8, C, 8, 0) == g.GRAV_EINVAL
