@@ -157,6 +157,8 @@ typedef struct {
     int restarts;              /* single CG solve: restarts from the recomputed true residual */
     double fp64_rel_err;       /* check_stations > 0: max |mixed - FP64| / max |FP64| over the checked stations;
                                   -1 when not checked */
+    double nys_shift;          /* precond = 2: the shift nu / lambda the Nystrom factorisation needed
+                                  (1e-3 unless T lost definiteness); 0 otherwise */
 } grav_solve_info;
 
 typedef struct grav_ctx grav_ctx;

@@ -907,6 +907,7 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             info->true_rel_res = true_rel;
             info->lambda = lam;
             info->trace = trace;
+            info->nys_shift = (o.precond == 2 && ns.mu > 0) ? ns.nu / ns.mu : 0.0;
         }
         rc = read_status(ctx, s, o.timeout_s);
     } while (false);

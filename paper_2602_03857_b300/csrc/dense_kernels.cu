@@ -11,9 +11,13 @@
 // * k_gram_df: G (+)= X^T X, lower triangle, for FP32 X.  Every product of
 //   two FP32 numbers is exact as p + e (p = a b rounded, e = fma(a, b, -p));
 //   the sums run in double-float arithmetic (a pair hi + lo of FP32 numbers,
-//   Knuth's TwoSum for hi, e and the TwoSum error into lo), so the Gram
-//   matrix is accurate to about 2^-44 relative to sum |a b| -- FP64-class --
-//   on the FP32 pipe, which this GPU runs at 64 times its FP64 rate.
+//   Knuth's TwoSum for hi, e and the TwoSum error into lo) over runs of 128
+//   products, and each run's hi + lo is added into an FP64 sum.  The low
+//   word is itself an FP32 sum, so a run of n products carries about n u^2
+//   (u = 2^-24) relative error: 128-term runs keep it near 5e-13 (FP64-class),
+//   where one run over all 178,797 stations of the paper-scale survey would
+//   reach 6e-10.  The products and runs use the FP32 pipe, which this GPU
+//   runs at 64 times its FP64 rate; the FP64 adds are one per 128 products.
 // * k_gemv_t_df / k_gemv_n_df: t = Y^T r and z = (r - Y v) / mu for an FP32
 //   matrix Y and FP64 vectors split into FP32 pairs, with the same exact
 //   products and double-float sums; k_trmv_lo / k_trmv_lo_t: lower-triangular
@@ -168,6 +172,8 @@ __device__ __forceinline__ void df_acc_prod(DF &x, float a, float b) {
 }
 
 constexpr int kGrT = 64, kGrBK = 16, kGrThreads = 256;
+constexpr int kGrFoldTiles = 8;   // 16-deep k slices per double-float run (128 products)
+constexpr int kDfRun = 128;       // terms per double-float run in the GEMVs
 
 // G[i + n j] (+)= sum_k X[k + ldx i] X[k + ldx j] for i >= j (lower
 // triangle), i, j < n, k < K; 64 x 64 tiles of the lower block triangle,
@@ -202,10 +208,14 @@ __global__ void __launch_bounds__(kGrThreads) k_gram_df(int n, int K, const floa
         Xj[buf][4 * kq + 2][cc] = rj.z; Xj[buf][4 * kq + 3][cc] = rj.w;
     };
     DF acc[4][4];
+    double acc64[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = DF{0.f, 0.f};
+        for (int b = 0; b < 4; ++b) {
+            acc[a][b] = DF{0.f, 0.f};
+            acc64[a][b] = 0.0;
+        }
     const int nk = (K + kGrBK - 1) / kGrBK;
     load_tile(0);
     store_tile(0);
@@ -224,6 +234,15 @@ __global__ void __launch_bounds__(kGrThreads) k_gram_df(int n, int K, const floa
 #pragma unroll
                 for (int q = 0; q < 4; ++q) df_acc_prod(acc[p][q], a[p], b[q]);
         }
+        if ((kt + 1) % kGrFoldTiles == 0 || kt + 1 == nk) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc64[p][q] += (double)acc[p][q].hi + (double)acc[p][q].lo;
+                    acc[p][q] = DF{0.f, 0.f};
+                }
+        }
         if (kt + 1 < nk) store_tile(buf ^ 1);
         __syncthreads();
     }
@@ -233,7 +252,7 @@ __global__ void __launch_bounds__(kGrThreads) k_gram_df(int n, int K, const floa
         for (int q = 0; q < 4; ++q) {
             const int i = i0 + 4 * ty + p, j = j0 + 4 * tx + q;
             if (i >= n || j >= n || i < j) continue;
-            const double v = (double)acc[p][q].hi + (double)acc[p][q].lo;
+            const double v = acc64[p][q];
             double *dst = G + (int64_t)i + (int64_t)n * j;
             *dst = accumulate ? *dst + v : v;
         }
@@ -269,12 +288,20 @@ __global__ void __launch_bounds__(256) k_gemv_t_df(const float *__restrict__ Y, 
     const float *y = Y + (int64_t)j * ldy;
     DF acc{0.f, 0.f};
     float small = 0.0f;
+    double v = 0.0;
+    int run = 0;
     for (int64_t s = threadIdx.x; s < n; s += blockDim.x) {
         const float a = __ldcs(y + s);
         df_acc_prod(acc, a, rh[s]);
         small = fmaf(a, rl[s], small);
+        if (++run == kDfRun) {   // runs of 128 terms into FP64
+            v += (double)acc.hi + (double)acc.lo + (double)small;
+            acc = DF{0.f, 0.f};
+            small = 0.0f;
+            run = 0;
+        }
     }
-    const double v = (double)acc.hi + (double)acc.lo + (double)small;
+    v += (double)acc.hi + (double)acc.lo + (double)small;
     const double tot = block_sum_fixed(v, red);
     if (threadIdx.x == 0) t[j] = tot;
 }
@@ -309,9 +336,15 @@ __global__ void __launch_bounds__(256) k_gemv_n_df(const float *__restrict__ Y, 
     if (s >= n) return;
     DF acc{0.f, 0.f};
     float small = 0.0f;
+    double yv = 0.0;
     const float *y = Y + s;
     int j = 0;
     for (; j + 4 <= ell; j += 4) {
+        if (j % kDfRun == 0 && j > 0) {   // runs of 128 terms into FP64
+            yv += (double)acc.hi + (double)acc.lo + (double)small;
+            acc = DF{0.f, 0.f};
+            small = 0.0f;
+        }
         const float a0 = __ldcs(y + (int64_t)ldy * j), a1 = __ldcs(y + (int64_t)ldy * (j + 1));
         const float a2 = __ldcs(y + (int64_t)ldy * (j + 2)), a3 = __ldcs(y + (int64_t)ldy * (j + 3));
         df_acc_prod(acc, a0, vh[j]);
@@ -328,7 +361,7 @@ __global__ void __launch_bounds__(256) k_gemv_n_df(const float *__restrict__ Y, 
         df_acc_prod(acc, a, vh[j]);
         small = fmaf(a, vl[j], small);
     }
-    const double yv = (double)acc.hi + (double)acc.lo + (double)small;
+    yv += (double)acc.hi + (double)acc.lo + (double)small;
     z[s] = (r[s] - yv) * inv_mu;
 }
 
