@@ -464,6 +464,31 @@ def extras(args, g, torch, wl, plan, d, line):
                 "needs ~100 s"}
     # the serving loop on the first 64 jobs of the seeded request stream
     line["serving_64_jobs"] = serve_replay(g, torch, 64, 20.0, 8)
+    # an inversion stream on one survey (80 x 80 x 40 cells x 6,561 stations, 16 data
+    # vectors at 20/s, mixed, tol 1e-4): resident plans against a plan per job
+    line["serving_same_survey_16_inversions"] = {
+        "workload": "vslab_80x80x40, 16 inversions of different data on one survey, 20/s, 4 slots",
+        "resident_plans": same_survey_stream(g, torch, wl2, S2, True),
+        "plan_per_job": same_survey_stream(g, torch, wl2, S2, False)}
+    # FP64 mode at paper scale, bounded: the operator pair on 1,024 of the stations
+    if args.workload == "paper_210x210x75":
+        sub = wl.survey.subset(np.linspace(0, wl.survey.n - 1, 1024).astype(int))
+        Ss = g.Survey(sub.x, sub.y, sub.z)
+        p64 = g.Plan(wl.mesh, Ss, precision="fp64")
+        m64 = torch.tensor(wl.m, device="cuda")
+        r64 = torch.tensor(synth.random_vector(sub.n, 5), device="cuda")
+        p64.forward(m64); p64.adjoint(r64)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        p64.forward(m64); p64.adjoint(r64)
+        b.record(); b.synchronize()
+        ms64 = a.elapsed_time(b)
+        p64.close()
+        line["fp64_paper_scale_1024_stations"] = {
+            "pairs_per_s": 2.0 * sub.n * wl.mesh.ncells / (ms64 * 1e-3), "ms_per_pair_of_products": ms64,
+            "what": "FP64 forward + adjoint on all 3,307,500 cells and 1,024 evenly spaced stations of the bench "
+                    "workload; the full survey at this rate is the FP64 operator pair's cost per CG iteration"}
     if args.precision == "mixed" and not args.no_bench_inversion:
         # the bench workload itself (210 x 210 x 75 cells x 178,797 stations by default):
         # data = the last timed forward product (mixed operator), Nystrom-preconditioned CG
@@ -554,6 +579,40 @@ def serve_replay(g, torch, n_jobs, rate, slots):
             "config": {"workload": "serving mix: 50k-500k cubic prisms (25-100 m), 1k-20k stations, "
                                    "block/dyke models, forward or inversion 50/50", "tol": 1e-4}}
     return line
+
+
+def same_survey_stream(g, torch, wl, S, resident):
+    """16 inversion jobs on one mesh and survey (different data: the forward of
+    the workload's model scaled and shifted per job), Poisson arrivals at
+    20/s through 4 slots; returns latency percentiles, jobs/s and how many
+    plans the scheduler built."""
+    rng = np.random.Generator(np.random.PCG64(4242))
+    d0 = g.forward(torch.tensor(wl.m, device="cuda"), wl.mesh, S, precision="mixed")
+    datas = [d0 * float(0.5 + k / 16.0) + float(0.01 * k) for k in range(16)]
+    outs = [torch.empty(wl.mesh.ncells, dtype=torch.float64, device="cuda") for _ in datas]
+    arrivals = np.cumsum(rng.exponential(1.0 / 20.0, len(datas)))
+    torch.cuda.synchronize()
+    ctx = g.Context(0)
+    ctx.serve_config(4)
+    ctx.plan_cache(16 if resident else 0)
+    opts = dict(precision="mixed", tol=1e-4, max_iter=500)
+    t0 = time.perf_counter()
+    ids = []
+    for t_arr, dk, ok in zip(arrivals, datas, outs):
+        delay = t_arr - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(ctx.submit("invert", wl.mesh, S, dk, ok, **opts))
+    res = [ctx.wait(i, 600.0) for i in ids]
+    wall = time.perf_counter() - t0
+    lat = [ctx.job_times(i)[2] - ctx.job_times(i)[0] for i in ids]
+    setup = [ctx.job_plan(i)["setup_s"] for i in ids]
+    st = ctx.serve_stats()
+    ctx.close()
+    return {"jobs": len(ids), "ok": res.count(0), "wall_s": wall, "jobs_per_s": len(ids) / wall,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "plans_built": st["plans_built"], "plans_reused": st["plans_reused"],
+            "plan_setup_s_total": float(sum(setup))}
 
 
 def run_invert(args):

@@ -35,6 +35,7 @@ namespace grav {
 namespace {
 
 constexpr int kGmBM = 128, kGmBN = 128, kGmBK = 16, kGmThreads = 256;
+static_assert(kGmBM == 128 && kGmBN == 128 && kGmBK == 16 && kGmThreads == 256, "tile load mapping");
 constexpr int kGmPad = 4;   // row stride 132 floats: 16-byte aligned rows
 
 __device__ __forceinline__ f2_t f2_dup(float a) { return f2_pack(a, a); }
@@ -58,8 +59,8 @@ __global__ void __launch_bounds__(kGmThreads, 2) k_sgemm(int M, int N, int K, co
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int idx = tid + kGmThreads * i;
-            if (A_KMAJ) {
-                const int kq = idx & 3, mm = idx >> 2;
+            if (A_KMAJ) {   // lanes take consecutive rows: the transposed stores below are conflict-free
+                const int mm = idx & (kGmBM - 1), kq = idx >> 7;
                 const int m = m0 + mm, k = k0 + 4 * kq;
                 ra[i] = (m < M && k < K) ? __ldg(reinterpret_cast<const float4 *>(A + (int64_t)m * lda + k)) : zero4;
             } else {
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) k_sgemm(int M, int N, int K, co
                 const int m = m0 + 4 * mq, k = k0 + kk;
                 ra[i] = (m < M && k < K) ? __ldg(reinterpret_cast<const float4 *>(A + (int64_t)k * lda + m)) : zero4;
             }
-            const int kq = idx & 3, nn = idx >> 2;
+            const int nn = idx & (kGmBN - 1), kq = idx >> 7;
             const int n = n0 + nn, k = k0 + 4 * kq;
             rb[i] = (n < N && k < K) ? __ldg(reinterpret_cast<const float4 *>(B + (int64_t)n * ldb + k)) : zero4;
         }
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) k_sgemm(int M, int N, int K, co
         for (int i = 0; i < 2; ++i) {
             const int idx = tid + kGmThreads * i;
             if (A_KMAJ) {
-                const int kq = idx & 3, mm = idx >> 2;
+                const int mm = idx & (kGmBM - 1), kq = idx >> 7;
                 As[buf][4 * kq + 0][mm] = ra[i].x;
                 As[buf][4 * kq + 1][mm] = ra[i].y;
                 As[buf][4 * kq + 2][mm] = ra[i].z;
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) k_sgemm(int M, int N, int K, co
                 const int mq = idx & 31, kk = idx >> 5;
                 *reinterpret_cast<float4 *>(&As[buf][kk][4 * mq]) = ra[i];
             }
-            const int kq = idx & 3, nn = idx >> 2;
+            const int nn = idx & (kGmBN - 1), kq = idx >> 7;
             Bs[buf][4 * kq + 0][nn] = rb[i].x;
             Bs[buf][4 * kq + 1][nn] = rb[i].y;
             Bs[buf][4 * kq + 2][nn] = rb[i].z;
@@ -193,15 +194,15 @@ __global__ void __launch_bounds__(kGrThreads) k_gram_df(int n, int K, const floa
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 ri, rj;
     // 64 columns x 16 k = 256 float4 per operand: one per thread
-    auto load_tile = [&](int k0) {
-        const int kq = tid & 3, cc = tid >> 2;
+    auto load_tile = [&](int k0) {   // lanes take consecutive columns (conflict-free transposed stores)
+        const int cc = tid & (kGrT - 1), kq = tid >> 6;
         const int k = k0 + 4 * kq;
         const int ci = i0 + cc, cj = j0 + cc;
         ri = (ci < n && k < K) ? __ldg(reinterpret_cast<const float4 *>(X + (int64_t)ci * ldx + k)) : zero4;
         rj = (cj < n && k < K) ? __ldg(reinterpret_cast<const float4 *>(X + (int64_t)cj * ldx + k)) : zero4;
     };
     auto store_tile = [&](int buf) {
-        const int kq = tid & 3, cc = tid >> 2;
+        const int cc = tid & (kGrT - 1), kq = tid >> 6;
         Xi[buf][4 * kq + 0][cc] = ri.x; Xi[buf][4 * kq + 1][cc] = ri.y;
         Xi[buf][4 * kq + 2][cc] = ri.z; Xi[buf][4 * kq + 3][cc] = ri.w;
         Xj[buf][4 * kq + 0][cc] = rj.x; Xj[buf][4 * kq + 1][cc] = rj.y;
