@@ -502,6 +502,7 @@ def extras(args, g, torch, wl, plan, d, line):
         line["inversion_to_1e-6_" + args.workload + "_nystrom"] = {
             "workload": args.workload, "precision": "mixed", "seconds": time.perf_counter() - t0,
             "iters": info["iters"], "converged": info["converged"], "true_rel_res": info["true_rel_res"],
+            "nys_setup_s": info["nys_setup_s"], "nys_shift_over_lambda": info["nys_shift"],
             "fp64_rel_err_of_predicted_data": info["fp64_rel_err"],
             "what": "one grav_datainv_solve call on the bench workload (data: its mixed forward product), "
                     "Nystrom-preconditioned, sketch and plan set-up included"}
@@ -648,6 +649,9 @@ def run_invert(args):
             "rms_misfit_mgal": float(torch.sqrt(torch.mean(misfit * misfit))),
             "rms_data_mgal": float(torch.sqrt(torch.mean(d * d))), "data": "synthetic",
             "fp64_rel_err_of_predicted_data": info["fp64_rel_err"]}
+    if args.precond == "nystrom":
+        line["nys_setup_s"] = info["nys_setup_s"]
+        line["nys_shift_over_lambda"] = info["nys_shift"]
     print(json.dumps(line), flush=True)
 
 

@@ -159,6 +159,8 @@ typedef struct {
                                   -1 when not checked */
     double nys_shift;          /* precond = 2: the shift nu / lambda the Nystrom factorisation needed
                                   (1e-3 unless T lost definiteness); 0 otherwise */
+    double nys_setup_s;        /* precond = 2: wall time of the preconditioner's set-up (sketch, Gram
+                                  matrices, host factorisation and inverse); 0 otherwise */
 } grav_solve_info;
 
 typedef struct grav_ctx grav_ctx;

@@ -75,7 +75,8 @@ class grav_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("rel_res", ctypes.c_double),
                 ("true_rel_res", ctypes.c_double), ("lambda_", ctypes.c_double), ("trace", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("outer", ctypes.c_int), ("alpha_min", ctypes.c_double),
-                ("restarts", ctypes.c_int), ("fp64_rel_err", ctypes.c_double), ("nys_shift", ctypes.c_double)]
+                ("restarts", ctypes.c_int), ("fp64_rel_err", ctypes.c_double), ("nys_shift", ctypes.c_double),
+                ("nys_setup_s", ctypes.c_double)]
 
 
 def _sig(name, res, args):
@@ -458,7 +459,8 @@ def datainv(d, mesh, survey, m_ref=None, return_y=False, stream=None, ctx: Optio
     inf = {"iters": info.iters, "converged": bool(info.converged), "rel_res": info.rel_res,
            "true_rel_res": info.true_rel_res, "lambda": info.lambda_, "trace": info.trace,
            "seconds": info.seconds, "status": rc, "outer": info.outer, "alpha_min": info.alpha_min,
-           "restarts": info.restarts, "fp64_rel_err": info.fp64_rel_err, "nys_shift": info.nys_shift}
+           "restarts": info.restarts, "fp64_rel_err": info.fp64_rel_err, "nys_shift": info.nys_shift,
+           "nys_setup_s": info.nys_setup_s}
     if hist is not None:
         h = hist.cpu().numpy()
         inf["res_hist"] = h[h >= 0]

@@ -631,7 +631,9 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             }
             if (jac) vec_jacobi_inv(dinv, lam, N, dinv, s);
         }
+        const double t_nys = now_s();
         if (nys && (rc = nys_build(p, lam, o.nys_rank, o.nys_coarsen, 0x243F6A8885A308D3ull, &ns, s))) break;
+        const double nys_setup_s = nys ? now_s() - t_nys : 0.0;
         // z = M^-1 r: Jacobi or the Nystrom preconditioner
         auto apply_prec = [&](const double *rv, double *z) {
             if (nys) nys_apply(ns, rv, z, s);
@@ -908,6 +910,7 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             info->lambda = lam;
             info->trace = trace;
             info->nys_shift = (o.precond == 2 && ns.mu > 0) ? ns.nu / ns.mu : 0.0;
+            info->nys_setup_s = nys_setup_s;
         }
         rc = read_status(ctx, s, o.timeout_s);
     } while (false);
