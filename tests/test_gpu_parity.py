@@ -909,3 +909,28 @@ def test_dense_kernels_sgemm_and_gram(g):
     C = torch.zeros((8, 8), dtype=torch.float32, device="cuda")
     assert run(0, 8, 8, 8, A, 10, A, 10, C, 8, 0) == g.GRAV_EINVAL
     assert run(1, 6, 8, 8, A, 8, A, 8, C, 8, 0) == g.GRAV_EINVAL
+
+
+def test_fp64_widest_node_row_and_the_cap(g):
+    """The FP64 forward stages one row of nx+1 node weights (rounded up to
+    even) in shared memory with two stage buffers: nx + 1 = 8527 fills the
+    200 KB limit exactly (128 + 24 * 8528 bytes) and still matches the oracle
+    (forward and adjoint, 1e-10 of max); one node more is refused with
+    GRAV_EINVAL before anything runs."""
+    nx = 8526
+    xe = np.linspace(0.0, 10.0 * nx, nx + 1)
+    mesh = synth.Mesh(xe, np.array([0.0, 10.0]), np.array([0.0, 10.0, 25.0]))
+    rng = np.random.Generator(np.random.PCG64(213))
+    n = 300
+    sv = synth.Survey(rng.uniform(-50, 10.0 * nx + 50, n), rng.uniform(-20, 30, n), -rng.uniform(0.5, 10, n))
+    m = rng.normal(0.0, 100.0, mesh.ncells)
+    S = g.Survey(sv.x, sv.y, sv.z)
+    d = g.forward(_dev(m), mesh, S).cpu().numpy()
+    assert _rel(d, oracle.forward(mesh, sv, m)) <= TOL64
+    r = synth.random_vector(n, 214)
+    a = g.adjoint(_dev(r), mesh, S).cpu().numpy()
+    assert _rel(a, oracle.adjoint(mesh, sv, r)) <= TOL64
+    wide = synth.Mesh(np.linspace(0.0, 10.0 * (nx + 2), nx + 3), mesh.ye, mesh.ze)
+    with pytest.raises(g.GravError) as e:
+        g.forward(_dev(np.zeros(wide.ncells)), wide, S)
+    assert e.value.code == g.GRAV_EINVAL and "nx+1 must be <=" in str(e.value)
