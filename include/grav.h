@@ -137,7 +137,7 @@ typedef struct {
                                   at this many evenly spaced stations (inversions: of G m_out; serving
                                   forward jobs: of d), in grav_solve_info.fp64_rel_err; 0 = off (default) */
     int nys_rank;              /* precond = 2: sketch size ell (products with the coarse operator), 1..8192;
-                                  0 = automatic: GRAV_MIXED N / 60 clamped to [100, 3000], GRAV_FP64
+                                  0 = automatic: GRAV_MIXED N / 45 clamped to [100, 4000], GRAV_FP64
                                   min(3000, N / 2) (default 0) */
     int nys_coarsen;           /* precond = 2: coarsening factor per axis of the sketch operator, 1..8;
                                   0 = automatic: GRAV_MIXED min(3, min(nx, ny, nz) / 8), at least 1;

@@ -228,11 +228,15 @@ inline int64_t pad4(int64_t v) { return (v + 3) / 4 * 4; }
 
 }  // namespace
 
-// Automatic sizes (0).  The sketch costs 4 N M_c ell FP32 GEMM flops plus an
-// FP64 Gram of ell^2 (N + M_c); a CG iteration costs two products with the
-// fine operator, ~0.3 s (mixed) or ~0.9 s (FP64) at the sizes below, so FP64
-// solves sketch the uncoarsened operator.
-//   mixed: rank N / 60 in [100, 3000], coarsening min(3, smallest cell count / 8);
+// Automatic sizes (0).  The sketch costs 4 N M_c ell FP32 GEMM flops plus a
+// double-float Gram of ell^2 (N + M_c) products and an ell^3 host factor; a CG
+// iteration costs two products with the fine operator, ~0.28 s (mixed) or
+// ~0.9 s (FP64) at the sizes below, so FP64 solves sketch the uncoarsened
+// operator.  With the Gram matrices on the FP32 pipe the mixed rank rose from
+// N / 60 (max 3000) to N / 45 (max 4000): at 210 x 210 x 75 x 178,797, ranks
+// 2980 / 3500 / 4000 / 4500 took 103 / 90 / 79 / 79 iterations and 37.4 /
+// 35.5 / 33.8 / 36.1 s (set-up 9.7 s at 4000).
+//   mixed: rank N / 45 in [100, 4000], coarsening min(3, smallest cell count / 8);
 //   FP64:  rank min(3000, N / 2), coarsening 1.
 // Measured (inversion to 1e-6; without a preconditioner in brackets):
 //   210 x 210 x 75 cells x 178,797 stations, mixed, rank 2980, coarsening 2 / 3 / 4:
@@ -246,7 +250,7 @@ void nys_sizes(const grav_plan *p, int *ell, int *cf) {
     const int mmin = std::min(p->nx, std::min(p->ny, p->nz));
     if (*ell <= 0)
         *ell = f64 ? (int)std::min<int64_t>(3000, std::max<int64_t>(1, N / 2))
-                   : (int)std::min<int64_t>(3000, std::max<int64_t>(100, (N + 30) / 60));
+                   : (int)std::min<int64_t>(4000, std::max<int64_t>(100, (N + 22) / 45));
     if (*cf <= 0) *cf = f64 ? 1 : std::max(1, std::min(3, mmin / 8));
     *ell = (int)std::min<int64_t>(*ell, N);
 }
