@@ -37,6 +37,9 @@ namespace {
 constexpr int kGmBM = 128, kGmBN = 128, kGmBK = 16, kGmThreads = 256;
 static_assert(kGmBM == 128 && kGmBN == 128 && kGmBK == 16 && kGmThreads == 256, "tile load mapping");
 constexpr int kGmPad = 4;   // row stride 132 floats: 16-byte aligned rows
+#ifndef GRAV_GEMM_MINB
+#define GRAV_GEMM_MINB 2        // CTAs per SM the GEMM's register budget is sized for
+#endif
 
 __device__ __forceinline__ f2_t f2_dup(float a) { return f2_pack(a, a); }
 
@@ -46,7 +49,7 @@ __device__ __forceinline__ f2_t f2_dup(float a) { return f2_pack(a, a); }
 // Requirements (checked by the launcher): lda, ldb, ldc, K and M multiples
 // of 4 and 16-byte aligned bases (float4 loads and stores).
 template <bool A_KMAJ>
-__global__ void __launch_bounds__(kGmThreads, 2) k_sgemm(int M, int N, int K, const float *__restrict__ A, int64_t lda,
+__global__ void __launch_bounds__(kGmThreads, GRAV_GEMM_MINB) k_sgemm(int M, int N, int K, const float *__restrict__ A, int64_t lda,
                                                          const float *__restrict__ B, int64_t ldb, float *__restrict__ C,
                                                          int64_t ldc, int accumulate) {
     __shared__ __align__(16) float As[2][kGmBK][kGmBM + kGmPad];
