@@ -250,7 +250,7 @@ class Context:
         self.check(_lib.grav_poll(self.h, ctypes.c_uint64(job_id), ctypes.byref(st), ctypes.byref(info)))
         return JOB_STATES[st.value], {"iters": info.iters, "converged": bool(info.converged),
                                        "true_rel_res": info.true_rel_res, "lambda": info.lambda_,
-                                       "fp64_rel_err": info.fp64_rel_err}
+                                       "fp64_rel_err": info.fp64_rel_err, "nys_setup_s": info.nys_setup_s}
 
     def wait(self, job_id: int, timeout_s: float = 600.0) -> int:
         """Job result code (GRAV_OK, GRAV_ENOTCONVERGED, GRAV_ECANCELED, ...) or GRAV_ETIMEDOUT."""

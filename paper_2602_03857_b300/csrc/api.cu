@@ -512,8 +512,18 @@ size_t solve_bytes(const grav_plan *p) {
     return 8ull * (12 * p->N + p->M + kDotBlocks + kSCount) + 16 * 256 + 8ull * (bases + cap) + 3 * 256;
 }
 
+size_t plan_resident_bytes(const grav_plan *p) {
+    return p->bytes + (p->nys_kept ? static_cast<const NysState *>(p->nys_kept)->bytes : 0);
+}
+
 void plan_destroy(grav_plan *p, cudaStream_t s) {
     if (!p) return;
+    if (p->nys_kept) {
+        NysState *k = static_cast<NysState *>(p->nys_kept);
+        nys_free(p, k, s);
+        delete k;
+        p->nys_kept = nullptr;
+    }
     for (cudaEvent_t e : p->timer.pool) cudaEventDestroy(e);
     if (p->arena.base) cudaFreeAsync(p->arena.base, s);
     p->ctx->hbm_used -= p->bytes;
@@ -632,7 +642,27 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
             if (jac) vec_jacobi_inv(dinv, lam, N, dinv, s);
         }
         const double t_nys = now_s();
-        if (nys && (rc = nys_build(p, lam, o.nys_rank, o.nys_coarsen, 0x243F6A8885A308D3ull, &ns, s))) break;
+        if (nys) {
+            int ell = o.nys_rank, cf = o.nys_coarsen;
+            nys_sizes(p, &ell, &cf);
+            const uint64_t seed = 0x243F6A8885A308D3ull;
+            const double key[4] = {lam, (double)ell, (double)cf, (double)(seed >> 11)};
+            NysState *kept = static_cast<NysState *>(p->nys_kept);
+            if (kept && std::equal(key, key + 4, p->nys_key)) {
+                ns = *kept;   // the resident preconditioner of an earlier solve on this plan
+                *kept = NysState{};
+                delete kept;
+                p->nys_kept = nullptr;
+            } else {
+                if (kept) {   // different lambda or sizes: replace it
+                    nys_free(p, kept, s);
+                    delete kept;
+                    p->nys_kept = nullptr;
+                }
+                if ((rc = nys_build(p, lam, ell, cf, seed, &ns, s))) break;
+            }
+            std::copy(key, key + 4, p->nys_key);
+        }
         const double nys_setup_s = nys ? now_s() - t_nys : 0.0;
         // z = M^-1 r: Jacobi or the Nystrom preconditioner
         auto apply_prec = [&](const double *rv, double *z) {
@@ -914,6 +944,10 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
         }
         rc = read_status(ctx, s, o.timeout_s);
     } while (false);
+    if (p->keep_nys && ns.mem && rc != GRAV_EDEVICE && rc != GRAV_ETIMEDOUT) {
+        p->nys_kept = new NysState(ns);   // stays with the plan (freed by plan_destroy)
+        ns = NysState{};
+    }
     nys_free(p, &ns, s);
     cudaFreeAsync(base, s);
     ctx->hbm_used -= bytes;

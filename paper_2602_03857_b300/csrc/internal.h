@@ -155,6 +155,12 @@ struct grav_plan {
     int cr_ldw = 0, cr_rows_per_chunk = 0, cr_nchunk = 0;
 
     double trace_cache = 0.0;             // trace(G W^-2 G^T) of an earlier solve on this plan (0: none)
+    // Resident Nystrom preconditioner (serving keeps plans): when keep_nys is
+    // set, a solve leaves its preconditioner here and a later solve with the
+    // same lambda, rank, coarsening and seed reuses it (nys_key: those four).
+    int keep_nys = 0;
+    void *nys_kept = nullptr;             // grav::NysState *, owned by the plan
+    double nys_key[4] = {0, 0, 0, 0};
 
     // CG / diag scratch
     double *diag = nullptr;               // [N]
@@ -210,6 +216,8 @@ int nys_coarse_apply(grav_plan *p, int cf, const double *X, int k, double *Y, cu
 int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState *st, cudaStream_t s);
 void nys_apply(const NysState &st, const double *r, double *z, cudaStream_t s);
 void nys_free(grav_plan *p, NysState *st, cudaStream_t s);
+// device bytes a plan holds, its resident Nystrom preconditioner included
+size_t plan_resident_bytes(const grav_plan *p);
 // bounded host wait for an event (GRAV_ETIMEDOUT after timeout_s)
 int host_wait(grav_ctx *ctx, cudaEvent_t ev, double timeout_s, const char *what);
 

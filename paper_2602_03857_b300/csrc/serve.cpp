@@ -76,6 +76,7 @@ struct PlanKey {
 struct CachedPlan {
     PlanKey key;
     grav_plan *plan = nullptr;
+    size_t bytes = 0;                 // device bytes it holds (plan + resident preconditioner)
     double last_used = 0;
 };
 
@@ -138,7 +139,7 @@ void evict(Scheduler *s, std::vector<grav_plan *> &out) {
         size_t lru = 0;
         for (size_t k = 1; k < s->cache.size(); ++k)
             if (s->cache[k].last_used < s->cache[lru].last_used) lru = k;
-        s->bytes_cached -= s->cache[lru].plan->bytes;
+        s->bytes_cached -= s->cache[lru].bytes;
         out.push_back(s->cache[lru].plan);
         s->cache.erase(s->cache.begin() + (long)lru);
     }
@@ -207,7 +208,7 @@ void run_job(Scheduler *s, Job *job, int slot) {
             for (size_t k = 0; k < s->cache.size(); ++k)
                 if (s->cache[k].key == key) {
                     p = s->cache[k].plan;
-                    s->bytes_cached -= p->bytes;
+                    s->bytes_cached -= s->cache[k].bytes;
                     s->cache.erase(s->cache.begin() + (long)k);
                     ++s->plans_reused;
                     break;
@@ -218,11 +219,13 @@ void run_job(Scheduler *s, Job *job, int slot) {
         if (p) {
             p->opt = d.opt;   // same plan-shaping fields (the key); the solve's own options are this job's
             job->plan_reused = 1;
+            if (use_cache) p->keep_nys = 1;
         } else {
             const double t0 = now_s();
             rc = plan_create(ctx, &mesh, &d.survey, d.opt, &p, stream);
             job->setup_s = now_s() - t0;
             if (rc == GRAV_OK) {
+                if (use_cache) p->keep_nys = 1;   // a Nystrom preconditioner stays with the plan
                 std::lock_guard<std::mutex> lk(s->mu);
                 ++s->plans_built;
             }
@@ -249,9 +252,10 @@ void run_job(Scheduler *s, Job *job, int slot) {
             CachedPlan c;
             c.key = std::move(key);
             c.plan = p;
+            c.bytes = plan_resident_bytes(p);
             c.last_used = now_s();
+            s->bytes_cached += c.bytes;
             s->cache.push_back(std::move(c));
-            s->bytes_cached += p->bytes;
             p = nullptr;
         }
         if (p) plan_destroy(p, stream);

@@ -325,3 +325,40 @@ def test_resident_plan_stream_and_changed_survey(g):
         _oracle_check("invert", "fp64", mesh, sv2, _dev(d), out, opts["tol"])
     finally:
         ctx.close()
+
+
+def test_resident_nystrom_preconditioner(g):
+    """Nystrom-preconditioned inversions of three data vectors on one survey
+    through one slot: the first job builds the plan and the preconditioner,
+    the next two run on both (same lambda from the resident trace, same rank
+    and coarsening) with no set-up, and every result equals its one-shot run
+    within 1e-9 of max |m| and passes the oracle check."""
+    mesh, sv, m = _problem(80, 40, 36, 12, 900, 50.0)
+    S = g.Survey(sv.x, sv.y, sv.z)
+    d = oracle.forward(mesh, sv, m)
+    datas = [d, 0.7 * d, d + synth.random_vector(sv.n, 81, 0.002)]
+    opts = dict(precision="mixed", tol=1e-5, max_iter=3000, precond="nystrom")
+    solo_ctx = g.context()
+    ctx = g.Context(0)
+    try:
+        ctx.serve_config(1)
+        outs, ids = [], []
+        for dk in datas:
+            out = torch.full((mesh.ncells,), float("nan"), dtype=torch.float64, device="cuda")
+            ids.append(ctx.submit("invert", mesh, S, _dev(dk), out, **opts))
+            outs.append(out)
+        for j in ids:
+            assert ctx.wait(j, 600.0) == g.GRAV_OK
+        infos = [ctx.poll(j)[1] for j in ids]
+        assert [ctx.job_plan(j)["plan_reused"] for j in ids] == [False, True, True]
+        assert infos[0]["nys_setup_s"] > 0
+        assert all(i["nys_setup_s"] < 0.05 * infos[0]["nys_setup_s"] for i in infos[1:]), infos
+        st = ctx.serve_stats()
+        assert st["plans_built"] == 1 and st["bytes_resident"] > 0
+        for dk, out in zip(datas, outs):
+            ref, info = g.datainv(_dev(dk), mesh, S, ctx=solo_ctx, **opts)
+            assert info["converged"]
+            assert float((out - ref).abs().max()) <= 1e-9 * float(ref.abs().max())
+            _oracle_check("invert", "mixed", mesh, sv, _dev(dk), out, opts["tol"])
+    finally:
+        ctx.close()
