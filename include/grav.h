@@ -268,11 +268,13 @@ int grav_plan_destroy(grav_plan *plan, grav_stream_t stream);
  * overlap on the device.
  *
  * Plans stay resident: a finished job leaves its plan (mesh tables, station
- * arrays, near-field table, the trace of G W^-2 G^T) in a cache of idle plans,
+ * arrays, near-field table, the trace of G W^-2 G^T and, after a precond = 2
+ * solve, its Nystrom preconditioner) in a cache of idle plans,
  * and a later job with the same mesh edges, the same survey arrays (device
  * pointers and n) holding the same values (a 64-bit fingerprint of x, y, z is
  * taken on the device when the job starts), and the same precision, z0,
- * near_cells and cache_g runs on it without building one.  Idle plans count
+ * near_cells and cache_g runs on it without building one; a Nystrom solve
+ * with the same lambda, rank and coarsening also reuses the preconditioner.  Idle plans count
  * against the HBM budget and are released, least recently used first, when
  * an admission needs the memory or the cache exceeds its entry limit.  Every
  * kernel is deterministic and a reused plan holds the same tables, so a
