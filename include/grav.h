@@ -444,8 +444,13 @@ int grav_nystrom_coarse_apply(grav_ctx *ctx, const grav_mesh *mesh, const grav_s
  *         (ops 0-1: B(k, n) = B[k + ldb n]; M x N output, inner dimension K)
  *   op 2: C (+)= A^T A, lower triangle only (C double, C[i + N j], i >= j, i, j < N),
  *         A(k, i) = A[k + lda i], k < K; exact FP32 products, double-float sums.
+ *   op 3: as op 1 with B(k, n) = B[n + ldb k] and C(m, n) = C[n + ldc m]
+ *   op 4: as op 1 with B(k, n) = B[n + ldb k]
+ *   op 5: as op 2 with A(k, i) = A[i + lda k]
  * accumulate = 1 adds to C.  All pointers DEVICE, 16-byte aligned; lda, ldb,
- * ldc, K (and M for ops 0-1) multiples of 4; GRAV_EINVAL otherwise. */
+ * ldc, K (and M for ops 0-1, 3-4) multiples of 4; an n-major B or C (and the
+ * op 5 A) needs rows of at least N rounded up to 4, whose padding may be
+ * read (op 3: written); GRAV_EINVAL otherwise. */
 int grav_dense_check(grav_ctx *ctx, int op, int M, int N, int K, const float *A, int64_t lda, const float *B,
                      int64_t ldb, void *C, int64_t ldc, int accumulate, grav_stream_t stream);
 

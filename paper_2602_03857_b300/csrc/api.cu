@@ -1279,13 +1279,14 @@ int grav_dense_check(grav_ctx *ctx, int op, int M, int N, int K, const float *A,
                      int64_t ldb, void *C, int64_t ldc, int accumulate, grav_stream_t stream) {
     if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
     DeviceGuard g(ctx->device);
-    if (op < 0 || op > 2 || M < 0 || N < 0 || K < 0) return set_error(ctx, GRAV_EINVAL, "bad op or size");
-    if (!is_device_ptr(A, ctx->device) || !is_device_ptr(C, ctx->device) ||
-        (op < 2 && !is_device_ptr(B, ctx->device)))
+    if (op < 0 || op > 5 || M < 0 || N < 0 || K < 0) return set_error(ctx, GRAV_EINVAL, "bad op or size");
+    const bool gram = op == 2 || op == 5;
+    if (!is_device_ptr(A, ctx->device) || !is_device_ptr(C, ctx->device) || (!gram && !is_device_ptr(B, ctx->device)))
         return set_error(ctx, GRAV_EINVAL, "A, B and C must be device pointers");
     const cudaStream_t s = (cudaStream_t)stream;
-    int rc = op < 2 ? launch_sgemm(op == 0, M, N, K, A, lda, B, ldb, (float *)C, ldc, accumulate != 0, s)
-                    : launch_gram_df(N, K, A, lda, (double *)C, accumulate != 0, s);
+    int rc = gram ? launch_gram_df(N, K, A, lda, (double *)C, accumulate != 0, s, op == 5)
+                  : launch_sgemm(op == 0, M, N, K, A, lda, B, ldb, (float *)C, ldc, accumulate != 0, s,
+                                 op == 3 || op == 4, op == 3);
     if (rc) return set_error(ctx, GRAV_EINVAL, "unsupported layout (leading dimensions, K, M multiples of 4, "
                                                "16-byte aligned pointers)");
     const cudaError_t e = cudaGetLastError();

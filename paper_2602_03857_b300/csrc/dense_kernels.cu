@@ -43,12 +43,18 @@ constexpr int kGmPad = 4;   // row stride 132 floats: 16-byte aligned rows
 
 __device__ __forceinline__ f2_t f2_dup(float a) { return f2_pack(a, a); }
 
-// C[m + ldc n] (+)= sum_k A(m, k) B(k, n), m < M, n < N, k < K.
+// C (+)= A B, m < M, n < N, k < K:
 //   A_KMAJ: A(m, k) = A[k + lda m]; else A(m, k) = A[m + lda k].
-//   B(k, n) = B[k + ldb n].
-// Requirements (checked by the launcher): lda, ldb, ldc, K and M multiples
-// of 4 and 16-byte aligned bases (float4 loads and stores).
-template <bool A_KMAJ>
+//   B_NMAJ: B(k, n) = B[n + ldb k]; else B(k, n) = B[k + ldb n].
+//   C_NMAJ: C(m, n) = C[n + ldc m]; else C(m, n) = C[m + ldc n].
+// An operand whose k index is the slow one (A m-major, B n-major) moves into
+// shared memory as it is; a k-fastest one is transposed on the way (four
+// scalar stores per float4).  Requirements (checked by the launcher): lda,
+// ldb, ldc, K and M multiples of 4, 16-byte aligned bases (float4 loads and
+// stores), and for B_NMAJ / C_NMAJ rows of at least N rounded up to 4 (a
+// float4 that starts below N may cover padding columns, whose results are
+// not stored, and C_NMAJ writes them).
+template <bool A_KMAJ, bool B_NMAJ, bool C_NMAJ>
 __global__ void __launch_bounds__(kGmThreads, GRAV_GEMM_MINB) k_sgemm(int M, int N, int K, const float *__restrict__ A, int64_t lda,
                                                          const float *__restrict__ B, int64_t ldb, float *__restrict__ C,
                                                          int64_t ldc, int accumulate) {
@@ -71,9 +77,15 @@ __global__ void __launch_bounds__(kGmThreads, GRAV_GEMM_MINB) k_sgemm(int M, int
                 const int m = m0 + 4 * mq, k = k0 + kk;
                 ra[i] = (m < M && k < K) ? __ldg(reinterpret_cast<const float4 *>(A + (int64_t)k * lda + m)) : zero4;
             }
-            const int nn = idx & (kGmBN - 1), kq = idx >> 7;
-            const int n = n0 + nn, k = k0 + 4 * kq;
-            rb[i] = (n < N && k < K) ? __ldg(reinterpret_cast<const float4 *>(B + (int64_t)n * ldb + k)) : zero4;
+            if (B_NMAJ) {
+                const int nq = idx & 31, kk = idx >> 5;
+                const int n = n0 + 4 * nq, k = k0 + kk;
+                rb[i] = (n < N && k < K) ? __ldg(reinterpret_cast<const float4 *>(B + (int64_t)k * ldb + n)) : zero4;
+            } else {
+                const int nn = idx & (kGmBN - 1), kq = idx >> 7;
+                const int n = n0 + nn, k = k0 + 4 * kq;
+                rb[i] = (n < N && k < K) ? __ldg(reinterpret_cast<const float4 *>(B + (int64_t)n * ldb + k)) : zero4;
+            }
         }
     };
     auto store_tile = [&](int buf) {
@@ -90,11 +102,16 @@ __global__ void __launch_bounds__(kGmThreads, GRAV_GEMM_MINB) k_sgemm(int M, int
                 const int mq = idx & 31, kk = idx >> 5;
                 *reinterpret_cast<float4 *>(&As[buf][kk][4 * mq]) = ra[i];
             }
-            const int nn = idx & (kGmBN - 1), kq = idx >> 7;
-            Bs[buf][4 * kq + 0][nn] = rb[i].x;
-            Bs[buf][4 * kq + 1][nn] = rb[i].y;
-            Bs[buf][4 * kq + 2][nn] = rb[i].z;
-            Bs[buf][4 * kq + 3][nn] = rb[i].w;
+            if (B_NMAJ) {
+                const int nq = idx & 31, kk = idx >> 5;
+                *reinterpret_cast<float4 *>(&Bs[buf][kk][4 * nq]) = rb[i];
+            } else {
+                const int nn = idx & (kGmBN - 1), kq = idx >> 7;
+                Bs[buf][4 * kq + 0][nn] = rb[i].x;
+                Bs[buf][4 * kq + 1][nn] = rb[i].y;
+                Bs[buf][4 * kq + 2][nn] = rb[i].z;
+                Bs[buf][4 * kq + 3][nn] = rb[i].w;
+            }
         }
     };
     // acc[i][p]: row r(i) = (i < 4 ? ty*4 + i : 64 + ty*4 + i - 4), columns of pair p:
@@ -128,6 +145,29 @@ __global__ void __launch_bounds__(kGmThreads, GRAV_GEMM_MINB) k_sgemm(int M, int
         }
         if (kt + 1 < nk) store_tile(buf ^ 1);
         __syncthreads();
+    }
+    if (C_NMAJ) {   // rows m, four consecutive columns per float4
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int m = m0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + i - 4);
+            if (m >= M) continue;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int n = n0 + 64 * half + 4 * tx;
+                if (n >= N) continue;
+                float a0, a1, a2, a3;
+                f2_unpack(acc[i][2 * half], a0, a1);
+                f2_unpack(acc[i][2 * half + 1], a2, a3);
+                float4 *dst = reinterpret_cast<float4 *>(C + (int64_t)m * ldc + n);
+                float4 out = make_float4(a0, a1, a2, a3);
+                if (accumulate) {
+                    const float4 o = *dst;
+                    out.x += o.x; out.y += o.y; out.z += o.z; out.w += o.w;
+                }
+                *dst = out;
+            }
+        }
+        return;
     }
 #pragma unroll
     for (int p = 0; p < 4; ++p)
@@ -179,9 +219,12 @@ constexpr int kGrT = 64, kGrBK = 16, kGrThreads = 256;
 constexpr int kGrFoldTiles = 8;   // 16-deep k slices per double-float run (128 products)
 constexpr int kDfRun = 128;       // terms per double-float run in the GEMVs
 
-// G[i + n j] (+)= sum_k X[k + ldx i] X[k + ldx j] for i >= j (lower
-// triangle), i, j < n, k < K; 64 x 64 tiles of the lower block triangle,
-// 4 x 4 outputs per thread.  ldx and K multiples of 4, X 16-byte aligned.
+// G[i + n j] (+)= sum_k X(k, i) X(k, j) for i >= j (lower triangle), i, j < n,
+// k < K, with X(k, i) = X[k + ldx i] (!KSLOW) or X[i + ldx k] (KSLOW); 64 x 64
+// tiles of the lower block triangle, 4 x 4 outputs per thread.  ldx and K
+// multiples of 4, X 16-byte aligned; for KSLOW rows of at least n rounded up
+// to 4 (padding columns may be read; their products are not stored).
+template <bool KSLOW>
 __global__ void __launch_bounds__(kGrThreads) k_gram_df(int n, int K, const float *__restrict__ X, int64_t ldx,
                                                         double *__restrict__ G, int accumulate) {
     __shared__ __align__(16) float Xi[2][kGrBK][kGrT + 4];
@@ -197,7 +240,16 @@ __global__ void __launch_bounds__(kGrThreads) k_gram_df(int n, int K, const floa
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 ri, rj;
     // 64 columns x 16 k = 256 float4 per operand: one per thread
-    auto load_tile = [&](int k0) {   // lanes take consecutive columns (conflict-free transposed stores)
+    auto load_tile = [&](int k0) {
+        if (KSLOW) {   // 16 rows k of 64 consecutive columns: one float4 per thread, stored as is
+            const int cq = tid & 15, kk = tid >> 4;
+            const int k = k0 + kk;
+            const int ci = i0 + 4 * cq, cj = j0 + 4 * cq;
+            ri = (ci < n && k < K) ? __ldg(reinterpret_cast<const float4 *>(X + (int64_t)k * ldx + ci)) : zero4;
+            rj = (cj < n && k < K) ? __ldg(reinterpret_cast<const float4 *>(X + (int64_t)k * ldx + cj)) : zero4;
+            return;
+        }
+        // lanes take consecutive columns (conflict-free transposed stores)
         const int cc = tid & (kGrT - 1), kq = tid >> 6;
         const int k = k0 + 4 * kq;
         const int ci = i0 + cc, cj = j0 + cc;
@@ -205,6 +257,12 @@ __global__ void __launch_bounds__(kGrThreads) k_gram_df(int n, int K, const floa
         rj = (cj < n && k < K) ? __ldg(reinterpret_cast<const float4 *>(X + (int64_t)cj * ldx + k)) : zero4;
     };
     auto store_tile = [&](int buf) {
+        if (KSLOW) {
+            const int cq = tid & 15, kk = tid >> 4;
+            *reinterpret_cast<float4 *>(&Xi[buf][kk][4 * cq]) = ri;
+            *reinterpret_cast<float4 *>(&Xj[buf][kk][4 * cq]) = rj;
+            return;
+        }
         const int cc = tid & (kGrT - 1), kq = tid >> 6;
         Xi[buf][4 * kq + 0][cc] = ri.x; Xi[buf][4 * kq + 1][cc] = ri.y;
         Xi[buf][4 * kq + 2][cc] = ri.z; Xi[buf][4 * kq + 3][cc] = ri.w;
@@ -376,27 +434,39 @@ inline unsigned blocks_for(int64_t n, int threads, int64_t cap = 148 * 32) {
 }  // namespace
 
 int launch_sgemm(bool a_kmajor, int M, int N, int K, const float *A, int64_t lda, const float *B, int64_t ldb,
-                 float *C, int64_t ldc, bool accumulate, cudaStream_t s) {
+                 float *C, int64_t ldc, bool accumulate, cudaStream_t s, bool b_nmajor, bool c_nmajor) {
     if (M <= 0 || N <= 0) return 0;
     if ((lda | ldb | ldc | K | M) & 3) return -1;
+    const int64_t n4 = ((int64_t)N + 3) / 4 * 4;
+    if ((b_nmajor && ldb < n4) || (c_nmajor && ldc < n4)) return -1;
     if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15)
         return -1;
     dim3 grid((unsigned)((M + kGmBM - 1) / kGmBM), (unsigned)((N + kGmBN - 1) / kGmBN));
     if (grid.y > 65535) return -1;
-    if (a_kmajor)
-        k_sgemm<true><<<grid, kGmThreads, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, accumulate ? 1 : 0);
-    else
-        k_sgemm<false><<<grid, kGmThreads, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, accumulate ? 1 : 0);
+    const int acc = accumulate ? 1 : 0;
+    auto go = [&](auto kern) { kern<<<grid, kGmThreads, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, acc); };
+    if (a_kmajor) {
+        if (b_nmajor) c_nmajor ? go(k_sgemm<true, true, true>) : go(k_sgemm<true, true, false>);
+        else c_nmajor ? go(k_sgemm<true, false, true>) : go(k_sgemm<true, false, false>);
+    } else {
+        if (b_nmajor) c_nmajor ? go(k_sgemm<false, true, true>) : go(k_sgemm<false, true, false>);
+        else c_nmajor ? go(k_sgemm<false, false, true>) : go(k_sgemm<false, false, false>);
+    }
     note_launches(1);
     return 0;
 }
 
-int launch_gram_df(int n, int K, const float *X, int64_t ldx, double *G, bool accumulate, cudaStream_t s) {
+int launch_gram_df(int n, int K, const float *X, int64_t ldx, double *G, bool accumulate, cudaStream_t s,
+                   bool k_slow) {
     if (n <= 0) return 0;
     if ((ldx | K) & 3 || (reinterpret_cast<uintptr_t>(X) & 15)) return -1;
+    if (k_slow && ldx < ((int64_t)n + 3) / 4 * 4) return -1;
     const int nt = (n + kGrT - 1) / kGrT;
     const int64_t tiles = (int64_t)nt * (nt + 1) / 2;
-    k_gram_df<<<(unsigned)tiles, kGrThreads, 0, s>>>(n, K, X, ldx, G, accumulate ? 1 : 0);
+    if (k_slow)
+        k_gram_df<true><<<(unsigned)tiles, kGrThreads, 0, s>>>(n, K, X, ldx, G, accumulate ? 1 : 0);
+    else
+        k_gram_df<false><<<(unsigned)tiles, kGrThreads, 0, s>>>(n, K, X, ldx, G, accumulate ? 1 : 0);
     note_launches(1);
     return 0;
 }

@@ -296,13 +296,17 @@ void launch_corner_fwd(const grav_plan *p, const double *m, cudaStream_t s);
 // dense kernels of the Nystrom preconditioner (dense_kernels.cu).  Return -1
 // (nothing launched) when the layout requirements are not met.
 // C (+)= A B in FP32: A(m, k) = A[k + lda m] (a_kmajor) or A[m + lda k];
-// B(k, n) = B[k + ldb n]; C(m, n) = C[m + ldc n].  lda, ldb, ldc, K, M
-// multiples of 4, bases 16-byte aligned.
+// B(k, n) = B[n + ldb k] (b_nmajor) or B[k + ldb n]; C(m, n) = C[n + ldc m]
+// (c_nmajor) or C[m + ldc n].  lda, ldb, ldc, K, M (and N when b_nmajor or
+// c_nmajor) multiples of 4, bases 16-byte aligned.
 int launch_sgemm(bool a_kmajor, int M, int N, int K, const float *A, int64_t lda, const float *B, int64_t ldb,
-                 float *C, int64_t ldc, bool accumulate, cudaStream_t s);
-// G (+)= X^T X (lower triangle, G[i + n j], i >= j) for X[k + ldx i], k < K,
-// i < n; exact FP32 products, double-float sums.  ldx, K multiples of 4.
-int launch_gram_df(int n, int K, const float *X, int64_t ldx, double *G, bool accumulate, cudaStream_t s);
+                 float *C, int64_t ldc, bool accumulate, cudaStream_t s, bool b_nmajor = false,
+                 bool c_nmajor = false);
+// G (+)= X^T X (lower triangle, G[i + n j], i >= j) for X(k, i) = X[k + ldx i]
+// (or X[i + ldx k] when k_slow), k < K, i < n; exact FP32 products,
+// double-float sums.  ldx, K (n when k_slow) multiples of 4.
+int launch_gram_df(int n, int K, const float *X, int64_t ldx, double *G, bool accumulate, cudaStream_t s,
+                   bool k_slow = false);
 // z = (r - Y Linv^T Linv Y^T r) / mu  (Y FP32 [ldy][ell], Linv FP64 lower)
 void launch_nys_apply(const float *Y, int64_t ldy, int64_t n, int ell, const double *Linv, double mu,
                       const double *r, double *z, float *rh, float *rl, double *t, double *u, double *v, float *vh,

@@ -72,15 +72,18 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     return x ^ (x >> 31);
 }
 
-// out[s + ld j] = scale * N(0, 1) (rounded to FP32) for s < n, j < k, from
-// the Box-Muller transform of two uniforms drawn from counters 2i and 2i+1,
-// i = s + n j, of the stream `seed` (deterministic); padding rows s >= n are 0.
-__global__ void k_randn32(float *__restrict__ out, int64_t n, int64_t ld, int k, uint64_t seed, double scale) {
+// Omega: out[j + ldo s] = scale * N(0, 1) (rounded to FP32) for s < n, j < k,
+// from the Box-Muller transform of two uniforms drawn from counters 2i and
+// 2i+1, i = s + n j, of the stream `seed` (deterministic); entries with
+// s >= n (up to ld_rows) or j >= k (up to ldo) are 0.  Station-major, so
+// that the sketch GEMM reads Omega with its reduction index (the station) slow.
+__global__ void k_randn32_t(float *__restrict__ out, int64_t n, int64_t ld_rows, int k, int64_t ldo, uint64_t seed,
+                            double scale) {
     const double two_pi = 6.283185307179586476925286766559;
-    const int64_t total = ld * k;
+    const int64_t total = ld_rows * ldo;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = q % ld, j = q / ld;
-        if (s >= n) {
+        const int64_t j = q % ldo, s = q / ldo;
+        if (s >= n || j >= k) {
             out[q] = 0.0f;
             continue;
         }
@@ -112,15 +115,17 @@ __global__ void k_widen(const float *__restrict__ x, int64_t ldx, int64_t n, int
 }
 
 // Explicit block of the scaled coarse operator B = G_c W_c^-1 / cf^(3/2)
-// (K_c = B B^T), cells c0 <= c < c0 + cb in natural order, column-major
-// B[(c - c0) ldb + s] (FP32).  The far part is the mixed operator's own FP32
+// (K_c = B B^T), cells c0 <= c < c0 + cb in natural order, station-fastest
+// B[(c - c0) ldb + s] (FP32) and, when Bt is given, also cell-fastest
+// Bt[(c - c0) + ldt s] (each thread's 16 consecutive cells as four float4).  The far part is the mixed operator's own FP32
 // point-mass (+ quadrupole) term of the pair; fac[l] = gamma V (zc_l + z0) / cf^1.5.
 constexpr int kNysCells = 16;   // cells per thread
 
 template <bool QUAD>
 __global__ void __launch_bounds__(256) k_nys_far(MixedGeo g, const float4 *__restrict__ st32,
                                                  const float2 *__restrict__ stz, int64_t N, int64_t ldb, int64_t c0,
-                                                 int cb, const float *__restrict__ fac, float *__restrict__ B) {
+                                                 int cb, const float *__restrict__ fac, float *__restrict__ B,
+                                                 float *__restrict__ Bt, int64_t ldt) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
     const float4 S = st32[s];
@@ -129,6 +134,9 @@ __global__ void __launch_bounds__(256) k_nys_far(MixedGeo g, const float4 *__res
     // (i, j, l) of cell c0 + k0, then stepped along x (meshes hold at most 2^30 cells)
     const int c = (int)(c0 + k0);
     int l = c / g.ncol, i = (c - l * g.ncol) % g.nx, j = (c - l * g.ncol) / g.nx;
+    float vals[kNysCells];
+#pragma unroll
+    for (int u = 0; u < kNysCells; ++u) vals[u] = 0.0f;
     for (int k = k0; k < k1; ++k) {
         const float2 X = make_float2(g.cx[2 * i], g.cx[2 * i + 1]);
         const float2 Y = make_float2(g.cy[2 * j], g.cy[2 * j + 1]);
@@ -138,7 +146,9 @@ __global__ void __launch_bounds__(256) k_nys_far(MixedGeo g, const float4 *__res
         const float ph = QUAD ? far_ph(X, Y, S.x, S.y, S.z, S.w, g.qa, g.qb) : 0.0f;
         const float dz = g.czc[l] - zs;
         const float R2 = fmaf(dz, dz, h2);
-        B[(int64_t)k * ldb + s] = far_k<QUAD>(dz, R2, g.qg, ph) * fac[l];
+        const float v = far_k<QUAD>(dz, R2, g.qg, ph) * fac[l];
+        B[(int64_t)k * ldb + s] = v;
+        vals[k - k0] = v;
         if (++i == g.nx) {
             i = 0;
             if (++j == g.ny) {
@@ -146,6 +156,13 @@ __global__ void __launch_bounds__(256) k_nys_far(MixedGeo g, const float4 *__res
                 ++l;
             }
         }
+    }
+    if (Bt) {   // cells k0 .. k0+15 of row s (ldt and k0 multiples of 4: 16-byte aligned)
+        float4 *dst = reinterpret_cast<float4 *>(Bt + (int64_t)s * ldt + k0);
+        const int nq = (k1 - k0 + 3) / 4;
+#pragma unroll
+        for (int u = 0; u < kNysCells / 4; ++u)
+            if (u < nq) dst[u] = make_float4(vals[4 * u], vals[4 * u + 1], vals[4 * u + 2], vals[4 * u + 3]);
     }
 }
 
@@ -155,7 +172,8 @@ __global__ void __launch_bounds__(256) k_nys_far(MixedGeo g, const float4 *__res
 __global__ void __launch_bounds__(256) k_nys_near(int nx, int ny, int nz, NearGeo ng, int64_t N, int64_t ldb,
                                                   const float *__restrict__ dG, const int *__restrict__ st_i0,
                                                   const int *__restrict__ st_j0, int64_t c0, int cb,
-                                                  const float *__restrict__ fac, float *__restrict__ B) {
+                                                  const float *__restrict__ fac, float *__restrict__ B,
+                                                  float *__restrict__ Bt, int64_t ldt) {
     const int lane = threadIdx.x & 31;
     const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (s >= N) return;
@@ -166,7 +184,11 @@ __global__ void __launch_bounds__(256) k_nys_near(int nx, int ny, int nz, NearGe
         const int64_t k = (int64_t)i + (int64_t)nx * (j + (int64_t)ny * l) - c0;
         if (k < 0 || k >= cb) continue;
         const float d = dG[s * ng.ld + t];
-        if (d != 0.0f) B[k * ldb + s] += d * fac[l];
+        if (d != 0.0f) {
+            const float v = d * fac[l];
+            B[k * ldb + s] += v;
+            if (Bt) Bt[s * ldt + k] += v;
+        }
     }
 }
 
@@ -275,9 +297,10 @@ size_t nys_peak_bytes(const grav_plan *p) {
     if (ell < 1 || cf < 1) return 0;
     const int64_t ldy = pad4(p->N);
     const int64_t Mc = (int64_t)((p->nx + cf - 1) / cf) * ((p->ny + cf - 1) / cf) * ((p->nz + cf - 1) / cf);
-    const int64_t cb = pad4(std::min<int64_t>({Mc, (1ll << 30) / ldy, (1ll << 27) / ell, 65535ll * kNysCells}));
-    // persistent + Omega (FP32) + the two Gram matrices + one explicit block and Z_b
-    return nys_bytes(p->N, ell) + 4ull * ldy * ell + 16ull * ell * ell + 4ull * cb * ldy + 4ull * cb * ell +
+    const int64_t ellp = pad4(ell);
+    const int64_t cb = pad4(std::min<int64_t>({Mc, (1ll << 30) / ldy, (1ll << 27) / ellp, 65535ll * kNysCells}));
+    // persistent + Omega (FP32) + the two Gram matrices + one explicit block in two layouts and Z_b
+    return nys_bytes(p->N, ell) + 4ull * ldy * ellp + 16ull * ell * ell + 8ull * cb * ldy + 4ull * cb * ellp +
            (1u << 20);
 }
 
@@ -304,25 +327,32 @@ int coarse_plan(grav_plan *p, int cf, grav_plan **cp, cudaStream_t s) {
     return plan_create(p->ctx, &cm, &sv, oc, cp, s);
 }
 
-// Y32 = K_c X32 = B (B^T X32) (ldy x k, FP32, column-major; rows >= N of X32
-// must be 0) with B = G_c W_c^-1 / cf^(3/2) formed explicitly one block of
-// cells at a time (FP32, at most 4 GB); when M is given, M (k x k, FP64,
-// lower triangle) = Z^T Z with Z = B^T X32 (exact FP32 products, double-float
-// sums).  Scratch comes from the context's pool and the context's HBM budget.
-int coarse_products(grav_plan *cp, int cf, double z0, const float *X32, int k, float *Y32, double *M,
-                    cudaStream_t s) {
+// Y32 = K_c X32 = B (B^T X32) (ldy x k, FP32, column-major: Y32[s + ldy j])
+// with B = G_c W_c^-1 / cf^(3/2) formed explicitly one block of cells at a
+// time (FP32).  X32 is station-major (X32[j + ldx s], x_nmajor: the sketch's
+// Omega) or station-fastest (X32[s + ldx j]); rows s >= N must be 0.  With a
+// station-major X32 the block is formed in both layouts, so that neither GEMM
+// transposes a tile: Z_b = B_b^T X32 reads the cell-fastest copy and X32 with
+// the station index slow and writes Z_b column-fastest (Z_b[j + kp c]); Y32
+// += B_b Z_b reads the station-fastest copy and Z_b with the cell index slow.
+// When M is given, M (k x k, FP64, lower triangle) = Z^T Z (exact FP32
+// products, double-float sums).  Scratch comes from the context's pool and
+// the context's HBM budget.
+int coarse_products(grav_plan *cp, int cf, double z0, const float *X32, int64_t ldx, bool x_nmajor, int k,
+                    float *Y32, double *M, cudaStream_t s) {
     grav_ctx *ctx = cp->ctx;
-    const int64_t N = cp->N, Mc = cp->M, ldy = pad4(N);
+    const int64_t N = cp->N, Mc = cp->M, ldy = pad4(N), kp = pad4(k);
     const int nzc = cp->nz;
-    const size_t used = ctx->hbm_used.load() + 4ull * nzc + 4 * 256;
+    const int layouts = x_nmajor ? 2 : 1;
+    const size_t used = ctx->hbm_used.load() + 4ull * nzc + 5 * 256;
     const size_t left = ctx->hbm_budget > used ? ctx->hbm_budget - used : 0;
-    int64_t cb = block_cells(Mc, ldy, k, left);
+    int64_t cb = block_cells(Mc, ldy, (int)kp, left / layouts);
     if (cb < std::min<int64_t>(Mc, 64))
         return set_error(ctx, GRAV_ENOMEM, "explicit coarse operator block (%d columns) exceeds the HBM budget", k);
     const int64_t nblk = (Mc + cb - 1) / cb;
     cb = (Mc + nblk - 1) / nblk;   // equal blocks
     const int64_t cbp = pad4(cb);   // GEMM inner dimension, zero columns at the end
-    const size_t bytes = 4ull * nzc + 4ull * cbp * ldy + 4ull * cbp * k + 4 * 256;
+    const size_t bytes = 4ull * nzc + 4ull * layouts * cbp * ldy + 4ull * cbp * kp + 5 * 256;
     char *mem = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync((void **)&mem, bytes, ctx->pool, s);
     if (e != cudaSuccess) return cuda_error(ctx, e, "explicit coarse operator block");
@@ -330,8 +360,14 @@ int coarse_products(grav_plan *cp, int cf, double z0, const float *X32, int k, f
     Arena ta;
     ta.base = mem; ta.size = bytes;
     float *fac = (float *)ta.take(4ull * nzc);
-    float *Bb = (float *)ta.take(4ull * ldy * cbp);
-    float *Zb = (float *)ta.take(4ull * cbp * k);
+    float *Bb = (float *)ta.take(4ull * ldy * cbp);                      // B_b[c ldy + s]
+    float *Bt = x_nmajor ? (float *)ta.take(4ull * ldy * cbp) : nullptr;  // B_b[s cbp + c]
+    float *Zb = (float *)ta.take(4ull * cbp * kp);   // x_nmajor: Z_b[c kp + j]; else Z_b[j cbp + c]
+    if (ta.overflow) {
+        cudaFreeAsync(mem, s);
+        ctx->hbm_used -= bytes;
+        return set_error(ctx, GRAV_EDEVICE, "explicit coarse operator layout");
+    }
     // fac[l] = gamma V_c (zc_l + z0) / cf^(3/2): K ~ G_c W_c^-2 G_c^T / cf^3 = B B^T
     std::vector<float> hfac(nzc);
     const double vol_mgal = kGammaMgal * cp->cell_a * cp->cell_b * cp->cell_c;
@@ -342,20 +378,28 @@ int coarse_products(grav_plan *cp, int cf, double z0, const float *X32, int k, f
     for (int64_t b = 0; b < nblk && !rc; ++b) {
         const int64_t c0 = b * cb;
         const int nb = (int)std::min<int64_t>(cb, Mc - c0);
-        // zero block: padding rows (stations >= N) and columns (cells >= nb) stay 0
+        // zero blocks: padding rows (stations >= N) and columns (cells >= nb) stay 0
         cudaMemsetAsync(Bb, 0, 4ull * ldy * cbp, s);
+        if (Bt) cudaMemsetAsync(Bt, 0, 4ull * ldy * cbp, s);
         dim3 gf((unsigned)((N + 255) / 256), (unsigned)((nb + kNysCells - 1) / kNysCells));
         if (cp->cubic)
-            k_nys_far<false><<<gf, 256, 0, s>>>(cp->mg, cp->st32, cp->stz, N, ldy, c0, nb, fac, Bb);
+            k_nys_far<false><<<gf, 256, 0, s>>>(cp->mg, cp->st32, cp->stz, N, ldy, c0, nb, fac, Bb, Bt, cbp);
         else
-            k_nys_far<true><<<gf, 256, 0, s>>>(cp->mg, cp->st32, cp->stz, N, ldy, c0, nb, fac, Bb);
+            k_nys_far<true><<<gf, 256, 0, s>>>(cp->mg, cp->st32, cp->stz, N, ldy, c0, nb, fac, Bb, Bt, cbp);
         k_nys_near<<<(unsigned)((N * 32 + 255) / 256), 256, 0, s>>>(cp->nx, cp->ny, nzc, cp->ng, N, ldy, cp->dG,
-                                                                  cp->st_i0, cp->st_j0, c0, nb, fac, Bb);
+                                                                  cp->st_i0, cp->st_j0, c0, nb, fac, Bb, Bt, cbp);
         note_launches(2);
-        // Z_b = B_b^T X32 (cbp x k), Y32 (+)= B_b Z_b, M (+)= Z_b^T Z_b
-        bool ok = launch_sgemm(true, (int)cbp, k, (int)ldy, Bb, ldy, X32, ldy, Zb, cbp, false, s) == 0;
-        ok = ok && launch_sgemm(false, (int)ldy, k, (int)cbp, Bb, ldy, Zb, cbp, Y32, ldy, b > 0, s) == 0;
-        if (M) ok = ok && launch_gram_df(k, (int)cbp, Zb, cbp, M, b > 0, s) == 0;
+        bool ok;
+        if (x_nmajor) {
+            // Z_b = B_b^T X32 (cbp x k, column-fastest), Y32 (+)= B_b Z_b, M (+)= Z_b^T Z_b
+            ok = launch_sgemm(false, (int)cbp, k, (int)ldy, Bt, cbp, X32, ldx, Zb, kp, false, s, true, true) == 0;
+            ok = ok && launch_sgemm(false, (int)ldy, k, (int)cbp, Bb, ldy, Zb, kp, Y32, ldy, b > 0, s, true, false) == 0;
+            if (M) ok = ok && launch_gram_df(k, (int)cbp, Zb, kp, M, b > 0, s, true) == 0;
+        } else {
+            ok = launch_sgemm(true, (int)cbp, k, (int)ldy, Bb, ldy, X32, ldx, Zb, cbp, false, s) == 0;
+            ok = ok && launch_sgemm(false, (int)ldy, k, (int)cbp, Bb, ldy, Zb, cbp, Y32, ldy, b > 0, s) == 0;
+            if (M) ok = ok && launch_gram_df(k, (int)cbp, Zb, cbp, M, b > 0, s) == 0;
+        }
         if (!ok) rc = set_error(ctx, GRAV_EINVAL, "explicit coarse products: unsupported layout");
     }
     cudaFreeAsync(mem, s);
@@ -387,7 +431,7 @@ int nys_coarse_apply(grav_plan *p, int cf, const double *X, int k, double *Y, cu
     float *Y32 = (float *)ta.take(4ull * ldy * k);
     k_narrow<<<grid_n(ldy * k), 256, 0, s>>>(X, N, k, X32, ldy);
     note_launches(1);
-    rc = coarse_products(cp, cf, p->opt.z0, X32, k, Y32, nullptr, s);
+    rc = coarse_products(cp, cf, p->opt.z0, X32, ldy, false, k, Y32, nullptr, s);
     if (!rc) {
         k_widen<<<grid_n(N * k), 256, 0, s>>>(Y32, ldy, N, k, Y);
         note_launches(1);
@@ -415,7 +459,8 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
     // persistent block; temporary block: Omega (FP32, ldy x ell), M and Y^T Y
     // (ell x ell FP64); the explicit blocks take what the budget leaves
     st->bytes = nys_bytes(N, ell);
-    const size_t tmp_bytes = 4ull * ldy * ell + 16ull * ell * ell + 4 * 256;
+    const int64_t ellp = pad4(ell);
+    const size_t tmp_bytes = 4ull * ldy * ellp + 16ull * ell * ell + 4 * 256;
     if (ctx->hbm_used.load() + st->bytes + tmp_bytes > ctx->hbm_budget) {
         plan_destroy(cp, s);
         return set_error(ctx, GRAV_ENOMEM, "Nystrom preconditioner (rank %d) exceeds the HBM budget", ell);
@@ -443,7 +488,7 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
     st->rl = (float *)pa.take(4ull * ldy);
     Arena ta;
     ta.base = tmp; ta.size = tmp_bytes;
-    float *Om32 = (float *)ta.take(4ull * ldy * ell);
+    float *Om32 = (float *)ta.take(4ull * ldy * ellp);   // station-major: Om32[j + ellp s]
     double *Mm = (double *)ta.take(8ull * ell * ell);
     double *Gy = (double *)ta.take(8ull * ell * ell);
     std::vector<double> hM((size_t)ell * ell), hG((size_t)ell * ell);
@@ -453,10 +498,10 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
             rc = set_error(ctx, GRAV_EDEVICE, "Nystrom scratch layout");
             break;
         }
-        k_randn32<<<grid_n(ldy * ell), 256, 0, s>>>(Om32, N, ldy, ell, seed, 1.0 / std::sqrt((double)N));
+        k_randn32_t<<<grid_n(ldy * ellp), 256, 0, s>>>(Om32, N, ldy, ell, ellp, seed, 1.0 / std::sqrt((double)N));
         note_launches(1);
         // Y = K_c Omega and M = Z^T Z, Z = B^T Omega
-        if ((rc = coarse_products(cp, cf, p->opt.z0, Om32, ell, st->Y, Mm, s))) break;
+        if ((rc = coarse_products(cp, cf, p->opt.z0, Om32, ellp, true, ell, st->Y, Mm, s))) break;
         if (launch_gram_df(ell, (int)ldy, st->Y, ldy, Gy, false, s) != 0) {
             rc = set_error(ctx, GRAV_EINVAL, "Nystrom Gram matrix: unsupported layout");
             break;

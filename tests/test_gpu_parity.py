@@ -904,11 +904,50 @@ def test_dense_kernels_sgemm_and_gram(g):
         assert run(2, 0, n, K, Xt, ldx, None, 0, Gt, n, 1) == g.GRAV_OK
         got2 = Gt.cpu().numpy().T
         assert np.all(np.abs(got2 - 2 * ref)[low] <= 2 * tol * scale[low])
+    # k-slow layouts (no transposed tiles): op 3 / 4 take B(k, n) = B[n + ldb k]
+    # (op 3 also writes C(m, n) = C[n + ldc m]), op 5 the Gram of X(k, i) = X[i + ldx k];
+    # N not a multiple of 4, rows padded to a multiple of 4
+    for op, M, N, K in ((3, 260, 77, 1000), (4, 132, 130, 52), (3, 4, 1, 4), (4, 388, 257, 1028)):
+        lda = M + 8
+        A = rng.standard_normal((K, lda)).astype(np.float32)            # A(m, k) = A[k, m]
+        ldb = (N + 3) // 4 * 4 + 4
+        B = rng.standard_normal((K, ldb)).astype(np.float32)            # B(k, n) = B[k, n]
+        Am, Bm = A[:, :M].T.astype(np.float64), B[:, :N].astype(np.float64)
+        ref = Am @ Bm
+        bound = (K + 2) * u * (np.abs(Am) @ np.abs(Bm))
+        if op == 3:
+            ldc = (N + 3) // 4 * 4
+            C0 = rng.standard_normal((M, ldc)).astype(np.float32)       # C(m, n) = C[m, n]
+        else:
+            ldc = M + 4
+            C0 = rng.standard_normal((N, ldc)).astype(np.float32)       # C(m, n) = C[n, m]
+        for acc in (0, 1):
+            At, Bt, Ct = (torch.tensor(x, device="cuda") for x in (A, B, C0))
+            assert run(op, M, N, K, At, lda, Bt, ldb, Ct, ldc, acc) == g.GRAV_OK
+            c = Ct.cpu().numpy()
+            got = c[:, :N].astype(np.float64) if op == 3 else c[:, :M].T.astype(np.float64)
+            c0 = C0[:, :N] if op == 3 else C0[:, :M].T
+            want = ref + (c0.astype(np.float64) if acc else 0.0)
+            assert np.all(np.abs(got - want) <= bound + (np.abs(c0) * u * 2 if acc else 0.0)), (op, M, N, K)
+    for n, K in ((150, 1004), (63, 16), (5, 4)):
+        ldx = (n + 3) // 4 * 4 + 4
+        X = rng.standard_normal((K, ldx)).astype(np.float32)            # X(k, i) = X[k, i]
+        Xm = X[:, :n].astype(np.float64)
+        ref = Xm.T @ Xm
+        scale = np.abs(Xm).T @ np.abs(Xm)
+        tol = min(K, 128) * 2.0 ** -48 + K * 2.0 ** -53
+        Gt = torch.full((n, n), 7.0, dtype=torch.float64, device="cuda")
+        assert run(5, 0, n, K, torch.tensor(X, device="cuda"), ldx, None, 0, Gt, n, 0) == g.GRAV_OK
+        got = Gt.cpu().numpy().T
+        low = np.tril(np.ones((n, n), bool))
+        assert np.all(np.abs(got - ref)[low] <= tol * scale[low]), (n, K)
+        assert np.all(got[~low] == 7.0)
     # refused layouts: nothing launched
     A = torch.zeros((8, 10), dtype=torch.float32, device="cuda")
     C = torch.zeros((8, 8), dtype=torch.float32, device="cuda")
     assert run(0, 8, 8, 8, A, 10, A, 10, C, 8, 0) == g.GRAV_EINVAL
     assert run(1, 6, 8, 8, A, 8, A, 8, C, 8, 0) == g.GRAV_EINVAL
+    assert run(3, 8, 9, 8, A, 8, A, 8, C, 12, 0) == g.GRAV_EINVAL      # n-major B rows shorter than 12
 
 
 def test_fp64_widest_node_row_and_the_cap(g):
