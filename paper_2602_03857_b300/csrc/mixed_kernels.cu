@@ -1166,9 +1166,141 @@ __global__ void __launch_bounds__(kNaThreads) k_near_adj_rows(
     }
 }
 
+// Near-field adjoint, warp-private form (the default when its shared memory
+// fits).  CTA = tile of kNwTile x kNwTile station bins, region of RX x RY x lz
+// cells (RX = kNwTile + bx - 1); each of the 8 warps owns a private FP32
+// accumulator over the whole region and takes stations w, w + 8, ... of the
+// tile in order.  A warp streams its station's table row (ld floats,
+// contiguous) with 16-byte evict-first loads, kNwChunk per lane in flight,
+// and adds dG * r into its own accumulator (one station's slots are distinct
+// cells, so no lane races another; no other warp touches this accumulator, so
+// no barrier separates stations).  Every kNwPass stations per warp the eight
+// accumulators are summed cell by cell in warp order (FP32) and added into
+// the tile's FP64 region sums in global memory (tpart[tile], the same
+// per-tile layout k_near_adj_gather reads), then cleared: bitwise
+// deterministic, at most 8 kNwPass FP32 terms per cell between FP64 folds.
+// The table is read once, in whole rows, with no per-station barrier.
+constexpr int kNwTile = 4;
+constexpr int kNwWarps = 8;
+constexpr int kNwPass = 16;
+constexpr int kNwChunk = 8;
+constexpr size_t kNwSmemBudget = 112 * 1024;   // two CTAs per SM
+
+struct NearWarpShape {
+    bool ok = false;
+    int RX = 0, RY = 0, lz = 0, RC = 0, ntx = 0, nty = 0;
+    size_t o_roff = 0, o_acc = 0, smem = 0;
+};
+
+static NearWarpShape near_warp_shape(const grav_plan *p) {
+    NearWarpShape z;
+    z.RX = kNwTile + p->ng.bx - 1;
+    z.RY = kNwTile + p->ng.by - 1;
+    z.lz = std::min(p->ng.bz, p->nz);
+    z.RC = z.RX * z.RY * z.lz;
+    z.ntx = (p->ng.nbx + kNwTile - 1) / kNwTile;
+    z.nty = (p->ng.nby + kNwTile - 1) / kNwTile;
+    z.o_roff = 128;                                             // header: row table [2 kNwTile + 1]
+    z.o_acc = align_up(z.o_roff + 4ull * p->ng.ld, 16);        // roff[ld]
+    z.smem = z.o_acc + 4ull * kNwWarps * z.RC;                 // kNwWarps private accumulators
+    z.ok = z.smem <= kNwSmemBudget && p->ng.ld % 4 == 0;
+    return z;
+}
+
+__global__ void __launch_bounds__(kNwWarps * 32, 2) k_near_adj_warp(
+    NearGeo ng, int RX, int RY, int lz, int ntx, uint32_t o_roff, uint32_t o_acc, const float *__restrict__ dG,
+    const int *__restrict__ bin_start, const int *__restrict__ bin_st, const int *__restrict__ st_i0,
+    const int *__restrict__ st_j0, const float2 *__restrict__ stz, double *__restrict__ tpart) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    int *rowinfo = reinterpret_cast<int *>(smem_raw);                  // [2 kNwTile + 1]
+    int *roff = reinterpret_cast<int *>(smem_raw + o_roff);
+    float *acc_all = reinterpret_cast<float *>(smem_raw + o_acc);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
+    const int I0 = tx * kNwTile, J0 = ty * kNwTile;
+    const int RC = RX * RY * lz;
+    float *accw = acc_all + (size_t)warp * RC;
+    double *acc64 = tpart + (size_t)blockIdx.x * RC;
+    for (int u = tid; u < ng.ld; u += kNwWarps * 32) {
+        int v = -1;
+        if (u < ng.slots) {
+            const int a = u % ng.bx, b = (u / ng.bx) % ng.by, l = u / (ng.bx * ng.by);
+            if (l < lz) v = a + RX * (b + RY * l);
+        }
+        roff[u] = v;
+    }
+    for (int c = tid; c < kNwWarps * RC; c += kNwWarps * 32) acc_all[c] = 0.0f;
+    for (int c = tid; c < RC; c += kNwWarps * 32) acc64[c] = 0.0;
+    if (tid == 0) {
+        int q = 0;
+        const int i1 = min(I0 + kNwTile, ng.nbx);
+        for (int r = 0; r < kNwTile; ++r) {
+            const int sbj = J0 + r;
+            int p0 = 0, p1 = 0;
+            if (sbj < ng.nby) {
+                p0 = bin_start[I0 + ng.nbx * sbj];
+                p1 = bin_start[i1 + ng.nbx * sbj];
+            }
+            rowinfo[r] = p0;
+            rowinfo[kNwTile + r] = q;
+            q += p1 - p0;
+        }
+        rowinfo[2 * kNwTile] = q;
+    }
+    __syncthreads();
+    const int Q = rowinfo[2 * kNwTile];
+    const int n4 = ng.ld >> 2;
+    const float4 *dG4 = reinterpret_cast<const float4 *>(dG);
+    const int4 *roff4 = reinterpret_cast<const int4 *>(roff);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int pass0 = 0; pass0 < Q; pass0 += kNwWarps * kNwPass) {
+        const int pass1 = min(Q, pass0 + kNwWarps * kNwPass);
+        for (int q = pass0 + warp; q < pass1; q += kNwWarps) {
+            int r = 0;
+            while (r + 1 < kNwTile && rowinfo[kNwTile + r + 1] <= q) ++r;
+            const int sidx = bin_st[rowinfo[r] + (q - rowinfo[kNwTile + r])];
+            const int ri = st_i0[sidx] + ng.bx - 1 - I0;
+            const int rj = st_j0[sidx] + ng.by - 1 - J0;
+            const float rv = stz[sidx].y;
+            if (ri < 0 || ri >= kNwTile || rj < 0 || rj >= kNwTile || rv == 0.0f) continue;   // warp-uniform
+            float *acc = accw + (ri + RX * rj);
+            const float4 *row = dG4 + (int64_t)sidx * n4;
+            for (int v0 = 0; v0 < n4; v0 += 32 * kNwChunk) {
+                float4 gq[kNwChunk];
+#pragma unroll
+                for (int c = 0; c < kNwChunk; ++c) {
+                    const int v = v0 + lane + 32 * c;
+                    gq[c] = v < n4 ? __ldcs(row + v) : zero4;
+                }
+#pragma unroll
+                for (int c = 0; c < kNwChunk; ++c) {
+                    const int v = v0 + lane + 32 * c;
+                    if (v >= n4) continue;
+                    const int4 o = roff4[v];
+                    if (o.x >= 0) acc[o.x] = fmaf(gq[c].x, rv, acc[o.x]);
+                    if (o.y >= 0) acc[o.y] = fmaf(gq[c].y, rv, acc[o.y]);
+                    if (o.z >= 0) acc[o.z] = fmaf(gq[c].z, rv, acc[o.z]);
+                    if (o.w >= 0) acc[o.w] = fmaf(gq[c].w, rv, acc[o.w]);
+                }
+            }
+        }
+        __syncthreads();
+        for (int c = tid; c < RC; c += kNwWarps * 32) {
+            float t = 0.0f;
+#pragma unroll
+            for (int w = 0; w < kNwWarps; ++w) {
+                t += acc_all[(size_t)w * RC + c];
+                acc_all[(size_t)w * RC + c] = 0.0f;
+            }
+            acc64[c] += (double)t;
+        }
+        __syncthreads();
+    }
+}
+
 // out[x + nx (y + ny l)] = sum over the station tiles (tx, ty) whose region holds
 // the cell, ty then tx ascending (fixed order).
-__global__ void k_near_adj_gather(int nx, int ny, int lz, int bx, int by, int RX, int RY, int ntx,
+__global__ void k_near_adj_gather(int nx, int ny, int lz, int bx, int by, int RX, int RY, int ntx, int tile,
                                   const double *__restrict__ tpart, double *__restrict__ out) {
     const int64_t total = (int64_t)nx * ny * lz;
     const int64_t RC = (int64_t)RX * RY * lz;
@@ -1178,9 +1310,9 @@ __global__ void k_near_adj_gather(int nx, int ny, int lz, int bx, int by, int RX
         const int y = (int)((k / nx) % ny);
         const int l = (int)(k / ((int64_t)nx * ny));
         double s = 0.0;
-        for (int ty = y / kNaTile; ty <= (y + by - 1) / kNaTile; ++ty)
-            for (int tx = x / kNaTile; tx <= (x + bx - 1) / kNaTile; ++tx) {
-                const int ri = x - (tx * kNaTile - bx + 1), rj = y - (ty * kNaTile - by + 1);
+        for (int ty = y / tile; ty <= (y + by - 1) / tile; ++ty)
+            for (int tx = x / tile; tx <= (x + bx - 1) / tile; ++tx) {
+                const int ri = x - (tx * tile - bx + 1), rj = y - (ty * tile - by + 1);
                 s += tpart[(int64_t)(ty * ntx + tx) * RC + ri + (int64_t)RX * (rj + (int64_t)RY * l)];
             }
         out[k] = s;
@@ -1428,7 +1560,10 @@ size_t mixed_scratch_bytes(const grav_plan *p) {
     add(8ull * p->nx * p->ny * lz);                                         // near adjoint
     {
         const NearAdjShape na = near_adj_shape(p);
-        if (na.ok) add(8ull * na.ntx * na.nty * na.RC);                     // per-tile near sums
+        const NearWarpShape nw = near_warp_shape(p);
+        const size_t tb = std::max(na.ok ? 8ull * na.ntx * na.nty * na.RC : 0ull,
+                                   nw.ok ? 8ull * nw.ntx * nw.nty * nw.RC : 0ull);
+        if (tb) add(tb);                                                    // per-tile near sums
     }
     add(4ull * N); add(4ull * N); add(4ull * N); add(4ull * N);             // keys, keys_sorted, vals, bin_st
     add(4ull * (z.nbins + 2));                                              // bin_start
@@ -1511,10 +1646,18 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
     const int64_t lz = std::min(p->ng.bz, nz);
     p->m_cellacc = (double *)take(p, 8ull * nx * ny * lz);
     {
+        // form: warp-private if its shared memory fits, else station-streaming,
+        // else cell-tiled; GRAV_NEAR_ADJ=warp|rows|tiles restricts the choice
         const NearAdjShape na = near_adj_shape(p);
-        const char *ev = std::getenv("GRAV_NEAR_ADJ");   // "tiles": the cell-tiled form below
-        p->near_adj_rows = na.ok && !(ev && std::strcmp(ev, "tiles") == 0);
-        if (p->near_adj_rows) p->near_tpart = (double *)take(p, 8ull * na.ntx * na.nty * na.RC);
+        const NearWarpShape nw = near_warp_shape(p);
+        const char *ev = std::getenv("GRAV_NEAR_ADJ");
+        const bool want_tiles = ev && std::strcmp(ev, "tiles") == 0;
+        const bool want_rows = ev && std::strcmp(ev, "rows") == 0;
+        p->near_adj_rows = 0;
+        if (!want_tiles && !want_rows && nw.ok) p->near_adj_rows = 2;
+        else if (!want_tiles && na.ok) p->near_adj_rows = 1;
+        if (p->near_adj_rows == 2) p->near_tpart = (double *)take(p, 8ull * nw.ntx * nw.nty * nw.RC);
+        if (p->near_adj_rows == 1) p->near_tpart = (double *)take(p, 8ull * na.ntx * na.nty * na.RC);
     }
     unsigned *keys = (unsigned *)take(p, 4ull * p->N);
     unsigned *keys_sorted = (unsigned *)take(p, 4ull * p->N);
@@ -1726,7 +1869,17 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
     stage_end(p, kStageAdjMain, s);
     const int lz = std::min(p->ng.bz, p->nz);
     stage_begin(p, kStageAdjNear, s);
-    if (p->near_adj_rows) {
+    if (p->near_adj_rows == 2) {
+        const NearWarpShape nw = near_warp_shape(p);
+        cudaFuncSetAttribute(k_near_adj_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nw.smem);
+        k_near_adj_warp<<<(unsigned)(nw.ntx * nw.nty), kNwWarps * 32, nw.smem, s>>>(
+            p->ng, nw.RX, nw.RY, nw.lz, nw.ntx, (uint32_t)nw.o_roff, (uint32_t)nw.o_acc, p->dG, p->bin_start,
+            p->bin_st, p->st_i0, p->st_j0, p->stz, p->near_tpart);
+        const int64_t cells = (int64_t)p->nx * p->ny * lz;
+        k_near_adj_gather<<<grid_for(cells, 256), 256, 0, s>>>(p->nx, p->ny, lz, p->ng.bx, p->ng.by, nw.RX, nw.RY,
+                                                               nw.ntx, kNwTile, p->near_tpart, p->m_cellacc);
+        note_launches(1);
+    } else if (p->near_adj_rows == 1) {
         const NearAdjShape na = near_adj_shape(p);
         auto go = [&](auto kern) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)na.smem);
@@ -1744,7 +1897,7 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
         }
         const int64_t cells = (int64_t)p->nx * p->ny * lz;
         k_near_adj_gather<<<grid_for(cells, 256), 256, 0, s>>>(p->nx, p->ny, lz, p->ng.bx, p->ng.by, na.RX, na.RY,
-                                                               na.ntx, p->near_tpart, p->m_cellacc);
+                                                               na.ntx, kNaTile, p->near_tpart, p->m_cellacc);
         note_launches(1);
     } else {
         dim3 gna((unsigned)((p->nx + 31) / 32), (unsigned)((p->ny + 7) / 8), (unsigned)lz);

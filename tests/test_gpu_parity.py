@@ -225,14 +225,16 @@ def test_mixed_forward_adjoint_vs_oracle(g, shape, cell, h, seed, adjoint_layout
 
 @pytest.mark.parametrize("near_cells", [8.0, 3.0, 5.0])
 def test_near_adjoint_forms_agree_and_match_oracle(g, near_cells, monkeypatch):
-    """The near-field adjoint in both forms: station-streaming (whole table rows
-    by TMA bulk copy, FP32 region sums folded into FP64; the default) and
+    """The near-field adjoint in its three forms: warp-private (each warp
+    streams its stations' table rows into its own FP32 region accumulator;
+    the default), station-streaming (whole rows by TMA bulk copy into one
+    shared accumulator, a barrier per station; GRAV_NEAR_ADJ=rows) and
     cell-tiled (GRAV_NEAR_ADJ=tiles).  Windows 3 and 5 give 147- and
     605-slot boxes, not multiples of 4, so the table rows carry padding that
     the forward's 16-byte fast path and the streaming adjoint read.  Each form
     is within 1e-6 of the definition of the approximation (exact prism inside
     the window, point mass outside), 1e-5 of the exact oracle at the default
-    window, bitwise repeatable, and the two agree to FP32 rounding."""
+    window, bitwise repeatable, and the forms agree to FP32 rounding."""
     mesh = synth.uniform_mesh(45, 38, 14, 30.0, 30.0, 30.0)
     rng = np.random.Generator(np.random.PCG64(211))
     n = 1500
@@ -243,7 +245,7 @@ def test_near_adjoint_forms_agree_and_match_oracle(g, near_cells, monkeypatch):
     m = rng.normal(0.0, 100.0, mesh.ncells)
     Gk = _mixed_definition(mesh, sv, G, 30.0, near_cells)
     out = {}
-    for form in ("rows", "tiles"):
+    for form in ("warp", "rows", "tiles"):
         monkeypatch.setenv("GRAV_NEAR_ADJ", form)
         plan = g.Plan(mesh, S, precision="mixed", near_cells=near_cells)
         a = plan.adjoint(_dev(r))
@@ -256,7 +258,8 @@ def test_near_adjoint_forms_agree_and_match_oracle(g, near_cells, monkeypatch):
             assert _rel(a, G.T @ r) <= TOLMIX, form
         out[form] = a
         plan.close()
-    assert np.abs(out["rows"] - out["tiles"]).max() <= 1e-7 * np.abs(out["tiles"]).max()
+    for form in ("warp", "rows"):
+        assert np.abs(out[form] - out["tiles"]).max() <= 1e-7 * np.abs(out["tiles"]).max(), form
 
 
 @pytest.mark.parametrize("shape,cells", [((1, 1, 1), (20.0, 20.0, 20.0)), ((7, 1, 1), (20.0, 20.0, 20.0)),
