@@ -1189,7 +1189,7 @@ constexpr size_t kNwSmemBudget = 112 * 1024;   // two CTAs per SM
 struct NearWarpShape {
     bool ok = false;
     int RX = 0, RY = 0, lz = 0, RC = 0, ntx = 0, nty = 0;
-    size_t o_roff = 0, o_acc = 0, smem = 0;
+    size_t o_meta = 0, o_roff = 0, o_acc = 0, smem = 0;
 };
 
 static NearWarpShape near_warp_shape(const grav_plan *p) {
@@ -1200,7 +1200,8 @@ static NearWarpShape near_warp_shape(const grav_plan *p) {
     z.RC = z.RX * z.RY * z.lz;
     z.ntx = (p->ng.nbx + kNwTile - 1) / kNwTile;
     z.nty = (p->ng.nby + kNwTile - 1) / kNwTile;
-    z.o_roff = 128;                                             // header: row table [2 kNwTile + 1]
+    z.o_meta = 128;                                             // header: row table [2 kNwTile + 1]
+    z.o_roff = z.o_meta + 3ull * 4 * kNwWarps * kNwPass;        // a pass's stations: row, base, r
     z.o_acc = align_up(z.o_roff + 4ull * p->ng.ld, 16);        // roff[ld]
     z.smem = z.o_acc + 4ull * kNwWarps * z.RC;                 // kNwWarps private accumulators
     z.ok = z.smem <= kNwSmemBudget && p->ng.ld % 4 == 0;
@@ -1208,11 +1209,15 @@ static NearWarpShape near_warp_shape(const grav_plan *p) {
 }
 
 __global__ void __launch_bounds__(kNwWarps * 32, 2) k_near_adj_warp(
-    NearGeo ng, int RX, int RY, int lz, int ntx, uint32_t o_roff, uint32_t o_acc, const float *__restrict__ dG,
+    NearGeo ng, int RX, int RY, int lz, int ntx, uint32_t o_meta, uint32_t o_roff, uint32_t o_acc,
+    const float *__restrict__ dG,
     const int *__restrict__ bin_start, const int *__restrict__ bin_st, const int *__restrict__ st_i0,
     const int *__restrict__ st_j0, const float2 *__restrict__ stz, double *__restrict__ tpart) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     int *rowinfo = reinterpret_cast<int *>(smem_raw);                  // [2 kNwTile + 1]
+    int *msidx = reinterpret_cast<int *>(smem_raw + o_meta);           // [kNwWarps kNwPass]
+    int *mbase = msidx + kNwWarps * kNwPass;
+    float *mrv = reinterpret_cast<float *>(mbase + kNwWarps * kNwPass);
     int *roff = reinterpret_cast<int *>(smem_raw + o_roff);
     float *acc_all = reinterpret_cast<float *>(smem_raw + o_acc);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1255,15 +1260,27 @@ __global__ void __launch_bounds__(kNwWarps * 32, 2) k_near_adj_warp(
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int pass0 = 0; pass0 < Q; pass0 += kNwWarps * kNwPass) {
         const int pass1 = min(Q, pass0 + kNwWarps * kNwPass);
-        for (int q = pass0 + warp; q < pass1; q += kNwWarps) {
+        // the pass's station metadata, one station per thread (the dependent
+        // loads run in parallel instead of once per station and warp)
+        if (tid < kNwWarps * kNwPass && pass0 + tid < pass1) {
+            const int q = pass0 + tid;
             int r = 0;
             while (r + 1 < kNwTile && rowinfo[kNwTile + r + 1] <= q) ++r;
             const int sidx = bin_st[rowinfo[r] + (q - rowinfo[kNwTile + r])];
             const int ri = st_i0[sidx] + ng.bx - 1 - I0;
             const int rj = st_j0[sidx] + ng.by - 1 - J0;
             const float rv = stz[sidx].y;
-            if (ri < 0 || ri >= kNwTile || rj < 0 || rj >= kNwTile || rv == 0.0f) continue;   // warp-uniform
-            float *acc = accw + (ri + RX * rj);
+            msidx[tid] = sidx;
+            mbase[tid] = (ri >= 0 && ri < kNwTile && rj >= 0 && rj < kNwTile && rv != 0.0f) ? ri + RX * rj : -1;
+            mrv[tid] = rv;
+        }
+        __syncthreads();
+        for (int q = pass0 + warp; q < pass1; q += kNwWarps) {
+            const int base = mbase[q - pass0];
+            if (base < 0) continue;   // warp-uniform
+            const int sidx = msidx[q - pass0];
+            const float rv = mrv[q - pass0];
+            float *acc = accw + base;
             const float4 *row = dG4 + (int64_t)sidx * n4;
             for (int v0 = 0; v0 < n4; v0 += 32 * kNwChunk) {
                 float4 gq[kNwChunk];
@@ -1873,7 +1890,8 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
         const NearWarpShape nw = near_warp_shape(p);
         cudaFuncSetAttribute(k_near_adj_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nw.smem);
         k_near_adj_warp<<<(unsigned)(nw.ntx * nw.nty), kNwWarps * 32, nw.smem, s>>>(
-            p->ng, nw.RX, nw.RY, nw.lz, nw.ntx, (uint32_t)nw.o_roff, (uint32_t)nw.o_acc, p->dG, p->bin_start,
+            p->ng, nw.RX, nw.RY, nw.lz, nw.ntx, (uint32_t)nw.o_meta, (uint32_t)nw.o_roff, (uint32_t)nw.o_acc, p->dG,
+            p->bin_start,
             p->bin_st, p->st_i0, p->st_j0, p->stz, p->near_tpart);
         const int64_t cells = (int64_t)p->nx * p->ny * lz;
         k_near_adj_gather<<<grid_for(cells, 256), 256, 0, s>>>(p->nx, p->ny, lz, p->ng.bx, p->ng.by, nw.RX, nw.RY,
