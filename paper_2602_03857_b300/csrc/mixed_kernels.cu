@@ -1275,45 +1275,31 @@ __global__ void __launch_bounds__(kNwWarps * 32, 2) k_near_adj_warp(
             mrv[tid] = rv;
         }
         __syncthreads();
-        // this warp's stations of the pass, (station, chunk) pairs in order,
-        // each chunk's loads issued one step ahead of its processing
-        const int mine = pass1 > pass0 + warp ? (pass1 - (pass0 + warp) + kNwWarps - 1) / kNwWarps : 0;
-        const int nch = (n4 + 32 * kNwChunk - 1) / (32 * kNwChunk);
-        const int F = mine * nch;
-        auto load = [&](int f, float4 (&g)[kNwChunk]) {
-            const int i = f / nch, c = f - i * nch;
-            const int qi = warp + kNwWarps * i;
-            const bool on = mbase[qi] >= 0;
-            const float4 *row = dG4 + (int64_t)msidx[qi] * n4;
+        for (int q = pass0 + warp; q < pass1; q += kNwWarps) {
+            const int base = mbase[q - pass0];
+            if (base < 0) continue;   // warp-uniform
+            const int sidx = msidx[q - pass0];
+            const float rv = mrv[q - pass0];
+            float *acc = accw + base;
+            const float4 *row = dG4 + (int64_t)sidx * n4;
+            for (int v0 = 0; v0 < n4; v0 += 32 * kNwChunk) {
+                float4 gq[kNwChunk];
 #pragma unroll
-            for (int u = 0; u < kNwChunk; ++u) {
-                const int v = c * 32 * kNwChunk + lane + 32 * u;
-                g[u] = (on && v < n4) ? __ldcs(row + v) : zero4;
-            }
-        };
-        float4 cur[kNwChunk], nxt[kNwChunk];
-        if (F > 0) load(0, cur);
-        for (int f = 0; f < F; ++f) {
-            if (f + 1 < F) load(f + 1, nxt);
-            const int i = f / nch, c = f - i * nch;
-            const int qi = warp + kNwWarps * i;
-            const int base = mbase[qi];   // warp-uniform
-            if (base >= 0) {
-                const float rv = mrv[qi];
-                float *acc = accw + base;
+                for (int c = 0; c < kNwChunk; ++c) {
+                    const int v = v0 + lane + 32 * c;
+                    gq[c] = v < n4 ? __ldcs(row + v) : zero4;
+                }
 #pragma unroll
-                for (int u = 0; u < kNwChunk; ++u) {
-                    const int v = c * 32 * kNwChunk + lane + 32 * u;
+                for (int c = 0; c < kNwChunk; ++c) {
+                    const int v = v0 + lane + 32 * c;
                     if (v >= n4) continue;
                     const int4 o = roff4[v];
-                    if (o.x >= 0) acc[o.x] = fmaf(cur[u].x, rv, acc[o.x]);
-                    if (o.y >= 0) acc[o.y] = fmaf(cur[u].y, rv, acc[o.y]);
-                    if (o.z >= 0) acc[o.z] = fmaf(cur[u].z, rv, acc[o.z]);
-                    if (o.w >= 0) acc[o.w] = fmaf(cur[u].w, rv, acc[o.w]);
+                    if (o.x >= 0) acc[o.x] = fmaf(gq[c].x, rv, acc[o.x]);
+                    if (o.y >= 0) acc[o.y] = fmaf(gq[c].y, rv, acc[o.y]);
+                    if (o.z >= 0) acc[o.z] = fmaf(gq[c].z, rv, acc[o.z]);
+                    if (o.w >= 0) acc[o.w] = fmaf(gq[c].w, rv, acc[o.w]);
                 }
             }
-#pragma unroll
-            for (int u = 0; u < kNwChunk; ++u) cur[u] = nxt[u];
         }
         __syncthreads();
         for (int c = tid; c < RC; c += kNwWarps * 32) {
