@@ -1289,15 +1289,28 @@ __global__ void __launch_bounds__(kNwWarps * 32, 2) k_near_adj_warp(
                     const int v = v0 + lane + 32 * c;
                     gq[c] = v < n4 ? __ldcs(row + v) : zero4;
                 }
+                int4 oq[kNwChunk];
 #pragma unroll
                 for (int c = 0; c < kNwChunk; ++c) {
                     const int v = v0 + lane + 32 * c;
-                    if (v >= n4) continue;
-                    const int4 o = roff4[v];
-                    if (o.x >= 0) acc[o.x] = fmaf(gq[c].x, rv, acc[o.x]);
-                    if (o.y >= 0) acc[o.y] = fmaf(gq[c].y, rv, acc[o.y]);
-                    if (o.z >= 0) acc[o.z] = fmaf(gq[c].z, rv, acc[o.z]);
-                    if (o.w >= 0) acc[o.w] = fmaf(gq[c].w, rv, acc[o.w]);
+                    oq[c] = v < n4 ? roff4[v] : make_int4(-1, -1, -1, -1);
+                }
+                // a station's slots are distinct cells: all accumulator loads,
+                // then all stores (independent, so their latencies overlap)
+                float av[4 * kNwChunk];
+#pragma unroll
+                for (int c = 0; c < kNwChunk; ++c) {
+                    av[4 * c + 0] = oq[c].x >= 0 ? acc[oq[c].x] : 0.0f;
+                    av[4 * c + 1] = oq[c].y >= 0 ? acc[oq[c].y] : 0.0f;
+                    av[4 * c + 2] = oq[c].z >= 0 ? acc[oq[c].z] : 0.0f;
+                    av[4 * c + 3] = oq[c].w >= 0 ? acc[oq[c].w] : 0.0f;
+                }
+#pragma unroll
+                for (int c = 0; c < kNwChunk; ++c) {
+                    if (oq[c].x >= 0) acc[oq[c].x] = fmaf(gq[c].x, rv, av[4 * c + 0]);
+                    if (oq[c].y >= 0) acc[oq[c].y] = fmaf(gq[c].y, rv, av[4 * c + 1]);
+                    if (oq[c].z >= 0) acc[oq[c].z] = fmaf(gq[c].z, rv, av[4 * c + 2]);
+                    if (oq[c].w >= 0) acc[oq[c].w] = fmaf(gq[c].w, rv, av[4 * c + 3]);
                 }
             }
         }
