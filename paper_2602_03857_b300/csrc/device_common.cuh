@@ -105,6 +105,12 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t
         : "memory");
 }
 
+// Bulk prefetch of [src, src + bytes) into L2 (no shared memory, no
+// completion): src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void set_status(int *status, int bit) {
     if (status) atomicOr(status, bit);
 }

@@ -825,10 +825,10 @@ __global__ void k_bin_bounds(const unsigned *__restrict__ ks, int64_t n, int nbi
 // per term.
 //
 // Stations whose box lies inside the mesh (all but those near its edges) take
-// a fast path: the table row (padded to a multiple of 4 floats) streams in
-// 16-byte loads (read once, evict-first), the cell of each slot comes from the
-// plan's slot-offset table off[t] = a + nx (bj + ny l) (L1-resident), and no
-// slot needs a bounds check.
+// a fast path: the table row (padded to a multiple of 4 floats) is prefetched
+// into L2 whole and streams in 16-byte loads (read once, evict-first), the
+// cell of each slot comes from the plan's slot-offset table
+// off[t] = a + nx (bj + ny l) (L1-resident), and no slot needs a bounds check.
 __global__ void __launch_bounds__(256) k_near_fwd(int nx, int ny, int nz, NearGeo ng, int64_t N,
                                                   const float *__restrict__ dG, const int *__restrict__ st_i0,
                                                   const int *__restrict__ st_j0, const int *__restrict__ off,
@@ -844,6 +844,8 @@ __global__ void __launch_bounds__(256) k_near_fwd(int nx, int ny, int nz, NearGe
         const int4 *o4 = reinterpret_cast<const int4 *>(off);
         const float *qb = qn + i0 + (int64_t)nx * j0;
         const int n4 = ng.ld >> 2;
+        // the whole row requested at once: the loop's loads then hit L2
+        if (lane == 0) prefetch_l2_bulk(gs, 4u * (uint32_t)ng.ld);
         double acc = 0.0;
         for (int v = lane; v < n4; v += 64) {   // 8 slots per lane and step, loads issued together
             const bool two = v + 32 < n4;
@@ -1170,15 +1172,17 @@ __global__ void __launch_bounds__(kNaThreads) k_near_adj_rows(
 // fits).  CTA = tile of kNwTile x kNwTile station bins, region of RX x RY x lz
 // cells (RX = kNwTile + bx - 1); each of the 8 warps owns a private FP32
 // accumulator over the whole region and takes stations w, w + 8, ... of the
-// tile in order.  A warp streams its station's table row (ld floats,
-// contiguous) with 16-byte evict-first loads, kNwChunk per lane in flight,
+// tile in order.  A warp requests its station's table row (ld floats,
+// contiguous) and its next station's row from L2 by bulk prefetch, streams
+// the row with 16-byte evict-first loads, kNwChunk per lane in flight,
 // and adds dG * r into its own accumulator (one station's slots are distinct
 // cells, so no lane races another; no other warp touches this accumulator, so
 // no barrier separates stations).  Every kNwPass stations per warp the eight
 // accumulators are summed cell by cell in warp order (FP32) and added into
 // the tile's FP64 region sums in global memory (tpart[tile], the same
-// per-tile layout k_near_adj_gather reads), then cleared: bitwise
-// deterministic, at most 8 kNwPass FP32 terms per cell between FP64 folds.
+// per-tile layout k_near_adj_gather reads; the first pass writes them), then
+// cleared: bitwise deterministic, at most 8 kNwPass FP32 terms per cell
+// between FP64 folds.
 // The table is read once, in whole rows, with no per-station barrier.
 constexpr int kNwTile = 4;
 constexpr int kNwWarps = 8;
@@ -1235,7 +1239,6 @@ __global__ void __launch_bounds__(kNwWarps * 32, 2) k_near_adj_warp(
         roff[u] = v;
     }
     for (int c = tid; c < kNwWarps * RC; c += kNwWarps * 32) acc_all[c] = 0.0f;
-    for (int c = tid; c < RC; c += kNwWarps * 32) acc64[c] = 0.0;
     if (tid == 0) {
         int q = 0;
         const int i1 = min(I0 + kNwTile, ng.nbx);
@@ -1254,6 +1257,8 @@ __global__ void __launch_bounds__(kNwWarps * 32, 2) k_near_adj_warp(
     }
     __syncthreads();
     const int Q = rowinfo[2 * kNwTile];
+    if (Q == 0)   // otherwise the first pass writes the region sums
+        for (int c = tid; c < RC; c += kNwWarps * 32) acc64[c] = 0.0;
     const int n4 = ng.ld >> 2;
     const float4 *dG4 = reinterpret_cast<const float4 *>(dG);
     const int4 *roff4 = reinterpret_cast<const int4 *>(roff);
@@ -1275,6 +1280,7 @@ __global__ void __launch_bounds__(kNwWarps * 32, 2) k_near_adj_warp(
             mrv[tid] = rv;
         }
         __syncthreads();
+        int pf_q = -1;
         for (int q = pass0 + warp; q < pass1; q += kNwWarps) {
             const int base = mbase[q - pass0];
             if (base < 0) continue;   // warp-uniform
@@ -1282,6 +1288,15 @@ __global__ void __launch_bounds__(kNwWarps * 32, 2) k_near_adj_warp(
             const float rv = mrv[q - pass0];
             float *acc = accw + base;
             const float4 *row = dG4 + (int64_t)sidx * n4;
+            // this row (unless requested one station earlier) and the row of
+            // the warp's next station, each requested whole
+            const int qnext = q + kNwWarps;
+            const bool pf_next = qnext < pass1 && mbase[qnext - pass0] >= 0;
+            if (lane == 0) {
+                if (pf_q != q) prefetch_l2_bulk(row, 16u * (uint32_t)n4);
+                if (pf_next) prefetch_l2_bulk(dG4 + (int64_t)msidx[qnext - pass0] * n4, 16u * (uint32_t)n4);
+            }
+            pf_q = pf_next ? qnext : -1;
             for (int v0 = 0; v0 < n4; v0 += 32 * kNwChunk) {
                 float4 gq[kNwChunk];
 #pragma unroll
@@ -1322,7 +1337,7 @@ __global__ void __launch_bounds__(kNwWarps * 32, 2) k_near_adj_warp(
                 t += acc_all[(size_t)w * RC + c];
                 acc_all[(size_t)w * RC + c] = 0.0f;
             }
-            acc64[c] += (double)t;
+            acc64[c] = pass0 == 0 ? (double)t : acc64[c] + (double)t;
         }
         __syncthreads();
     }
