@@ -1343,6 +1343,157 @@ __global__ void __launch_bounds__(kNwWarps * 32, 2) k_near_adj_warp(
     }
 }
 
+// Near-field forward, tile form (the default when its shared memory fits):
+// corr[s] = sum over slots of dG[s][t] q[cell(s, t)], the stations taken per
+// tile of kNwTile x kNwTile station bins as in k_near_adj_warp.  The tile's
+// q values over its region (RX x RY x lz cells, zero outside the mesh, whose
+// table entries are zero anyway) and the slot -> region offset table are
+// staged in shared memory once, so a station's gathers are shared-memory
+// loads instead of scattered L2 sectors.  Each warp takes stations w, w + 8,
+// ... of the tile, requests its rows (this one and the next) from L2 by bulk
+// prefetch and streams each row in 16-byte evict-first loads, kNfChunk per
+// lane in flight.  FP32 runs of 16 terms are summed in double-float per lane
+// and across the warp (fixed butterfly): bitwise deterministic, no FP64
+// operation per term or per run.  Stations whose box misses the mesh (sorted
+// after every bin) get 0 from the first CTA.
+constexpr int kNfChunk = 4;
+constexpr size_t kNfSmemBudget = 64 * 1024;
+
+struct NearFwdShape {
+    bool ok = false;
+    int RX = 0, RY = 0, lz = 0, RC = 0, ntx = 0, nty = 0;
+    size_t o_meta = 0, o_roff = 0, o_q = 0, smem = 0;
+};
+
+static NearFwdShape near_fwd_shape(const grav_plan *p) {
+    NearFwdShape z;
+    z.RX = kNwTile + p->ng.bx - 1;
+    z.RY = kNwTile + p->ng.by - 1;
+    z.lz = std::min(p->ng.bz, p->nz);
+    z.RC = z.RX * z.RY * z.lz;
+    z.ntx = (p->ng.nbx + kNwTile - 1) / kNwTile;
+    z.nty = (p->ng.nby + kNwTile - 1) / kNwTile;
+    z.o_meta = 128;                                             // header: row table [2 kNwTile + 1]
+    z.o_roff = z.o_meta + 2ull * 4 * kNwWarps * kNwPass;        // a pass's stations: index, base
+    z.o_q = align_up(z.o_roff + 4ull * p->ng.ld, 16);          // roff[ld]
+    z.smem = z.o_q + 4ull * z.RC;                              // q over the region
+    z.ok = z.smem <= kNfSmemBudget && p->ng.ld % 4 == 0;
+    return z;
+}
+
+__global__ void __launch_bounds__(kNwWarps * 32) k_near_fwd_tile(
+    int nx, int ny, NearGeo ng, int RX, int RY, int lz, int ntx, uint32_t o_meta, uint32_t o_roff, uint32_t o_q,
+    const float *__restrict__ dG, const int *__restrict__ bin_start, const int *__restrict__ bin_st,
+    const int *__restrict__ st_i0, const int *__restrict__ st_j0, const float *__restrict__ qn, int64_t N,
+    double *__restrict__ corr) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    int *rowinfo = reinterpret_cast<int *>(smem_raw);                  // [2 kNwTile + 1]
+    int *msidx = reinterpret_cast<int *>(smem_raw + o_meta);           // [kNwWarps kNwPass]
+    int *mbase = msidx + kNwWarps * kNwPass;
+    int *roff = reinterpret_cast<int *>(smem_raw + o_roff);
+    float *qreg = reinterpret_cast<float *>(smem_raw + o_q);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
+    const int I0 = tx * kNwTile, J0 = ty * kNwTile;
+    const int RC = RX * RY * lz;
+    // slot -> region offset; slots of layers below lz and row padding hold
+    // dG = 0 and point at region cell 0
+    for (int u = tid; u < ng.ld; u += kNwWarps * 32) {
+        int v = 0;
+        if (u < ng.slots) {
+            const int a = u % ng.bx, b = (u / ng.bx) % ng.by, l = u / (ng.bx * ng.by);
+            if (l < lz) v = a + RX * (b + RY * l);
+        }
+        roff[u] = v;
+    }
+    // region cell (x, y, l) is mesh cell (I0 - bx + 1 + x, J0 - by + 1 + y, l)
+    const int X0 = I0 - ng.bx + 1, Y0 = J0 - ng.by + 1;
+    for (int c = tid; c < RC; c += kNwWarps * 32) {
+        const int x = c % RX, y = (c / RX) % RY, l = c / (RX * RY);
+        const int i = X0 + x, j = Y0 + y;
+        qreg[c] = (i >= 0 && i < nx && j >= 0 && j < ny) ? qn[i + (int64_t)nx * (j + (int64_t)ny * l)] : 0.0f;
+    }
+    if (tid == 0) {
+        int q = 0;
+        const int i1 = min(I0 + kNwTile, ng.nbx);
+        for (int r = 0; r < kNwTile; ++r) {
+            const int sbj = J0 + r;
+            int p0 = 0, p1 = 0;
+            if (sbj < ng.nby) {
+                p0 = bin_start[I0 + ng.nbx * sbj];
+                p1 = bin_start[i1 + ng.nbx * sbj];
+            }
+            rowinfo[r] = p0;
+            rowinfo[kNwTile + r] = q;
+            q += p1 - p0;
+        }
+        rowinfo[2 * kNwTile] = q;
+    }
+    if (blockIdx.x == 0)   // stations whose box misses the mesh
+        for (int64_t p = bin_start[ng.nbx * ng.nby] + (int64_t)tid; p < N; p += kNwWarps * 32) corr[bin_st[p]] = 0.0;
+    __syncthreads();
+    const int Q = rowinfo[2 * kNwTile];
+    const int n4 = ng.ld >> 2;
+    const float4 *dG4 = reinterpret_cast<const float4 *>(dG);
+    const int4 *roff4 = reinterpret_cast<const int4 *>(roff);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int pass0 = 0; pass0 < Q; pass0 += kNwWarps * kNwPass) {
+        const int pass1 = min(Q, pass0 + kNwWarps * kNwPass);
+        if (pass0 > 0) __syncthreads();   // the previous pass's metadata is consumed
+        if (tid < kNwWarps * kNwPass && pass0 + tid < pass1) {
+            const int q = pass0 + tid;
+            int r = 0;
+            while (r + 1 < kNwTile && rowinfo[kNwTile + r + 1] <= q) ++r;
+            const int sidx = bin_st[rowinfo[r] + (q - rowinfo[kNwTile + r])];
+            const int ri = st_i0[sidx] + ng.bx - 1 - I0;
+            const int rj = st_j0[sidx] + ng.by - 1 - J0;
+            msidx[tid] = sidx;
+            mbase[tid] = ri + RX * rj;
+        }
+        __syncthreads();
+        for (int q = pass0 + warp; q < pass1; q += kNwWarps) {
+            const int sidx = msidx[q - pass0];
+            const float *qb = qreg + mbase[q - pass0];
+            const float4 *row = dG4 + (int64_t)sidx * n4;
+            if (lane == 0) {
+                if (q == pass0 + warp) prefetch_l2_bulk(row, 16u * (uint32_t)n4);
+                if (q + kNwWarps < pass1)
+                    prefetch_l2_bulk(dG4 + (int64_t)msidx[q + kNwWarps - pass0] * n4, 16u * (uint32_t)n4);
+            }
+            float hi = 0.0f, lo = 0.0f;
+            for (int v0 = 0; v0 < n4; v0 += 32 * kNfChunk) {
+                float4 gq[kNfChunk];
+#pragma unroll
+                for (int c = 0; c < kNfChunk; ++c) {
+                    const int v = v0 + lane + 32 * c;
+                    gq[c] = v < n4 ? __ldcs(row + v) : zero4;
+                }
+                float run = 0.0f;
+#pragma unroll
+                for (int c = 0; c < kNfChunk; ++c) {
+                    const int v = v0 + lane + 32 * c;
+                    const int4 o = v < n4 ? roff4[v] : make_int4(0, 0, 0, 0);
+                    run = fmaf(gq[c].x, qb[o.x], run);
+                    run = fmaf(gq[c].y, qb[o.y], run);
+                    run = fmaf(gq[c].z, qb[o.z], run);
+                    run = fmaf(gq[c].w, qb[o.w], run);
+                }
+                float e;
+                two_sum(hi, run, hi, e);
+                lo += e;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ho = __shfl_xor_sync(0xffffffffu, hi, o), lo2 = __shfl_xor_sync(0xffffffffu, lo, o);
+                float e;
+                two_sum(hi, ho, hi, e);
+                lo += lo2 + e;
+            }
+            if (lane == 0) corr[sidx] = (double)hi + (double)lo;
+        }
+    }
+}
+
 // out[x + nx (y + ny l)] = sum over the station tiles (tx, ty) whose region holds
 // the cell, ty then tx ascending (fixed order).
 __global__ void k_near_adj_gather(int nx, int ny, int lz, int bx, int by, int RX, int RY, int ntx, int tile,
@@ -1701,6 +1852,9 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
         p->near_adj_rows = 0;
         if (!want_tiles && !want_rows && nw.ok) p->near_adj_rows = 2;
         else if (!want_tiles && na.ok) p->near_adj_rows = 1;
+        // near forward: tile form when it fits; GRAV_NEAR_FWD=warp forces a warp per station
+        const char *fv = std::getenv("GRAV_NEAR_FWD");
+        p->near_fwd_tile = near_fwd_shape(p).ok && !(fv && std::strcmp(fv, "warp") == 0);
         if (p->near_adj_rows == 2) p->near_tpart = (double *)take(p, 8ull * nw.ntx * nw.nty * nw.RC);
         if (p->near_adj_rows == 1) p->near_tpart = (double *)take(p, 8ull * na.ntx * na.nty * na.RC);
     }
@@ -1840,6 +1994,16 @@ void launch_mixed_near_fwd(const grav_plan *p, const double *m, cudaStream_t s) 
     const int64_t threads = p->N * 32;
     stage_begin(p, kStageFwdNear, s);
     (void)m;   // the near field reads the FP32 q that launch_mixed_prep_q formed from m
+    if (p->near_fwd_tile) {
+        const NearFwdShape nf = near_fwd_shape(p);
+        cudaFuncSetAttribute(k_near_fwd_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nf.smem);
+        k_near_fwd_tile<<<(unsigned)(nf.ntx * nf.nty), kNwWarps * 32, nf.smem, s>>>(
+            p->nx, p->ny, p->ng, nf.RX, nf.RY, nf.lz, nf.ntx, (uint32_t)nf.o_meta, (uint32_t)nf.o_roff,
+            (uint32_t)nf.o_q, p->dG, p->bin_start, p->bin_st, p->st_i0, p->st_j0, p->qN, p->N, p->near_corr);
+        stage_end(p, kStageFwdNear, s);
+        note_launches(1);
+        return;
+    }
     k_near_fwd<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(p->nx, p->ny, p->nz, p->ng, p->N, p->dG,
                                                                 p->st_i0, p->st_j0, p->near_off, p->qN,
                                                                 p->near_corr);
