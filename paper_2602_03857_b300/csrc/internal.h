@@ -149,7 +149,7 @@ struct grav_plan {
     double *near_corr = nullptr;          // [N] forward near-field correction scratch
     double *m_cellacc = nullptr;          // [M] adjoint scratch
     double *near_tpart = nullptr;         // per station tile: FP64 near adjoint sums over its cell region
-    int near_adj_rows = 0;                // near adjoint: 2 warp-private, 1 station-streaming, 0 cell-tiled
+    int near_adj_rows = 0;                // near adjoint: 3 layer-split, 2 warp-private, 1 station-streaming, 0 cell-tiled
     int near_fwd_tile = 0;                // near forward: 1 per station-bin tile (q staged), 0 warp per station
     float *cr_w32 = nullptr;              // GRAV_MIXED_CORNER: node weights, FP32 rows of cr_ldw
     double *cr_part = nullptr;            // [cr_nchunk][N] row-chunk partials of the corner forward

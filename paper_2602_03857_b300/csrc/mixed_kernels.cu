@@ -1328,6 +1328,7 @@ __global__ void __launch_bounds__(kNwWarps * 32, 2) k_near_adj_warp(
                     if (oq[c].w >= 0) acc[oq[c].w] = fmaf(gq[c].w, rv, av[4 * c + 3]);
                 }
             }
+            __syncwarp();   // the next station's lanes read cells these lanes wrote
         }
         __syncthreads();
         for (int c = tid; c < RC; c += kNwWarps * 32) {
@@ -1340,6 +1341,149 @@ __global__ void __launch_bounds__(kNwWarps * 32, 2) k_near_adj_warp(
             acc64[c] = pass0 == 0 ? (double)t : acc64[c] + (double)t;
         }
         __syncthreads();
+    }
+}
+
+// Near-field adjoint, layer-split form (the default when its shared memory
+// fits).  CTA = tile of kNwTile x kNwTile station bins with one FP32
+// accumulator over its region (RX x RY x lz cells), as in k_near_adj_warp,
+// but warp w owns the region's layers w, w + W, ... (W = min(lz, 8) warps):
+// a station's slots in layer l only touch region layer l, so the warps never
+// share a cell and need no private copies (8x less shared memory, several
+// CTAs per SM).  Every warp walks all of the tile's stations in order and,
+// for each, streams the contiguous bx*by-float segment of its layer in the
+// station's table row (lane-consecutive slots, evict-first, the next
+// station's segment prefetched into L2) into its planes.  Every kNlPass
+// stations each warp adds its FP32 planes into the tile's FP64 region sums
+// in global memory (the first pass writes them; same layout as
+// k_near_adj_warp, read by k_near_adj_gather) and clears them: each cell sees
+// its stations in tile order, at most kNlPass FP32 terms between FP64 folds,
+// bitwise deterministic.
+constexpr int kNlPass = 128;
+constexpr int kNlUnroll = 10;   // slots per lane in flight (bx*by = 289 at the default window)
+constexpr size_t kNlSmemBudget = 64 * 1024;
+
+struct NearLayerShape {
+    bool ok = false;
+    int RX = 0, RY = 0, lz = 0, RC = 0, ntx = 0, nty = 0, nwarps = 0;
+    size_t o_meta = 0, o_roff = 0, o_acc = 0, smem = 0;
+};
+
+static NearLayerShape near_layer_shape(const grav_plan *p) {
+    NearLayerShape z;
+    z.RX = kNwTile + p->ng.bx - 1;
+    z.RY = kNwTile + p->ng.by - 1;
+    z.lz = std::min(p->ng.bz, p->nz);
+    z.RC = z.RX * z.RY * z.lz;
+    z.ntx = (p->ng.nbx + kNwTile - 1) / kNwTile;
+    z.nty = (p->ng.nby + kNwTile - 1) / kNwTile;
+    z.nwarps = std::min(z.lz, 8);
+    z.o_meta = 128;                                              // header: row table [2 kNwTile + 1]
+    z.o_roff = z.o_meta + 3ull * 4 * kNlPass;                    // a pass's stations: index, base, r
+    z.o_acc = align_up(z.o_roff + 4ull * p->ng.bx * p->ng.by, 16);   // in-layer slot -> region offset
+    z.smem = z.o_acc + 4ull * z.RC;                              // FP32 accumulator over the region
+    z.ok = z.smem <= kNlSmemBudget;
+    return z;
+}
+
+__global__ void __launch_bounds__(256) k_near_adj_layer(
+    NearGeo ng, int RX, int RY, int lz, int ntx, uint32_t o_meta, uint32_t o_roff, uint32_t o_acc,
+    const float *__restrict__ dG, const int *__restrict__ bin_start, const int *__restrict__ bin_st,
+    const int *__restrict__ st_i0, const int *__restrict__ st_j0, const float2 *__restrict__ stz,
+    double *__restrict__ tpart) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    int *rowinfo = reinterpret_cast<int *>(smem_raw);                  // [2 kNwTile + 1]
+    int *msidx = reinterpret_cast<int *>(smem_raw + o_meta);           // [kNlPass]
+    int *mbase = msidx + kNlPass;
+    float *mrv = reinterpret_cast<float *>(mbase + kNlPass);
+    int *roff = reinterpret_cast<int *>(smem_raw + o_roff);
+    float *acc = reinterpret_cast<float *>(smem_raw + o_acc);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x, nw = nthr >> 5;
+    const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
+    const int I0 = tx * kNwTile, J0 = ty * kNwTile;
+    const int plane = RX * RY, RC = plane * lz, bxy = ng.bx * ng.by;
+    double *acc64 = tpart + (size_t)blockIdx.x * RC;
+    for (int u = tid; u < bxy; u += nthr) roff[u] = u % ng.bx + RX * (u / ng.bx);
+    for (int c = tid; c < RC; c += nthr) acc[c] = 0.0f;
+    if (tid == 0) {
+        int q = 0;
+        const int i1 = min(I0 + kNwTile, ng.nbx);
+        for (int r = 0; r < kNwTile; ++r) {
+            const int sbj = J0 + r;
+            int p0 = 0, p1 = 0;
+            if (sbj < ng.nby) {
+                p0 = bin_start[I0 + ng.nbx * sbj];
+                p1 = bin_start[i1 + ng.nbx * sbj];
+            }
+            rowinfo[r] = p0;
+            rowinfo[kNwTile + r] = q;
+            q += p1 - p0;
+        }
+        rowinfo[2 * kNwTile] = q;
+    }
+    __syncthreads();
+    const int Q = rowinfo[2 * kNwTile];
+    if (Q == 0)   // otherwise the first pass writes the region sums
+        for (int c = tid; c < RC; c += nthr) acc64[c] = 0.0;
+    for (int pass0 = 0; pass0 < Q; pass0 += kNlPass) {
+        const int pass1 = min(Q, pass0 + kNlPass);
+        for (int t = tid; t < pass1 - pass0; t += nthr) {
+            const int q = pass0 + t;
+            int r = 0;
+            while (r + 1 < kNwTile && rowinfo[kNwTile + r + 1] <= q) ++r;
+            const int sidx = bin_st[rowinfo[r] + (q - rowinfo[kNwTile + r])];
+            const int ri = st_i0[sidx] + ng.bx - 1 - I0;
+            const int rj = st_j0[sidx] + ng.by - 1 - J0;
+            const float rv = stz[sidx].y;
+            msidx[t] = sidx;
+            mbase[t] = (ri >= 0 && ri < kNwTile && rj >= 0 && rj < kNwTile && rv != 0.0f) ? ri + RX * rj : -1;
+            mrv[t] = rv;
+        }
+        __syncthreads();
+        for (int l = warp; l < lz; l += nw) {
+            float *accl = acc + (size_t)l * plane;
+            // [lo16, hi16): this layer's segment of a row, widened to 16-byte bounds
+            const uint32_t lo16 = (4u * (uint32_t)(l * bxy)) & ~15u;
+            const uint32_t hi16 = (4u * (uint32_t)((l + 1) * bxy) + 15u) & ~15u;
+            for (int q = 0; q < pass1 - pass0; ++q) {
+                const int base = mbase[q];
+                if (base < 0) continue;   // warp-uniform
+                const float rv = mrv[q];
+                const float *seg = dG + (int64_t)msidx[q] * ng.ld + (int64_t)l * bxy;
+                if (lane == 0) {
+                    if (q == 0) prefetch_l2_bulk(reinterpret_cast<const char *>(dG + (int64_t)msidx[q] * ng.ld) + lo16,
+                                                 hi16 - lo16);
+                    if (q + 1 < pass1 - pass0 && mbase[q + 1] >= 0)
+                        prefetch_l2_bulk(reinterpret_cast<const char *>(dG + (int64_t)msidx[q + 1] * ng.ld) + lo16,
+                                         hi16 - lo16);
+                }
+                float *a = accl + base;
+                for (int t0 = 0; t0 < bxy; t0 += 32 * kNlUnroll) {
+                    float gv[kNlUnroll];
+                    int ov[kNlUnroll];
+#pragma unroll
+                    for (int u = 0; u < kNlUnroll; ++u) {
+                        const int t = t0 + lane + 32 * u;
+                        gv[u] = t < bxy ? __ldcs(seg + t) : 0.0f;
+                        ov[u] = t < bxy ? roff[t] : -1;
+                    }
+                    float av[kNlUnroll];
+#pragma unroll
+                    for (int u = 0; u < kNlUnroll; ++u) av[u] = ov[u] >= 0 ? a[ov[u]] : 0.0f;
+#pragma unroll
+                    for (int u = 0; u < kNlUnroll; ++u)
+                        if (ov[u] >= 0) a[ov[u]] = fmaf(gv[u], rv, av[u]);
+                }
+                __syncwarp();   // the next station's lanes read cells these lanes wrote
+            }
+            double *p64 = acc64 + (size_t)l * plane;
+            for (int c = lane; c < plane; c += 32) {
+                p64[c] = pass0 == 0 ? (double)accl[c] : p64[c] + (double)accl[c];
+                accl[c] = 0.0f;
+            }
+            __syncwarp();
+        }
+        __syncthreads();   // the metadata is rewritten by the next pass
     }
 }
 
@@ -1757,8 +1901,10 @@ size_t mixed_scratch_bytes(const grav_plan *p) {
     {
         const NearAdjShape na = near_adj_shape(p);
         const NearWarpShape nw = near_warp_shape(p);
-        const size_t tb = std::max(na.ok ? 8ull * na.ntx * na.nty * na.RC : 0ull,
-                                   nw.ok ? 8ull * nw.ntx * nw.nty * nw.RC : 0ull);
+        const NearLayerShape nl = near_layer_shape(p);
+        const size_t tb = std::max(std::max(na.ok ? 8ull * na.ntx * na.nty * na.RC : 0ull,
+                                            nw.ok ? 8ull * nw.ntx * nw.nty * nw.RC : 0ull),
+                                   nl.ok ? 8ull * nl.ntx * nl.nty * nl.RC : 0ull);
         if (tb) add(tb);                                                    // per-tile near sums
     }
     add(4ull * N); add(4ull * N); add(4ull * N); add(4ull * N);             // keys, keys_sorted, vals, bin_st
@@ -1842,19 +1988,24 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
     const int64_t lz = std::min(p->ng.bz, nz);
     p->m_cellacc = (double *)take(p, 8ull * nx * ny * lz);
     {
-        // form: warp-private if its shared memory fits, else station-streaming,
-        // else cell-tiled; GRAV_NEAR_ADJ=warp|rows|tiles restricts the choice
+        // form: layer-split if its shared memory fits, else warp-private, else
+        // station-streaming, else cell-tiled; GRAV_NEAR_ADJ=warp|rows|tiles
+        // restricts the choice
         const NearAdjShape na = near_adj_shape(p);
         const NearWarpShape nw = near_warp_shape(p);
+        const NearLayerShape nl = near_layer_shape(p);
         const char *ev = std::getenv("GRAV_NEAR_ADJ");
         const bool want_tiles = ev && std::strcmp(ev, "tiles") == 0;
         const bool want_rows = ev && std::strcmp(ev, "rows") == 0;
+        const bool want_warp = ev && std::strcmp(ev, "warp") == 0;
         p->near_adj_rows = 0;
-        if (!want_tiles && !want_rows && nw.ok) p->near_adj_rows = 2;
+        if (!want_tiles && !want_rows && !want_warp && nl.ok) p->near_adj_rows = 3;
+        else if (!want_tiles && !want_rows && nw.ok) p->near_adj_rows = 2;
         else if (!want_tiles && na.ok) p->near_adj_rows = 1;
         // near forward: tile form when it fits; GRAV_NEAR_FWD=warp forces a warp per station
         const char *fv = std::getenv("GRAV_NEAR_FWD");
         p->near_fwd_tile = near_fwd_shape(p).ok && !(fv && std::strcmp(fv, "warp") == 0);
+        if (p->near_adj_rows == 3) p->near_tpart = (double *)take(p, 8ull * nl.ntx * nl.nty * nl.RC);
         if (p->near_adj_rows == 2) p->near_tpart = (double *)take(p, 8ull * nw.ntx * nw.nty * nw.RC);
         if (p->near_adj_rows == 1) p->near_tpart = (double *)take(p, 8ull * na.ntx * na.nty * na.RC);
     }
@@ -2078,7 +2229,17 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
     stage_end(p, kStageAdjMain, s);
     const int lz = std::min(p->ng.bz, p->nz);
     stage_begin(p, kStageAdjNear, s);
-    if (p->near_adj_rows == 2) {
+    if (p->near_adj_rows == 3) {
+        const NearLayerShape nl = near_layer_shape(p);
+        cudaFuncSetAttribute(k_near_adj_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nl.smem);
+        k_near_adj_layer<<<(unsigned)(nl.ntx * nl.nty), 32 * nl.nwarps, nl.smem, s>>>(
+            p->ng, nl.RX, nl.RY, nl.lz, nl.ntx, (uint32_t)nl.o_meta, (uint32_t)nl.o_roff, (uint32_t)nl.o_acc, p->dG,
+            p->bin_start, p->bin_st, p->st_i0, p->st_j0, p->stz, p->near_tpart);
+        const int64_t cells = (int64_t)p->nx * p->ny * lz;
+        k_near_adj_gather<<<grid_for(cells, 256), 256, 0, s>>>(p->nx, p->ny, lz, p->ng.bx, p->ng.by, nl.RX, nl.RY,
+                                                               nl.ntx, kNwTile, p->near_tpart, p->m_cellacc);
+        note_launches(1);
+    } else if (p->near_adj_rows == 2) {
         const NearWarpShape nw = near_warp_shape(p);
         cudaFuncSetAttribute(k_near_adj_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nw.smem);
         k_near_adj_warp<<<(unsigned)(nw.ntx * nw.nty), kNwWarps * 32, nw.smem, s>>>(

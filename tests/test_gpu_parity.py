@@ -225,9 +225,11 @@ def test_mixed_forward_adjoint_vs_oracle(g, shape, cell, h, seed, adjoint_layout
 
 @pytest.mark.parametrize("near_cells", [8.0, 3.0, 5.0])
 def test_near_adjoint_forms_agree_and_match_oracle(g, near_cells, monkeypatch):
-    """The near-field adjoint in its three forms: warp-private (each warp
-    streams its stations' table rows into its own FP32 region accumulator;
-    the default), station-streaming (whole rows by TMA bulk copy into one
+    """The near-field adjoint in its four forms: layer-split (warp w owns
+    the region's layers w, w + 8, ... of one shared FP32 accumulator and
+    streams that layer's segment of every station's row; the default),
+    warp-private (each warp streams its stations' table rows into its own
+    FP32 region accumulator; GRAV_NEAR_ADJ=warp), station-streaming (whole rows by TMA bulk copy into one
     shared accumulator, a barrier per station; GRAV_NEAR_ADJ=rows) and
     cell-tiled (GRAV_NEAR_ADJ=tiles).  Windows 3 and 5 give 147- and
     605-slot boxes, not multiples of 4, so the table rows carry padding that
@@ -245,7 +247,7 @@ def test_near_adjoint_forms_agree_and_match_oracle(g, near_cells, monkeypatch):
     m = rng.normal(0.0, 100.0, mesh.ncells)
     Gk = _mixed_definition(mesh, sv, G, 30.0, near_cells)
     out = {}
-    for form in ("warp", "rows", "tiles"):
+    for form in ("layer", "warp", "rows", "tiles"):
         monkeypatch.setenv("GRAV_NEAR_ADJ", form)
         plan = g.Plan(mesh, S, precision="mixed", near_cells=near_cells)
         a = plan.adjoint(_dev(r))
@@ -258,7 +260,7 @@ def test_near_adjoint_forms_agree_and_match_oracle(g, near_cells, monkeypatch):
             assert _rel(a, G.T @ r) <= TOLMIX, form
         out[form] = a
         plan.close()
-    for form in ("warp", "rows"):
+    for form in ("layer", "warp", "rows"):
         assert np.abs(out[form] - out["tiles"]).max() <= 1e-7 * np.abs(out["tiles"]).max(), form
 
 
