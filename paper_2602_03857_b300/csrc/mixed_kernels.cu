@@ -1494,9 +1494,9 @@ __global__ void __launch_bounds__(256) k_near_adj_layer(
 // table entries are zero anyway) and the slot -> region offset table are
 // staged in shared memory once, so a station's gathers are shared-memory
 // loads instead of scattered L2 sectors.  Each warp takes stations w, w + 8,
-// ... of the tile, requests its rows (this one and the next) from L2 by bulk
-// prefetch and streams each row in 16-byte evict-first loads, kNfChunk per
-// lane in flight.  FP32 runs of 16 terms are summed in double-float per lane
+// ... of the tile, requests each row whole from L2 by bulk prefetch (one row
+// per warp in flight keeps the requests within L2) and streams it in 16-byte
+// evict-first loads, kNfChunk per lane in flight.  FP32 runs of 16 terms are summed in double-float per lane
 // and across the warp (fixed butterfly): bitwise deterministic, no FP64
 // operation per term or per run.  Stations whose box misses the mesh (sorted
 // after every bin) get 0 from the first CTA.
@@ -1599,11 +1599,7 @@ __global__ void __launch_bounds__(kNwWarps * 32) k_near_fwd_tile(
             const int sidx = msidx[q - pass0];
             const float *qb = qreg + mbase[q - pass0];
             const float4 *row = dG4 + (int64_t)sidx * n4;
-            if (lane == 0) {
-                if (q == pass0 + warp) prefetch_l2_bulk(row, 16u * (uint32_t)n4);
-                if (q + kNwWarps < pass1)
-                    prefetch_l2_bulk(dG4 + (int64_t)msidx[q + kNwWarps - pass0] * n4, 16u * (uint32_t)n4);
-            }
+            if (lane == 0) prefetch_l2_bulk(row, 16u * (uint32_t)n4);
             float hi = 0.0f, lo = 0.0f;
             for (int v0 = 0; v0 < n4; v0 += 32 * kNfChunk) {
                 float4 gq[kNfChunk];
