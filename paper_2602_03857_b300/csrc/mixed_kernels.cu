@@ -1365,7 +1365,7 @@ constexpr size_t kNlSmemBudget = 64 * 1024;
 
 struct NearLayerShape {
     bool ok = false;
-    int RX = 0, RY = 0, lz = 0, RC = 0, ntx = 0, nty = 0, nwarps = 0;
+    int RX = 0, RY = 0, SX = 0, lz = 0, RC = 0, ntx = 0, nty = 0, nwarps = 0;
     size_t o_meta = 0, o_roff = 0, o_acc = 0, smem = 0;
 };
 
@@ -1381,13 +1381,17 @@ static NearLayerShape near_layer_shape(const grav_plan *p) {
     z.o_meta = 128;                                              // header: row table [2 kNwTile + 1]
     z.o_roff = z.o_meta + 3ull * 4 * kNlPass;                    // a pass's stations: index, base, r
     z.o_acc = align_up(z.o_roff + 4ull * p->ng.bx * p->ng.by, 16);   // in-layer slot -> region offset
-    z.smem = z.o_acc + 4ull * z.RC;                              // FP32 accumulator over the region
+    // shared-memory row stride SX = bx (mod 32): 32 consecutive slots of a
+    // layer then fall on 32 distinct banks; RX when the padded planes do not fit
+    z.SX = z.RX + ((p->ng.bx - z.RX) % 32 + 32) % 32;
+    if (z.o_acc + 4ull * z.SX * z.RY * z.lz > kNlSmemBudget) z.SX = z.RX;
+    z.smem = z.o_acc + 4ull * z.SX * z.RY * z.lz;               // FP32 accumulator over the region
     z.ok = z.smem <= kNlSmemBudget;
     return z;
 }
 
 __global__ void __launch_bounds__(256) k_near_adj_layer(
-    NearGeo ng, int RX, int RY, int lz, int ntx, uint32_t o_meta, uint32_t o_roff, uint32_t o_acc,
+    NearGeo ng, int RX, int RY, int SX, int lz, int ntx, uint32_t o_meta, uint32_t o_roff, uint32_t o_acc,
     const float *__restrict__ dG, const int *__restrict__ bin_start, const int *__restrict__ bin_st,
     const int *__restrict__ st_i0, const int *__restrict__ st_j0, const float2 *__restrict__ stz,
     double *__restrict__ tpart) {
@@ -1402,9 +1406,10 @@ __global__ void __launch_bounds__(256) k_near_adj_layer(
     const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
     const int I0 = tx * kNwTile, J0 = ty * kNwTile;
     const int plane = RX * RY, RC = plane * lz, bxy = ng.bx * ng.by;
+    const int splane = SX * RY;   // a layer in shared memory (rows of SX >= RX)
     double *acc64 = tpart + (size_t)blockIdx.x * RC;
-    for (int u = tid; u < bxy; u += nthr) roff[u] = u % ng.bx + RX * (u / ng.bx);
-    for (int c = tid; c < RC; c += nthr) acc[c] = 0.0f;
+    for (int u = tid; u < bxy; u += nthr) roff[u] = u % ng.bx + SX * (u / ng.bx);
+    for (int c = tid; c < splane * lz; c += nthr) acc[c] = 0.0f;
     if (tid == 0) {
         int q = 0;
         const int i1 = min(I0 + kNwTile, ng.nbx);
@@ -1436,12 +1441,12 @@ __global__ void __launch_bounds__(256) k_near_adj_layer(
             const int rj = st_j0[sidx] + ng.by - 1 - J0;
             const float rv = stz[sidx].y;
             msidx[t] = sidx;
-            mbase[t] = (ri >= 0 && ri < kNwTile && rj >= 0 && rj < kNwTile && rv != 0.0f) ? ri + RX * rj : -1;
+            mbase[t] = (ri >= 0 && ri < kNwTile && rj >= 0 && rj < kNwTile && rv != 0.0f) ? ri + SX * rj : -1;
             mrv[t] = rv;
         }
         __syncthreads();
         for (int l = warp; l < lz; l += nw) {
-            float *accl = acc + (size_t)l * plane;
+            float *accl = acc + (size_t)l * splane;
             // [lo16, hi16): this layer's segment of a row, widened to 16-byte bounds
             const uint32_t lo16 = (4u * (uint32_t)(l * bxy)) & ~15u;
             const uint32_t hi16 = (4u * (uint32_t)((l + 1) * bxy) + 15u) & ~15u;
@@ -1478,8 +1483,9 @@ __global__ void __launch_bounds__(256) k_near_adj_layer(
             }
             double *p64 = acc64 + (size_t)l * plane;
             for (int c = lane; c < plane; c += 32) {
-                p64[c] = pass0 == 0 ? (double)accl[c] : p64[c] + (double)accl[c];
-                accl[c] = 0.0f;
+                const int sc = c % RX + SX * (c / RX);
+                p64[c] = pass0 == 0 ? (double)accl[sc] : p64[c] + (double)accl[sc];
+                accl[sc] = 0.0f;
             }
             __syncwarp();
         }
@@ -2229,8 +2235,8 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
         const NearLayerShape nl = near_layer_shape(p);
         cudaFuncSetAttribute(k_near_adj_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nl.smem);
         k_near_adj_layer<<<(unsigned)(nl.ntx * nl.nty), 32 * nl.nwarps, nl.smem, s>>>(
-            p->ng, nl.RX, nl.RY, nl.lz, nl.ntx, (uint32_t)nl.o_meta, (uint32_t)nl.o_roff, (uint32_t)nl.o_acc, p->dG,
-            p->bin_start, p->bin_st, p->st_i0, p->st_j0, p->stz, p->near_tpart);
+            p->ng, nl.RX, nl.RY, nl.SX, nl.lz, nl.ntx, (uint32_t)nl.o_meta, (uint32_t)nl.o_roff, (uint32_t)nl.o_acc,
+            p->dG, p->bin_start, p->bin_st, p->st_i0, p->st_j0, p->stz, p->near_tpart);
         const int64_t cells = (int64_t)p->nx * p->ny * lz;
         k_near_adj_gather<<<grid_for(cells, 256), 256, 0, s>>>(p->nx, p->ny, lz, p->ng.bx, p->ng.by, nl.RX, nl.RY,
                                                                nl.ntx, kNwTile, p->near_tpart, p->m_cellacc);
