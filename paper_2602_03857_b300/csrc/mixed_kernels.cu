@@ -693,7 +693,7 @@ __global__ void __launch_bounds__(kCfThreads) k_cfwd32(MixedGeo g, int ldw, cons
 // ---------------------------------------------------------------------------
 template <bool CORNER>
 __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
-    Geo g, MixedGeo mg, NearGeo ng, double x0, double y0, double a, double b, double vol_mgal,
+    Geo g, MixedGeo mg, NearGeo ng, double x0, double y0, double a, double b, double vol_mgal, double node_r2,
     const double *__restrict__ sx, const double *__restrict__ sy, const double *__restrict__ sz,
     const double *__restrict__ w2, const float4 *__restrict__ st32, const float2 *__restrict__ stz,
     float *__restrict__ dG, int *__restrict__ st_i0, int *__restrict__ st_j0, double *__restrict__ diag_corr,
@@ -717,17 +717,50 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
     const double fy = fmin(fmax((ys - y0) / b - 0.5 - rad / b, -lim), lim);
     const int i0 = (int)floor(fx) + 1;
     const int j0 = (int)floor(fy) + 1;
-    for (int t = lane; t < nnode; t += 32) {
+    // Psi only at the nodes a cell inside the window can use: a cell whose
+    // centre lies within the radius has its 8 corners within node_r2 (radius
+    // plus half a cell diagonal, squared, with a margin).  The nodes that pass
+    // are queued (warp ballot) and evaluated 32 at a time, so the FP64 work
+    // follows the window's hemisphere (~half the box) with every lane busy.
+    int *queue = reinterpret_cast<int *>(reinterpret_cast<double *>(smem_raw) + (size_t)nwarps * nnode) +
+                 (CORNER ? (size_t)nwarps * nnode : 0) + (size_t)warp * 64;
+    auto psi_node = [&](int t) {
         const int ia = i0 + t % nbx1;
         const int jb = j0 + (t / nbx1) % nby1;
         const int c = t / (nbx1 * nby1);
-        double v = 0.0;
-        if (ia >= 0 && ia <= g.nx && jb >= 0 && jb <= g.ny && c <= g.nz) {
-            const double x = g.xe[ia] - xs, y = g.ye[jb] - ys, z = g.ze[c] - zs;
-            v = psi64(x, y, z, x * x, y * y, z * z, g.fn);
+        const double x = g.xe[ia] - xs, y = g.ye[jb] - ys, z = g.ze[c] - zs;
+        P[t] = psi64(x, y, z, x * x, y * y, z * z, g.fn);
+    };
+    int qn = 0;   // queued nodes (warp-uniform)
+    for (int t0 = 0; t0 < nnode; t0 += 32) {
+        const int t = t0 + lane;
+        bool need = false;
+        if (t < nnode) {
+            const int ia = i0 + t % nbx1;
+            const int jb = j0 + (t / nbx1) % nby1;
+            const int c = t / (nbx1 * nby1);
+            if (ia >= 0 && ia <= g.nx && jb >= 0 && jb <= g.ny && c <= g.nz) {
+                const double x = g.xe[ia] - xs, y = g.ye[jb] - ys, z = g.ze[c] - zs;
+                need = x * x + y * y + z * z < node_r2;
+            }
+            if (!need) P[t] = 0.0;
         }
-        P[t] = v;
+        const unsigned mask = __ballot_sync(0xffffffffu, need);
+        if (need) queue[qn + __popc(mask & ((1u << lane) - 1u))] = t;
+        qn += __popc(mask);
+        __syncwarp();
+        if (qn >= 32) {
+            psi_node(queue[lane]);
+            __syncwarp();
+            const int rest = qn - 32;
+            const int moved = lane < rest ? queue[32 + lane] : 0;
+            __syncwarp();
+            if (lane < rest) queue[lane] = moved;
+            qn = rest;
+            __syncwarp();
+        }
     }
+    if (lane < qn) psi_node(queue[lane]);
     const float4 S = st32[s];
     const float zf = stz[s].x;
     if (CORNER) {
@@ -1929,7 +1962,7 @@ static void *take(grav_plan *p, size_t bytes) {
 
 int near_setup_warps(const grav_plan *p) {
     const size_t per_node = p->opt.precision == GRAV_MIXED_CORNER ? 12 : 8;   // FP64 (+ FP32) corner values
-    const size_t per_warp = (size_t)(p->ng.bx + 1) * (p->ng.by + 1) * (p->ng.bz + 1) * per_node;
+    const size_t per_warp = (size_t)(p->ng.bx + 1) * (p->ng.by + 1) * (p->ng.bz + 1) * per_node + 256;   // + node queue
     const size_t cap = 200 * 1024;
     return (int)std::min<size_t>(kNsWarps, cap / per_warp);
 }
@@ -2078,12 +2111,17 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
     k_prep_stations<<<grid_for(p->N, 256), 256, 0, s>>>(p->sx, p->sy, p->sz, p->N, xref, yref, p->st32, p->stz);
 
     const int nnode = (p->ng.bx + 1) * (p->ng.by + 1) * (p->ng.bz + 1);
-    const size_t smem = (size_t)ns_warps * nnode * (corner ? 12 : 8);
+    const size_t smem = (size_t)ns_warps * (nnode * (corner ? 12 : 8) + 256);
     const double vol_mgal = kGammaMgal * p->cell_a * p->cell_b * p->cell_c;
+    // nodes within the window radius plus half a cell diagonal (relative margin 1e-9)
+    const double node_r = (p->ng.radius_cells * p->ng.width +
+                           0.5 * std::sqrt(p->cell_a * p->cell_a + p->cell_b * p->cell_b + p->cell_c * p->cell_c)) *
+                          (1.0 + 1e-9);
     auto setup = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         kern<<<(unsigned)((p->N + ns_warps - 1) / ns_warps), ns_warps * 32, smem, s>>>(
-            make_geo(p), p->mg, p->ng, p->xe[0], p->ye[0], a, p->ye[1] - p->ye[0], vol_mgal, p->sx, p->sy, p->sz,
+            make_geo(p), p->mg, p->ng, p->xe[0], p->ye[0], a, p->ye[1] - p->ye[0], vol_mgal, node_r * node_r,
+            p->sx, p->sy, p->sz,
             p->d_w2, p->st32,
             p->stz, p->dG, p->st_i0, p->st_j0, p->diag_corr, keys, vals, (unsigned)z.nbins);
     };
