@@ -684,8 +684,9 @@ __global__ void __launch_bounds__(kCfThreads) k_cfwd32(MixedGeo g, int ldw, cons
 }
 
 // ---------------------------------------------------------------------------
-// Near-field set-up: warp per station.  Psi on the (bx+1)(by+1)(bz+1) nodes
-// of the station's window box (FP64, each node evaluated once), then per box
+// Near-field set-up: warp per station.  Psi on those of the (bx+1)(by+1)(bz+1)
+// nodes of the station's window box that a cell inside the window radius
+// uses (FP64, each node evaluated once), then per box
 // cell: dG = G_exact - G_far when the cell centre lies within the window
 // radius, else 0.  Also returns the near-field part of diag(G W^-2 G^T),
 // sum w2 (G_exact^2 - G_far^2), the box origin and the station's bin key.
