@@ -419,7 +419,7 @@ int plan_allocate(grav_plan *p, cudaStream_t s) {
         p->w = (double *)p->arena.take(nrows * p->ldw * 8);
         p->part = (double *)p->arena.take((size_t)std::max(std::max(p->f64_nchunk, p->f64_diag_nchunk), p->c_nchunk) *
                                           p->N * 8);
-        p->st4 = (double4 *)p->arena.take((size_t)p->N * 32);
+        p->st4 = (double4_16a *)p->arena.take((size_t)p->N * 32);
         p->upart = (double *)p->arena.take((size_t)p->a64_nschunk * p->Nn * 8);
         p->u = (double *)p->arena.take((size_t)p->Nn * 8);
         if (p->cached) p->Gc = (double *)p->arena.take((size_t)p->N * p->M * 8);

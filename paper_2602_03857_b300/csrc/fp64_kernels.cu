@@ -205,15 +205,15 @@ __global__ void __launch_bounds__(kRedWarps * 32) k_reduce_rows(const double *__
 }
 
 // st4[s].w = r[s]
-__global__ void k_set_r(double4 *__restrict__ st4, const double *__restrict__ r, int64_t n) {
+__global__ void k_set_r(double4_16a *__restrict__ st4, const double *__restrict__ r, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         st4[i].w = r[i];
 }
 
-__global__ void k_init_st4(double4 *__restrict__ st4, const double *__restrict__ x, const double *__restrict__ y,
+__global__ void k_init_st4(double4_16a *__restrict__ st4, const double *__restrict__ x, const double *__restrict__ y,
                            const double *__restrict__ z, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        st4[i] = make_double4(x[i], y[i], z[i], 0.0);
+        st4[i] = make_double4_16a(x[i], y[i], z[i], 0.0);
 }
 
 // ---------------------------------------------------------------------------
@@ -224,13 +224,13 @@ __global__ void k_init_st4(double4 *__restrict__ st4, const double *__restrict__
 // per node at the end (fixed order: deterministic).
 // ---------------------------------------------------------------------------
 template <int TZ>
-__global__ void __launch_bounds__(kAdjWarps * 32) k_adj64(Geo g, const double4 *__restrict__ st4,
+__global__ void __launch_bounds__(kAdjWarps * 32) k_adj64(Geo g, const double4_16a *__restrict__ st4,
                                                           int64_t schunk_len, double *__restrict__ upart,
                                                           int64_t Nn, int *status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
     int *flag = reinterpret_cast<int *>(smem_raw + 16);
-    double4 *sbuf = reinterpret_cast<double4 *>(smem_raw + 128);
+    double4_16a *sbuf = reinterpret_cast<double4_16a *>(smem_raw + 128);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ngz = (g.nz + 1 + TZ - 1) / TZ;
@@ -284,10 +284,10 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adj64(Geo g, const double4 *
         }
         const int64_t sa = s0 + (int64_t)st * kAdjStage;
         const int cnt = (int)min((int64_t)kAdjStage, s1 - sa);
-        const double4 *sb = sbuf + buf * kAdjStage;
+        const double4_16a *sb = sbuf + buf * kAdjStage;
         if (gvalid) {
             for (int k = lane; k < cnt; k += 32) {
-                const double4 S = sb[k];
+                const double4_16a S = sb[k];
                 if (S.w == 0.0) continue;
                 const double dx = Xa - S.x, dy = Yb - S.y;
                 const double x2 = dx * dx, y2 = dy * dy;
@@ -543,7 +543,7 @@ void launch_reduce_rows(const double *part, int nchunk, int64_t n, double scale,
 void launch_adj64(const grav_plan *p, const double *r, cudaStream_t s) {
     k_set_r<<<grid_for(p->N, 256), 256, 0, s>>>(p->st4, r, p->N);
     dim3 grid((p->a64_groups + kAdjWarps - 1) / kAdjWarps, p->a64_nschunk);
-    const size_t smem = 128 + 2ull * kAdjStage * sizeof(double4);
+    const size_t smem = 128 + 2ull * kAdjStage * sizeof(double4_16a);
     stage_begin(p, kStageAdjMain, s);
     k_adj64<kAdjTZ><<<grid, kAdjWarps * 32, smem, s>>>(make_geo(p), p->st4, p->a64_schunk_len, p->upart,
                                                        p->Nn, p->ctx->d_status);

@@ -117,7 +117,7 @@ struct grav_plan {
     int f64_diag_jrows = 0, f64_diag_nchunk = 0;
     double *w = nullptr;                  // node weights [(ny+1)(nz+1)][ldw]
     double *part = nullptr;               // forward partials [nchunk][N]
-    double4 *st4 = nullptr;               // stations (x, y, z, r)
+    double4_16a *st4 = nullptr;               // stations (x, y, z, r)
     double *upart = nullptr;              // adjoint partials [nschunk][Nn]
     double *u = nullptr;                  // [Nn]
     int cached = 0;                       // 1: explicit G stored (FP64, cell-major [M][N])

@@ -428,10 +428,24 @@ constexpr int kAbStage = 1024;
 // floor, so 128 trades 0.4 % of the adjoint for a lower floor.
 constexpr int kAbFold = 128;
 
-template <int TZ, bool QUAD>
+// One lane's NL cells (layers l0 .. l0 + NL - 1 of one column): NL / 2 layer
+// pairs in packed f32x2 chains and, for odd NL, the last layer alone through
+// the same operations in scalar form (far_one), so no padded layer costs a
+// reciprocal square root.
+template <bool QUAD>
+__device__ __forceinline__ float far_one(float zc, float nzs, float h2, float w, float acc, float qg, float ph) {
+    const float dz = zc + nzs;
+    const float R2 = fmaf(dz, dz, h2);
+    return fmaf(w, far_k<QUAD>(dz, R2, qg, ph), acc);
+}
+
+template <int NL, bool QUAD>
 __device__ __forceinline__ void madj_bc_body(const MixedGeo &g, const float4 *__restrict__ st32,
                                              const float2 *__restrict__ stz, int l0, int cb, int64_t schunk_len,
                                              double *__restrict__ apart, int *status, unsigned char *smem_raw) {
+    constexpr int NP = NL / 2;            // packed layer pairs
+    constexpr bool ODD = (NL & 1) != 0;   // one more layer, scalar
+    constexpr int NPA = NP > 0 ? NP : 1;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
     int *flag = reinterpret_cast<int *>(smem_raw + 16);
     float4 *sxy = reinterpret_cast<float4 *>(smem_raw + 128);
@@ -443,17 +457,18 @@ __device__ __forceinline__ void madj_bc_body(const MixedGeo &g, const float4 *__
     const int i = cc % g.nx, j = cc / g.nx;
     const float2 X = make_float2(g.cx[2 * i], g.cx[2 * i + 1]);
     const float2 Y = make_float2(g.cy[2 * j], g.cy[2 * j + 1]);
-    static_assert(TZ % 2 == 0, "layer pairs");
     const f2_t qg2 = f2_pack(g.qg, g.qg);
-    f2_t zcp[TZ / 2], cs2[TZ / 2];
-    double acc[TZ];
+    f2_t zcp[NPA], cs2[NPA];
+    double acc[NL];
 #pragma unroll
-    for (int u = 0; u < TZ / 2; ++u) {
+    for (int u = 0; u < NP; ++u) {
         zcp[u] = f2_pack(g.czc[min(l0 + 2 * u, g.nzp - 1)], g.czc[min(l0 + 2 * u + 1, g.nzp - 1)]);
         cs2[u] = 0ull;
-        acc[2 * u] = 0.0;
-        acc[2 * u + 1] = 0.0;
     }
+#pragma unroll
+    for (int t = 0; t < NL; ++t) acc[t] = 0.0;
+    const float zc1 = ODD ? g.czc[min(l0 + NL - 1, g.nzp - 1)] : 0.0f;
+    float cs1 = 0.0f;
     const int64_t s0 = (int64_t)blockIdx.y * schunk_len;
     const int64_t s1 = min(g.N, s0 + schunk_len);
     const int nst = (s1 > s0) ? (int)((s1 - s0 + kAbStage - 1) / kAbStage) : 0;
@@ -500,20 +515,26 @@ __device__ __forceinline__ void madj_bc_body(const MixedGeo &g, const float4 *__
                 const float h = far_h2(X, Y, P.x, P.y, P.z, P.w);
                 const f2_t h2p = f2_pack(h, h), nz2 = f2_pack(-Z.x, -Z.x), w2 = f2_pack(Z.y, Z.y);
                 f2_t ph2 = 0ull;
+                float ph = 0.0f;
                 if (QUAD) {
-                    const float ph = far_ph(X, Y, P.x, P.y, P.z, P.w, g.qa, g.qb);
+                    ph = far_ph(X, Y, P.x, P.y, P.z, P.w, g.qa, g.qb);
                     ph2 = f2_pack(ph, ph);
                 }
 #pragma unroll
-                for (int u = 0; u < TZ / 2; ++u) cs2[u] = far_pair<QUAD>(zcp[u], nz2, h2p, w2, cs2[u], qg2, ph2);
+                for (int u = 0; u < NP; ++u) cs2[u] = far_pair<QUAD>(zcp[u], nz2, h2p, w2, cs2[u], qg2, ph2);
+                if (ODD) cs1 = far_one<QUAD>(zc1, -Z.x, h, Z.y, cs1, g.qg, ph);
             }
 #pragma unroll
-            for (int u = 0; u < TZ / 2; ++u) {
+            for (int u = 0; u < NP; ++u) {
                 float a, b;
                 f2_unpack(cs2[u], a, b);
                 acc[2 * u] += (double)a;
                 acc[2 * u + 1] += (double)b;
                 cs2[u] = 0ull;
+            }
+            if (ODD) {
+                acc[NL - 1] += (double)cs1;
+                cs1 = 0.0f;
             }
         }
         __syncthreads();
@@ -524,17 +545,18 @@ __device__ __forceinline__ void madj_bc_body(const MixedGeo &g, const float4 *__
     }
     if (!cvalid) return;
 #pragma unroll
-    for (int t = 0; t < TZ; ++t)
+    for (int t = 0; t < NL; ++t)
         if (l0 + t < g.nz) apart[(int64_t)blockIdx.y * g.ncol * (int64_t)g.nz + col + (int64_t)g.ncol * (l0 + t)] = acc[t];
 }
 
-// Layer groups 0 .. ngz-2 hold TZ layers, the last group TZL (TZL <= TZ, a
-// multiple of 4 covering the remaining layers), so at most 3 padded layers.
+// Layer groups 0 .. ngz-2 hold TZ layers (even), the last group exactly the
+// TZL layers left (1 <= TZL <= TZ), so no layer is padded.
 template <int TZ, int TZL, bool QUAD>
 __global__ void __launch_bounds__(kAbWarps * 32, GRAV_AB_MINB) k_madj_bc(MixedGeo g, const float4 *__restrict__ st32,
                                                                         const float2 *__restrict__ stz, int ngz,
                                                                         int64_t schunk_len,
                                                                         double *__restrict__ apart, int *status) {
+    static_assert(TZ % 2 == 0 && TZL >= 1 && TZL <= TZ, "layer groups");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int cblocks = (g.ncol + kAbWarps * 32 - 1) / (kAbWarps * 32);
     const int cb = blockIdx.x % cblocks;
@@ -1781,19 +1803,18 @@ constexpr int kMfColsPerStage = 32;
 
 // Layer groups of the broadcast adjoint: 16 layers (8 packed pairs; measured
 // fastest per layer among 8/12/16/20 at 2 CTAs per SM), the last group
-// rounded up to a multiple of 4.  Meshes with fewer than 16 layers use one
-// group of ceil4(nz).
+// exactly the layers left (an odd count ends with one scalar layer).  At
+// nz = 75 that is 16, 16, 16, 16, 11: the 12-layer last group used before (a
+// multiple of 4) spent one reciprocal square root in 76 on a padded layer.
 #ifndef GRAV_AB_TZ
 #define GRAV_AB_TZ 16
 #endif
 constexpr int kAbTz = GRAV_AB_TZ;
 static_assert(kAbTz % 4 == 0 && kAbTz >= 16, "layer group: a multiple of 4, at least 16");
-int adj_tz_bc(int nz) { return nz >= kAbTz ? kAbTz : nz >= 16 ? 16 : (nz + 3) / 4 * 4; }
+int adj_tz_bc(int nz) { (void)nz; return kAbTz; }
 int adj_tzl_bc(int nz) {
     const int tz = adj_tz_bc(nz);
-    if (nz < 16) return tz;
-    const int rem = nz - tz * ((nz + tz - 1) / tz - 1);
-    return (rem + 3) / 4 * 4;
+    return nz - tz * ((nz + tz - 1) / tz - 1);
 }
 
 // Layer group of the shuffle adjoint layout (small meshes): TZ in
@@ -2203,12 +2224,12 @@ void launch_mixed_near_fwd(const grav_plan *p, const double *m, cudaStream_t s) 
     note_launches(1);
 }
 
-// k_madj_bc<TZ, tzl> for the run-time last-group size tzl (a multiple of 4, <= TZ)
+// k_madj_bc<TZ, tzl> for the run-time last-group size tzl (1 <= tzl <= TZ)
 template <int TZ, int L, bool Q, typename F>
 void pick_bc_last(int tzl, F &gob) {
     if constexpr (L < TZ) {
         if (tzl == L) { gob(k_madj_bc<TZ, L, Q>); return; }
-        pick_bc_last<TZ, L + 4, Q>(tzl, gob);
+        pick_bc_last<TZ, L + 1, Q>(tzl, gob);
     } else {
         gob(k_madj_bc<TZ, TZ, Q>);
     }
@@ -2241,17 +2262,7 @@ void launch_mixed_adj(const grav_plan *p, const double *r, cudaStream_t s) {
         const int tzl = adj_tzl_bc(p->nz);
         auto pick = [&](auto quad) {
             constexpr bool Q = decltype(quad)::value;
-            if (p->m_adj_tz == kAbTz) {
-                pick_bc_last<kAbTz, 4, Q>(tzl, gob);
-            } else if (p->m_adj_tz == 16) {
-                pick_bc_last<16, 4, Q>(tzl, gob);
-            } else {
-                switch (p->m_adj_tz) {
-                    case 4: gob(k_madj_bc<4, 4, Q>); break;
-                    case 8: gob(k_madj_bc<8, 8, Q>); break;
-                    default: gob(k_madj_bc<12, 12, Q>); break;
-                }
-            }
+            pick_bc_last<kAbTz, 1, Q>(tzl, gob);
         };
         if (p->cubic) pick(std::false_type{}); else pick(std::true_type{});
     } else {
