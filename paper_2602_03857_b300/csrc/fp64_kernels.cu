@@ -91,6 +91,10 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd64(Geo g, int ldw, const dou
     const int nst = (r1 > r0) ? (r1 - r0 + rows_per_stage - 1) / rows_per_stage : 0;
 
     const int64_t s_base = (int64_t)blockIdx.x * (kFwdThreads * T) + threadIdx.x;
+    // a warp whose first station is past N has no station at all (t adds
+    // whole CTAs of threads): it skips the evaluation and only keeps the
+    // CTA's barriers (surveys of a few stations, e.g. the FP64 error check)
+    const bool live = s_base - (threadIdx.x & 31) < g.N;
     double xs[T], ys[T], zs[T], acc[T];
 #pragma unroll
     for (int t = 0; t < T; ++t) {
@@ -136,7 +140,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd64(Geo g, int ldw, const dou
         const double *wb = wbuf + (size_t)buf * rows_per_stage * ldw;
         const int ra = r0 + st * rows_per_stage;
         const int rb = min(r1, ra + rows_per_stage);
-        for (int r = ra; r < rb; ++r) {
+        for (int r = ra; live && r < rb; ++r) {
             const int b = r % (g.ny + 1);
             const int c = r / (g.ny + 1);
             const double Yb = g.ye[b], Zc = g.ze[c];
