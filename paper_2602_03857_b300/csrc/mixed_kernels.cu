@@ -1876,10 +1876,18 @@ static MixedSizes mixed_sizes(const grav_plan *p) {
     // 210 x 210 x 75 x 178,797, 2 chunks (5.8 waves) 143.2 ms, 6 chunks
     // 138.9 ms, 12 chunks (35 waves) 137.5 ms; the partials (chunks x M
     // doubles) are capped at 512 MB
+    //
+    // Smaller meshes (serving-sized) get the broadcast layout too when station
+    // chunks of >= 64 stations can fill one wave: measured on the first 24
+    // jobs of the serving stream, the shuffle layout reached 65 % of the MUFU
+    // peak (pairs-weighted) and the broadcast layout 76 % with 1024-station
+    // chunks; the chunk count is then chosen by a wave model (below).
     const int tz_bc = adj_tz_bc(p->nz);
     const int64_t slots = 148LL * GRAV_AB_MINB;
     const int64_t bc_ctas = (int64_t)((ncol + kAbWarps * 32 - 1) / (kAbWarps * 32)) * ((p->nz + tz_bc - 1) / tz_bc);
-    z.bc = (GRAV_AB_FORCE >= 0) ? GRAV_AB_FORCE : (bc_ctas >= slots ? 1 : 0);
+    const int64_t part_cap = std::max<int64_t>(1, (512ll << 20) / (8 * std::max<int64_t>(p->M, 1)));
+    const bool bc_fills = bc_ctas >= slots || bc_ctas * std::min<int64_t>(part_cap, p->N / 64) >= slots;
+    z.bc = (GRAV_AB_FORCE >= 0) ? GRAV_AB_FORCE : (bc_fills ? 1 : 0);
     // run-time override of the layout choice: GRAV_ADJOINT_LAYOUT=broadcast|shuffle|auto
     if (const char *env = std::getenv("GRAV_ADJOINT_LAYOUT")) {
         if (std::strcmp(env, "broadcast") == 0) z.bc = 1;
@@ -1888,18 +1896,46 @@ static MixedSizes mixed_sizes(const grav_plan *p) {
     z.tz = z.bc ? tz_bc : adj_tz(p->nz, ncol, p->N);
     z.ngz = (p->nz + z.tz - 1) / z.tz;
     int64_t nsch, stage;
+    bool modelled = false;
     if (z.bc) {
         nsch = std::max<int64_t>(1, (32 * slots + bc_ctas - 1) / bc_ctas);
-        nsch = std::min<int64_t>(nsch, std::max<int64_t>(1, (512ll << 20) / (8 * std::max<int64_t>(p->M, 1))));
+        nsch = std::min<int64_t>(nsch, part_cap);
         stage = kAbStage;
+        const int64_t nsch_stages = std::min<int64_t>(nsch, (p->N + stage - 1) / stage);
+        if (bc_ctas * nsch_stages < 8 * slots && p->N >= 64) {
+            // fewer than 8 waves with whole 1024-station stages: chunks of any
+            // multiple of 32 stations (>= 64), the count minimising a list-
+            // scheduling model in units of one station through a full
+            // 16-layer group: total work / slots + the longest CTA (the
+            // groups differ in size, so one tight wave leaves slots idle) +
+            // each CTA's fixed cost (~32 stations) + the finish kernel's read
+            // of the chunk partials (M doubles per chunk, ~M / 2e5)
+            const int ngz_bc = (p->nz + tz_bc - 1) / tz_bc;
+            const double layers = (double)(tz_bc * (ngz_bc - 1) + adj_tzl_bc(p->nz)) / tz_bc;   // groups' work
+            const int64_t cblocks = (ncol + kAbWarps * 32 - 1) / (kAbWarps * 32);
+            double best = 1e300;
+            int64_t best_n = 1;
+            const int64_t hi = std::min<int64_t>(part_cap, p->N / 64);
+            for (int64_t n = 1; n <= std::max<int64_t>(1, hi); ++n) {
+                int64_t len = (p->N + n - 1) / n;
+                len = (len + 31) / 32 * 32;
+                const int64_t ns = (p->N + len - 1) / len;
+                const double work = (double)ns * (double)cblocks * layers * (double)(len + 32);
+                const double c = work / (double)slots + (double)(len + 32) + (double)ns * (double)p->M / 2e5;
+                if (c < best) { best = c; best_n = n; }
+            }
+            nsch = best_n;
+            stage = 32;
+            modelled = true;
+        }
     } else {
         const int64_t groups_ctas = ((int64_t)ncol * z.ngz + kMaWarps - 1) / kMaWarps;
         nsch = std::max<int64_t>(1, (148LL * 8 + groups_ctas - 1) / groups_ctas);
         stage = kMaStage;
     }
-    nsch = std::min<int64_t>(nsch, (p->N + stage - 1) / stage);
+    if (!modelled) nsch = std::min<int64_t>(nsch, (p->N + stage - 1) / stage);
     int64_t len = (p->N + nsch - 1) / nsch;
-    len = (len + stage - 1) / stage * stage;   // keeps every chunk start 16-byte aligned
+    len = (len + stage - 1) / stage * stage;   // keeps every chunk start 16-byte aligned (stage even)
     z.schunk_len = len;
     z.nschunk = (int)((p->N + len - 1) / len);
     z.nbins = p->ng.nbx * p->ng.nby;
