@@ -580,8 +580,8 @@ def serve_replay(g, torch, n_jobs, rate, slots):
             "results": {str(k): results.count(k) for k in sorted(set(results))},
             "fp64_rel_err": {"jobs_checked": len(errs), "stations_per_job": 16,
                              "median": pct(errs, 50), "max": max(errs) if errs else None,
-                             "what": "max |mixed - FP64| / max |FP64| of each job's output (forward: d; "
-                                     "inversion: G m_out) at 16 stations"},
+                             "what": "max |mixed - FP64| of each job's output (forward: d; inversion: G m_out) "
+                                     "at 16 stations, relative to max |g| over the job's survey"},
             "pairs_per_forward_pass_total": pairs, "pairs_evaluated": pairs_done,
             "achieved_pairs_per_s": pairs_done / wall, "data": "synthetic",
             "config": {"workload": "serving mix: 50k-500k cubic prisms (25-100 m), 1k-20k stations, "

@@ -155,8 +155,9 @@ typedef struct {
     int outer;                 /* outer updates performed (outer_max > 0) */
     double alpha_min;          /* smallest accepted step length of the outer loop (1 if never backtracked) */
     int restarts;              /* single CG solve: restarts from the recomputed true residual */
-    double fp64_rel_err;       /* check_stations > 0: max |mixed - FP64| / max |FP64| over the checked stations;
-                                  -1 when not checked */
+    double fp64_rel_err;       /* check_stations > 0: max |mixed - FP64| over the checked stations relative to
+                                  max |g|: the larger of max |FP64| there and max |d_i| over every station
+                                  (see grav_plan_check_fp64); -1 when not checked */
     double nys_shift;          /* precond = 2: the shift nu / lambda the Nystrom factorisation needed
                                   (1e-3 unless T lost definiteness); 0 otherwise */
     double nys_setup_s;        /* precond = 2: wall time of the preconditioner's set-up (sketch, Gram
@@ -371,7 +372,9 @@ int grav_forward_fp64_noalloc(const grav_mesh *mesh, const grav_survey *survey, 
  * d (DEVICE, survey n doubles) is compared at n_check evenly spaced stations
  * (index floor(k n / n_check)) with G m evaluated in FP64 (Eq. 1-3, node
  * shared) on those stations alone.  m: DEVICE, M doubles.  *max_abs_err and
- * *rel_err (HOST; max |d - d64| and that over max |d64|) may be NULL.
+ * *rel_err (HOST; max |d - d64| at the checked stations, and that over max |g|,
+ * taken as the larger of max |d64| there and max |d_i| over all n stations, so
+ * that a sample missing the anomaly does not inflate it) may be NULL.
  * Synchronises `stream`.  Costs n_check / N of one FP64 forward product.
  * 1 <= n_check <= n, else GRAV_EINVAL. */
 int grav_plan_check_fp64(grav_plan *plan, const double *m, const double *d, int n_check, double *max_abs_err,

@@ -272,6 +272,9 @@ void launch_mixed_adj_finish(const grav_plan *p, const double *r, int depth_weig
                              double *out, cudaStream_t s);
 void launch_mixed_diag(const grav_plan *p, double *diag, cudaStream_t s);
 size_t mixed_scratch_bytes(const grav_plan *p);
+// *bits = bit pattern of max |v_i| (a non-negative double), for n doubles on the device
+void launch_absmax(const double *v, int64_t n, unsigned long long *bits, cudaStream_t s);
+int mixed_fwd_tail(const grav_plan *p);   // 1: the far-field forward runs the layers left after groups of 4
 int mixed_adj_last_group(const grav_plan *p);
 // out_{x,y,z}[k] = s{x,y,z}[i_k], out_d[k] = d[i_k], i_k = floor(k n / n_check)
 void launch_gather_check(const double *sx, const double *sy, const double *sz, const double *d, int64_t n,

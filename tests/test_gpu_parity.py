@@ -728,6 +728,10 @@ def test_fp64_error_statement(g):
     dd = d.cpu().numpy()[idx]
     assert abs(ea - np.abs(dd - d_ref).max()) <= 1e-10 * np.abs(d_ref).max()
     assert 0 < er <= TOLMIX
+    # relative to max |g|: the larger of the checked stations' FP64 values and
+    # the product's largest magnitude over every station
+    scale = max(np.abs(d_ref).max(), np.abs(d.cpu().numpy()).max())
+    assert abs(er - ea / scale) <= 1e-12 * er
     plan.close()
     p64 = g.Plan(wl.mesh, S)
     assert p64.check_fp64(m, p64.forward(m), 16)[1] <= 1e-13
