@@ -144,7 +144,17 @@ constexpr int kFnLog = 0;                               // [3 j + 0..2] = 1/F, l
 constexpr int kFnLn2 = kFnLog + 3 * (kFnLogJ + 1);      // ln 2 hi, ln 2 lo
 constexpr int kFnAtanJ = 64;                            // atan table: c = j/64, j = 0..64
 constexpr int kFnAtan = kFnLn2 + 2;                     // [4 j + 0..3] = atan c hi, lo, pi/2 - atan c hi, lo
-constexpr int kFnTableSize = kFnAtan + 4 * (kFnAtanJ + 1);
+constexpr int kFnDf = kFnAtan + 4 * (kFnAtanJ + 1);     // start of the FP32 table of the double-float functions
+// double-float tables (FP32 offsets from T + kFnDf): ln c and 1/c for
+// c = 1 + j/128, atan(j/64), ln 2, pi/2, each as a high + low float
+constexpr int kDfLogJ = 128;
+constexpr int kDfLog = 0;                               // [4 j + 0..3] = ln c hi, lo, 1/c hi, lo
+constexpr int kDfAtanJ = 64;
+constexpr int kDfAtan = kDfLog + 4 * (kDfLogJ + 1);     // [2 j + 0..1] = atan(j/64) hi, lo
+constexpr int kDfLn2 = kDfAtan + 2 * (kDfAtanJ + 1);    // ln 2 hi, lo
+constexpr int kDfPio2 = kDfLn2 + 2;                     // pi/2 hi, lo
+constexpr int kDfTableFloats = kDfPio2 + 2;
+constexpr int kFnTableSize = kFnDf + (kDfTableFloats + 1) / 2;
 
 __device__ __forceinline__ double log64(double x, const double *__restrict__ T) {
     const long long b = __double_as_longlong(x);
@@ -225,6 +235,142 @@ __device__ __forceinline__ float psi32(float x, float y, float z) {
     if (y >= 0.0f) ry = R + y; else ry = (x2 + z2) / (R - y);
     if (x >= 0.0f) rx = R + x; else rx = (y2 + z2) / (R - x);
     return t_atan - x * logf(ry) - y * logf(rx);
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic (T. J. Dekker, "A floating-point technique for
+// extending the available precision", Numer. Math. 18 (1971) 224-242; Knuth's
+// TwoSum): a value is the unevaluated sum hi + lo of two FP32 numbers,
+// |lo| <= ulp(hi)/2, about 44-48 significant bits, computed on the FP32 pipe
+// (64x the FP64 rate on this GPU).  The rounded intrinsics keep the compiler
+// from contracting the error-free transformations into FMAs.
+// ---------------------------------------------------------------------------
+struct df32 {
+    float hi, lo;
+};
+__device__ __forceinline__ df32 df_make(float hi, float lo) {
+    df32 r;
+    r.hi = hi;
+    r.lo = lo;
+    return r;
+}
+// |a| >= |b| or a = 0: s + e = a + b exactly
+__device__ __forceinline__ df32 df_fast2sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return df_make(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ df32 df_2sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return df_make(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ df32 df_2prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return df_make(p, __fmaf_rn(a, b, -p));
+}
+__device__ __forceinline__ df32 df_add(df32 a, df32 b) {
+    const df32 s = df_2sum(a.hi, b.hi);
+    return df_fast2sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df32 df_neg(df32 a) { return df_make(-a.hi, -a.lo); }
+__device__ __forceinline__ df32 df_sub(df32 a, df32 b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df32 df_mul(df32 a, df32 b) {
+    const df32 p = df_2prod(a.hi, b.hi);
+    return df_fast2sum(p.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo)));
+}
+__device__ __forceinline__ df32 df_mulf(df32 a, float b) {
+    const df32 p = df_2prod(a.hi, b);
+    return df_fast2sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+__device__ __forceinline__ df32 df_sqr(df32 a) {
+    const df32 p = df_2prod(a.hi, a.hi);
+    return df_fast2sum(p.hi, __fmaf_rn(__fmul_rn(2.0f, a.hi), a.lo, p.lo));
+}
+// a / b: the FP32 quotient, then two corrections from the residual a - b q
+__device__ __forceinline__ df32 df_div(df32 a, df32 b) {
+    const float r = __frcp_rn(b.hi);
+    const float q1 = __fmul_rn(a.hi, r);
+    const float q2 = __fmul_rn(df_sub(a, df_mulf(b, q1)).hi, r);
+    const df32 q = df_fast2sum(q1, q2);
+    const float q3 = __fmul_rn(df_sub(a, df_mul(b, q)).hi, r);
+    return df_add(q, df_make(q3, 0.0f));
+}
+// sqrt(a), a >= 0: the FP32 root and one correction from the residual
+__device__ __forceinline__ df32 df_sqrt(df32 a) {
+    if (!(a.hi > 0.0f)) return df_make(0.0f, 0.0f);
+    const float s = __fsqrt_rn(a.hi);
+    const df32 p = df_2prod(s, s);
+    const float d = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p.hi), p.lo), a.lo);
+    return df_fast2sum(s, __fmul_rn(d, __fmul_rn(0.5f, __frcp_rn(s))));
+}
+__device__ __forceinline__ df32 df_from_double(double x) {
+    const float h = __double2float_rn(x);
+    return df_make(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ double df_to_double(df32 a) { return (double)a.hi + (double)a.lo; }
+
+// ln a for a double-float a > 0 (a.hi normal): the table method of log64
+// (Tang, 1990) in double-float.  a = 2^e m, c = 1 + j/128 nearest to m,
+// f = (m - c + a.lo 2^-e) / c with |f| <= 2^-8, ln a = e ln 2 + ln c +
+// ln(1 + f), ln(1 + f) = f - f^2/2 (double-float) + f^3 (1/3 - f/4 + f^2/5 -
+// f^3/6 + f^4/7) (FP32; the first term left out, f^8/8, is below 2^-66).
+// D = T + kFnDf as floats.
+__device__ __forceinline__ df32 df_log(df32 a, const float *__restrict__ D) {
+    const int b = __float_as_int(a.hi);
+    const int e = ((b >> 23) & 0xff) - 127;
+    const int mb = b & 0x7fffff;
+    const float m = __int_as_float(mb | 0x3f800000);            // [1, 2)
+    const int j = (mb + (1 << 15)) >> 16;                        // 0 .. 128
+    const float c = __fmaf_rn((float)j, 1.0f / kDfLogJ, 1.0f);   // exact
+    const df32 u = df_2sum(__fsub_rn(m, c), ldexpf(a.lo, -e));   // m - c exact
+    const df32 f = df_mul(u, df_make(__ldg(D + kDfLog + 4 * j + 2), __ldg(D + kDfLog + 4 * j + 3)));
+    const float fh = f.hi;
+    float p = __fmaf_rn(1.0f / 7.0f, fh, -1.0f / 6.0f);
+    p = __fmaf_rn(p, fh, 1.0f / 5.0f);
+    p = __fmaf_rn(p, fh, -0.25f);
+    p = __fmaf_rn(p, fh, 1.0f / 3.0f);
+    const float f3 = __fmul_rn(__fmul_rn(__fmul_rn(fh, fh), fh), p);
+    const df32 f2 = df_sqr(f);
+    df32 r = df_add(f, df_make(-0.5f * f2.hi, -0.5f * f2.lo));
+    r = df_add(r, df_make(f3, 0.0f));
+    const df32 t = df_add(df_mulf(df_make(__ldg(D + kDfLn2), __ldg(D + kDfLn2 + 1)), (float)e),
+                          df_make(__ldg(D + kDfLog + 4 * j), __ldg(D + kDfLog + 4 * j + 1)));
+    return df_add(t, r);
+}
+
+// atan(a / b) for b > 0 in double-float: the reduction of atan_ratio64 —
+// v = min(|a|, b) / max(|a|, b), c = j/64 nearest, atan v = atan c + atan w,
+// w = (p - c q) / (q + c p), |w| <= 2^-7, atan w = w + w^3 (-1/3 + w^2/5 -
+// w^4/7) (the cubic part in FP32; w^9/9 is below 2^-65); for |a| > b,
+// atan(a/b) = sign(a) (pi/2 - atan(b/|a|)).
+__device__ __forceinline__ df32 df_atan_ratio(df32 a, df32 b, const float *__restrict__ D) {
+    const bool neg = a.hi < 0.0f;
+    const df32 pa = neg ? df_neg(a) : a;
+    const bool big = pa.hi > b.hi;
+    const df32 p = big ? b : pa, q = big ? pa : b;
+    int j = __float2int_rn(__fmul_rn(__fdividef(p.hi, q.hi), (float)kDfAtanJ));
+    j = min(max(j, 0), kDfAtanJ);
+    const float c = (float)j * (1.0f / kDfAtanJ);   // exact
+    const df32 w = df_div(df_sub(p, df_mulf(q, c)), df_add(q, df_mulf(p, c)));
+    const float wh = w.hi, w2 = __fmul_rn(wh, wh);
+    float r = __fmaf_rn(w2, -1.0f / 7.0f, 1.0f / 5.0f);
+    r = __fmaf_rn(r, w2, -1.0f / 3.0f);
+    df32 s = df_add(w, df_make(__fmul_rn(__fmul_rn(wh, w2), r), 0.0f));
+    s = df_add(df_make(__ldg(D + kDfAtan + 2 * j), __ldg(D + kDfAtan + 2 * j + 1)), s);
+    if (big) s = df_sub(df_make(__ldg(D + kDfPio2), __ldg(D + kDfPio2 + 1)), s);
+    return neg ? df_neg(s) : s;
+}
+
+// Eq. 2-3 in double-float, with the same cancellation-free logarithm forms
+// and limits as psi64 (z > 0).  Error about 2^-45 of R (|ln R| + 1); the
+// near-field set-up needs about 2^-39 for the FP32 entries of its table.
+__device__ __forceinline__ df32 psi_df(df32 x, df32 y, df32 z, const float *__restrict__ D) {
+    const df32 x2 = df_sqr(x), y2 = df_sqr(y), z2 = df_sqr(z);
+    const df32 R = df_sqrt(df_add(df_add(x2, y2), z2));
+    const df32 ta = df_mul(z, df_atan_ratio(df_mul(x, y), df_mul(z, R), D));
+    const df32 ry = (y.hi >= 0.0f) ? df_add(R, y) : df_div(df_add(x2, z2), df_sub(R, y));
+    const df32 rx = (x.hi >= 0.0f) ? df_add(R, x) : df_div(df_add(y2, z2), df_sub(R, x));
+    return df_sub(df_sub(ta, df_mul(x, df_log(ry, D))), df_mul(y, df_log(rx, D)));
 }
 
 // ---------------------------------------------------------------------------

@@ -659,6 +659,21 @@ void fill_fn_table(double *t) {
         t[kFnAtan + 4 * j + 2] = (double)b;
         t[kFnAtan + 4 * j + 3] = (double)(b - (long double)(double)b);
     }
+    // double-float tables: each value as a high float and the float nearest
+    // to the remainder
+    float *f = reinterpret_cast<float *>(t + kFnDf);
+    auto split32 = [&](long double v, float *out) {
+        out[0] = (float)v;
+        out[1] = (float)(v - (long double)out[0]);
+    };
+    for (int j = 0; j <= kDfLogJ; ++j) {
+        const long double c = 1.0L + (long double)j / kDfLogJ;
+        split32(logl(c), f + kDfLog + 4 * j);
+        split32(1.0L / c, f + kDfLog + 4 * j + 2);
+    }
+    for (int j = 0; j <= kDfAtanJ; ++j) split32(atanl((long double)j / kDfAtanJ), f + kDfAtan + 2 * j);
+    split32(logl(2.0L), f + kDfLn2);
+    split32(half_pi, f + kDfPio2);
 }
 
 }  // namespace grav

@@ -782,14 +782,47 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
     // plus half a cell diagonal, squared, with a margin).  The nodes that pass
     // are queued (warp ballot) and evaluated 32 at a time, so the FP64 work
     // follows the window's hemisphere (~half the box) with every lane busy.
-    int *queue = reinterpret_cast<int *>(reinterpret_cast<double *>(smem_raw) + (size_t)nwarps * nnode) +
-                 (CORNER ? (size_t)nwarps * nnode : 0) + (size_t)warp * 64;
+    int *queue0 = reinterpret_cast<int *>(reinterpret_cast<double *>(smem_raw) + (size_t)nwarps * nnode) +
+                  (CORNER ? (size_t)nwarps * nnode : 0);
+    int *queue = queue0 + (size_t)warp * 64;
+    // Without CORNER, Psi runs in double-float (psi_df, ~2^-45 of R ln R; the
+    // FP32 entries of the table need ~2^-39) from the node offsets of the
+    // window box, split once per station into double-float in shared memory;
+    // P then holds (hi, lo) pairs.  CORNER keeps the FP64 corner function.
+    const int ncrd = nbx1 + nby1 + ng.bz + 1;
+    float2 *crd = reinterpret_cast<float2 *>(queue0 + (size_t)nwarps * 64) + (size_t)warp * ncrd;
+    float2 *P2 = reinterpret_cast<float2 *>(P);
+    const float *Ddf = reinterpret_cast<const float *>(g.fn + kFnDf);
+    if (!CORNER) {
+        for (int u = lane; u < ncrd; u += 32) {
+            double v = 0.0;
+            if (u < nbx1) {
+                const int ia = i0 + u;
+                v = (ia >= 0 && ia <= g.nx) ? g.xe[ia] - xs : 0.0;
+            } else if (u < nbx1 + nby1) {
+                const int jb = j0 + u - nbx1;
+                v = (jb >= 0 && jb <= g.ny) ? g.ye[jb] - ys : 0.0;
+            } else {
+                const int c = u - nbx1 - nby1;
+                v = (c <= g.nz) ? g.ze[c] - zs : 0.0;
+            }
+            const df32 dv = df_from_double(v);
+            crd[u] = make_float2(dv.hi, dv.lo);
+        }
+        __syncwarp();
+    }
     auto psi_node = [&](int t) {
-        const int ia = i0 + t % nbx1;
-        const int jb = j0 + (t / nbx1) % nby1;
+        const int ta = t % nbx1;
+        const int tb = (t / nbx1) % nby1;
         const int c = t / (nbx1 * nby1);
-        const double x = g.xe[ia] - xs, y = g.ye[jb] - ys, z = g.ze[c] - zs;
-        P[t] = psi64(x, y, z, x * x, y * y, z * z, g.fn);
+        if (CORNER) {
+            const double x = g.xe[i0 + ta] - xs, y = g.ye[j0 + tb] - ys, z = g.ze[c] - zs;
+            P[t] = psi64(x, y, z, x * x, y * y, z * z, g.fn);
+        } else {
+            const float2 X = crd[ta], Y = crd[nbx1 + tb], Z = crd[nbx1 + nby1 + c];
+            const df32 v = psi_df(df_make(X.x, X.y), df_make(Y.x, Y.y), df_make(Z.x, Z.y), Ddf);
+            P2[t] = make_float2(v.hi, v.lo);
+        }
     };
     int qn = 0;   // queued nodes (warp-uniform)
     for (int t0 = 0; t0 < nnode; t0 += 32) {
@@ -844,12 +877,14 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
     const double r2max = (ng.radius_cells * ng.width) * (ng.radius_cells * ng.width);
     const int sxs = 1, sys = nbx1, szs = nbx1 * nby1;
     double dcorr = 0.0;
+    const df32 gam_df = df_from_double(kGammaMgal), vol_df = df_from_double(vol_mgal),
+               ivol_df = df_from_double(1.0 / vol_mgal);
     for (int t = lane; t < ng.slots; t += 32) {
         const int ai = t % ng.bx;
         const int bj = (t / ng.bx) % ng.by;
         const int l = t / (ng.bx * ng.by);
         const int i = i0 + ai, j = j0 + bj;
-        double val = 0.0;
+        float dgv = 0.0f;
         if (i >= 0 && i < g.nx && j >= 0 && j < g.ny && l < g.nz) {
             const double xc = 0.5 * (g.xe[i] + g.xe[i + 1]) - xs;
             const double yc = 0.5 * (g.ye[j] + g.ye[j + 1]) - ys;
@@ -857,32 +892,49 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
             if (xc * xc + yc * yc + zc * zc < r2max) {
                 const int n0 = ai + sys * bj + szs * l;
                 // sigma(n, k) = -(-1)^(da+db+dc) for the vertex (i+da, j+db, l+dc)
-                const double E = -P[n0] + P[n0 + sxs] + P[n0 + sys] - P[n0 + sxs + sys] + P[n0 + szs] -
-                                 P[n0 + sxs + szs] - P[n0 + sys + szs] + P[n0 + sxs + sys + szs];
-                const double gex = kGammaMgal * E;
-                double gfar;
                 if (CORNER) {
+                    const double E = -P[n0] + P[n0 + sxs] + P[n0 + sys] - P[n0 + sxs + sys] + P[n0 + szs] -
+                                     P[n0 + sxs + szs] - P[n0 + sys + szs] + P[n0 + sxs + sys + szs];
+                    const double gex = kGammaMgal * E;
                     const double E32 = -(double)P32[n0] + (double)P32[n0 + sxs] + (double)P32[n0 + sys] -
                                        (double)P32[n0 + sxs + sys] + (double)P32[n0 + szs] -
                                        (double)P32[n0 + sxs + szs] - (double)P32[n0 + sys + szs] +
                                        (double)P32[n0 + sxs + sys + szs];
-                    gfar = kGammaMgal * E32;
+                    const double gfar = kGammaMgal * E32;
+                    const double val = gex - gfar;
+                    dgv = (float)(val / vol_mgal);
+                    dcorr += w2[l] * (gex * gex - gfar * gfar);
                 } else {
+                    // double-float: neighbouring nodes are differenced first (x,
+                    // then the y and z pairs of those), so each subtraction of
+                    // nearly equal values is done exactly by TwoSum
+                    auto Pd = [&](int n) {
+                        const float2 v = P2[n];
+                        return df_make(v.x, v.y);
+                    };
+                    const df32 ex0 = df_sub(Pd(n0 + sxs), Pd(n0));
+                    const df32 ex1 = df_sub(Pd(n0 + sxs + sys), Pd(n0 + sys));
+                    const df32 ex2 = df_sub(Pd(n0 + sxs + szs), Pd(n0 + szs));
+                    const df32 ex3 = df_sub(Pd(n0 + sxs + sys + szs), Pd(n0 + sys + szs));
+                    const df32 E = df_sub(df_sub(ex0, ex1), df_sub(ex2, ex3));
+                    const df32 gex = df_mul(E, gam_df);
                     const float2 X = make_float2(mg.cx[2 * i], mg.cx[2 * i + 1]);
                     const float2 Y = make_float2(mg.cy[2 * j], mg.cy[2 * j + 1]);
                     const float h2 = far_h2(X, Y, S.x, S.y, S.z, S.w);
                     const float ph = far_ph(X, Y, S.x, S.y, S.z, S.w, mg.qa, mg.qb);
                     const float dz = mg.czc[l] - zf;
                     const float R2 = fmaf(dz, dz, h2);
-                    gfar = vol_mgal * (double)far_kernel_q(dz, R2, mg.qg, ph);
+                    const df32 gfar = df_mulf(vol_df, far_kernel_q(dz, R2, mg.qg, ph));
+                    const df32 v = df_sub(gex, gfar);
+                    dgv = df_mul(v, ivol_df).hi;
+                    // gex^2 - gfar^2 = (gex - gfar)(gex + gfar)
+                    dcorr += w2[l] * (double)(v.hi * (gex.hi + gfar.hi));
                 }
-                val = gex - gfar;
-                dcorr += w2[l] * (gex * gex - gfar * gfar);
             }
         }
-        // formed in FP64, stored in FP32 per unit q = gamma V rho (so the products
-        // use the FP32 q of the far field); relative rounding 6e-8
-        dG[s * ng.ld + t] = (float)(val / vol_mgal);
+        // formed in FP64 (double-float), stored in FP32 per unit q = gamma V rho
+        // (so the products use the FP32 q of the far field); relative rounding 6e-8
+        dG[s * ng.ld + t] = dgv;
     }
     if (lane < ng.ld - ng.slots) dG[s * ng.ld + ng.slots + lane] = 0.0f;   // row padding
     dcorr = warp_sum(dcorr);
@@ -2056,8 +2108,9 @@ static void *take(grav_plan *p, size_t bytes) {
 }
 
 int near_setup_warps(const grav_plan *p) {
-    const size_t per_node = p->opt.precision == GRAV_MIXED_CORNER ? 12 : 8;   // FP64 (+ FP32) corner values
-    const size_t per_warp = (size_t)(p->ng.bx + 1) * (p->ng.by + 1) * (p->ng.bz + 1) * per_node + 256;   // + node queue
+    const size_t per_node = p->opt.precision == GRAV_MIXED_CORNER ? 12 : 8;   // FP64 (+ FP32) or double-float values
+    const size_t per_warp = (size_t)(p->ng.bx + 1) * (p->ng.by + 1) * (p->ng.bz + 1) * per_node + 256 +   // + node queue
+                            8ull * (p->ng.bx + p->ng.by + p->ng.bz + 3);   // + box node offsets (double-float)
     const size_t cap = 200 * 1024;
     return (int)std::min<size_t>(kNsWarps, cap / per_warp);
 }
@@ -2206,7 +2259,7 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
     k_prep_stations<<<grid_for(p->N, 256), 256, 0, s>>>(p->sx, p->sy, p->sz, p->N, xref, yref, p->st32, p->stz);
 
     const int nnode = (p->ng.bx + 1) * (p->ng.by + 1) * (p->ng.bz + 1);
-    const size_t smem = (size_t)ns_warps * (nnode * (corner ? 12 : 8) + 256);
+    const size_t smem = (size_t)ns_warps * (nnode * (corner ? 12 : 8) + 256 + 8ull * (p->ng.bx + p->ng.by + p->ng.bz + 3));
     const double vol_mgal = kGammaMgal * p->cell_a * p->cell_b * p->cell_c;
     // nodes within the window radius plus half a cell diagonal (relative margin 1e-9)
     const double node_r = (p->ng.radius_cells * p->ng.width +
