@@ -422,8 +422,12 @@ int grav_selftest_wait(grav_ctx *ctx, double limit_ms, grav_stream_t stream);
 /* Self-check of the FP64 elementary functions inside Eq. 2-3 (the paper has
  * no counterpart): out[i] = f(a[i], b[i]) on ctx's device, with fn = 0 this
  * library's log(a), 1 its atan(a / b) (b > 0), 2 CUDA's log(a), 3 CUDA's
- * atan(a / b).  a, b (fn 1 and 3 only), out: DEVICE, n doubles.  Enqueued on
- * `stream`; GRAV_EINVAL for a bad fn, n < 0 or NULL pointers. */
+ * atan(a / b); and the double-float (FP32 pair) forms the near-field set-up
+ * uses, arguments rounded to double-float and results returned as hi + lo:
+ * 4 log(a), 5 atan(a / b) (b > 0), 6 Psi(x, y, z) of Eq. 2-3 with x = a[i],
+ * y = b[i], z = a[n + i] > 0 (a holds 2n doubles for fn 6).  a, b (fn 1, 3,
+ * 5 and 6), out: DEVICE, n doubles.  Enqueued on `stream`; GRAV_EINVAL for a
+ * bad fn, n < 0 or NULL pointers. */
 int grav_eval_fn64(grav_ctx *ctx, int fn, const double *a, const double *b, double *out, int64_t n,
                    grav_stream_t stream);
 

@@ -147,16 +147,19 @@ STAGES = ("fwd_main", "adj_main", "fwd_near", "adj_near")
 
 
 def eval_fn64(fn: str, a, b=None, stream=None, ctx: Optional["Context"] = None):
-    """Self-check hook: the library's FP64 log(a) / atan(a / b) ("log", "atan")
-    or CUDA's ("cuda_log", "cuda_atan") on CUDA float64 tensors."""
+    """Self-check hook: the library's FP64 log(a) / atan(a / b) ("log", "atan"),
+    CUDA's ("cuda_log", "cuda_atan"), or the double-float forms of the
+    near-field set-up ("df_log", "df_atan", and "df_psi" with a = (x, z)
+    concatenated, b = y) on CUDA float64 tensors."""
     torch = _torch()
     ctx = ctx or context()
-    code = {"log": 0, "atan": 1, "cuda_log": 2, "cuda_atan": 3}[fn]
+    code = {"log": 0, "atan": 1, "cuda_log": 2, "cuda_atan": 3, "df_log": 4, "df_atan": 5, "df_psi": 6}[fn]
+    n = a.numel() // 2 if code == 6 else a.numel()
     a = _f64(a, a.numel(), "a")
-    b = _f64(b, a.numel(), "b") if b is not None else None
-    out = torch.empty_like(a)
+    b = _f64(b, n, "b") if b is not None else None
+    out = torch.empty(n, dtype=torch.float64, device=a.device)
     ctx.check(_lib.grav_eval_fn64(ctx.h, code, a.data_ptr(), b.data_ptr() if b is not None else None,
-                                  out.data_ptr(), a.numel(), _stream(stream)))
+                                  out.data_ptr(), n, _stream(stream)))
     return out
 
 

@@ -146,11 +146,11 @@ constexpr int kFnAtanJ = 64;                            // atan table: c = j/64,
 constexpr int kFnAtan = kFnLn2 + 2;                     // [4 j + 0..3] = atan c hi, lo, pi/2 - atan c hi, lo
 constexpr int kFnDf = kFnAtan + 4 * (kFnAtanJ + 1);     // start of the FP32 table of the double-float functions
 // double-float tables (FP32 offsets from T + kFnDf): ln c and 1/c for
-// c = 1 + j/128, atan(j/64), ln 2, pi/2, each as a high + low float
-constexpr int kDfLogJ = 128;
+// c = 1 + j/256, atan(j/256), ln 2, pi/2, each as a high + low float
+constexpr int kDfLogJ = 256;
 constexpr int kDfLog = 0;                               // [4 j + 0..3] = ln c hi, lo, 1/c hi, lo
-constexpr int kDfAtanJ = 64;
-constexpr int kDfAtan = kDfLog + 4 * (kDfLogJ + 1);     // [2 j + 0..1] = atan(j/64) hi, lo
+constexpr int kDfAtanJ = 256;
+constexpr int kDfAtan = kDfLog + 4 * (kDfLogJ + 1);     // [2 j + 0..1] = atan(j/256) hi, lo
 constexpr int kDfLn2 = kDfAtan + 2 * (kDfAtanJ + 1);    // ln 2 hi, lo
 constexpr int kDfPio2 = kDfLn2 + 2;                     // pi/2 hi, lo
 constexpr int kDfTableFloats = kDfPio2 + 2;
@@ -310,17 +310,17 @@ __device__ __forceinline__ df32 df_from_double(double x) {
 __device__ __forceinline__ double df_to_double(df32 a) { return (double)a.hi + (double)a.lo; }
 
 // ln a for a double-float a > 0 (a.hi normal): the table method of log64
-// (Tang, 1990) in double-float.  a = 2^e m, c = 1 + j/128 nearest to m,
-// f = (m - c + a.lo 2^-e) / c with |f| <= 2^-8, ln a = e ln 2 + ln c +
+// (Tang, 1990) in double-float.  a = 2^e m, c = 1 + j/256 nearest to m,
+// f = (m - c + a.lo 2^-e) / c with |f| <= 2^-9, ln a = e ln 2 + ln c +
 // ln(1 + f), ln(1 + f) = f - f^2/2 (double-float) + f^3 (1/3 - f/4 + f^2/5 -
-// f^3/6 + f^4/7) (FP32; the first term left out, f^8/8, is below 2^-66).
+// f^3/6 + f^4/7) (FP32, ~2^-53 absolute; f^8/8 is below 2^-74).
 // D = T + kFnDf as floats.
 __device__ __forceinline__ df32 df_log(df32 a, const float *__restrict__ D) {
     const int b = __float_as_int(a.hi);
     const int e = ((b >> 23) & 0xff) - 127;
     const int mb = b & 0x7fffff;
     const float m = __int_as_float(mb | 0x3f800000);            // [1, 2)
-    const int j = (mb + (1 << 15)) >> 16;                        // 0 .. 128
+    const int j = (mb + (1 << 14)) >> 15;                        // 0 .. 256
     const float c = __fmaf_rn((float)j, 1.0f / kDfLogJ, 1.0f);   // exact
     const df32 u = df_2sum(__fsub_rn(m, c), ldexpf(a.lo, -e));   // m - c exact
     const df32 f = df_mul(u, df_make(__ldg(D + kDfLog + 4 * j + 2), __ldg(D + kDfLog + 4 * j + 3)));
@@ -339,9 +339,10 @@ __device__ __forceinline__ df32 df_log(df32 a, const float *__restrict__ D) {
 }
 
 // atan(a / b) for b > 0 in double-float: the reduction of atan_ratio64 —
-// v = min(|a|, b) / max(|a|, b), c = j/64 nearest, atan v = atan c + atan w,
-// w = (p - c q) / (q + c p), |w| <= 2^-7, atan w = w + w^3 (-1/3 + w^2/5 -
-// w^4/7) (the cubic part in FP32; w^9/9 is below 2^-65); for |a| > b,
+// v = min(|a|, b) / max(|a|, b), c = j/256 nearest, atan v = atan c + atan w,
+// w = (p - c q) / (q + c p), |w| <= 2^-9, atan w = w + w^3 (-1/3 + w^2/5 -
+// w^4/7) (the cubic part in FP32 at w.hi, with its first-order term in w.lo;
+// w^9/9 is below 2^-65); for |a| > b,
 // atan(a/b) = sign(a) (pi/2 - atan(b/|a|)).
 __device__ __forceinline__ df32 df_atan_ratio(df32 a, df32 b, const float *__restrict__ D) {
     const bool neg = a.hi < 0.0f;
@@ -355,7 +356,9 @@ __device__ __forceinline__ df32 df_atan_ratio(df32 a, df32 b, const float *__res
     const float wh = w.hi, w2 = __fmul_rn(wh, wh);
     float r = __fmaf_rn(w2, -1.0f / 7.0f, 1.0f / 5.0f);
     r = __fmaf_rn(r, w2, -1.0f / 3.0f);
-    df32 s = df_add(w, df_make(__fmul_rn(__fmul_rn(wh, w2), r), 0.0f));
+    // cubic part at wh (its FP32 rounding: ~2^-43 of w at |w| = 2^-9, the
+    // reason for the 256-entry table), plus its first-order change with w.lo
+    df32 s = df_add(w, df_make(__fmaf_rn(__fmul_rn(wh, w2), r, -__fmul_rn(w2, w.lo)), 0.0f));
     s = df_add(df_make(__ldg(D + kDfAtan + 2 * j), __ldg(D + kDfAtan + 2 * j + 1)), s);
     if (big) s = df_sub(df_make(__ldg(D + kDfPio2), __ldg(D + kDfPio2 + 1)), s);
     return neg ? df_neg(s) : s;

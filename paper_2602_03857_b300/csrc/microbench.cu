@@ -159,7 +159,13 @@ __global__ void k_eval_fn(int fn, const double *__restrict__ a, const double *__
         if (fn == 0) v = log64(a[i], T);
         else if (fn == 1) v = atan_ratio64(a[i], b[i], T);
         else if (fn == 2) v = log(a[i]);
-        else v = atan(a[i] / b[i]);
+        else if (fn == 3) v = atan(a[i] / b[i]);
+        else {
+            const float *D = reinterpret_cast<const float *>(T + kFnDf);
+            if (fn == 4) v = df_to_double(df_log(df_from_double(a[i]), D));
+            else if (fn == 5) v = df_to_double(df_atan_ratio(df_from_double(a[i]), df_from_double(b[i]), D));
+            else v = df_to_double(psi_df(df_from_double(a[i]), df_from_double(b[i]), df_from_double(a[n + i]), D));
+        }
         out[i] = v;
     }
 }
@@ -198,10 +204,10 @@ extern "C" int grav_eval_fn64(grav_ctx *ctx, int fn, const double *a, const doub
                               grav_stream_t stream) {
     using namespace grav;
     if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
-    if (fn < 0 || fn > 3) return set_error(ctx, GRAV_EINVAL, "fn must be 0..3");
+    if (fn < 0 || fn > 6) return set_error(ctx, GRAV_EINVAL, "fn must be 0..6");
     if (n < 0) return set_error(ctx, GRAV_EINVAL, "n must be >= 0");
     if (n == 0) return GRAV_OK;
-    if (!a || !out || ((fn == 1 || fn == 3) && !b)) return set_error(ctx, GRAV_EINVAL, "NULL argument");
+    if (!a || !out || ((fn == 1 || fn == 3 || fn == 5 || fn == 6) && !b)) return set_error(ctx, GRAV_EINVAL, "NULL argument");
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);

@@ -85,3 +85,50 @@ def test_atan_ratio64_within_one_ulp(g):
           f"CUDA atan(a/b): max {float(err_cuda.max()):.3f}")
     assert float(err.max()) <= 1.5 and float(err.max()) <= max(1.0, float(err_cuda.max()))
     assert np.all(got[~nz] == 0.0)
+
+
+def _df_round(x):
+    """x rounded to a double-float pair (the inputs the device sees)."""
+    h = x.astype(np.float32).astype(np.float64)
+    return h + (x - h).astype(np.float32).astype(np.float64)
+
+
+def test_double_float_log_and_atan(g):
+    """The double-float log and atan(a/b) of the near-field set-up (FP32
+    pairs on the FP32 pipe) against the long-double reference, over the ranges
+    the corner function meets: log within 2^-44 of |result| + 1, atan within
+    2^-42 of max(|result|, 2^-9) (the FP32 cubic term of its series)."""
+    rng = np.random.Generator(np.random.PCG64(7011))
+    x = _df_round(np.exp(rng.uniform(-10, 12, 200_000)))
+    got = g.eval_fn64("df_log", _dev(x)).cpu().numpy()
+    ref = np.log(x.astype(np.longdouble))
+    err = np.abs(got.astype(np.longdouble) - ref) / (np.abs(ref) + 1)
+    assert float(err.max()) <= 2.0 ** -44
+    a = _df_round(rng.normal(0, 1, 200_000) * np.exp(rng.uniform(-8, 8, 200_000)))
+    b = _df_round(np.exp(rng.uniform(-8, 8, 200_000)))
+    got = g.eval_fn64("df_atan", _dev(a), _dev(b)).cpu().numpy()
+    ref = np.arctan(a.astype(np.longdouble) / b.astype(np.longdouble))
+    err = np.abs(got.astype(np.longdouble) - ref) / np.maximum(np.abs(ref), 2.0 ** -9)
+    assert float(err.max()) <= 2.0 ** -42
+
+
+def test_double_float_corner_function_against_oracle(g):
+    """Psi of Eq. 2-3 in double-float against the FP64 oracle at vertex
+    offsets from 0.1 m to 30 km (x, y of either sign and exactly 0, z > 0):
+    within 2^-42 of R (|ln R| + 1), the scale of the cancellation the
+    near-field table's 8-corner differences face (they need ~2^-39)."""
+    import oracle
+    rng = np.random.Generator(np.random.PCG64(7012))
+    n = 20_000
+    s = 10.0 ** rng.uniform(-1, 4.5, n)
+    x = s * rng.uniform(-1, 1, n)
+    y = s * rng.uniform(-1, 1, n)
+    z = s * rng.uniform(0.001, 1, n)
+    x[::17] = 0.0
+    y[::19] = 0.0
+    x, y, z = _df_round(x), _df_round(y), _df_round(z)
+    got = g.eval_fn64("df_psi", _dev(np.concatenate([x, z])), _dev(y)).cpu().numpy()
+    ref = np.array([oracle.psi(float(a), float(b), float(c)) for a, b, c in zip(x, y, z)])
+    R = np.sqrt(x * x + y * y + z * z)
+    err = np.abs(got - ref) / (R * (np.abs(np.log(R)) + 1))
+    assert err.max() <= 2.0 ** -42, err.max()
