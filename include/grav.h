@@ -454,6 +454,13 @@ int grav_nystrom_coarse_apply(grav_ctx *ctx, const grav_mesh *mesh, const grav_s
  *   op 3: as op 1 with B(k, n) = B[n + ldb k] and C(m, n) = C[n + ldc m]
  *   op 4: as op 1 with B(k, n) = B[n + ldb k]
  *   op 5: as op 2 with A(k, i) = A[i + lda k]
+ *   op 6: the preconditioner's FP64 factorisation: A is an N x N symmetric
+ *         positive definite matrix of doubles (column-major, lower triangle
+ *         read), C receives 2 N^2 doubles: L with T = L L^T in its lower
+ *         triangle (the upper triangle keeps A's values) and then L^-1
+ *         (column-major, zeros above the diagonal).  Synchronises the stream;
+ *         GRAV_EDEVICE if a pivot is not positive.  M, K, B, lda, ldb, ldc and
+ *         accumulate are not used.
  * accumulate = 1 adds to C.  All pointers DEVICE, 16-byte aligned; lda, ldb,
  * ldc, K (and M for ops 0-1, 3-4) multiples of 4; an n-major B or C (and the
  * op 5 A) needs rows of at least N rounded up to 4, whose padding may be

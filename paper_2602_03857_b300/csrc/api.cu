@@ -1290,11 +1290,30 @@ int grav_dense_check(grav_ctx *ctx, int op, int M, int N, int K, const float *A,
                      int64_t ldb, void *C, int64_t ldc, int accumulate, grav_stream_t stream) {
     if (!ctx) return set_error(nullptr, GRAV_EINVAL, "ctx is NULL");
     DeviceGuard g(ctx->device);
-    if (op < 0 || op > 5 || M < 0 || N < 0 || K < 0) return set_error(ctx, GRAV_EINVAL, "bad op or size");
+    if (op < 0 || op > 6 || M < 0 || N < 0 || K < 0) return set_error(ctx, GRAV_EINVAL, "bad op or size");
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (op == 6) {   // FP64 Cholesky and triangular inverse of the Nystrom factorisation
+        if (!is_device_ptr(A, ctx->device) || !is_device_ptr(C, ctx->device))
+            return set_error(ctx, GRAV_EINVAL, "A and C must be device pointers");
+        if (N == 0) return GRAV_OK;
+        double *L = (double *)C, *Li = L + (size_t)N * N;
+        int *fail = nullptr;
+        cudaError_t e = cudaMallocFromPoolAsync((void **)&fail, sizeof(int), ctx->pool, s);
+        if (e != cudaSuccess) return cuda_error(ctx, e, "dense check scratch");
+        cudaMemcpyAsync(L, A, 8ull * N * N, cudaMemcpyDeviceToDevice, s);
+        cudaMemsetAsync(fail, 0, sizeof(int), s);
+        launch_potrf_lower(L, N, fail, s);
+        launch_trinv_lower(L, Li, N, s);
+        int hf = 0;
+        cudaMemcpyAsync(&hf, fail, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaFreeAsync(fail, s);
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_error(ctx, e, "dense check factorisation");
+        return hf ? set_error(ctx, GRAV_EDEVICE, "matrix is not positive definite") : GRAV_OK;
+    }
     const bool gram = op == 2 || op == 5;
     if (!is_device_ptr(A, ctx->device) || !is_device_ptr(C, ctx->device) || (!gram && !is_device_ptr(B, ctx->device)))
         return set_error(ctx, GRAV_EINVAL, "A, B and C must be device pointers");
-    const cudaStream_t s = (cudaStream_t)stream;
     int rc = gram ? launch_gram_df(N, K, A, lda, (double *)C, accumulate != 0, s, op == 5)
                   : launch_sgemm(op == 0, M, N, K, A, lda, B, ldb, (float *)C, ldc, accumulate != 0, s,
                                  op == 3 || op == 4, op == 3);

@@ -297,6 +297,13 @@ void fill_fn_table(double *t);
 int fn_table_size();
 void launch_corner_fwd(const grav_plan *p, const double *m, cudaStream_t s);
 
+// Device factorisation of the Nystrom matrix (chol_kernels.cu), FP64,
+// column-major lower n x n: T = lam (M + nu I) + G; T = L L^T in place
+// (*fail |= 1 on a pivot that is not positive); Li = L^-1 (zeros above the
+// diagonal).  Enqueued on s.
+void launch_form_T(int n, double lam, double nu, const double *M, const double *G, double *T, cudaStream_t s);
+void launch_potrf_lower(double *A, int n, int *fail, cudaStream_t s);
+void launch_trinv_lower(const double *L, double *Li, int n, cudaStream_t s);
 // dense kernels of the Nystrom preconditioner (dense_kernels.cu).  Return -1
 // (nothing launched) when the layout requirements are not met.
 // C (+)= A B in FP32: A(m, k) = A[k + lda m] (a_kmajor) or A[m + lda k];

@@ -30,7 +30,7 @@
 //     (lambda I + Y M_nu^-1 Y^T)^-1 r = (r - Y T^-1 Y^T r) / lambda,
 //     T = lambda M_nu + Y^T Y,
 //   with one ell x ell Cholesky factor T = L L^T and its inverse L^-1 (on
-//   the host, ell^3 / 2 flops; ell <= 8192).  Applying it costs two GEMVs
+//   the device, FP64, blocked, chol_kernels.cu; ell^3 / 3 FMAs; ell <= 8192).  Applying it costs two GEMVs
 //   with the N x ell matrix Y and two triangular products with L^-1
 //   (T^-1 = L^-T L^-1).  Y holds FP32 values (the sketch products are FP32),
 //   so Y is kept in FP32 and the GEMVs take exact FP32 products of Y with
@@ -192,66 +192,12 @@ __global__ void __launch_bounds__(256) k_nys_near(int nx, int ny, int nz, NearGe
     }
 }
 
-// sum_k a[k] b[k], k < n, in four interleaved partial sums
-inline double dot4(const double *a, const double *b, int n) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int k = 0;
-    for (; k + 4 <= n; k += 4) {
-        s0 += a[k] * b[k];
-        s1 += a[k + 1] * b[k + 1];
-        s2 += a[k + 2] * b[k + 2];
-        s3 += a[k + 3] * b[k + 3];
-    }
-    for (; k < n; ++k) s0 += a[k] * b[k];
-    return (s0 + s1) + (s2 + s3);
-}
-
-// In-place Cholesky A = L L^T of a symmetric n x n row-major matrix (lower
-// triangle used and overwritten with L), column by column (Cholesky-Crout:
-// L_ij = (A_ij - L_i,<j . L_j,<j) / L_jj, rows of a column in parallel);
-// false if a pivot is not positive.
-bool cholesky_rowmajor(std::vector<double> &A, int n) {
-    for (int j = 0; j < n; ++j) {
-        double *Lj = &A[(size_t)j * n];
-        const double d = Lj[j] - dot4(Lj, Lj, j);
-        if (!(d > 0.0) || !std::isfinite(d)) return false;
-        const double ljj = std::sqrt(d);
-        Lj[j] = ljj;
-        const double inv = 1.0 / ljj;
-#pragma omp parallel for schedule(static) if (n - j > 256)
-        for (int i = j + 1; i < n; ++i) {
-            double *Li = &A[(size_t)i * n];
-            Li[j] = (Li[j] - dot4(Li, Lj, j)) * inv;
-        }
-    }
-    return true;
-}
-
-// Inverse of the lower triangular factor: Li (column-major, Li[i + n j],
-// zeros above the diagonal) from L (row-major lower, as cholesky_rowmajor
-// leaves it), by forward substitution on each unit vector (columns in
-// parallel): Li_jj = 1 / L_jj, Li_ij = -(sum_{j <= k < i} L_ik Li_kj) / L_ii.
-void tri_inverse_lower(const std::vector<double> &L, int n, std::vector<double> &Li) {
-    Li.assign((size_t)n * n, 0.0);
-#pragma omp parallel for schedule(dynamic, 8)
-    for (int j = 0; j < n; ++j) {
-        double *x = &Li[(size_t)n * j];
-        x[j] = 1.0 / L[(size_t)j * n + j];
-        for (int i = j + 1; i < n; ++i) {
-            const double *Lr = &L[(size_t)i * n];
-            double acc = 0.0;
-            for (int k = j; k < i; ++k) acc += Lr[k] * x[k];
-            x[i] = -acc / Lr[i];
-        }
-    }
-}
-
 inline int64_t pad4(int64_t v) { return (v + 3) / 4 * 4; }
 
 }  // namespace
 
 // Automatic sizes (0).  The sketch costs 4 N M_c ell FP32 GEMM flops plus a
-// double-float Gram of ell^2 (N + M_c) products and an ell^3 host factor; a CG
+// double-float Gram of ell^2 (N + M_c) products and an ell^3 / 3 FP64 factor; a CG
 // iteration costs two products with the fine operator, ~0.28 s (mixed) or
 // ~0.9 s (FP64) at the sizes below, so FP64 solves sketch the uncoarsened
 // operator.  With the Gram matrices on the FP32 pipe the mixed rank rose from
@@ -460,7 +406,7 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
     // (ell x ell FP64); the explicit blocks take what the budget leaves
     st->bytes = nys_bytes(N, ell);
     const int64_t ellp = pad4(ell);
-    const size_t tmp_bytes = 4ull * ldy * ellp + 16ull * ell * ell + 4 * 256;
+    const size_t tmp_bytes = 4ull * ldy * ellp + 24ull * ell * ell + 5 * 256;
     if (ctx->hbm_used.load() + st->bytes + tmp_bytes > ctx->hbm_budget) {
         plan_destroy(cp, s);
         return set_error(ctx, GRAV_ENOMEM, "Nystrom preconditioner (rank %d) exceeds the HBM budget", ell);
@@ -491,7 +437,10 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
     float *Om32 = (float *)ta.take(4ull * ldy * ellp);   // station-major: Om32[j + ellp s]
     double *Mm = (double *)ta.take(8ull * ell * ell);
     double *Gy = (double *)ta.take(8ull * ell * ell);
-    std::vector<double> hM((size_t)ell * ell), hG((size_t)ell * ell);
+    double *Tm = (double *)ta.take(8ull * ell * ell);   // T, factored in place into L
+    int *d_fail = (int *)ta.take(256);
+    int *h_fail = nullptr;
+    cudaMallocHost((void **)&h_fail, sizeof(int));
     cudaEvent_t ev = nullptr;
     do {
         if (pa.overflow || ta.overflow) {
@@ -506,38 +455,34 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
             rc = set_error(ctx, GRAV_EINVAL, "Nystrom Gram matrix: unsupported layout");
             break;
         }
-        cudaMemcpyAsync(hM.data(), Mm, 8ull * ell * ell, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(hG.data(), Gy, 8ull * ell * ell, cudaMemcpyDeviceToHost, s);
         cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        cudaEventRecord(ev, s);
-        if ((rc = host_wait(ctx, ev, p->opt.timeout_s, "Nystrom Gram matrices"))) break;
-        // T = mu (M + nu I) + Y^T Y, row-major lower triangle (both Gram
-        // matrices are column-major lower: element (i, j), i >= j, at i + ell j).
-        // nu starts at 1e-3 lambda and grows tenfold (to at most 10 lambda)
-        // while the factorisation finds a non-positive pivot.
+        // T = mu (M + nu I) + Y^T Y (column-major lower, as the Gram matrices),
+        // factored on the device.  nu starts at 1e-3 lambda and grows tenfold
+        // (to at most 10 lambda) while the factorisation meets a pivot that is
+        // not positive; the host reads one flag per attempt.
         st->mu = lam;
-        std::vector<double> T((size_t)ell * ell);
         bool factored = false;
         for (double nu = 1e-3 * lam; !factored && nu <= 10.0 * lam * 1.0000001; nu *= 10.0) {
-            for (int i = 0; i < ell; ++i)
-                for (int j = 0; j <= i; ++j) {
-                    const size_t cij = (size_t)i + (size_t)ell * j;
-                    T[(size_t)i * ell + j] = lam * (hM[cij] + (i == j ? nu : 0.0)) + hG[cij];
-                }
+            launch_form_T(ell, lam, nu, Mm, Gy, Tm, s);
+            cudaMemsetAsync(d_fail, 0, sizeof(int), s);
+            launch_potrf_lower(Tm, ell, d_fail, s);
+            cudaMemcpyAsync(h_fail, d_fail, sizeof(int), cudaMemcpyDeviceToHost, s);
+            cudaEventRecord(ev, s);
+            if ((rc = host_wait(ctx, ev, p->opt.timeout_s, "Nystrom factorisation"))) break;
             st->nu = nu;
-            factored = cholesky_rowmajor(T, ell);
+            factored = (*h_fail == 0);
         }
+        if (rc) break;
         if (!factored) {
             rc = set_error(ctx, GRAV_EDEVICE, "Nystrom matrix T is not positive definite (rank %d)", ell);
             break;
         }
-        std::vector<double> Li;
-        tri_inverse_lower(T, ell, Li);
-        cudaMemcpyAsync(st->Linv, Li.data(), 8ull * ell * ell, cudaMemcpyHostToDevice, s);
-        cudaEventRecord(ev, s);
-        rc = host_wait(ctx, ev, p->opt.timeout_s, "Nystrom factor upload");
+        launch_trinv_lower(Tm, st->Linv, ell, s);
+        const cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) rc = cuda_error(ctx, le, "Nystrom factorisation launch");
     } while (false);
     if (ev) cudaEventDestroy(ev);
+    if (h_fail) cudaFreeHost(h_fail);
     cudaFreeAsync(tmp, s);
     ctx->hbm_used -= tmp_bytes;
     plan_destroy(cp, s);

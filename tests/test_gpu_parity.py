@@ -1033,3 +1033,48 @@ def test_fp64_widest_node_row_and_the_cap(g):
     with pytest.raises(g.GravError) as e:
         g.forward(_dev(np.zeros(wide.ncells)), wide, S)
     assert e.value.code == g.GRAV_EINVAL and "nx+1 must be <=" in str(e.value)
+
+
+def test_dense_cholesky_and_triangular_inverse(g):
+    """The device factorisation of the Nystrom matrix (blocked FP64 Cholesky
+    and explicit inverse of the factor): on SPD matrices of sizes around the
+    32-wide blocks and the 64-wide update tiles, L L^T reproduces A to the
+    backward-error scale n 2^-53 |L| |L|^T, L equals numpy's Cholesky factor on
+    a well-conditioned matrix, and L^-1 L = I to n 2^-53 |L^-1| |L|; a matrix
+    that is not positive definite is reported as GRAV_EDEVICE."""
+    ctx = g.context()
+    rng = np.random.default_rng(77)
+    u = 2.0 ** -53
+
+    def factor(A):
+        n = A.shape[0]
+        At = torch.tensor(np.asfortranarray(A).ravel(order="F"), device="cuda")
+        Ct = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+        rc = g._lib.grav_dense_check(ctx.h, 6, 0, n, 0, At.data_ptr(), 0, None, 0, Ct.data_ptr(), 0, 0,
+                                     g._stream(None))
+        C = Ct.cpu().numpy()
+        return rc, np.tril(C[:n * n].reshape(n, n, order="F")), C[n * n:].reshape(n, n, order="F")
+
+    for n in (1, 5, 31, 32, 33, 64, 100, 257, 1000):
+        X = rng.standard_normal((n, n + 3))
+        A = X @ X.T + n * np.eye(n)
+        rc, L, Li = factor(A)
+        assert rc == g.GRAV_OK, n
+        assert np.all(np.abs(L @ L.T - A) <= 4 * n * u * (np.abs(L) @ np.abs(L).T) + 1e-300), n
+        Lnp = np.linalg.cholesky(A)
+        assert np.abs(L - Lnp).max() <= 1e-12 * np.abs(Lnp).max(), n
+        assert np.array_equal(np.triu(Li, 1), np.zeros((n, n))), n
+        assert np.all(np.abs(Li @ L - np.eye(n)) <= 4 * n * u * (np.abs(Li) @ np.abs(L)) + 1e-300), n
+    # ill-conditioned, shaped like the preconditioner's T (a Gram matrix plus a small shift)
+    n = 300
+    Y = rng.standard_normal((2000, n)) * np.logspace(0, -5, n)
+    A = Y.T @ Y + 1e-9 * np.eye(n)
+    rc, L, Li = factor(A)
+    assert rc == g.GRAV_OK
+    assert np.all(np.abs(L @ L.T - A) <= 4 * n * u * (np.abs(L) @ np.abs(L).T))
+    assert np.all(np.abs(Li @ L - np.eye(n)) <= 4 * n * u * (np.abs(Li) @ np.abs(L)))
+    # not positive definite
+    A = np.eye(40)
+    A[20, 20] = -1.0
+    rc, _, _ = factor(A)
+    assert rc == g.GRAV_EDEVICE
