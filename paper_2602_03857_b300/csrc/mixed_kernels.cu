@@ -2004,7 +2004,8 @@ static MixedSizes mixed_sizes(const grav_plan *p) {
             const int64_t cblocks = (ncol + kAbWarps * 32 - 1) / (kAbWarps * 32);
             double best = 1e300;
             int64_t best_n = 1;
-            const int64_t hi = std::min<int64_t>(part_cap, p->N / 64);
+            // (more than 64 waves of chunks gains nothing: the search stays short)
+            const int64_t hi = std::min<int64_t>(std::min<int64_t>(part_cap, p->N / 64), 64 * slots / bc_ctas + 1);
             for (int64_t n = 1; n <= std::max<int64_t>(1, hi); ++n) {
                 int64_t len = (p->N + n - 1) / n;
                 len = (len + 31) / 32 * 32;
