@@ -340,32 +340,71 @@ __device__ __forceinline__ double block_sum_fixed(double v, double *red) {
     return s;
 }
 
-// t[j] = sum_s Y[s + ldy j] (rh[s] + rl[s]), s < n; one CTA per column,
-// double-float sums per thread, FP64 across threads.
-__global__ void __launch_bounds__(256) k_gemv_t_df(const float *__restrict__ Y, int64_t ldy, int64_t n,
+// tp[c ell + j] = sum over the rows s of chunk c of Y[s + ldy j] (rh[s] + rl[s]):
+// a CTA per (16 columns, 8192-row chunk); each thread walks rows s0 + tid,
+// s0 + tid + 256, ... and reads rh, rl once for its 16 columns (one
+// double-float accumulator per column, runs of 128 rows folded into FP64;
+// 18 independent loads per row in flight), then the 256 threads' sums of
+// each column are added in a fixed order.  One CTA per column, reading r
+// for every column, spent ~8 ms per launch at 178,797 x 3,973 (every CTA
+// streamed the same 1.4 MB of r through L2) for 2.8 GB of Y.
+constexpr int kGtCols = 16, kGtRows = 8192;
+__global__ void __launch_bounds__(256) k_gemv_t_df(const float *__restrict__ Y, int64_t ldy, int64_t n, int ell,
                                                    const float *__restrict__ rh, const float *__restrict__ rl,
-                                                   double *__restrict__ t) {
-    __shared__ double red[8];
-    const int j = blockIdx.x;
-    const float *y = Y + (int64_t)j * ldy;
-    DF acc{0.f, 0.f};
-    float small = 0.0f;
-    double v = 0.0;
+                                                   double *__restrict__ tp) {
+    __shared__ double red[kGtCols][256 + 1];
+    const int j0 = blockIdx.x * kGtCols;
+    const int nc = min(kGtCols, ell - j0);
+    const int64_t s0 = (int64_t)blockIdx.y * kGtRows, s1 = min(n, s0 + kGtRows);
+    DF acc[kGtCols];
+    float small[kGtCols];
+    double v[kGtCols];
+#pragma unroll
+    for (int c = 0; c < kGtCols; ++c) {
+        acc[c] = DF{0.f, 0.f};
+        small[c] = 0.0f;
+        v[c] = 0.0;
+    }
     int run = 0;
-    for (int64_t s = threadIdx.x; s < n; s += blockDim.x) {
-        const float a = __ldcs(y + s);
-        df_acc_prod(acc, a, rh[s]);
-        small = fmaf(a, rl[s], small);
+    for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        const float h = rh[s], l = rl[s];
+        float a[kGtCols];
+#pragma unroll
+        for (int c = 0; c < kGtCols; ++c) a[c] = (c < nc) ? __ldcs(Y + s + ldy * (int64_t)(j0 + c)) : 0.0f;
+#pragma unroll
+        for (int c = 0; c < kGtCols; ++c) {
+            df_acc_prod(acc[c], a[c], h);
+            small[c] = fmaf(a[c], l, small[c]);
+        }
         if (++run == kDfRun) {   // runs of 128 terms into FP64
-            v += (double)acc.hi + (double)acc.lo + (double)small;
-            acc = DF{0.f, 0.f};
-            small = 0.0f;
+#pragma unroll
+            for (int c = 0; c < kGtCols; ++c) {
+                v[c] += (double)acc[c].hi + (double)acc[c].lo + (double)small[c];
+                acc[c] = DF{0.f, 0.f};
+                small[c] = 0.0f;
+            }
             run = 0;
         }
     }
-    v += (double)acc.hi + (double)acc.lo + (double)small;
-    const double tot = block_sum_fixed(v, red);
-    if (threadIdx.x == 0) t[j] = tot;
+#pragma unroll
+    for (int c = 0; c < kGtCols; ++c) red[c][threadIdx.x] = v[c] + ((double)acc[c].hi + (double)acc[c].lo + (double)small[c]);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c = warp; c < nc; c += (int)(blockDim.x >> 5)) {
+        double x = 0.0;
+        for (int k = lane; k < 256; k += 32) x += red[c][k];
+        x = warp_sum(x);
+        if (lane == 0) tp[(int64_t)blockIdx.y * ell + j0 + c] = x;
+    }
+}
+
+// t[j] = sum_c tp[c ell + j] over the row chunks, in chunk order
+__global__ void k_sum_chunks(const double *__restrict__ tp, int nch, int ell, double *__restrict__ t) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ell) return;
+    double x = 0.0;
+    for (int c = 0; c < nch; ++c) x += tp[(int64_t)c * ell + j];
+    t[j] = x;
 }
 
 // u[i] = sum_{j <= i} Li[i + ell j] t[j]   (thread per row)
@@ -401,22 +440,27 @@ __global__ void __launch_bounds__(256) k_gemv_n_df(const float *__restrict__ Y, 
     double yv = 0.0;
     const float *y = Y + s;
     int j = 0;
-    for (; j + 4 <= ell; j += 4) {
+    // 16 columns per step: 16 independent loads in flight per thread (4 per
+    // step reached ~1.2 TB/s at 178,797 x 3,973, latency-bound)
+    for (; j + 16 <= ell; j += 16) {
         if (j % kDfRun == 0 && j > 0) {   // runs of 128 terms into FP64
             yv += (double)acc.hi + (double)acc.lo + (double)small;
             acc = DF{0.f, 0.f};
             small = 0.0f;
         }
-        const float a0 = __ldcs(y + (int64_t)ldy * j), a1 = __ldcs(y + (int64_t)ldy * (j + 1));
-        const float a2 = __ldcs(y + (int64_t)ldy * (j + 2)), a3 = __ldcs(y + (int64_t)ldy * (j + 3));
-        df_acc_prod(acc, a0, vh[j]);
-        small = fmaf(a0, vl[j], small);
-        df_acc_prod(acc, a1, vh[j + 1]);
-        small = fmaf(a1, vl[j + 1], small);
-        df_acc_prod(acc, a2, vh[j + 2]);
-        small = fmaf(a2, vl[j + 2], small);
-        df_acc_prod(acc, a3, vh[j + 3]);
-        small = fmaf(a3, vl[j + 3], small);
+        float a[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) a[q] = __ldcs(y + (int64_t)ldy * (j + q));
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            df_acc_prod(acc, a[q], vh[j + q]);
+            small = fmaf(a[q], vl[j + q], small);
+        }
+    }
+    if (j % kDfRun == 0 && j > 0 && j < ell) {
+        yv += (double)acc.hi + (double)acc.lo + (double)small;
+        acc = DF{0.f, 0.f};
+        small = 0.0f;
     }
     for (; j < ell; ++j) {
         const float a = __ldcs(y + (int64_t)ldy * j);
@@ -471,16 +515,21 @@ int launch_gram_df(int n, int K, const float *X, int64_t ldx, double *G, bool ac
     return 0;
 }
 
+int64_t nys_tpart_chunks(int64_t n) { return std::max<int64_t>(1, (n + kGtRows - 1) / kGtRows); }
+
 void launch_nys_apply(const float *Y, int64_t ldy, int64_t n, int ell, const double *Linv, double mu,
-                      const double *r, double *z, float *rh, float *rl, double *t, double *u, double *v, float *vh,
-                      float *vl, cudaStream_t s) {
+                      const double *r, double *z, float *rh, float *rl, double *tp, double *t, double *u, double *v,
+                      float *vh, float *vl, cudaStream_t s) {
     k_split_df<<<blocks_for(n, 256), 256, 0, s>>>(r, n, rh, rl);
-    k_gemv_t_df<<<(unsigned)ell, 256, 0, s>>>(Y, ldy, n, rh, rl, t);
+    const int nch = (int)nys_tpart_chunks(n);
+    k_gemv_t_df<<<dim3((unsigned)((ell + kGtCols - 1) / kGtCols), (unsigned)nch), 256, 0, s>>>(Y, ldy, n, ell, rh, rl,
+                                                                                              tp);
+    k_sum_chunks<<<(unsigned)((ell + 127) / 128), 128, 0, s>>>(tp, nch, ell, t);
     k_trmv_lo<<<(unsigned)((ell + 127) / 128), 128, 0, s>>>(Linv, ell, t, u);
     k_trmv_lo_t<<<(unsigned)((ell * 32 + 255) / 256), 256, 0, s>>>(Linv, ell, u, v);
     k_split_df<<<blocks_for(ell, 256), 256, 0, s>>>(v, ell, vh, vl);
     k_gemv_n_df<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Y, ldy, n, ell, vh, vl, r, 1.0 / mu, z);
-    note_launches(6);
+    note_launches(7);
 }
 
 }  // namespace grav

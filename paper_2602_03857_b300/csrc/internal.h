@@ -204,6 +204,7 @@ struct NysState {
     float *Y = nullptr;                   // Y = K_c Omega, ldy x ell, column-major (FP32 values)
     double *Linv = nullptr;               // L^-1, ell x ell column-major, lower (T = L L^T)
     double *t = nullptr, *u = nullptr, *v = nullptr;   // [ell] application scratch
+    double *tp = nullptr;                 // [row chunks][ell] partial sums of Y^T r
     float *vh = nullptr, *vl = nullptr;   // [ell] v as FP32 pairs
     float *rh = nullptr, *rl = nullptr;   // [ldy] r as FP32 pairs
     char *mem = nullptr;
@@ -319,9 +320,10 @@ int launch_sgemm(bool a_kmajor, int M, int N, int K, const float *A, int64_t lda
 int launch_gram_df(int n, int K, const float *X, int64_t ldx, double *G, bool accumulate, cudaStream_t s,
                    bool k_slow = false);
 // z = (r - Y Linv^T Linv Y^T r) / mu  (Y FP32 [ldy][ell], Linv FP64 lower)
+int64_t nys_tpart_chunks(int64_t n);   // row chunks of the Y^T r partial sums (tp: chunks x ell doubles)
 void launch_nys_apply(const float *Y, int64_t ldy, int64_t n, int ell, const double *Linv, double mu,
-                      const double *r, double *z, float *rh, float *rl, double *t, double *u, double *v, float *vh,
-                      float *vl, cudaStream_t s);
+                      const double *r, double *z, float *rh, float *rl, double *tp, double *t, double *u, double *v,
+                      float *vh, float *vl, cudaStream_t s);
 
 // vector kernels (cg_kernels.cu)
 void launch_dot(const double *a, const double *b, int64_t n, double *partials, double *out, cudaStream_t s);

@@ -225,9 +225,10 @@ void nys_sizes(const grav_plan *p, int *ell, int *cf) {
 
 size_t nys_bytes(int64_t N, int ell) {
     // persistent part: Y (FP32, ldy x ell), L^-1 (ell x ell), t, u, v (ell doubles),
-    // vh, vl (ell floats), rh, rl (ldy floats)
+    // vh, vl (ell floats), rh, rl (ldy floats), the row-chunk partials of Y^T r
     const size_t ldy = (size_t)pad4(N);
-    return 4ull * ldy * ell + 8ull * ell * ell + 24ull * ell + 8ull * ell + 8ull * ldy + 9 * 256;
+    return 4ull * ldy * ell + 8ull * ell * ell + 24ull * ell + 8ull * ell + 8ull * ldy +
+           8ull * ell * (size_t)nys_tpart_chunks(N) + 10 * 256;
 }
 
 // Explicit-block width: cells per block of the coarse operator (multiple of 4).
@@ -432,6 +433,7 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
     st->vl = (float *)pa.take(4ull * ell);
     st->rh = (float *)pa.take(4ull * ldy);
     st->rl = (float *)pa.take(4ull * ldy);
+    st->tp = (double *)pa.take(8ull * ell * nys_tpart_chunks(N));
     Arena ta;
     ta.base = tmp; ta.size = tmp_bytes;
     float *Om32 = (float *)ta.take(4ull * ldy * ellp);   // station-major: Om32[j + ellp s]
@@ -491,7 +493,7 @@ int nys_build(grav_plan *p, double lam, int ell, int cf, uint64_t seed, NysState
 }
 
 void nys_apply(const NysState &st, const double *r, double *z, cudaStream_t s) {
-    launch_nys_apply(st.Y, st.ldy, st.N, st.ell, st.Linv, st.mu, r, z, st.rh, st.rl, st.t, st.u, st.v, st.vh, st.vl,
+    launch_nys_apply(st.Y, st.ldy, st.N, st.ell, st.Linv, st.mu, r, z, st.rh, st.rl, st.tp, st.t, st.u, st.v, st.vh, st.vl,
                      s);
 }
 
