@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--nys-rank", type=int, default=0, help="--precond nystrom: sketch size (0: automatic)")
     ap.add_argument("--nys-coarsen", type=int, default=0,
                     help="--precond nystrom: coarsening factor per axis (0: automatic)")
+    ap.add_argument("--refine", type=int, default=0,
+                    help="--invert --precision fp64: at most this many mixed-precision refinement steps "
+                         "(FP64 residuals) instead of FP64 CG (0: FP64 CG)")
     return ap.parse_args()
 
 
@@ -454,21 +457,27 @@ def extras(args, g, torch, wl, plan, d, line):
     d2 = g.forward(torch.tensor(wl2.m, device="cuda"), wl2.mesh, S2, precision="fp64").cpu().numpy()
     d2 = torch.tensor(synth.add_noise(d2, wl2.noise_abs, wl2.noise_rel, 0), device="cuda")
     vs = {}
-    for prec, pc in (("fp64", "nystrom"), ("mixed", "none")):
+    for key, prec, pc, refine in (("fp64", "fp64", "nystrom", 0), ("fp64_refined", "fp64", "none", 8),
+                                  ("mixed", "mixed", "none", 0)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         mm, info = g.datainv(d2, wl2.mesh, S2, precision=prec, tol=1e-6, max_iter=5000, precond=pc,
-                             check_stations=64 if prec == "mixed" else 0)
+                             check_stations=64 if prec == "mixed" else 0, refine=refine)
         torch.cuda.synchronize()
-        vs[prec] = {"seconds": time.perf_counter() - t0, "precond": pc, "iters": info["iters"],
-                    "converged": info["converged"], "true_rel_res": info["true_rel_res"]}
+        vs[key] = {"seconds": time.perf_counter() - t0, "precond": pc, "iters": info["iters"],
+                   "converged": info["converged"], "true_rel_res": info["true_rel_res"]}
         if prec == "mixed":
-            vs[prec]["fp64_rel_err_of_predicted_data"] = info["fp64_rel_err"]
+            vs[key]["fp64_rel_err_of_predicted_data"] = info["fp64_rel_err"]
+        if refine:
+            vs[key]["refine_steps"] = info["outer"]
     line["inversion_to_1e-6_vslab_80x80x40"] = {
         "workload": "vslab_80x80x40", **vs, "fp64_over_mixed_seconds": vs["fp64"]["seconds"] / vs["mixed"]["seconds"],
+        "fp64_refined_over_mixed_seconds": vs["fp64_refined"]["seconds"] / vs["mixed"]["seconds"],
         "what": "one grav_datainv_solve call each (plan set-up, trace, CG to a true relative residual of 1e-6, "
-                "recovery); the FP64 solve takes the Nystrom preconditioner (sketch included), without it it "
-                "needs ~100 s"}
+                "recovery); fp64: FP64 CG with the Nystrom preconditioner (sketch included; without it ~100 s); "
+                "fp64_refined: the same FP64 system by mixed-precision iterative refinement (mixed CG "
+                "corrections, FP64 residuals; true_rel_res is the FP64 residual, iters the mixed CG "
+                "iterations)"}
     # the serving loop on the first 64 jobs of the seeded request stream
     line["serving_64_jobs"] = serve_replay(g, torch, 64, 20.0, 8)
     # an inversion stream on one survey (80 x 80 x 40 cells x 6,561 stations, 16 data
@@ -639,8 +648,8 @@ def run_invert(args):
     d = g.forward(m, wl.mesh, S, precision=data_prec, near_cells=args.near_cells)
     torch.cuda.synchronize()
     opts = dict(precision=args.precision, near_cells=args.near_cells, tol=args.tol, max_iter=args.max_iter,
-                precond=args.precond, check_stations=64, reorth=args.reorth, nys_rank=args.nys_rank,
-                nys_coarsen=args.nys_coarsen)
+                precond=args.precond, check_stations=64 if args.precision != "fp64" else 0, reorth=args.reorth,
+                nys_rank=args.nys_rank, nys_coarsen=args.nys_coarsen, refine=args.refine)
     t0 = time.perf_counter()
     m_out, info = g.datainv(d, wl.mesh, S, **opts)
     torch.cuda.synchronize()
@@ -659,6 +668,10 @@ def run_invert(args):
     if args.precond == "nystrom":
         line["nys_setup_s"] = info["nys_setup_s"]
         line["nys_shift_over_lambda"] = info["nys_shift"]
+    if args.refine:
+        line["refine_steps"] = info["outer"]
+        line["what"] = ("FP64 system solved by mixed-precision iterative refinement: iters counts the mixed CG "
+                        "iterations, true_rel_res is the FP64 operator's residual")
     print(json.dumps(line), flush=True)
 
 

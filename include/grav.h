@@ -142,6 +142,15 @@ typedef struct {
     int nys_coarsen;           /* precond = 2: coarsening factor per axis of the sketch operator, 1..8;
                                   0 = automatic: GRAV_MIXED min(3, min(nx, ny, nz) / 8), at least 1;
                                   GRAV_FP64 1 (default 0) */
+    int refine;                /* GRAV_FP64 inversions (grav_datainv_solve*, uniform meshes): > 0 solves the FP64
+                                  system by mixed-precision iterative refinement, at most `refine` correction
+                                  steps: each runs a GRAV_MIXED CG solve (near_cells, precond, nys_*, reorth,
+                                  max_iter apply to it; tolerance tol for the first step, 1e-2 of the current
+                                  residual after that) on the current residual, adds its solution to y and
+                                  recomputes the residual dd - (G W^-2 G^T + lambda I) y with the FP64
+                                  operator; it stops when that FP64 residual is <= tol ||dd||.  lambda comes
+                                  from the FP64 trace as in FP64 mode, and m = m_ref + W^-2 G^T y from the FP64
+                                  adjoint.  No counterpart in the paper.  0 = FP64 CG (default) */
 } grav_options;
 
 typedef struct {
@@ -152,7 +161,7 @@ typedef struct {
     double lambda;             /* lambda used */
     double trace;              /* trace(G W^-2 G^T) (0 if lambda was given) */
     double seconds;            /* wall time of the solve */
-    int outer;                 /* outer updates performed (outer_max > 0) */
+    int outer;                 /* outer updates performed (outer_max > 0); with refine, FP64 residual evaluations */
     double alpha_min;          /* smallest accepted step length of the outer loop (1 if never backtracked) */
     int restarts;              /* single CG solve: restarts from the recomputed true residual */
     double fp64_rel_err;       /* check_stations > 0: max |mixed - FP64| over the checked stations relative to

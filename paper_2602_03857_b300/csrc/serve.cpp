@@ -411,10 +411,16 @@ int grav_submit(grav_ctx *ctx, const grav_job *job, uint64_t *job_id) {
     if (prev != ctx->device) cudaSetDevice(ctx->device);
     grav_plan *p = nullptr;
     int rc = plan_prepare(ctx, &job->mesh, &job->survey, job->opt, &p);
+    if (rc == GRAV_OK && job->opt.refine > 0)
+        rc = set_error(ctx, GRAV_EINVAL, "refine is supported by grav_datainv_solve only, not by serving jobs");
     if (rc == GRAV_OK) {
         const bool ok = is_device(job->input, ctx->device) && is_device(job->output, ctx->device) &&
                         (!job->m_ref || is_device(job->m_ref, ctx->device));
         if (!ok) rc = set_error(ctx, GRAV_EINVAL, "job input/output (and m_ref) must be device pointers");
+    }
+    if (rc != GRAV_OK) {   // the prepared (host-only) plan of a rejected job
+        delete p;
+        p = nullptr;
     }
     size_t est = 0;
     if (rc == GRAV_OK) {

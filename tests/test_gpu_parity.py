@@ -164,6 +164,53 @@ def test_datainv_fp64_block_vs_dense_lu(g, precond):
     assert info["true_rel_res"] <= 1.5e-8
 
 
+@pytest.mark.parametrize("tol,precond", [(1e-6, "none"), (1e-8, "none"), (1e-8, "nystrom")])
+def test_fp64_inversion_by_mixed_refinement(g, tol, precond):
+    """FP64 inversion with refine: mixed-precision CG solves of the current
+    residual, which is recomputed with the FP64 operator after each step.  On
+    the block workload the reported residual is the FP64 one (recomputed here
+    from the oracle's explicit G) and meets tol, lambda is the FP64 trace
+    rule's, and the model is the oracle's dense-LU minimiser of Eq. 11 within
+    the bound the residual implies, ||y - y*|| <= ||dd - A y|| / lambda, also
+    with a reference model; the mixed inner solves take the Nystrom
+    preconditioner as well."""
+    wl = synth.make_workload("block_20x20x10")
+    G = oracle.G_explicit(wl.mesh, wl.survey)
+    d = synth.add_noise(G @ wl.m, wl.noise_abs, wl.noise_rel, 0)
+    m_ref = np.full(wl.mesh.ncells, 0.1)
+    ref = oracle.invert_dense(wl.mesh, wl.survey, d, m_ref=m_ref, z0=50.0)
+    S = g.Survey(wl.survey.x, wl.survey.y, wl.survey.z)
+    m, y, info = g.datainv(_dev(d), wl.mesh, S, m_ref=_dev(m_ref), return_y=True, tol=tol, max_iter=2000,
+                           refine=8, precond=precond)
+    assert info["converged"], info
+    assert 1 <= info["outer"] <= 8 and info["iters"] > 0
+    assert info["lambda"] == pytest.approx(ref["lam"], rel=1e-10)
+    y = y.cpu().numpy(); m = m.cpu().numpy()
+    A = (G * ref["wm"]) @ G.T + ref["lam"] * np.eye(len(d))
+    dd = d - G @ m_ref
+    res = np.linalg.norm(dd - A @ y)
+    assert res <= tol * np.linalg.norm(dd)
+    assert info["true_rel_res"] == pytest.approx(res / np.linalg.norm(dd), rel=1e-6, abs=1e-12)
+    assert np.linalg.norm(y - ref["y"]) <= 1.01 * res / ref["lam"]
+    m_from_y = m_ref + ref["wm"] * (G.T @ y)
+    scale = np.max(ref["wm"] * (np.abs(G).T @ np.abs(y)))
+    assert np.abs(m - m_from_y).max() <= 1e-10 * scale
+
+
+def test_refine_is_refused_where_it_does_not_apply(g):
+    """refine needs precision fp64 (mixed is refused), and serving jobs refuse it."""
+    wl = synth.make_workload("block_20x20x10")
+    S = g.Survey(wl.survey.x, wl.survey.y, wl.survey.z)
+    d = _dev(np.ones(wl.survey.n))
+    with pytest.raises(g.GravError):
+        g.datainv(d, wl.mesh, S, precision="mixed", refine=4)
+    ctx = g.Context(0)
+    out = torch.empty(wl.mesh.ncells, dtype=torch.float64, device="cuda")
+    with pytest.raises(g.GravError):
+        ctx.submit("invert", wl.mesh, S, d, out, refine=4)
+    ctx.close()
+
+
 def test_datainv_with_reference_model(g):
     mesh, sv, m_true = synth.small_random_problem(8, 7, 5, 60, seed=31)
     G = oracle.G_explicit(mesh, sv)
