@@ -145,7 +145,7 @@ typedef struct {
     int refine;                /* GRAV_FP64 inversions (grav_datainv_solve*, uniform meshes): > 0 solves the FP64
                                   system by mixed-precision iterative refinement, at most `refine` correction
                                   steps: each runs a GRAV_MIXED CG solve (near_cells, precond, nys_*, reorth,
-                                  max_iter apply to it; tolerance tol for the first step, 1e-2 of the current
+                                  max_iter apply to it; tolerance tol / 2 (not below 2e-7) for the first step, 1e-2 of the current
                                   residual after that) on the current residual, adds its solution to y and
                                   recomputes the residual dd - (G W^-2 G^T + lambda I) y with the FP64
                                   operator; it stops when that FP64 residual is <= tol ||dd||.  lambda comes

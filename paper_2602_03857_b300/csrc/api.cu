@@ -1075,7 +1075,10 @@ int solve_refined(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *surve
         for (int k = 0; k < o.refine && !converged; ++k) {
             pm->opt = om;
             pm->opt.lambda = lam;
-            pm->opt.tol = (k == 0) ? o.tol : 1e-2;
+            // first step: half the requested tolerance (not below 2e-7, near the mixed
+            // operator's rounding floor), so that its FP64 residual -- the inner one
+            // plus the operators' difference, a few 1e-7 -- usually meets tol at once
+            pm->opt.tol = (k == 0) ? std::max(0.5 * o.tol, std::min(o.tol, 2e-7)) : 1e-2;
             grav_solve_info ii{};
             const int rci = solve_on_plan(pm, r, nullptr, mscr, dl, &ii, s, nullptr, nullptr, nullptr, 0);
             if (rci != GRAV_OK && rci != GRAV_ENOTCONVERGED) {
