@@ -151,6 +151,11 @@ typedef struct {
                                   operator; it stops when that FP64 residual is <= tol ||dd||.  lambda comes
                                   from the FP64 trace as in FP64 mode, and m = m_ref + W^-2 G^T y from the FP64
                                   adjoint.  No counterpart in the paper.  0 = FP64 CG (default) */
+    int near_fp64;             /* GRAV_MIXED: 1 = form the near-field table from the corner function in FP64;
+                                  0 (default) = in double-float (pairs of FP32 numbers on the FP32 pipe,
+                                  ~2^-45 of R (|ln R| + 1) per corner value against the ~2^-39 the table's
+                                  FP32 entries need; the products differ from the FP64-formed table's by
+                                  <= ~1e-9 of max, and the set-up is ~3x faster) */
 } grav_options;
 
 typedef struct {
@@ -206,7 +211,7 @@ int grav_ctx_sync(grav_ctx *ctx, grav_stream_t stream, double timeout_s);
 /* ---- one-shot operator calls (Section 2.1, Eq. 5-6) ----------------------- */
 /* d[i] = sum_k G_ik m[k] (mGal).  m: DEVICE, nx*ny*nz doubles (kg/m^3).
  * d: DEVICE, survey->n doubles.  opt may be NULL (defaults).  Builds a
- * transient plan (GRAV_MIXED: includes the FP64 near-field set-up), enqueues
+ * transient plan (GRAV_MIXED: includes the near-field set-up), enqueues
  * the product and releases the plan in stream order. */
 int grav_forward(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey,
                  const double *m, double *d, const grav_options *opt, grav_stream_t stream);
@@ -251,7 +256,7 @@ int grav_datainv_solve_ex(grav_ctx *ctx, const grav_mesh *mesh, const grav_surve
 /* ---- reusable plans ------------------------------------------------------- */
 /* A plan holds one (mesh, survey, options) problem resident on the device:
  * the mesh edges, the station arrays' derived forms, the operator scratch and,
- * for GRAV_MIXED, the FP64 near-field correction of every station.  The
+ * for GRAV_MIXED, the near-field correction of every station.  The
  * survey arrays are read when the plan is created and must not change while
  * the plan is used.  Creation enqueues set-up work on `stream`. */
 int grav_plan_create(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey,

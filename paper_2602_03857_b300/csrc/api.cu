@@ -114,6 +114,7 @@ int check_options(grav_ctx *ctx, const grav_options &o) {
     if (o.reorth < 0 || o.reorth > kReorthMaxBasis)
         return set_error(ctx, GRAV_EINVAL, "reorth must lie in [0, %d]", kReorthMaxBasis);
     if (o.refine < 0 || o.refine > 64) return set_error(ctx, GRAV_EINVAL, "refine must lie in [0, 64]");
+    if (o.near_fp64 != 0 && o.near_fp64 != 1) return set_error(ctx, GRAV_EINVAL, "near_fp64 must be 0 or 1");
     if (o.refine > 0 && (o.precision != GRAV_FP64 || o.outer_max > 0))
         return set_error(ctx, GRAV_EINVAL, "refine needs precision GRAV_FP64 and outer_max = 0");
     return GRAV_OK;
@@ -1165,6 +1166,7 @@ void grav_options_default(grav_options *o) {
     o->nys_rank = 0;
     o->nys_coarsen = 0;
     o->refine = 0;
+    o->near_fp64 = 0;
 }
 
 const char *grav_version(void) { return "libgrav 0.1.0 (sm_103a)"; }

@@ -140,7 +140,7 @@ struct grav_plan {
     int m_adj_bc = 0;                     // 1: broadcast adjoint layout (large meshes), 0: lanes split stations
     double *m_part = nullptr;             // [nchunk][N] forward partials (hi+lo in FP64)
     double *m_apart = nullptr;            // [nschunk][M] adjoint partials
-    float *dG = nullptr;                  // [N][slots] near-field correction (mGal per kg/m^3), formed in FP64
+    float *dG = nullptr;                  // [N][slots] near-field correction (mGal per kg/m^3), formed in double-float or FP64
     int *st_i0 = nullptr, *st_j0 = nullptr;   // box origin per station
     int *near_off = nullptr;              // [slots] cell offset of each window-box slot from the box origin
     double *diag_corr = nullptr;          // [N] near-field correction of diag(G W^-2 G^T)

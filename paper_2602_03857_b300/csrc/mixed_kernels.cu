@@ -751,13 +751,18 @@ __global__ void __launch_bounds__(kCfThreads) k_cfwd32(MixedGeo g, int ldw, cons
 // sum w2 (G_exact^2 - G_far^2), the box origin and the station's bin key.
 // The mesh is uniform: x edges x0 + i a, y edges y0 + j b.
 // ---------------------------------------------------------------------------
-template <bool CORNER>
+// MODE: kNsDF (corner function in double-float, the default), kNsF64 (in FP64:
+// the near_fp64 option), kNsCorner (FP64 plus the FP32 corner function of the
+// GRAV_MIXED_CORNER diagnostic).
+constexpr int kNsDF = 0, kNsF64 = 1, kNsCorner = 2;
+template <int MODE>
 __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
     Geo g, MixedGeo mg, NearGeo ng, double x0, double y0, double a, double b, double vol_mgal, double node_r2,
     const double *__restrict__ sx, const double *__restrict__ sy, const double *__restrict__ sz,
     const double *__restrict__ w2, const float4 *__restrict__ st32, const float2 *__restrict__ stz,
     float *__restrict__ dG, int *__restrict__ st_i0, int *__restrict__ st_j0, double *__restrict__ diag_corr,
     unsigned *__restrict__ keys, int *__restrict__ vals, unsigned key_sentinel) {
+    constexpr bool CORNER = MODE == kNsCorner, DF = MODE == kNsDF;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nbx1 = ng.bx + 1, nby1 = ng.by + 1;
@@ -785,15 +790,15 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
     int *queue0 = reinterpret_cast<int *>(reinterpret_cast<double *>(smem_raw) + (size_t)nwarps * nnode) +
                   (CORNER ? (size_t)nwarps * nnode : 0);
     int *queue = queue0 + (size_t)warp * 64;
-    // Without CORNER, Psi runs in double-float (psi_df, ~2^-45 of R ln R; the
-    // FP32 entries of the table need ~2^-39) from the node offsets of the
-    // window box, split once per station into double-float in shared memory;
-    // P then holds (hi, lo) pairs.  CORNER keeps the FP64 corner function.
+    // DF: Psi runs in double-float (psi_df, ~2^-45 of R ln R; the FP32 entries
+    // of the table need ~2^-39) from the node offsets of the window box, split
+    // once per station into double-float in shared memory; P then holds
+    // (hi, lo) pairs.  The other modes evaluate the FP64 corner function.
     const int ncrd = nbx1 + nby1 + ng.bz + 1;
     float2 *crd = reinterpret_cast<float2 *>(queue0 + (size_t)nwarps * 64) + (size_t)warp * ncrd;
     float2 *P2 = reinterpret_cast<float2 *>(P);
     const float *Ddf = reinterpret_cast<const float *>(g.fn + kFnDf);
-    if (!CORNER) {
+    if (DF) {
         for (int u = lane; u < ncrd; u += 32) {
             double v = 0.0;
             if (u < nbx1) {
@@ -815,7 +820,7 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
         const int ta = t % nbx1;
         const int tb = (t / nbx1) % nby1;
         const int c = t / (nbx1 * nby1);
-        if (CORNER) {
+        if (!DF) {
             const double x = g.xe[i0 + ta] - xs, y = g.ye[j0 + tb] - ys, z = g.ze[c] - zs;
             P[t] = psi64(x, y, z, x * x, y * y, z * z, g.fn);
         } else {
@@ -892,15 +897,26 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
             if (xc * xc + yc * yc + zc * zc < r2max) {
                 const int n0 = ai + sys * bj + szs * l;
                 // sigma(n, k) = -(-1)^(da+db+dc) for the vertex (i+da, j+db, l+dc)
-                if (CORNER) {
+                if (!DF) {
                     const double E = -P[n0] + P[n0 + sxs] + P[n0 + sys] - P[n0 + sxs + sys] + P[n0 + szs] -
                                      P[n0 + sxs + szs] - P[n0 + sys + szs] + P[n0 + sxs + sys + szs];
                     const double gex = kGammaMgal * E;
-                    const double E32 = -(double)P32[n0] + (double)P32[n0 + sxs] + (double)P32[n0 + sys] -
-                                       (double)P32[n0 + sxs + sys] + (double)P32[n0 + szs] -
-                                       (double)P32[n0 + sxs + szs] - (double)P32[n0 + sys + szs] +
-                                       (double)P32[n0 + sxs + sys + szs];
-                    const double gfar = kGammaMgal * E32;
+                    double gfar;
+                    if (CORNER) {
+                        const double E32 = -(double)P32[n0] + (double)P32[n0 + sxs] + (double)P32[n0 + sys] -
+                                           (double)P32[n0 + sxs + sys] + (double)P32[n0 + szs] -
+                                           (double)P32[n0 + sxs + szs] - (double)P32[n0 + sys + szs] +
+                                           (double)P32[n0 + sxs + sys + szs];
+                        gfar = kGammaMgal * E32;
+                    } else {
+                        const float2 X = make_float2(mg.cx[2 * i], mg.cx[2 * i + 1]);
+                        const float2 Y = make_float2(mg.cy[2 * j], mg.cy[2 * j + 1]);
+                        const float h2 = far_h2(X, Y, S.x, S.y, S.z, S.w);
+                        const float ph = far_ph(X, Y, S.x, S.y, S.z, S.w, mg.qa, mg.qb);
+                        const float dz = mg.czc[l] - zf;
+                        const float R2 = fmaf(dz, dz, h2);
+                        gfar = vol_mgal * (double)far_kernel_q(dz, R2, mg.qg, ph);
+                    }
                     const double val = gex - gfar;
                     dgv = (float)(val / vol_mgal);
                     dcorr += w2[l] * (gex * gex - gfar * gfar);
@@ -932,7 +948,7 @@ __global__ void __launch_bounds__(kNsWarps * 32) k_near_setup(
                 }
             }
         }
-        // formed in FP64 (double-float), stored in FP32 per unit q = gamma V rho
+        // formed in double-float (or FP64), stored in FP32 per unit q = gamma V rho
         // (so the products use the FP32 q of the far field); relative rounding 6e-8
         dG[s * ng.ld + t] = dgv;
     }
@@ -2274,7 +2290,9 @@ int mixed_setup(grav_plan *p, cudaStream_t s) {
             p->d_w2, p->st32,
             p->stz, p->dG, p->st_i0, p->st_j0, p->diag_corr, keys, vals, (unsigned)z.nbins);
     };
-    if (corner) setup(k_near_setup<true>); else setup(k_near_setup<false>);
+    if (corner) setup(k_near_setup<kNsCorner>);
+    else if (p->opt.near_fp64) setup(k_near_setup<kNsF64>);
+    else setup(k_near_setup<kNsDF>);
     size_t tmp = z.cub_temp;
     cub::DeviceRadixSort::SortPairs(cub_tmp, tmp, keys, keys_sorted, vals, p->bin_st, (int)p->N, 0, z.key_bits, s);
     k_bin_bounds<<<grid_for(z.nbins + 1, 256), 256, 0, s>>>(keys_sorted, p->N, z.nbins, p->bin_start);

@@ -311,6 +311,37 @@ def test_near_adjoint_forms_agree_and_match_oracle(g, near_cells, monkeypatch):
         assert np.abs(out[form] - out["tiles"]).max() <= 1e-7 * np.abs(out["tiles"]).max(), form
 
 
+@pytest.mark.parametrize("near_cells", [8.0, 3.0])
+def test_near_table_double_float_against_fp64(g, near_cells):
+    """The near-field table formed from the corner function in double-float
+    (the default) against the same table formed in FP64 (near_fp64): forward
+    and adjoint products agree within 1e-8 of max (the double-float corner
+    values carry ~2^-45 of R (|ln R| + 1)), and both implement the definition
+    of the mixed operator within 1e-6 of max (exact prism inside the window,
+    point mass outside), on stations inside and outside the footprint."""
+    mesh = synth.uniform_mesh(33, 29, 14, 40.0, 40.0, 40.0)
+    rng = np.random.Generator(np.random.PCG64(219))
+    n = 900
+    sv = synth.Survey(rng.uniform(-300, 33 * 40 + 300, n), rng.uniform(-300, 29 * 40 + 300, n),
+                      -rng.uniform(0.5, 20, n))
+    S = g.Survey(sv.x, sv.y, sv.z)
+    G = oracle.G_explicit(mesh, sv)
+    Gk = _mixed_definition(mesh, sv, G, 40.0, near_cells)
+    m = rng.normal(0.0, 100.0, mesh.ncells) + 20.0
+    r = synth.random_vector(n, 220)
+    out = {}
+    for f64 in (False, True):
+        plan = g.Plan(mesh, S, precision="mixed", near_cells=near_cells, near_fp64=f64)
+        d = plan.forward(_dev(m)).cpu().numpy()
+        a = plan.adjoint(_dev(r)).cpu().numpy()
+        plan.close()
+        assert np.abs(d - Gk @ m).max() <= 1e-6 * np.abs(Gk @ m).max(), f64
+        assert np.abs(a - Gk.T @ r).max() <= 1e-6 * np.abs(Gk.T @ r).max(), f64
+        out[f64] = (d, a)
+    for k in (0, 1):
+        assert np.abs(out[False][k] - out[True][k]).max() <= 1e-8 * np.abs(out[True][k]).max(), k
+
+
 @pytest.mark.parametrize("near_cells", [8.0, 3.0, 5.0])
 def test_near_forward_forms_agree_and_match_oracle(g, near_cells, monkeypatch):
     """The near-field forward in its two forms: per tile of station bins with
