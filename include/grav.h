@@ -149,13 +149,20 @@ typedef struct {
                                   residual after that) on the current residual, adds its solution to y and
                                   recomputes the residual dd - (G W^-2 G^T + lambda I) y with the FP64
                                   operator; it stops when that FP64 residual is <= tol ||dd||.  lambda comes
-                                  from the FP64 trace as in FP64 mode, and m = m_ref + W^-2 G^T y from the FP64
-                                  adjoint.  No counterpart in the paper.  0 = FP64 CG (default) */
+                                  from the trace as in FP64 mode (diag_fp64 picks its arithmetic), and
+                                  m = m_ref + W^-2 G^T y from the FP64 adjoint of the final y (the one its
+                                  residual used).  No counterpart in the paper.  0 = FP64 CG (default) */
     int near_fp64;             /* GRAV_MIXED: 1 = form the near-field table from the corner function in FP64;
                                   0 (default) = in double-float (pairs of FP32 numbers on the FP32 pipe,
                                   ~2^-45 of R (|ln R| + 1) per corner value against the ~2^-39 the table's
                                   FP32 entries need; the products differ from the FP64-formed table's by
                                   <= ~1e-9 of max, and the set-up is ~3x faster) */
+    int diag_fp64;             /* GRAV_FP64 (matrix-free): 1 = the diagonal of G W^-2 G^T (the trace for lambda
+                                  and the Jacobi preconditioner) from the corner function in FP64; 0 (default)
+                                  = in double-float (FP32 pairs on the FP32 pipe): a sum of squares, so the
+                                  ~2^-45 per-node error stays at <= ~3e-13 of each entry for stations over
+                                  the mesh (~1e-11 for stations far off it, whose entries are all far
+                                  field), 13x faster */
 } grav_options;
 
 typedef struct {

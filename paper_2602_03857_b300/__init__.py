@@ -64,7 +64,8 @@ class grav_options(ctypes.Structure):
                 ("precond", ctypes.c_int), ("cache_g", ctypes.c_int), ("outer_max", ctypes.c_int),
                 ("inner_max", ctypes.c_int), ("reorth", ctypes.c_int), ("check_stations", ctypes.c_int),
                 ("nys_rank", ctypes.c_int), ("nys_coarsen", ctypes.c_int), ("refine", ctypes.c_int),
-                ("near_fp64", ctypes.c_int)]
+                ("near_fp64", ctypes.c_int),
+                ("diag_fp64", ctypes.c_int)]
 
 
 class grav_job(ctypes.Structure):
@@ -353,7 +354,7 @@ class Survey:
 def options(precision="fp64", z0=50.0, lambda_scale=1e-2, lam=0.0, tol=1e-6, max_iter=1000,
             check_every=0, near_cells=8.0, timeout_s=3600.0, precond="none", cache_g=False, outer_max=0,
             inner_max=20, reorth=1000, check_stations=0, nys_rank=0, nys_coarsen=0, refine=0,
-            near_fp64=False) -> grav_options:
+            near_fp64=False, diag_fp64=False) -> grav_options:
     o = grav_options()
     _lib.grav_options_default(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -368,6 +369,7 @@ def options(precision="fp64", z0=50.0, lambda_scale=1e-2, lam=0.0, tol=1e-6, max
     o.nys_rank, o.nys_coarsen = int(nys_rank), int(nys_coarsen)
     o.refine = int(refine)
     o.near_fp64 = int(bool(near_fp64))
+    o.diag_fp64 = int(bool(diag_fp64))
     return o
 
 

@@ -115,6 +115,7 @@ int check_options(grav_ctx *ctx, const grav_options &o) {
         return set_error(ctx, GRAV_EINVAL, "reorth must lie in [0, %d]", kReorthMaxBasis);
     if (o.refine < 0 || o.refine > 64) return set_error(ctx, GRAV_EINVAL, "refine must lie in [0, 64]");
     if (o.near_fp64 != 0 && o.near_fp64 != 1) return set_error(ctx, GRAV_EINVAL, "near_fp64 must be 0 or 1");
+    if (o.diag_fp64 != 0 && o.diag_fp64 != 1) return set_error(ctx, GRAV_EINVAL, "diag_fp64 must be 0 or 1");
     if (o.refine > 0 && (o.precision != GRAV_FP64 || o.outer_max > 0))
         return set_error(ctx, GRAV_EINVAL, "refine needs precision GRAV_FP64 and outer_max = 0");
     return GRAV_OK;
@@ -931,8 +932,12 @@ int solve_on_plan(grav_plan *p, const double *d, const double *m_ref, double *m_
         }
         if (rc) break;
         }  // single CG solve
-        // m = m_ref + W^-2 G^T y
-        if ((rc = plan_adjoint_ex(p, y, m_out, 1, m_ref, s))) break;
+        // m = m_ref + W^-2 G^T y: q already holds W^-2 G^T y of the final y (the
+        // true residual's adjoint, the last product of either branch), so the
+        // recovery is one vector add (the adjoint's own add of m_ref is the same
+        // last operation: the result is bitwise that of another adjoint)
+        if (m_ref) vec_axpby(1.0, m_ref, 1.0, q, M, m_out, s);
+        else cudaMemcpyAsync(m_out, q, 8ull * M, cudaMemcpyDeviceToDevice, s);
         if (y_out) cudaMemcpyAsync(y_out, y, 8ull * N, cudaMemcpyDeviceToDevice, s);
         if ((rc = sync_scalars("cg finish"))) break;
         double fp64_rel = -1.0;
@@ -1101,8 +1106,11 @@ int solve_refined(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *surve
             converged = rel <= o.tol;
         }
         if (rc) break;
-        // m = m_ref + W^-2 G^T y with the FP64 adjoint
-        if ((rc = plan_adjoint_ex(p64, y, m_out, 1, m_ref, s))) break;
+        // m = m_ref + W^-2 G^T y: q holds the FP64 W^-2 G^T y of the final y
+        // (the last residual's adjoint); y = 0 when no step ran
+        if (steps == 0) vec_fill(q, M, 0.0, s);
+        if (m_ref) vec_axpby(1.0, m_ref, 1.0, q, M, m_out, s);
+        else cudaMemcpyAsync(m_out, q, 8ull * M, cudaMemcpyDeviceToDevice, s);
         if (y_out) cudaMemcpyAsync(y_out, y, 8ull * N, cudaMemcpyDeviceToDevice, s);
         rc = read_status(ctx, s, o.timeout_s);
     } while (false);
@@ -1167,6 +1175,7 @@ void grav_options_default(grav_options *o) {
     o->nys_coarsen = 0;
     o->refine = 0;
     o->near_fp64 = 0;
+    o->diag_fp64 = 0;
 }
 
 const char *grav_version(void) { return "libgrav 0.1.0 (sm_103a)"; }

@@ -25,6 +25,7 @@ constexpr int kAdjWarps = 8;        // warps per CTA in the adjoint
 constexpr int kAdjTZ = 8;           // node levels per warp
 constexpr int kAdjStage = 256;      // stations per TMA stage
 constexpr int kDiagZC = 4;          // cell layers per sweep in the diagonal kernel
+constexpr int kDiagDfZC = 16;       // cell layers per sweep in the double-float diagonal kernel
 constexpr int kDiagKMax = 7;        // cells per lane of the warp-per-station diagonal (nx <= 224)
 
 // ---------------------------------------------------------------------------
@@ -479,6 +480,96 @@ __global__ void __launch_bounds__(128) k_diag64w(Geo g, const double *__restrict
     if (lane == 0) part[(int64_t)blockIdx.y * g.N + s] = acc;
 }
 
+// The diagonal with the corner function in double-float (psi_df: pairs of
+// FP32 numbers on the FP32 pipe, 64x the FP64 rate here; ~2^-45 of
+// R (|ln R| + 1) per node value).  A diagonal entry is a sum of squares, so
+// the per-node errors do not meet the node-shared products' cancellation
+// across the mesh: emulated at that error bound they move an entry by
+// ~1e-13 of its value (tested against the FP64 kernel and the oracle).
+// A warp per station: lane t holds x node a0 + t of a 32-node segment and
+// owns the cell a0 + t (lanes 0..30), whose right node comes from lane t + 1
+// by a shuffle; Psi of the lane's node on the previous y edge, at the ZC + 1
+// levels of a layer group, is kept in shared memory (lane fastest).
+// Evaluations per cell: (32/31) ((ZC + 1)/ZC) (1 + 1/rows).  Differences in
+// the order of k_diag64w (y, then x, then z; adjacent nodes first, so each
+// cancellation is exact in TwoSum); G^2 w2 is summed in double-float over a
+// sweep (segment x layer group x rows) and folded into FP64 per sweep.  The
+// y offsets of 32 rows are split by the lanes and broadcast by shuffles, and
+// the levels' offsets and weights sit in shared memory, so no FP64
+// operation runs per node.  The level loop is not unrolled (one inlined
+// corner function keeps the loop body in the instruction cache).
+template <int ZC>
+__global__ void __launch_bounds__(128) k_diagdf(Geo g, const double *__restrict__ w2, int jrows,
+                                                const double *__restrict__ sx, const double *__restrict__ sy,
+                                                const double *__restrict__ sz, double *__restrict__ part) {
+    __shared__ float2 zw_s[4][2 * ZC + 1];    // per warp: level offsets (ZC + 1), then w2 of the ZC layers
+    __shared__ float2 prev_s[4][ZC + 1][32];  // per warp: Psi on the previous y edge [level][lane]
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (s >= g.N) return;   // warp-uniform
+    float2 *zw = zw_s[wid];
+    float2(*prev)[32] = prev_s[wid];
+    const float *D = reinterpret_cast<const float *>(g.fn + kFnDf);
+    const double xs = sx[s], ys = sy[s], zs = sz[s];
+    const int j0 = blockIdx.y * jrows;
+    const int j1 = min(g.ny, j0 + jrows);
+    const df32 gam = df_from_double(kGammaMgal);
+    const unsigned full = 0xffffffffu;
+    double acc = 0.0;
+    for (int a0 = 0; a0 < g.nx; a0 += 31) {
+        const int a = min(a0 + lane, g.nx);   // lanes past the last node repeat it (their values are not used)
+        const bool own = lane < 31 && a0 + lane < g.nx;
+        const df32 X = df_from_double(g.xe[a] - xs);
+        for (int l0 = 0; l0 < g.nz; l0 += ZC) {
+            const int nl = min(ZC, g.nz - l0);
+            __syncwarp();
+            for (int u = lane; u <= 2 * ZC; u += 32) {   // 2 ZC + 1 entries (more than a warp for ZC >= 16)
+                const df32 v = u <= ZC ? df_from_double(g.ze[l0 + min(u, nl)] - zs)
+                                       : df_from_double(w2[l0 + min(u - ZC - 1, nl - 1)]);
+                zw[u] = make_float2(v.hi, v.lo);
+            }
+            __syncwarp();
+            {
+                const df32 Y = df_from_double(g.ye[j0] - ys);
+#pragma unroll 1
+                for (int c = 0; c <= nl; ++c) {
+                    const float2 z = zw[c];
+                    const df32 v = psi_df(X, Y, df_make(z.x, z.y), D);
+                    prev[c][lane] = make_float2(v.hi, v.lo);
+                }
+            }
+            df32 sacc = df_make(0.0f, 0.0f);
+            for (int jb = j0; jb < j1; jb += 32) {
+                const df32 Yl = df_from_double(g.ye[min(jb + 1 + lane, g.ny)] - ys);   // edge jb + 1 + lane
+                const int nrow = min(32, j1 - jb);
+                for (int r = 0; r < nrow; ++r) {
+                    const df32 Y = df_make(__shfl_sync(full, Yl.hi, r), __shfl_sync(full, Yl.lo, r));
+                    df32 exl = df_make(0.0f, 0.0f);   // x difference at the level below
+#pragma unroll 1
+                    for (int c = 0; c <= nl; ++c) {
+                        const float2 z = zw[c];
+                        const df32 v = psi_df(X, Y, df_make(z.x, z.y), D);
+                        const float2 pv = prev[c][lane];
+                        prev[c][lane] = make_float2(v.hi, v.lo);
+                        const df32 ey = df_sub(v, df_make(pv.x, pv.y));   // y difference at this lane's node
+                        const df32 er = df_make(__shfl_down_sync(full, ey.hi, 1), __shfl_down_sync(full, ey.lo, 1));
+                        const df32 ex = df_sub(er, ey);                    // then x: right node minus left
+                        if (c >= 1 && own) {                               // cell layer l0 + c - 1: then z
+                            const df32 G = df_mul(df_sub(ex, exl), gam);
+                            const float2 wv = zw[ZC + c];
+                            sacc = df_add(sacc, df_mul(df_sqr(G), df_make(wv.x, wv.y)));
+                        }
+                        exl = ex;
+                    }
+                }
+            }
+            acc += df_to_double(sacc);
+        }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) part[(int64_t)blockIdx.y * g.N + s] = acc;
+}
+
 inline int grid_for(int64_t n, int threads, int cap = 148 * 32) {
     int64_t b = (n + threads - 1) / threads;
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
@@ -638,6 +729,19 @@ void launch_adj_finish(const grav_plan *p, const double *u, double scale, int de
 }
 
 void launch_diag64(const grav_plan *p, double *diag, cudaStream_t s) {
+    if (!p->opt.diag_fp64) {   // double-float corner function, warp per station
+        // row chunks only as far as needed for >= 64 warps per SM: each chunk
+        // evaluates its first y edge once more
+        int64_t nch = std::max<int64_t>(1, (148LL * 64 + p->N - 1) / p->N);
+        nch = std::min<int64_t>(nch, p->f64_diag_nchunk);
+        const int jrows = (int)((p->ny + nch - 1) / nch);
+        nch = (p->ny + jrows - 1) / jrows;
+        dim3 grid((unsigned)((p->N + 3) / 4), (unsigned)nch);
+        k_diagdf<kDiagDfZC><<<grid, 128, 0, s>>>(make_geo(p), p->d_w2, jrows, p->sx, p->sy, p->sz, p->part);
+        note_launches(1);
+        launch_reduce_rows(p->part, (int)nch, p->N, 1.0, nullptr, 0.0, nullptr, diag, s);
+        return;
+    }
     if (p->nx <= 32 * kDiagKMax) {   // warp per station (x nodes across the lanes)
         // row chunks only as far as needed for >= 64 warps per SM: each chunk
         // evaluates its first y edge once more

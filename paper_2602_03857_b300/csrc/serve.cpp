@@ -64,12 +64,12 @@ struct PlanKey {
     const double *sx = nullptr, *sy = nullptr, *sz = nullptr;
     int64_t n = 0;
     uint64_t survey_hash = 0;
-    int precision = 0, cache_g = 0, near_fp64 = 0;
+    int precision = 0, cache_g = 0, near_fp64 = 0, diag_fp64 = 0;
     double z0 = 0, near_cells = 0;
     bool operator==(const PlanKey &o) const {
         return sx == o.sx && sy == o.sy && sz == o.sz && n == o.n && survey_hash == o.survey_hash &&
                precision == o.precision && cache_g == o.cache_g && z0 == o.z0 && near_cells == o.near_cells &&
-               near_fp64 == o.near_fp64 &&
+               near_fp64 == o.near_fp64 && diag_fp64 == o.diag_fp64 &&
                xe == o.xe && ye == o.ye && ze == o.ze;
     }
 };
@@ -203,6 +203,7 @@ void run_job(Scheduler *s, Job *job, int slot) {
         key.sx = d.survey.x; key.sy = d.survey.y; key.sz = d.survey.z; key.n = d.survey.n;
         key.precision = d.opt.precision; key.cache_g = d.opt.cache_g;
         key.z0 = d.opt.z0; key.near_cells = d.opt.near_cells; key.near_fp64 = d.opt.near_fp64;
+        key.diag_fp64 = d.opt.diag_fp64;
         rc = survey_hash(s, slot, d.survey, d.opt.timeout_s, &key.survey_hash);
         if (rc == GRAV_OK) {
             std::lock_guard<std::mutex> lk(s->mu);

@@ -72,12 +72,46 @@ def test_stations_above_nodes_edges_and_outside(g):
     assert _rel(a, a_ref) <= TOL64
 
 
-def test_diag_fp64(g):
+@pytest.mark.parametrize("diag_fp64", [False, True])
+def test_diag_fp64(g, diag_fp64):
     mesh, sv, _ = synth.small_random_problem(11, 9, 6, 150, seed=12, irregular=True)
     ref = oracle.diag_GWG(mesh, sv, 50.0)
-    dg, tr = g.diag(mesh, g.Survey(sv.x, sv.y, sv.z))
-    assert _rel(dg.cpu().numpy(), ref) <= TOL64
+    dg, tr = g.diag(mesh, g.Survey(sv.x, sv.y, sv.z), diag_fp64=diag_fp64)
+    dg = dg.cpu().numpy()
+    assert _rel(dg, ref) <= TOL64
+    assert float(np.max(np.abs(dg - ref) / ref)) <= TOL64   # every entry, relative to itself
     assert tr == pytest.approx(ref.sum(), rel=1e-10)
+
+
+def test_diag_double_float_against_fp64(g):
+    """The default diagonal (corner function in double-float) against the FP64
+    kernel's, entry by entry: several 31-cell x segments with a ragged last
+    one, layer groups with a ragged last one, several row chunks, irregular
+    spacing, stations above nodes and edges and outside the footprint; then
+    every station of the 80 x 80 x 40 slab workload.  A diagonal entry is a
+    sum of squares, so the double-float corner function's ~2^-45 per node
+    stays near 1e-13 of the entry; stations far outside the footprint, whose
+    entries are all far field (large corner values, small differences), lose
+    most (1.1e-11 measured for the station 300 m off this mesh's edge)."""
+    mesh, sv, _ = synth.small_random_problem(70, 45, 37, 1500, seed=31, irregular=True)
+    xs = np.concatenate([sv.x, mesh.xe[[0, 5, 70]], [mesh.xe[0] - 300.0, mesh.xe[-1] + 50.0]])
+    ys = np.concatenate([sv.y, mesh.ye[[0, 20, 45]], [mesh.ye[-1] + 10.0, mesh.ye[0] - 400.0]])
+    zs = np.concatenate([sv.z, -np.array([0.5, 2.0, 1e-3, 5.0, 30.0])])
+    S = g.Survey(xs, ys, zs)
+    ddf, tdf = g.diag(mesh, S)
+    d64, t64 = g.diag(mesh, S, diag_fp64=True)
+    ddf, d64 = ddf.cpu().numpy(), d64.cpu().numpy()
+    assert np.all(d64 > 0)
+    assert float(np.max(np.abs(ddf - d64) / d64)) <= TOL64
+    assert float(np.max(np.abs(ddf - d64)[:1500] / d64[:1500])) <= 1e-11   # stations over or near the mesh
+    assert tdf == pytest.approx(t64, rel=1e-12)
+    w = synth.vslab_80x80x40()
+    S = g.Survey(w.survey.x, w.survey.y, w.survey.z)
+    ddf, tdf = g.diag(w.mesh, S)
+    d64, t64 = g.diag(w.mesh, S, diag_fp64=True)
+    ddf, d64 = ddf.cpu().numpy(), d64.cpu().numpy()
+    assert float(np.max(np.abs(ddf - d64) / d64)) <= 1e-11
+    assert tdf == pytest.approx(t64, rel=1e-13)
 
 
 def test_dot_test_and_determinism(g):
