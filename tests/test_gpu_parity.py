@@ -83,6 +83,24 @@ def test_diag_fp64(g, diag_fp64):
     assert tr == pytest.approx(ref.sum(), rel=1e-10)
 
 
+@pytest.mark.parametrize("shape,ns,seed", [
+    ((1, 1, 1), 5, 41), ((31, 2, 16), 40, 42), ((32, 3, 17), 60, 43), ((62, 5, 33), 90, 44),
+    ((63, 1, 2), 33, 45), ((5, 70, 3), 70, 46), ((2, 2, 48), 200, 47),
+])
+def test_diag_double_float_shapes(g, shape, ns, seed):
+    """The double-float diagonal at the edges of its layout: one cell; x
+    segments of exactly 31 and 32 cells and one past two segments; layer
+    groups of exactly 16 layers, one layer over, several groups with a
+    ragged last one; long y (more rows than a 32-row broadcast block); many
+    stations over a thin column (several row chunks)."""
+    mesh, sv, _ = synth.small_random_problem(*shape, ns, seed=seed, irregular=True)
+    ref = oracle.diag_GWG(mesh, sv, 50.0)
+    dg, tr = g.diag(mesh, g.Survey(sv.x, sv.y, sv.z))
+    dg = dg.cpu().numpy()
+    assert float(np.max(np.abs(dg - ref) / ref)) <= TOL64
+    assert tr == pytest.approx(ref.sum(), rel=1e-12)
+
+
 def test_diag_double_float_against_fp64(g):
     """The default diagonal (corner function in double-float) against the FP64
     kernel's, entry by entry: several 31-cell x segments with a ragged last
