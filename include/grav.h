@@ -121,8 +121,11 @@ typedef struct {
                                   meshes; single CG solve; N*(nys_rank + reorth)*8 extra bytes, and during
                                   the set-up 8*N*nys_rank bytes more plus one block of the explicit coarse
                                   operator of at most 4 GB) (default 0) */
-    int cache_g;               /* GRAV_FP64 only: 1 = build G explicitly once (FP64, N*M*8 bytes) when it fits the
-                                  context budget and stream it for every product; 0 = always recompute (default 0) */
+    int cache_g;               /* GRAV_FP64 only: 1 = build G explicitly once when it fits the context budget
+                                  (formed in FP64, kept as double-float pairs: N*M*8 bytes, a 48-bit
+                                  significand) and stream it for every product, computed in double-float
+                                  arithmetic (an FP64 GEMV is bound by this GPU's FP64 pipe, below HBM
+                                  speed); 0 = always recompute (default 0) */
     int outer_max;             /* > 0: the paper's outer model-update loop (Section 2.2): at most outer_max
                                   updates y += alpha dy, dy from <= inner_max CG iterations on A dy = dd - A y,
                                   alpha by backtracking on the objective of Eq. 7; 0 = one CG solve (default) */

@@ -348,12 +348,18 @@ int plan_prepare(grav_ctx *ctx, const grav_mesh *mesh, const grav_survey *survey
         bytes += fp64_bytes(p);
         // stored G when asked for and it fits next to what is already in use
         const double gbytes = 8.0 * (double)p->N * (double)p->M;
-        if (o.cache_g && (double)ctx->hbm_used.load() + (double)bytes + gbytes + 8.0 * p->N * 64 <= (double)ctx->hbm_budget) {
+        // forward: tiles of 4,096 stations x cell chunks, four full waves of
+        // resident CTAs (a wave that is only partly filled costs as much as a
+        // full one: 2 tiles x 256 chunks at 3 CTAs per SM ran 1.15 waves and
+        // 34 % slower), at most 1,024 chunks of partials
+        const int64_t tiles = cached_fwd_tiles(p->N);
+        const int64_t resident = (int64_t)ctx->sm_count * cached_fwd_ctas_per_sm();
+        const int cnch = (int)std::min<int64_t>(
+            std::min<int64_t>(std::max<int64_t>(1, (4 * resident + tiles - 1) / tiles), 1024), p->M);
+        if (o.cache_g && (double)ctx->hbm_used.load() + (double)bytes + gbytes + 8.0 * p->N * cnch <= (double)ctx->hbm_budget) {
             p->cached = 1;
-            const int64_t tiles = (p->N + 127) / 128;
-            p->c_nchunk = (int)std::min<int64_t>(std::max<int64_t>(1, (int64_t)ctx->sm_count * 16 / tiles), 64);
-            p->c_nchunk = (int)std::min<int64_t>(p->c_nchunk, p->M);
-            bytes += (size_t)gbytes + 256;
+            p->c_nchunk = cnch;
+            bytes += (size_t)gbytes + 256 + 8ull * (p->M + p->N) + 512;   // G, m and r as pairs
             // the forward partials reuse `part`; make sure it has c_nchunk rows
             const int rows = std::max(p->f64_nchunk, p->f64_diag_nchunk);
             if (p->c_nchunk > rows) bytes += (size_t)(p->c_nchunk - rows) * p->N * 8 + 256;
@@ -427,7 +433,11 @@ int plan_allocate(grav_plan *p, cudaStream_t s) {
         p->st4 = (double4_16a *)p->arena.take((size_t)p->N * 32);
         p->upart = (double *)p->arena.take((size_t)p->a64_nschunk * p->Nn * 8);
         p->u = (double *)p->arena.take((size_t)p->Nn * 8);
-        if (p->cached) p->Gc = (double *)p->arena.take((size_t)p->N * p->M * 8);
+        if (p->cached) {
+            p->Gc = (float2 *)p->arena.take((size_t)p->N * p->M * 8);
+            p->m_df = (float2 *)p->arena.take((size_t)p->M * 8);
+            p->r_df = (float2 *)p->arena.take((size_t)p->N * 8);
+        }
         if (!p->arena.overflow) {
             fp64_setup(p, s);
             if (p->cached) launch_build_g64(p, p->Gc, nullptr, s);

@@ -350,7 +350,7 @@ template <int ZC, bool WRITE_G>
 __global__ void __launch_bounds__(128) k_diag64(Geo g, const double *__restrict__ w2, int jrows,
                                                 const double *__restrict__ sx, const double *__restrict__ sy,
                                                 const double *__restrict__ sz, double *__restrict__ part,
-                                                double *__restrict__ Gout) {
+                                                float2 *__restrict__ Gout) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.N) return;
     const double xs = sx[s], ys = sy[s], zs = sz[s];
@@ -398,7 +398,11 @@ __global__ void __launch_bounds__(128) k_diag64(Geo g, const double *__restrict_
                     if (c < nl) {
                         const double G = kGammaMgal * (E[c + 1] - E[c]);
                         acc = fma(G * G, w2l[c], acc);
-                        if (WRITE_G) Gout[(i + (int64_t)g.nx * (j + (int64_t)g.ny * (l0 + c))) * g.N + s] = G;
+                        if (WRITE_G) {   // the FP64 value as a double-float pair (48-bit significand)
+                            const float gh = __double2float_rn(G);
+                            Gout[(i + (int64_t)g.nx * (j + (int64_t)g.ny * (l0 + c))) * g.N + s] =
+                                make_float2(gh, __double2float_rn(G - (double)gh));
+                        }
                     }
                 }
             }
@@ -582,60 +586,108 @@ int fwd_rows_per_stage(const grav_plan *p) {
 }
 
 // ---------------------------------------------------------------------------
-// Stored-G products (G built once in FP64, cell-major: Gc[k][i], station i
-// fastest).  Both read the matrix once, coalesced: HBM-bound.
-// d: CTA = (128 stations, chunk of cells) -> partials [chunk][N].
-// G^T r: warp per cell, lanes over stations, shuffle reduction.
+// Stored-G products (G formed once in FP64 with node-shared differencing,
+// cell-major Gc[k][i], station i fastest).  An FP64 GEMV on this GPU is
+// bound by the FP64 pipe, not by HBM: one DFMA per 8-byte entry at
+// 1.65 DFMA/clk/SM is 4.96e11 entries/s against HBM's 8.1e11 (measured:
+// FP64 pipe 93-96 % busy, DRAM 57 %).  G is therefore kept as double-float
+// pairs (hi, lo FP32: the FP64 value to a 48-bit significand, same 8 bytes)
+// and the products run in double-float arithmetic on the FP32 pipe (~18
+// FP32 operations per entry, 64x the FP64 rate), which leaves HBM the bound.
+// The input vector is split into pairs once per product (k_split_df).
+// d: CTA = (128 stations, chunk of cells) -> FP64 partials [chunk][N].
+// G^T r: warp per cell, lanes over stations, FP64 shuffle reduction.
 // ---------------------------------------------------------------------------
-// SQUARE: sum_k G_ik^2 w2[layer(k)] (the diagonal of G W^-2 G^T) instead of G m.
-template <bool SQUARE>
-__global__ void __launch_bounds__(128) k_gemv_cached(const double *__restrict__ Gc, int64_t N, int64_t M,
-                                                     int64_t plane, int64_t cells_per_chunk,
-                                                     const double *__restrict__ m, double *__restrict__ part) {
+__global__ void k_split_df(const double *__restrict__ x, int64_t n, float2 *__restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        const float h = __double2float_rn(v);
+        y[i] = make_float2(h, __double2float_rn(v - (double)h));
+    }
+}
+
+__device__ __forceinline__ df32 df_of(float2 v) { return df_make(v.x, v.y); }
+
+// d partials: CTA = 4,096 consecutive stations (thread t: t + 256 j, j < 16)
+// x a chunk of cells, so each row of G is read as one 32 KB contiguous run
+// with 16 independent loads per thread; double-float sums in registers, each
+// station's cells in order.
+constexpr int kGfJ = 16;
+constexpr int kGfTile = 256 * kGfJ;
+__global__ void __launch_bounds__(256) k_gemv_cached(const float2 *__restrict__ Gc, int64_t N, int64_t M,
+                                                     int64_t cells_per_chunk, const float2 *__restrict__ m,
+                                                     double *__restrict__ part) {
+    const int64_t ib = (int64_t)blockIdx.x * kGfTile + threadIdx.x;
+    const int64_t k0 = (int64_t)blockIdx.y * cells_per_chunk;
+    const int64_t k1 = min(M, k0 + cells_per_chunk);
+    df32 a[kGfJ];
+#pragma unroll
+    for (int j = 0; j < kGfJ; ++j) a[j] = df_make(0.0f, 0.0f);
+    for (int64_t k = k0; k < k1; ++k) {
+        const float2 *row = Gc + k * N;
+        const df32 mk = df_of(m[k]);
+        float2 g[kGfJ];
+#pragma unroll
+        for (int j = 0; j < kGfJ; ++j) {
+            const int64_t i = ib + 256 * j;
+            g[j] = i < N ? row[i] : make_float2(0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int j = 0; j < kGfJ; ++j) a[j] = df_add(a[j], df_mul(df_of(g[j]), mk));
+    }
+#pragma unroll
+    for (int j = 0; j < kGfJ; ++j) {
+        const int64_t i = ib + 256 * j;
+        if (i < N) part[(int64_t)blockIdx.y * N + i] = df_to_double(a[j]);
+    }
+}
+
+// sum_k G_ik^2 w2[layer(k)] (the diagonal of G W^-2 G^T), once per plan: FP64
+__global__ void __launch_bounds__(128) k_gemv_cached_sq(const float2 *__restrict__ Gc, int64_t N, int64_t M,
+                                                        int64_t plane, int64_t cells_per_chunk,
+                                                        const double *__restrict__ w2, double *__restrict__ part) {
     const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
     const int64_t k0 = (int64_t)blockIdx.y * cells_per_chunk;
     const int64_t k1 = min(M, k0 + cells_per_chunk);
     if (i >= N) return;
-    double a0 = 0.0, a1 = 0.0;
-    int64_t k = k0;
-    for (; k + 1 < k1; k += 2) {
-        const double g0 = Gc[k * N + i], g1 = Gc[(k + 1) * N + i];
-        if (SQUARE) {
-            a0 = fma(g0 * g0, m[k / plane], a0);
-            a1 = fma(g1 * g1, m[(k + 1) / plane], a1);
-        } else {
-            a0 = fma(g0, m[k], a0);
-            a1 = fma(g1, m[k + 1], a1);
-        }
+    double a = 0.0;
+    for (int64_t k = k0; k < k1; ++k) {
+        const float2 gv = Gc[k * N + i];
+        const double g = (double)gv.x + (double)gv.y;
+        a = fma(g * g, w2[k / plane], a);
     }
-    if (k < k1) {
-        const double g0 = Gc[k * N + i];
-        a0 = SQUARE ? fma(g0 * g0, m[k / plane], a0) : fma(g0, m[k], a0);
-    }
-    part[(int64_t)blockIdx.y * N + i] = a0 + a1;
+    part[(int64_t)blockIdx.y * N + i] = a;
 }
 
-__global__ void __launch_bounds__(256) k_gemvt_cached(const double *__restrict__ Gc, int64_t N, int64_t M, int nx,
-                                                      int ny, const double *__restrict__ r,
+__global__ void __launch_bounds__(256) k_gemvt_cached(const float2 *__restrict__ Gc, int64_t N, int64_t M, int nx,
+                                                      int ny, const float2 *__restrict__ r,
                                                       const double *__restrict__ w2, const double *__restrict__ add,
                                                       double *__restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (k >= M) return;
-    const double *row = Gc + k * N;
-    double a = 0.0;
-    for (int64_t i = lane; i < N; i += 32) a = fma(row[i], r[i], a);
-    a = warp_sum(a);
+    const float2 *row = Gc + k * N;
+    df32 a = df_make(0.0f, 0.0f);
+    for (int64_t i = lane; i < N; i += 32) a = df_add(a, df_mul(df_of(row[i]), df_of(r[i])));
+    double s = warp_sum(df_to_double(a));
     if (lane == 0) {
-        if (w2) a *= w2[k / ((int64_t)nx * ny)];
-        if (add) a += add[k];
-        out[k] = a;
+        if (w2) s *= w2[k / ((int64_t)nx * ny)];
+        if (add) s += add[k];
+        out[k] = s;
     }
 }
 
 }  // namespace
 
-void launch_build_g64(const grav_plan *p, double *Gc, double *diag, cudaStream_t s) {
+int cached_fwd_tiles(int64_t N) { return (int)((N + kGfTile - 1) / kGfTile); }
+
+int cached_fwd_ctas_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gemv_cached, 256, 0) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
+void launch_build_g64(const grav_plan *p, float2 *Gc, double *diag, cudaStream_t s) {
     const int tiles = (int)((p->N + 127) / 128);
     dim3 grid(tiles, p->f64_diag_nchunk);
     k_diag64<kDiagZC, true><<<grid, 128, 0, s>>>(make_geo(p), p->d_w2, p->f64_diag_jrows, p->sx, p->sy, p->sz,
@@ -647,18 +699,19 @@ void launch_build_g64(const grav_plan *p, double *Gc, double *diag, cudaStream_t
 void launch_cached_fwd(const grav_plan *p, const double *m, const double *add, double add_scale, double *d,
                        cudaStream_t s) {
     const int64_t per = (p->M + p->c_nchunk - 1) / p->c_nchunk;
-    dim3 grid((unsigned)((p->N + 127) / 128), (unsigned)p->c_nchunk);
+    dim3 grid((unsigned)cached_fwd_tiles(p->N), (unsigned)p->c_nchunk);
     stage_begin(p, kStageFwdMain, s);
-    k_gemv_cached<false><<<grid, 128, 0, s>>>(p->Gc, p->N, p->M, (int64_t)p->nx * p->ny, per, m, p->part);
+    k_split_df<<<grid_for(p->M, 256), 256, 0, s>>>(m, p->M, p->m_df);
+    k_gemv_cached<<<grid, 256, 0, s>>>(p->Gc, p->N, p->M, per, p->m_df, p->part);
     stage_end(p, kStageFwdMain, s);
-    note_launches(1);
+    note_launches(2);
     launch_reduce_rows(p->part, p->c_nchunk, p->N, 1.0, add, add_scale, nullptr, d, s);
 }
 
 void launch_cached_diag(const grav_plan *p, double *diag, cudaStream_t s) {
     const int64_t per = (p->M + p->c_nchunk - 1) / p->c_nchunk;
     dim3 grid((unsigned)((p->N + 127) / 128), (unsigned)p->c_nchunk);
-    k_gemv_cached<true><<<grid, 128, 0, s>>>(p->Gc, p->N, p->M, (int64_t)p->nx * p->ny, per, p->d_w2, p->part);
+    k_gemv_cached_sq<<<grid, 128, 0, s>>>(p->Gc, p->N, p->M, (int64_t)p->nx * p->ny, per, p->d_w2, p->part);
     note_launches(1);
     launch_reduce_rows(p->part, p->c_nchunk, p->N, 1.0, nullptr, 0.0, nullptr, diag, s);
 }
@@ -667,10 +720,11 @@ void launch_cached_adj(const grav_plan *p, const double *r, int depth_weighted, 
                        cudaStream_t s) {
     const int64_t threads = p->M * 32;
     stage_begin(p, kStageAdjMain, s);
-    k_gemvt_cached<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(p->Gc, p->N, p->M, p->nx, p->ny, r,
+    k_split_df<<<grid_for(p->N, 256), 256, 0, s>>>(r, p->N, p->r_df);
+    k_gemvt_cached<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(p->Gc, p->N, p->M, p->nx, p->ny, p->r_df,
                                                                     depth_weighted ? p->d_w2 : nullptr, add, out);
     stage_end(p, kStageAdjMain, s);
-    note_launches(1);
+    note_launches(2);
 }
 
 size_t fwd64_smem_bytes(const grav_plan *p) {

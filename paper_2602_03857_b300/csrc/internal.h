@@ -120,9 +120,10 @@ struct grav_plan {
     double4_16a *st4 = nullptr;               // stations (x, y, z, r)
     double *upart = nullptr;              // adjoint partials [nschunk][Nn]
     double *u = nullptr;                  // [Nn]
-    int cached = 0;                       // 1: explicit G stored (FP64, cell-major [M][N])
+    int cached = 0;                       // 1: explicit G stored (cell-major [M][N], double-float pairs)
     int c_nchunk = 0;                     // cell chunks of the stored-G forward product
-    double *Gc = nullptr;
+    float2 *Gc = nullptr;                 // G formed in FP64, kept as (hi, lo) FP32 pairs (8 bytes per entry)
+    float2 *m_df = nullptr, *r_df = nullptr;   // the product's input vector split the same way ([M], [N])
 
     // mixed path
     grav::MixedGeo mg{};
@@ -244,10 +245,12 @@ void launch_adj64(const grav_plan *p, const double *r, cudaStream_t s);
 void launch_adj_finish(const grav_plan *p, const double *u, double scale, int depth_weighted,
                        const double *add, double *out, cudaStream_t s);
 void launch_diag64(const grav_plan *p, double *diag, cudaStream_t s);
-void launch_build_g64(const grav_plan *p, double *Gc, double *diag, cudaStream_t s);
+void launch_build_g64(const grav_plan *p, float2 *Gc, double *diag, cudaStream_t s);
 void launch_cached_fwd(const grav_plan *p, const double *m, const double *add, double add_scale, double *d,
                        cudaStream_t s);
 void launch_cached_diag(const grav_plan *p, double *diag, cudaStream_t s);
+int cached_fwd_tiles(int64_t N);   // station tiles of the stored-G forward
+int cached_fwd_ctas_per_sm();      // its resident CTAs per SM
 void launch_cached_adj(const grav_plan *p, const double *r, int depth_weighted, const double *add, double *out,
                        cudaStream_t s);
 size_t fwd64_smem_bytes(const grav_plan *p);
