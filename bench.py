@@ -430,7 +430,7 @@ def extras(args, g, torch, wl, plan, d, line):
             "forward_frac": gbytes / tf / peak, "adjoint_frac": gbytes / ta / peak,
             "rel_diff_vs_matrix_free": max(float((dc - d64).abs().max() / d64.abs().max()),
                                            float((ac - a64).abs().max() / a64.abs().max())),
-            "what": "FP64 G built once (cache_g) and streamed per product; algorithmic bytes = N x M x 8 per product"}
+            "what": "G formed once in FP64 (cache_g), stored as double-float pairs and streamed per product (double-float arithmetic); algorithmic bytes = N x M x 8 per product"}
     pc.close()
     # the literal FP32 corner-term scheme (forward only) against the FP64 mode
     # on every station of the 80x80x40 workload, next to the mixed scheme
