@@ -91,3 +91,23 @@ def test_preconditioner_options_without_gpu(lib):
     assert c.nys_rank == 0 and c.nys_coarsen == 0   # automatic sizes
     with pytest.raises(KeyError):
         g.options(precond="ilu")
+
+
+def test_options_struct_matches_header(lib):
+    """The binding's grav_options has the header's fields, in the header's
+    order and C types, and grav_options_default fills every byte of it (a
+    field the binding lacks or adds would leave sentinel bytes behind or
+    shift the later fields)."""
+    import paper_2602_03857_b300 as g
+    text = open(HEADER).read()
+    body = text[text.index("typedef struct {", text.index("grav_survey;")):text.index("} grav_options;")]
+    fields = re.findall(r"^\s+(int|double)\s+(\w+);", body, re.M)
+    py = [(n, t) for n, t in g.grav_options._fields_]
+    assert [n.rstrip("_") for n, _ in py] == [n for _, n in fields]
+    ctypes_of = {"int": ctypes.c_int, "double": ctypes.c_double}
+    assert [t for _, t in py] == [ctypes_of[t] for t, _ in fields]
+    o = g.grav_options()
+    ctypes.memset(ctypes.byref(o), 0xFF, ctypes.sizeof(o))
+    g._lib.grav_options_default(ctypes.byref(o))
+    assert (o.refine, o.near_fp64, o.diag_fp64, o.nys_coarsen) == (0, 0, 0, 0)
+    assert o.timeout_s == 3600.0 and o.inner_max == 20
