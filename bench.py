@@ -510,8 +510,8 @@ def extras(args, g, torch, wl, plan, d, line):
         "fp64_stored_g_over_mixed_seconds": vs["fp64_stored_g"]["seconds"] / vs["mixed"]["seconds"],
         "what": "one grav_datainv_solve call each (plan set-up, trace, CG to a true relative residual of 1e-6, "
                 "recovery); fp64: FP64 CG with the Nystrom preconditioner (sketch included; without it ~100 s); "
-                "fp64_stored_g: FP64 CG with G formed once in FP64 and stored (cache_g; 13.4 GB, build "
-                "included); fp64_refined: the same FP64 system by mixed-precision iterative refinement (mixed "
+                "fp64_stored_g: FP64 CG with G formed once in FP64 and stored as double-float pairs (cache_g; "
+                "13.4 GB, build included; products in double-float arithmetic); fp64_refined: the same FP64 system by mixed-precision iterative refinement (mixed "
                 "CG corrections, FP64 residuals; true_rel_res is the FP64 residual, iters the mixed CG "
                 "iterations)"}
     # the serving loop on the first 64 jobs of the seeded request stream
